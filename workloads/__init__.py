@@ -1,0 +1,121 @@
+"""Seeded synthetic inputs and workload descriptions for tests, smoke and bench.
+
+This module holds no arithmetic of the method: it draws magnetisation
+patterns from numpy's seeded generators and lists grid sizes, materials and
+mechanics of the film-pair workloads.  Both the CPU oracle side and the CUDA
+side of every comparison receive the arrays made here.
+
+Patterns (reading of the workload descriptions):
+  * random unit vectors: normalised Gaussian triples, default_rng(seed);
+  * PMA up/down domains of ~`size` cells: random signs on a coarse grid of
+    `size`-cell blocks (block boundaries shifted by a random phase), mz = +-1
+    with a small seeded in-plane tilt, normalised;
+  * vortex: m = normalise(-chi (y - yc), chi (x - xc), p exp(-rho^2 / rc^2))
+    with random chirality chi, polarity p and core offset.
+Arrays are float64, shape (3, nz, ny, nx), x fastest.
+"""
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+def random_unit(shape_xyz, seed):
+    nx, ny, nz = shape_xyz
+    rng = np.random.default_rng(seed)
+    m = rng.standard_normal((3, nz, ny, nx))
+    return m / np.sqrt(np.sum(m * m, axis=0, keepdims=True))
+
+
+def pma_domains(shape_xyz, seed, size=20, tilt=0.05):
+    nx, ny, nz = shape_xyz
+    rng = np.random.default_rng(seed)
+    cx = -(-nx // size) + 1
+    cy = -(-ny // size) + 1
+    signs = rng.choice([-1.0, 1.0], size=(cy, cx))
+    sx, sy = rng.integers(0, size, size=2)
+    ix = (np.arange(nx) + sx) // size
+    iy = (np.arange(ny) + sy) // size
+    mz = signs[iy][:, ix]
+    m = np.empty((3, nz, ny, nx))
+    m[2] = mz[None]
+    m[0:2] = tilt * rng.standard_normal((2, nz, ny, nx))
+    return m / np.sqrt(np.sum(m * m, axis=0, keepdims=True))
+
+
+def vortex(shape_xyz, seed, rc=4.0, core_jitter=8):
+    nx, ny, nz = shape_xyz
+    rng = np.random.default_rng(seed)
+    chi = rng.choice([-1.0, 1.0])
+    pol = rng.choice([-1.0, 1.0])
+    xc = (nx - 1) / 2 + rng.uniform(-core_jitter, core_jitter)
+    yc = (ny - 1) / 2 + rng.uniform(-core_jitter, core_jitter)
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    rho2 = (x - xc) ** 2 + (y - yc) ** 2
+    m = np.stack([-chi * (y - yc), chi * (x - xc), pol * np.exp(-rho2 / rc ** 2)])
+    return m / np.sqrt(np.sum(m * m, axis=0, keepdims=True))
+
+
+@dataclass
+class Material:
+    Ms: float
+    Aex: float = 0.0
+    Ku: float = 0.0
+    ku_axis: tuple = (0.0, 0.0, 1.0)
+    alpha: float = 0.5
+
+    def as_dict(self):
+        return dict(Ms=self.Ms, Aex=self.Aex, Ku=self.Ku, ku_axis=self.ku_axis, alpha=self.alpha)
+
+
+@dataclass
+class Mechanics:
+    mass: float = 2.5e-18       # kg
+    k: float = 1e-3             # N/m
+    v_drive: float = 1.0        # m/s
+    gamma_v: float = 4e7        # 1/s  (critical damping 2 sqrt(k/mass))
+    dir: tuple = (1.0, 0.0, 0.0)
+    x0_spring: float = 0.0      # m, spring end ahead of the slider at t = 0
+
+    def as_dict(self):
+        return dict(mass=self.mass, k=self.k, v_drive=self.v_drive, gamma_v=self.gamma_v,
+                    dir=self.dir, x0_spring=self.x0_spring)
+
+
+@dataclass
+class FilmPair:
+    """Two magnets stacked along z: base at the origin, slider `gap` cells above."""
+    name: str
+    n_base: tuple
+    n_slider: tuple
+    cell: tuple
+    gap: int
+    mat_base: Material
+    mat_slider: Material
+    mech: Mechanics = field(default_factory=Mechanics)
+    u0: tuple = (0.0, 0.0, 0.0)
+    H_ext: tuple = (0.0, 0.0, 0.0)
+
+    @property
+    def offsets(self):
+        return [(0, 0, 0), (0, 0, self.n_base[2] + self.gap)]
+
+    def cells(self):
+        return int(np.prod(self.n_base)) + int(np.prod(self.n_slider))
+
+
+def film_pair_plain(n=(64, 64, 1), gap=1, seed=0):
+    """Two random-unit films of 4 nm cells, Ms = 8e5 A/m (plain stray-field sweep)."""
+    mat = Material(Ms=8e5, Aex=1.3e-11, Ku=0.0, alpha=0.5)
+    fp = FilmPair("film_pair_%dx%dx%d_gap%d" % (n + (gap,)), n, n, (4e-9, 4e-9, 4e-9), gap,
+                  mat, mat)
+    return fp, random_unit(n, seed), random_unit(n, seed + 1)
+
+
+def film_pair_stick_slip(n=(1024, 256, 2), gap=5, seed=0):
+    """Spring-pulled PMA films, 4 nm cells, Ms=1.1e6, Aex=1.5e-11, Ku=1e6 (z), alpha=0.5."""
+    mat = Material(Ms=1.1e6, Aex=1.5e-11, Ku=1.0e6, ku_axis=(0.0, 0.0, 1.0), alpha=0.5)
+    mech = Mechanics(mass=2.5e-18, k=1e-3, v_drive=1.0, gamma_v=4e7, dir=(1.0, 0.0, 0.0))
+    fp = FilmPair("stick_slip_%dx%dx%d_gap%d" % (n + (gap,)), n, n, (4e-9, 4e-9, 4e-9), gap,
+                  mat, mat, mech)
+    return fp, pma_domains(n, seed), pma_domains(n, seed + 1)
