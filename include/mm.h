@@ -1,0 +1,195 @@
+/*
+ * libmm -- stray field between two magnets at a continuous relative
+ * displacement, their own demagnetising fields, and the LLG / slider step that
+ * consumes them, on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: I. Rissanen and L. Laurson, "Moving magnets in a micromagnetic
+ * finite difference framework", arXiv:1801.04181.
+ *
+ * Conventions for every call
+ *  - Units are SI.  Magnetisation arrays are unit vectors m = M / Ms, float32,
+ *    structure of arrays [3][nz][ny][nx] (x fastest), N = nx ny nz cells.
+ *  - Magnet 0 is the base, magnet 1 the slider (Sec. III).  The slider is
+ *    displaced from its lattice place by the vector u (metres); cell i of
+ *    magnet g has its centre at (offset_g + i) * cell (+ u for the slider).
+ *  - Pointers named *_dev are CUDA device pointers, *_host host pointers.  The
+ *    caller owns every pointer it passes; the library copies in and writes
+ *    out and never keeps or frees caller memory.  The library owns its own
+ *    buffers, allocated when the geometry is planned (first compute after
+ *    mm_set_grid / mm_set_displacement), never per call.
+ *  - Work is enqueued on the stream given in mm_options (NULL = legacy default
+ *    stream).  Calls returning host values (forces, step results, state)
+ *    synchronise that stream.
+ *  - Errors are returned as mm_status, never by aborting; mm_last_error()
+ *    gives a message.  Device-side range errors (displacement beyond the
+ *    planned box during a step) surface as MM_ERANGE from the call that
+ *    synchronises.
+ */
+#ifndef MM_H
+#define MM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mm_ctx mm_ctx;
+
+typedef enum {
+  MM_OK = 0,
+  MM_EINVAL = -1,   /* bad argument or call order */
+  MM_ENOMEM = -2,   /* device allocation failed */
+  MM_ECUDA = -3,    /* CUDA runtime error (message in mm_last_error) */
+  MM_ERANGE = -4,   /* displacement left the planned potential box */
+  MM_ETIMEOUT = -5, /* reserved */
+  MM_ESTATE = -6,   /* state buffer of the wrong size or version */
+  MM_ENOTSUP = -7   /* geometry outside what this build supports */
+} mm_status;
+
+enum { MM_FP32 = 0 };
+
+typedef struct {
+  int precision;     /* MM_FP32 */
+  int margin;        /* potential box margin in cells beyond the spline support (Sec. III.A: 4) */
+  int adaptive;      /* 1: Dormand-Prince 5(4) step-size control; 0: fixed dt */
+  double rtol;       /* adaptive: accepted max-norm error of m per step */
+  double dt_min, dt_max;
+  void* stream;      /* cudaStream_t */
+} mm_options;
+
+/* Defaults: FP32, margin 4, adaptive, rtol 1e-5, dt in [1e-16, 1e-11] s, default stream. */
+void mm_default_options(mm_options* opt);
+
+/* Context.  Does not allocate device memory until a grid is planned. */
+mm_status mm_create(mm_ctx** out, const mm_options* opt);
+void mm_destroy(mm_ctx* ctx);
+const char* mm_last_error(const mm_ctx* ctx);
+const char* mm_status_string(mm_status s);
+
+/*
+ * Grid of magnet `mag` (0 base, 1 slider): nx x ny x nz cuboid cells of size
+ * dx x dy x dz metres (Sec. II: uniform M per cell at its centre) with lattice
+ * offset `offset_cells` (x, y, z).  Both magnets must use the same cell size.
+ * This build supports nz <= 4 (thin films; z by direct plane mixing).
+ */
+mm_status mm_set_grid(mm_ctx* ctx, int mag, int nx, int ny, int nz, double dx, double dy, double dz,
+                      const long long offset_cells[3]);
+
+/* Material of magnet `mag` (Sec. II): saturation magnetisation Ms (A/m),
+ * exchange constant Aex (J/m), uniaxial anisotropy Ku (J/m^3) along ku_axis,
+ * Gilbert damping alpha. */
+mm_status mm_set_material(mm_ctx* ctx, int mag, double Ms, double Aex, double Ku,
+                          const double ku_axis[3], double alpha);
+
+/* Uniform Zeeman field (A/m) acting on both magnets. */
+mm_status mm_set_external_field(mm_ctx* ctx, const double H[3]);
+
+/*
+ * Spring drive of the slider (Sec. IV.B):  m x'' = k (v_d t + x0 - x) - gamma_v m x' + F_m . e,
+ * F_m the Eq. (EQForce) force of the base on the slider, x the slider position
+ * along the unit direction e (drive_dir, normalised here).  mass <= 0 keeps
+ * the slider fixed.
+ */
+mm_status mm_set_mechanics(mm_ctx* ctx, double mass, double k_spring, double v_drive,
+                           double gamma_visc, const double drive_dir[3], double x0_spring);
+
+/* Copy m of magnet `mag` in / out (3 N floats).  _dev: device pointer;
+ * _host: host pointer (pinned memory recommended; the copy is asynchronous on
+ * the context stream for upload, synchronous for download). */
+mm_status mm_set_magnetization(mm_ctx* ctx, int mag, const float* m_dev);
+mm_status mm_get_magnetization(mm_ctx* ctx, int mag, float* m_dev);
+mm_status mm_upload_magnetization(mm_ctx* ctx, int mag, const float* m_host);
+mm_status mm_download_magnetization(mm_ctx* ctx, int mag, float* m_host);
+
+/*
+ * Slider displacement u (metres, 3-vector) relative to its lattice place
+ * (Fig. 3: the partial movement x_p is its sub-cell part).  Resets the slider
+ * coordinate x along the drive direction to 0 and re-plans the potential boxes
+ * when the whole-cell part of u changes.
+ */
+mm_status mm_set_displacement(mm_ctx* ctx, const double u_m[3]);
+
+/* Slider mechanical state: position x (m) along the drive direction (added to
+ * the displacement), velocity v (m/s) and time t (s). */
+mm_status mm_set_slider_state(mm_ctx* ctx, double x, double v, double t);
+mm_status mm_get_slider_state(mm_ctx* ctx, double* x, double* v, double* t);
+
+/*
+ * Scalar potential phi = sum_j S(r_i - r_j) . M_j of source `src` on the box
+ * around the other magnet (Sec. III.A, cell-centred S, four-cell margin).
+ * prefiltered = 0: phi (A); 1: its cubic B-spline coefficients (mirror ends).
+ * out_dev receives dims[0]*dims[1]*dims[2] floats, x fastest; `capacity` is its
+ * size in floats (MM_EINVAL if too small; call with out_dev = NULL to query
+ * dims and lo).  lo: box origin in source lattice nodes.
+ */
+mm_status mm_compute_potential(mm_ctx* ctx, int src, int prefiltered, float* out_dev,
+                               size_t capacity, int dims[3], long long lo[3]);
+
+/*
+ * Stray field H = -grad phi_src (A/m) at the displaced cell centres of the
+ * other magnet (Sec. II.A, tricubic B-spline, 64 coefficients per centre), and
+ * the Eq. (EQForce) force / interaction energy on that magnet (mm_get_force).
+ * H_dev: 3 N_target floats, may be NULL.
+ */
+mm_status mm_compute_stray_field(mm_ctx* ctx, int src, float* H_dev);
+
+/* Own demagnetising field of `mag`, H = -sum_j N(r_i - r_j) M_j (A/m), 3 N floats. */
+mm_status mm_compute_demag(mm_ctx* ctx, int mag, float* H_dev);
+
+/* Whole field evaluation at the current m and u: both demag fields, both
+ * stray fields, both forces. */
+mm_status mm_compute_fields(mm_ctx* ctx);
+
+/* Force (N) on magnet `on_mag` from the other one's stray field, Eq. (EQForce),
+ * and the interaction energy (J) of that magnet in it, from the latest field
+ * evaluation.  FP64.  Synchronises. */
+mm_status mm_get_force(mm_ctx* ctx, int on_mag, double F_out[3], double* E_int_out);
+
+/* dm/dt (1/s) of the LLG equation (Sec. II eq. 1, Landau-Lifshitz form) at the
+ * current state, and the effective field (A/m); either pointer may be NULL. */
+mm_status mm_compute_torque(mm_ctx* ctx, int mag, float* dmdt_dev, float* Heff_dev);
+
+/*
+ * Advance magnetisation and slider by `nsteps` accepted Dormand-Prince 5(4)
+ * steps (Sec. III).  *dt_inout: step size to try (s), returns the next one.
+ * t_out: simulated time after the steps (may be NULL).  Synchronises once per
+ * step attempt to read the error norm.
+ */
+mm_status mm_step(mm_ctx* ctx, int nsteps, double* t_out, double* dt_inout);
+
+/* Accepted / rejected step counters since creation. */
+mm_status mm_get_step_stats(mm_ctx* ctx, long long* accepted, long long* rejected);
+
+/* Checkpoint: m of both magnets, slider state, displacement and time.
+ * mm_get_state with buf = NULL returns the size in *bytes. */
+mm_status mm_get_state(mm_ctx* ctx, void* buf, size_t* bytes);
+mm_status mm_set_state(mm_ctx* ctx, const void* buf, size_t bytes);
+
+/*
+ * Kernel values for tests: kind 0 -> S (3 values per offset, metres), kind 1
+ * -> N (6 values: xx yy zz xy xz yz), at n target-minus-source offsets
+ * (offsets_dev: 3n doubles, metres), evaluated in FP64 on the device by the
+ * same code that builds the spectra.  out_dev: 3n or 6n doubles.
+ */
+mm_status mm_eval_kernel_fp64(int kind, int n, const double* offsets_dev, double dx, double dy,
+                              double dz, double* out_dev);
+
+/* FFT grid and potential box of the path from `src` (for reporting). */
+mm_status mm_get_plan_info(mm_ctx* ctx, int src, int fft_dims[2], int box_dims[3],
+                           long long box_lo[3], int coef_dims[3]);
+
+/* Per-kernel timing with CUDA events on the context stream (off by default).
+ * Classes: 0 x-forward FFT, 1 y pass, 2 x-inverse FFT, 3 gather, 4 LLG stage,
+ * 5 slider/reduction, 6 combine/normalise. */
+mm_status mm_set_timing(mm_ctx* ctx, int on);
+mm_status mm_get_timing(mm_ctx* ctx, int kernel_class, double* total_ms, long long* launches);
+mm_status mm_reset_timing(mm_ctx* ctx);
+
+/* Number of kernel launches this context has issued (all classes). */
+long long mm_launch_count(const mm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MM_H */

@@ -1,0 +1,213 @@
+"""GB300 implementation of the moving-magnet stray-field path of arXiv:1801.04181.
+
+Python side of libmm (include/mm.h): `MovingMagnets` marshals torch tensors
+(device memory, the current CUDA stream) into the C ABI.  Every step of the
+computation runs in the CUDA kernels of the library; nothing here computes.
+"""
+
+import ctypes as C
+
+import torch
+
+from . import _native
+from ._native import MMError, mm_options
+
+__all__ = ["MovingMagnets", "MMError", "eval_kernel_fp64", "load_library"]
+
+
+def load_library():
+    return _native.load()
+
+
+def _check(lib, ctx, status):
+    if status != 0:
+        msg = lib.mm_last_error(ctx).decode() if ctx else ""
+        raise MMError(status, msg)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _need_cuda_f32(t, shape=None):
+    if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise ValueError("expected a contiguous float32 CUDA tensor")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError("expected shape %s, got %s" % (shape, tuple(t.shape)))
+
+
+class MovingMagnets:
+    """Two magnets (0 base, 1 slider) and the slider's motion; one libmm context."""
+
+    def __init__(self, margin=4, adaptive=True, rtol=1e-5, dt_min=1e-16, dt_max=1e-11, stream=None):
+        self.lib = _native.load()
+        opt = mm_options()
+        self.lib.mm_default_options(C.byref(opt))
+        opt.margin = margin
+        opt.adaptive = 1 if adaptive else 0
+        opt.rtol = rtol
+        opt.dt_min = dt_min
+        opt.dt_max = dt_max
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        opt.stream = C.c_void_p(stream.cuda_stream)
+        self.stream = stream
+        ctx = C.c_void_p()
+        _check(self.lib, None, self.lib.mm_create(C.byref(ctx), C.byref(opt)))
+        self.ctx = ctx
+        self.shapes = [None, None]
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.mm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _c(self, status):
+        _check(self.lib, self.ctx, status)
+
+    # ---------------------------------------------------------------- set-up
+    def set_grid(self, mag, n, cell, offset=(0, 0, 0)):
+        nx, ny, nz = n
+        self._c(self.lib.mm_set_grid(self.ctx, mag, nx, ny, nz, *[float(c) for c in cell],
+                                     _native._ll3(*[int(o) for o in offset])))
+        self.shapes[mag] = (3, nz, ny, nx)
+
+    def set_material(self, mag, Ms, Aex=0.0, Ku=0.0, ku_axis=(0.0, 0.0, 1.0), alpha=0.5):
+        self._c(self.lib.mm_set_material(self.ctx, mag, Ms, Aex, Ku, _native._d3(*ku_axis), alpha))
+
+    def set_external_field(self, H):
+        self._c(self.lib.mm_set_external_field(self.ctx, _native._d3(*H)))
+
+    def set_mechanics(self, mass, k, v_drive, gamma_v, direction=(1.0, 0.0, 0.0), x0_spring=0.0):
+        self._c(self.lib.mm_set_mechanics(self.ctx, mass, k, v_drive, gamma_v, _native._d3(*direction),
+                                          x0_spring))
+
+    def set_magnetization(self, mag, m):
+        _need_cuda_f32(m, self.shapes[mag])
+        self._c(self.lib.mm_set_magnetization(self.ctx, mag, _ptr(m)))
+
+    def get_magnetization(self, mag):
+        out = torch.empty(self.shapes[mag], dtype=torch.float32, device="cuda")
+        self._c(self.lib.mm_get_magnetization(self.ctx, mag, _ptr(out)))
+        return out
+
+    def upload_magnetization(self, mag, m_host):
+        if m_host.is_cuda or m_host.dtype != torch.float32 or not m_host.is_contiguous():
+            raise ValueError("expected a contiguous float32 host tensor")
+        self._c(self.lib.mm_upload_magnetization(self.ctx, mag, _ptr(m_host)))
+
+    def download_magnetization(self, mag, out_host):
+        if out_host.is_cuda or out_host.dtype != torch.float32 or not out_host.is_contiguous():
+            raise ValueError("expected a contiguous float32 host tensor")
+        self._c(self.lib.mm_download_magnetization(self.ctx, mag, _ptr(out_host)))
+        return out_host
+
+    def set_displacement(self, u_m):
+        self._c(self.lib.mm_set_displacement(self.ctx, _native._d3(*u_m)))
+
+    def set_slider_state(self, x, v, t):
+        self._c(self.lib.mm_set_slider_state(self.ctx, x, v, t))
+
+    def get_slider_state(self):
+        x, v, t = C.c_double(), C.c_double(), C.c_double()
+        self._c(self.lib.mm_get_slider_state(self.ctx, C.byref(x), C.byref(v), C.byref(t)))
+        return x.value, v.value, t.value
+
+    # ---------------------------------------------------------------- compute
+    def compute_potential(self, src, prefiltered=False):
+        dims = _native._i3()
+        lo = _native._ll3()
+        self._c(self.lib.mm_compute_potential(self.ctx, src, int(prefiltered), None, 0, dims, lo))
+        out = torch.empty((dims[2], dims[1], dims[0]), dtype=torch.float32, device="cuda")
+        self._c(self.lib.mm_compute_potential(self.ctx, src, int(prefiltered), _ptr(out), out.numel(),
+                                              dims, lo))
+        return out, (lo[0], lo[1], lo[2])
+
+    def compute_stray_field(self, src):
+        H = torch.empty(self.shapes[1 - src], dtype=torch.float32, device="cuda")
+        self._c(self.lib.mm_compute_stray_field(self.ctx, src, _ptr(H)))
+        return H
+
+    def compute_demag(self, mag):
+        H = torch.empty(self.shapes[mag], dtype=torch.float32, device="cuda")
+        self._c(self.lib.mm_compute_demag(self.ctx, mag, _ptr(H)))
+        return H
+
+    def compute_fields(self):
+        self._c(self.lib.mm_compute_fields(self.ctx))
+
+    def get_force(self, on_mag):
+        F = _native._d3()
+        E = C.c_double()
+        self._c(self.lib.mm_get_force(self.ctx, on_mag, F, C.byref(E)))
+        return [F[0], F[1], F[2]], E.value
+
+    def compute_torque(self, mag):
+        dm = torch.empty(self.shapes[mag], dtype=torch.float32, device="cuda")
+        H = torch.empty(self.shapes[mag], dtype=torch.float32, device="cuda")
+        self._c(self.lib.mm_compute_torque(self.ctx, mag, _ptr(dm), _ptr(H)))
+        return dm, H
+
+    def step(self, nsteps, dt):
+        t = C.c_double()
+        d = C.c_double(dt)
+        self._c(self.lib.mm_step(self.ctx, int(nsteps), C.byref(t), C.byref(d)))
+        return t.value, d.value
+
+    def step_stats(self):
+        a, r = C.c_longlong(), C.c_longlong()
+        self._c(self.lib.mm_get_step_stats(self.ctx, C.byref(a), C.byref(r)))
+        return a.value, r.value
+
+    def get_state(self):
+        n = C.c_size_t()
+        self._c(self.lib.mm_get_state(self.ctx, None, C.byref(n)))
+        buf = C.create_string_buffer(n.value)
+        self._c(self.lib.mm_get_state(self.ctx, buf, C.byref(n)))
+        return buf.raw
+
+    def set_state(self, blob):
+        buf = C.create_string_buffer(blob, len(blob))
+        self._c(self.lib.mm_set_state(self.ctx, buf, len(blob)))
+
+    def plan_info(self, src):
+        q = (C.c_int * 2)()
+        b = _native._i3()
+        lo = _native._ll3()
+        cd = _native._i3()
+        self._c(self.lib.mm_get_plan_info(self.ctx, src, q, b, lo, cd))
+        return dict(fft=(q[0], q[1]), box=(b[0], b[1], b[2]), box_lo=(lo[0], lo[1], lo[2]),
+                    coef=(cd[0], cd[1], cd[2]))
+
+    # ---------------------------------------------------------------- timing
+    def set_timing(self, on):
+        self._c(self.lib.mm_set_timing(self.ctx, int(on)))
+
+    def timing(self, cls):
+        ms, n = C.c_double(), C.c_longlong()
+        self._c(self.lib.mm_get_timing(self.ctx, cls, C.byref(ms), C.byref(n)))
+        return ms.value, n.value
+
+    def reset_timing(self):
+        self._c(self.lib.mm_reset_timing(self.ctx))
+
+    def launch_count(self):
+        return self.lib.mm_launch_count(self.ctx)
+
+
+def eval_kernel_fp64(kind, offsets_m, cell):
+    """S (kind 0) or N (kind 1) at target-minus-source offsets (n, 3) metres, FP64 on the GPU."""
+    lib = _native.load()
+    off = torch.as_tensor(offsets_m, dtype=torch.float64, device="cuda").contiguous()
+    n = off.shape[0]
+    out = torch.empty((n, 3 if kind == 0 else 6), dtype=torch.float64, device="cuda")
+    st = lib.mm_eval_kernel_fp64(kind, n, _ptr(off), *[float(c) for c in cell], _ptr(out))
+    if st != 0:
+        raise MMError(st, "mm_eval_kernel_fp64")
+    return out

@@ -1,0 +1,1326 @@
+// C ABI of libmm: planning, buffers and launch sequences (include/mm.h).
+//
+// Per source magnet s and target t = 1 - s (Sec. II.A: each magnet's stray
+// field is interpolated inside the other):
+//   box    per axis [floor(p_min) - 1 - margin, floor(p_max) + 2 + margin] in
+//          source lattice nodes, p = offset_t - offset_s + i + sigma u
+//          (Sec. III.A: potential extends `margin` cells past the support);
+//   FFT    one Qx x Qy circular grid serves the magnet's own demag field and its
+//          potential on the box: the kernels are laid on the window |d| <= W,
+//          W covering every source-to-box offset, and Q >= 2W + 2 keeps the
+//          circular sum equal to the linear one (no aliasing) and the kernels
+//          exactly even / odd on the grid;
+//   output coefficient nodes [margin - guard, margin + n_t + 3 + guard) per axis,
+//          the spline support of all targets plus `guard` nodes on an axis of
+//          motion so a step may cross a cell boundary without re-planning.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/mm.h"
+#include "mm_internal.h"
+
+using namespace mm;
+
+namespace {
+
+constexpr double kMu0 = 4e-7 * 3.14159265358979323846;
+constexpr double kGammaLL = 1.7595e11;  // rad / (s T)
+constexpr int kWindowSlack = 8;         // cells of displacement before the FFT grid is re-planned
+constexpr int kTimingClasses = 7;
+
+// Dormand-Prince 5(4)
+const double DP_C[7] = {0.0, 1.0 / 5, 3.0 / 10, 4.0 / 5, 8.0 / 9, 1.0, 1.0};
+const double DP_A[7][7] = {
+    {0, 0, 0, 0, 0, 0, 0},
+    {1.0 / 5, 0, 0, 0, 0, 0, 0},
+    {3.0 / 40, 9.0 / 40, 0, 0, 0, 0, 0},
+    {44.0 / 45, -56.0 / 15, 32.0 / 9, 0, 0, 0, 0},
+    {19372.0 / 6561, -25360.0 / 2187, 64448.0 / 6561, -212.0 / 729, 0, 0, 0},
+    {9017.0 / 3168, -355.0 / 33, 46732.0 / 5247, 49.0 / 176, -5103.0 / 18656, 0, 0},
+    {35.0 / 384, 0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84, 0}};
+const double DP_B5[7] = {35.0 / 384, 0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84, 0};
+const double DP_B4[7] = {5179.0 / 57600, 0, 7571.0 / 16695, 393.0 / 640, -92097.0 / 339200,
+                         187.0 / 2100, 1.0 / 40};
+
+struct FftRes {
+  FftTables t{};
+  float2* tw_f = nullptr;
+  double2* tw_d = nullptr;
+  int* pos = nullptr;
+  int* freq = nullptr;
+};
+
+struct Dir {
+  bool valid = false;
+  bool full_box = false;   // potential query: whole box, optional prefilter
+  int prefilter = 1;
+  int U0[3] = {0, 0, 0};
+  int box_lo[3] = {0, 0, 0}, box_len[3] = {0, 0, 0};
+  int start[3] = {0, 0, 0}, r[3] = {0, 0, 0}, guard[3] = {0, 0, 0};
+  int Tq_box_lo_z = 0, Tq_bz = 0, Tq_start_z = 0, Tq_nout = 0, Tq_prefilter = -1, Tq_Q[2] = {0, 0};
+  float* Tq = nullptr;
+  float2* YC = nullptr;
+  float* C = nullptr;
+  double* partial = nullptr;
+  int ntiles = 0;
+  size_t Tq_bytes = 0, YC_bytes = 0, C_bytes = 0, partial_bytes = 0;
+};
+
+struct Magnet {
+  bool grid = false, mat = false, mset = false;
+  int nx = 0, ny = 0, nz = 0;
+  long long off[3] = {0, 0, 0};
+  double d[3] = {0, 0, 0};
+  double Ms = 0, Aex = 0, Ku = 0, ku[3] = {0, 0, 1}, alpha = 0;
+  size_t N = 0;
+  float* m = nullptr;
+  float* ys[2] = {nullptr, nullptr};
+  float* k[7] = {};
+  float* Hself = nullptr;
+  float* Hstray = nullptr;
+  float* scratch3 = nullptr;  // 3N scratch for rhs-only evaluations
+  float* err_partial = nullptr;
+  int nerr = 0;
+  // as a source
+  int Qx = 0, Qy = 0, Wx = 0, Wy = 0, kxh = 0, kyq = 0;
+  double Nq_Ms = 0;
+  float2* X1 = nullptr;
+  float2* YH = nullptr;
+  float* Nq = nullptr;
+  Dir dir;   // hot path: coefficients around the other magnet
+  Dir aux;   // mm_compute_potential output
+};
+
+struct TimedLaunch {
+  int cls;
+  cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct mm_ctx {
+  mm_options opt{};
+  cudaStream_t st = nullptr;
+  std::string err;
+  Magnet mag[2];
+  std::map<int, FftRes> ffts;
+  double Hext[3] = {0, 0, 0};
+  // mechanics
+  bool move = false;
+  double mass = 0, k_spring = 0, v_drive = 0, gamma_v = 0, x0_spring = 0, e[3] = {1, 0, 0};
+  double u_base[3] = {0, 0, 0};       // metres
+  MechState host_mech{};
+  MechState* mech = nullptr;          // device
+  int* err_flag = nullptr;            // device
+  bool k1_valid = false;
+  long long accepted = 0, rejected = 0;
+  bool planned = false;
+  // setup scratch (FP64 spectra generation)
+  double2* gen_work = nullptr;
+  size_t gen_work_bytes = 0;
+  double* gen_q = nullptr;
+  size_t gen_q_bytes = 0;
+  double* W_dev = nullptr;
+  size_t W_bytes = 0;
+  // timing
+  bool timing = false;
+  std::vector<TimedLaunch> pending;
+  std::vector<cudaEvent_t> free_events;
+  double t_ms[kTimingClasses] = {};
+  long long t_n[kTimingClasses] = {};
+  long long launches = 0;
+};
+
+// ============================================================ helpers
+namespace {
+
+mm_status fail(mm_ctx* c, mm_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? MM_ENOMEM : MM_ECUDA,            \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                    \
+  } while (0)
+
+#define CKS(expr)              \
+  do {                         \
+    mm_status s_ = (expr);     \
+    if (s_ != MM_OK) return s_; \
+  } while (0)
+
+template <typename T>
+mm_status ensure_buf(mm_ctx* ctx, T** p, size_t* have, size_t bytes) {
+  if (*p && *have >= bytes) return MM_OK;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *have = 0;
+  if (bytes == 0) return MM_OK;
+  CK(cudaMalloc((void**)p, bytes));
+  *have = bytes;
+  return MM_OK;
+}
+
+mm_status alloc(mm_ctx* ctx, void** p, size_t bytes) {
+  CK(cudaMalloc(p, bytes));
+  return MM_OK;
+}
+
+int smooth_even_at_least(int n) {
+  for (int q = std::max(2, n);; ++q) {
+    if (q & 1) continue;
+    int r = q;
+    while (r % 2 == 0) r /= 2;
+    while (r % 3 == 0) r /= 3;
+    while (r % 5 == 0) r /= 5;
+    if (r == 1) return q;
+  }
+}
+
+mm_status get_fft(mm_ctx* ctx, int L, FftTables* out) {
+  auto it = ctx->ffts.find(L);
+  if (it != ctx->ffts.end()) {
+    *out = it->second.t;
+    return MM_OK;
+  }
+  FftRes R;
+  int p2 = 0, p3 = 0, p5 = 0, r = L;
+  while (r % 2 == 0) { r /= 2; ++p2; }
+  while (r % 3 == 0) { r /= 3; ++p3; }
+  while (r % 5 == 0) { r /= 5; ++p5; }
+  if (r != 1) return fail(ctx, MM_EINVAL, "FFT length is not 2^a 3^b 5^c");
+  std::vector<int> radix;
+  while (p2 >= 3) { radix.push_back(8); p2 -= 3; }
+  if (p2 == 2) radix.push_back(4);
+  if (p2 == 1) radix.push_back(2);
+  for (int i = 0; i < p5; ++i) radix.push_back(5);
+  for (int i = 0; i < p3; ++i) radix.push_back(3);
+  if ((int)radix.size() > kMaxStages) return fail(ctx, MM_ENOTSUP, "FFT length has too many factors");
+  FftPlanDev P{};
+  P.L = L;
+  P.nstages = (int)radix.size();
+  int Lb = L;
+  for (int s = 0; s < P.nstages; ++s) {
+    P.radix[s] = radix[s];
+    P.blocklen[s] = Lb;
+    Lb /= radix[s];
+  }
+  std::vector<float2> twf(L);
+  std::vector<double2> twd(L);
+  for (int t = 0; t < L; ++t) {
+    const double ang = -2.0 * 3.14159265358979323846 * (double)t / (double)L;
+    twd[t] = make_double2(cos(ang), sin(ang));
+    twf[t] = make_float2((float)twd[t].x, (float)twd[t].y);
+  }
+  std::vector<int> pos(L), freq(L);
+  for (int k = 0; k < L; ++k) {
+    int p = 0, rem = k, B = L;
+    for (int s = 0; s < P.nstages; ++s) {
+      const int M = B / P.radix[s];
+      p += M * (rem % P.radix[s]);
+      rem /= P.radix[s];
+      B = M;
+    }
+    pos[k] = p;
+    freq[p] = k;
+  }
+  CKS(alloc(ctx, (void**)&R.tw_f, sizeof(float2) * L));
+  CKS(alloc(ctx, (void**)&R.tw_d, sizeof(double2) * L));
+  CKS(alloc(ctx, (void**)&R.pos, sizeof(int) * L));
+  CKS(alloc(ctx, (void**)&R.freq, sizeof(int) * L));
+  CK(cudaMemcpy(R.tw_f, twf.data(), sizeof(float2) * L, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(R.tw_d, twd.data(), sizeof(double2) * L, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(R.pos, pos.data(), sizeof(int) * L, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(R.freq, freq.data(), sizeof(int) * L, cudaMemcpyHostToDevice));
+  R.t.plan = P;
+  R.t.tw_f = R.tw_f;
+  R.t.tw_d = R.tw_d;
+  R.t.pos = R.pos;
+  R.t.freq = R.freq;
+  ctx->ffts[L] = R;
+  *out = R.t;
+  return MM_OK;
+}
+
+double u_cells(const mm_ctx* ctx, int a, double x) {
+  return (ctx->u_base[a] + x * ctx->e[a]) / ctx->mag[0].d[a];
+}
+
+// ------------------------------------------------------------ timing
+cudaEvent_t grab_event(mm_ctx* ctx) {
+  if (!ctx->free_events.empty()) {
+    cudaEvent_t e = ctx->free_events.back();
+    ctx->free_events.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+
+struct Timer {
+  mm_ctx* ctx;
+  int cls;
+  cudaEvent_t a = nullptr, b = nullptr;
+  Timer(mm_ctx* c, int k) : ctx(c), cls(k) {
+    ctx->launches++;
+    if (ctx->timing) {
+      a = grab_event(ctx);
+      b = grab_event(ctx);
+      cudaEventRecord(a, ctx->st);
+    }
+  }
+  ~Timer() {
+    if (a) {
+      cudaEventRecord(b, ctx->st);
+      ctx->pending.push_back({cls, a, b});
+    }
+  }
+};
+
+void drain_timing(mm_ctx* ctx) {
+  if (ctx->pending.empty()) return;
+  cudaStreamSynchronize(ctx->st);
+  for (auto& p : ctx->pending) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, p.a, p.b);
+    ctx->t_ms[p.cls] += ms;
+    ctx->t_n[p.cls] += 1;
+    ctx->free_events.push_back(p.a);
+    ctx->free_events.push_back(p.b);
+  }
+  ctx->pending.clear();
+}
+
+// ------------------------------------------------------------ planning
+// B-spline prefilter taps sqrt(3) z1^|i|, z1 = sqrt(3) - 2
+void fir_taps(double* h) {
+  const double z1 = sqrt(3.0) - 2.0;
+  for (int i = 0; i <= kFirHalf; ++i) h[i] = sqrt(3.0) * pow(z1, i);
+}
+
+int host_mirror(int j, int b) {
+  if (b <= 1) return 0;
+  const int P = 2 * b - 2;
+  j %= P;
+  if (j < 0) j += P;
+  return j < b ? j : P - j;
+}
+
+void dir_geometry(const mm_ctx* ctx, int s, bool full_box, Dir* D) {
+  const int t = 1 - s;
+  const Magnet& S = ctx->mag[s];
+  const Magnet& T = ctx->mag[t];
+  const double sigma = t == 1 ? 1.0 : -1.0;
+  const int nt[3] = {T.nx, T.ny, T.nz};
+  const int m = ctx->opt.margin;
+  for (int a = 0; a < 3; ++a) {
+    const double su = sigma * u_cells(ctx, a, ctx->host_mech.x);
+    const int U = (int)floor(su);
+    D->U0[a] = U;
+    const long long Dd = T.off[a] - S.off[a];
+    D->box_lo[a] = (int)(Dd + U - 1 - m);
+    D->box_len[a] = nt[a] + 3 + 2 * m;
+    const int g = (!full_box && ctx->move && ctx->e[a] != 0.0) ? 1 : 0;
+    D->guard[a] = g;
+    if (full_box) {
+      D->start[a] = 0;
+      D->r[a] = D->box_len[a];
+    } else {
+      D->start[a] = m - g;
+      D->r[a] = nt[a] + 3 + 2 * g;
+    }
+  }
+  D->full_box = full_box;
+}
+
+int window_needed(const Magnet& S, const Dir& D, int a) {
+  const int n = a == 0 ? S.nx : S.ny;
+  int w = n - 1;  // self-demag offsets
+  w = std::max(w, std::abs(D.box_lo[a] - (n - 1)));
+  w = std::max(w, std::abs(D.box_lo[a] + D.box_len[a] - 1));
+  return w;
+}
+
+mm_status build_T(mm_ctx* ctx, int s, Dir* D) {
+  Magnet& S = ctx->mag[s];
+  const int n_out = D->r[2];
+  const int bz = D->box_len[2];
+  if (D->Tq && D->Tq_box_lo_z == D->box_lo[2] && D->Tq_bz == bz && D->Tq_start_z == D->start[2] &&
+      D->Tq_nout == n_out && D->Tq_prefilter == D->prefilter && D->Tq_Q[0] == S.Qx &&
+      D->Tq_Q[1] == S.Qy)
+    return MM_OK;
+  FftTables fx, fy;
+  CKS(get_fft(ctx, S.Qx, &fx));
+  CKS(get_fft(ctx, S.Qy, &fy));
+  const size_t qsize = (size_t)S.kxh * S.kyq;
+  CKS(ensure_buf(ctx, &D->Tq, &D->Tq_bytes, sizeof(float) * (size_t)n_out * S.nz * 3 * qsize));
+  // z mixing matrix: rows = output planes, columns = box planes
+  std::vector<double> W((size_t)n_out * bz, 0.0);
+  double h[kFirHalf + 1];
+  fir_taps(h);
+  for (int o = 0; o < n_out; ++o) {
+    const int c = D->start[2] + o;
+    if (D->prefilter) {
+      for (int i = -kFirHalf; i <= kFirHalf; ++i) W[(size_t)o * bz + host_mirror(c - i, bz)] += h[std::abs(i)];
+    } else {
+      W[(size_t)o * bz + c] = 1.0;
+    }
+  }
+  CKS(ensure_buf(ctx, &ctx->W_dev, &ctx->W_bytes, sizeof(double) * W.size()));
+  CK(cudaMemcpyAsync(ctx->W_dev, W.data(), sizeof(double) * W.size(), cudaMemcpyHostToDevice, ctx->st));
+  const size_t plane = (size_t)S.Qx * S.Qy;
+  CKS(ensure_buf(ctx, &ctx->gen_work, &ctx->gen_work_bytes, sizeof(double2) * 2 * 6 * plane));
+  const int nplanes = bz + S.nz - 1;
+  CKS(ensure_buf(ctx, &ctx->gen_q, &ctx->gen_q_bytes, sizeof(double) * (size_t)nplanes * 3 * qsize));
+  KernelPlan K{S.Qx, S.Qy, S.Wx, S.Wy, S.nz};
+  const double scale = S.Ms / ((double)S.Qx * S.Qy);
+  CK(build_T_spectra(K, fx, fy, S.d[0], S.d[1], S.d[2], scale, D->box_lo[2], bz, n_out, ctx->W_dev, D->Tq,
+                     ctx->gen_work, ctx->gen_q, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));  // W_dev / scratch reuse
+  D->Tq_box_lo_z = D->box_lo[2];
+  D->Tq_bz = bz;
+  D->Tq_start_z = D->start[2];
+  D->Tq_nout = n_out;
+  D->Tq_prefilter = D->prefilter;
+  D->Tq_Q[0] = S.Qx;
+  D->Tq_Q[1] = S.Qy;
+  return MM_OK;
+}
+
+mm_status alloc_dir_outputs(mm_ctx* ctx, int s, Dir* D) {
+  Magnet& S = ctx->mag[s];
+  const Magnet& T = ctx->mag[1 - s];
+  CKS(ensure_buf(ctx, &D->YC, &D->YC_bytes, sizeof(float2) * (size_t)D->r[2] * S.kxh * D->r[1]));
+  CKS(ensure_buf(ctx, &D->C, &D->C_bytes, sizeof(float) * (size_t)D->r[2] * D->r[1] * D->r[0]));
+  D->ntiles = gather_tiles(T.nx, T.ny);
+  CKS(ensure_buf(ctx, &D->partial, &D->partial_bytes, sizeof(double) * 4 * (size_t)D->ntiles));
+  return MM_OK;
+}
+
+mm_status alloc_magnet(mm_ctx* ctx, Magnet& M) {
+  if (M.m) return MM_OK;
+  const size_t b = sizeof(float) * 3 * M.N;
+  CKS(alloc(ctx, (void**)&M.m, b));
+  CK(cudaMemset(M.m, 0, b));
+  for (int i = 0; i < 2; ++i) CKS(alloc(ctx, (void**)&M.ys[i], b));
+  for (int i = 0; i < 7; ++i) CKS(alloc(ctx, (void**)&M.k[i], b));
+  CKS(alloc(ctx, (void**)&M.Hself, b));
+  CKS(alloc(ctx, (void**)&M.Hstray, b));
+  CKS(alloc(ctx, (void**)&M.scratch3, b));
+  M.nerr = (int)((M.N + 255) / 256);
+  CKS(alloc(ctx, (void**)&M.err_partial, sizeof(float) * M.nerr));
+  return MM_OK;
+}
+
+// (Re)plan both sources for the current displacement; rebuild spectra as needed.
+mm_status ensure_plan(mm_ctx* ctx) {
+  for (int g = 0; g < 2; ++g) {
+    if (!ctx->mag[g].grid) return fail(ctx, MM_EINVAL, "grid of magnet " + std::to_string(g) + " not set");
+    if (!ctx->mag[g].mat) return fail(ctx, MM_EINVAL, "material of magnet " + std::to_string(g) + " not set");
+  }
+  for (int s = 0; s < 2; ++s) {
+    Magnet& S = ctx->mag[s];
+    Dir& D = S.dir;
+    dir_geometry(ctx, s, false, &D);
+    D.prefilter = 1;
+    const int wx = window_needed(S, D, 0), wy = window_needed(S, D, 1);
+    const bool regrid = S.Qx == 0 || 2 * wx + 2 > S.Qx || 2 * wy + 2 > S.Qy;
+    if (regrid) {
+      S.Wx = wx + kWindowSlack;
+      S.Wy = wy + kWindowSlack;
+      S.Qx = smooth_even_at_least(2 * S.Wx + 2);
+      S.Qy = smooth_even_at_least(2 * S.Wy + 2);
+      // keep the window inside the grid: the largest W with 2W + 2 <= Q
+      S.Wx = (S.Qx - 2) / 2;
+      S.Wy = (S.Qy - 2) / 2;
+      S.kxh = S.Qx / 2 + 1;
+      S.kyq = S.Qy / 2 + 1;
+      if ((size_t)(kRowsPerCta / 2) * S.Qx * sizeof(float2) > 220 * 1024)
+        return fail(ctx, MM_ENOTSUP, "x extent too large for one shared-memory line");
+      const int P = std::max(3 * S.nz, 3 * S.nz + D.r[2]);
+      if ((size_t)P * S.Qy * sizeof(float2) > 220 * 1024)
+        return fail(ctx, MM_ENOTSUP, "y extent x planes too large for the fused y pass");
+      S.Nq_Ms = 0;  // force N rebuild
+      if (S.X1) { cudaFree(S.X1); S.X1 = nullptr; }
+      if (S.YH) { cudaFree(S.YH); S.YH = nullptr; }
+      if (S.Nq) { cudaFree(S.Nq); S.Nq = nullptr; }
+      S.aux.valid = false;
+    }
+    const size_t qsize = (size_t)S.kxh * S.kyq;
+    if (!S.X1) {
+      CKS(alloc(ctx, (void**)&S.X1, sizeof(float2) * 3 * S.nz * S.kxh * (size_t)S.ny));
+      CKS(alloc(ctx, (void**)&S.YH, sizeof(float2) * 3 * S.nz * S.kxh * (size_t)S.ny));
+      CKS(alloc(ctx, (void**)&S.Nq, sizeof(float) * 6 * S.nz * qsize));
+    }
+    if (S.Nq_Ms != S.Ms) {
+      FftTables fx, fy;
+      CKS(get_fft(ctx, S.Qx, &fx));
+      CKS(get_fft(ctx, S.Qy, &fy));
+      const size_t plane = (size_t)S.Qx * S.Qy;
+      CKS(ensure_buf(ctx, &ctx->gen_work, &ctx->gen_work_bytes, sizeof(double2) * 2 * 6 * plane));
+      CKS(ensure_buf(ctx, &ctx->gen_q, &ctx->gen_q_bytes,
+                     std::max(ctx->gen_q_bytes, sizeof(double) * 6 * qsize)));
+      KernelPlan K{S.Qx, S.Qy, S.Wx, S.Wy, S.nz};
+      CK(build_N_spectra(K, fx, fy, S.d[0], S.d[1], S.d[2], -S.Ms / ((double)S.Qx * S.Qy), S.Nq,
+                         ctx->gen_work, ctx->gen_q, ctx->st));
+      CK(cudaStreamSynchronize(ctx->st));
+      S.Nq_Ms = S.Ms;
+    }
+    CKS(build_T(ctx, s, &D));
+    CKS(alloc_dir_outputs(ctx, s, &D));
+    D.valid = true;
+  }
+  ctx->planned = true;
+  return MM_OK;
+}
+
+// Re-plan when the whole-cell part of the displacement moved outside the guard.
+mm_status replan_if_needed(mm_ctx* ctx) {
+  if (!ctx->planned) return ensure_plan(ctx);
+  for (int s = 0; s < 2; ++s) {
+    const Dir& D = ctx->mag[s].dir;
+    const double sigma = s == 0 ? 1.0 : -1.0;
+    for (int a = 0; a < 3; ++a) {
+      const int U = (int)floor(sigma * u_cells(ctx, a, ctx->host_mech.x));
+      if (U != D.U0[a]) return ensure_plan(ctx);
+    }
+  }
+  return MM_OK;
+}
+
+mm_status upload_mech(mm_ctx* ctx) {
+  MechState& H = ctx->host_mech;
+  H.xs = H.x; H.vs = H.v; H.ts = H.t;
+  for (int a = 0; a < 3; ++a) H.u[a] = u_cells(ctx, a, H.x);
+  CK(cudaMemcpyAsync(ctx->mech, &H, sizeof(MechState), cudaMemcpyHostToDevice, ctx->st));
+  return MM_OK;
+}
+
+// ------------------------------------------------------------ launch sequences
+Launch<XFwdJob> xfwd_launch(mm_ctx* ctx, const float* in[2], const int* which, int n, int* Qmax) {
+  Launch<XFwdJob> L{};
+  L.njobs = n;
+  int tiles = 0;
+  *Qmax = 0;
+  for (int i = 0; i < n; ++i) {
+    Magnet& S = ctx->mag[which[i]];
+    XFwdJob& J = L.job[i];
+    J.m = in[which[i]];
+    J.out = S.X1;
+    J.nx = S.nx; J.ny = S.ny; J.nz = S.nz; J.kxh = S.kxh;
+    get_fft(ctx, S.Qx, &J.fx);
+    L.tile_start[i] = tiles;
+    tiles += (3 * S.nz * S.ny + kRowsPerCta - 1) / kRowsPerCta;
+    *Qmax = std::max(*Qmax, S.Qx);
+  }
+  L.tile_start[n] = tiles;
+  return L;
+}
+
+// what: bit 1 = own demag, bit 2 = coefficients of Dir (hot or aux)
+mm_status run_source_passes(mm_ctx* ctx, const float* in[2], const int* which, int n, const int* what,
+                            Dir* const* dirs) {
+  cudaStream_t st = ctx->st;
+  int Qmax = 0;
+  {
+    Launch<XFwdJob> L = xfwd_launch(ctx, in, which, n, &Qmax);
+    Timer t(ctx, 0);
+    CK(launch_xfwd(L, Qmax, st));
+  }
+  {
+    Launch<YJob> L{};
+    L.njobs = n;
+    int tiles = 0;
+    size_t smem = 0;
+    for (int i = 0; i < n; ++i) {
+      Magnet& S = ctx->mag[which[i]];
+      Dir* D = dirs[i];
+      YJob& J = L.job[i];
+      J.in = S.X1;
+      J.nz = S.nz; J.ny = S.ny; J.kxh = S.kxh; J.kyq = S.kyq;
+      CKS(get_fft(ctx, S.Qy, &J.fy));
+      J.do_H = (what[i] & 1) ? 1 : 0;
+      J.Nq = S.Nq;
+      J.outH = S.YH;
+      J.do_C = (what[i] & 2) ? 1 : 0;
+      if (J.do_C) {
+        J.n_out = D->r[2];
+        J.Tq = D->Tq;
+        J.outC = D->YC;
+        J.box_lo = D->box_lo[1];
+        J.box_len = D->box_len[1];
+        J.start = D->start[1];
+        J.r = D->r[1];
+        J.fir = D->prefilter;
+      }
+      const int Pout = (J.do_H ? 3 * S.nz : 0) + (J.do_C ? J.n_out : 0);
+      const int P = std::max(3 * S.nz, Pout);
+      smem = std::max(smem, (size_t)P * S.Qy * sizeof(float2));
+      L.tile_start[i] = tiles;
+      tiles += S.kxh;
+    }
+    L.tile_start[n] = tiles;
+    Timer t(ctx, 1);
+    CK(launch_ypass(L, smem, st));
+  }
+  {
+    Launch<XInvJob> L{};
+    int nj = 0, tiles = 0;
+    for (int i = 0; i < n; ++i) {
+      Magnet& S = ctx->mag[which[i]];
+      FftTables fx;
+      CKS(get_fft(ctx, S.Qx, &fx));
+      if (what[i] & 1) {
+        XInvJob& J = L.job[nj];
+        J.in = S.YH;
+        J.out = S.Hself;
+        J.planes = 3 * S.nz; J.rows_per_plane = S.ny; J.kxh = S.kxh;
+        J.fx = fx;
+        J.box_lo = 0; J.box_len = S.nx; J.start = 0; J.out_len = S.nx; J.fir = 0;
+        L.tile_start[nj] = tiles;
+        tiles += (J.planes * J.rows_per_plane + kRowsPerCta - 1) / kRowsPerCta;
+        ++nj;
+      }
+      if (what[i] & 2) {
+        Dir* D = dirs[i];
+        XInvJob& J = L.job[nj];
+        J.in = D->YC;
+        J.out = D->C;
+        J.planes = D->r[2]; J.rows_per_plane = D->r[1]; J.kxh = S.kxh;
+        J.fx = fx;
+        J.box_lo = D->box_lo[0]; J.box_len = D->box_len[0]; J.start = D->start[0];
+        J.out_len = D->r[0]; J.fir = D->prefilter;
+        L.tile_start[nj] = tiles;
+        tiles += (J.planes * J.rows_per_plane + kRowsPerCta - 1) / kRowsPerCta;
+        ++nj;
+      }
+      Qmax = std::max(Qmax, S.Qx);
+    }
+    L.njobs = nj;
+    L.tile_start[nj] = tiles;
+    Timer t(ctx, 2);
+    CK(launch_xinv(L, Qmax, st));
+  }
+  return MM_OK;
+}
+
+GatherJob gather_job(mm_ctx* ctx, int s, const float* m_t, float* H) {
+  const Magnet& S = ctx->mag[s];
+  const Magnet& T = ctx->mag[1 - s];
+  const Dir& D = S.dir;
+  GatherJob J{};
+  J.C = D.C;
+  J.rx = D.r[0]; J.ry = D.r[1]; J.rz = D.r[2];
+  J.nx = T.nx; J.ny = T.ny; J.nz = T.nz;
+  J.u = ctx->mech->u;
+  J.sigma = s == 0 ? 1.0 : -1.0;
+  for (int a = 0; a < 3; ++a) {
+    J.U0[a] = D.U0[a];
+    J.guard[a] = D.guard[a];
+    J.inv_d[a] = (float)(1.0 / T.d[a]);
+  }
+  J.m = m_t;
+  J.H = H;
+  J.partial = D.partial;
+  J.err = ctx->err_flag;
+  return J;
+}
+
+mm_status run_gathers(mm_ctx* ctx, const float* in[2], const int* srcs, int n, float* const* Hout) {
+  Launch<GatherJob> L{};
+  L.njobs = n;
+  int tiles = 0, nzmax = 1;
+  for (int i = 0; i < n; ++i) {
+    const int s = srcs[i];
+    L.job[i] = gather_job(ctx, s, in[1 - s], Hout[i]);
+    L.tile_start[i] = tiles;
+    tiles += ctx->mag[s].dir.ntiles;
+    nzmax = std::max(nzmax, ctx->mag[1 - s].nz);
+  }
+  L.tile_start[n] = tiles;
+  Timer t(ctx, 3);
+  CK(launch_gather(L, nzmax, ctx->st));
+  return MM_OK;
+}
+
+MechParams mech_params(mm_ctx* ctx, int mode, int stage, double dt, bool dir0, bool dir1) {
+  MechParams P{};
+  P.state = ctx->mech;
+  const bool use[2] = {dir0, dir1};
+  for (int s = 0; s < 2; ++s) {
+    const Magnet& T = ctx->mag[1 - s];
+    // direction s -> t: partial index s (0: base -> slider, 1: slider -> base)
+    if (use[s]) {
+      P.partial[s] = ctx->mag[s].dir.partial;
+      P.ntiles[s] = ctx->mag[s].dir.ntiles;
+    }
+    const double V = T.d[0] * T.d[1] * T.d[2];
+    P.Fscale[s] = -kMu0 * V * T.Ms;
+    P.Escale[s] = kMu0 * V * T.Ms;
+    P.err_partial[s] = ctx->mag[s].err_partial;
+    P.nerr[s] = ctx->mag[s].nerr;
+  }
+  P.mode = mode;
+  P.stage = stage;
+  P.dt = dt;
+  if (stage >= 1 && stage < 7)
+    for (int j = 0; j < 7; ++j) P.a[j] = DP_A[stage][j];
+  if (mode == 2)
+    for (int j = 0; j < 7; ++j) P.a[j] = DP_A[1][j];
+  P.c_next = (mode == 2) ? DP_C[1] : (stage >= 1 && stage < 7 ? DP_C[stage] : 0.0);
+  P.move = ctx->move ? 1 : 0;
+  P.mass = ctx->mass;
+  P.k_spring = ctx->k_spring;
+  P.v_drive = ctx->v_drive;
+  P.x0_spring = ctx->x0_spring;
+  P.gamma_v = ctx->gamma_v;
+  for (int a = 0; a < 3; ++a) {
+    P.e[a] = ctx->e[a];
+    P.inv_d[a] = 1.0 / ctx->mag[0].d[a];
+    P.u_base[a] = ctx->u_base[a] / ctx->mag[0].d[a];
+  }
+  return P;
+}
+
+mm_status run_mech(mm_ctx* ctx, const MechParams& P) {
+  Timer t(ctx, 5);
+  CK(launch_mech(P, ctx->st));
+  return MM_OK;
+}
+
+// All fields of both magnets for stage inputs `in` (demag, stray, forces).
+mm_status evaluate_fields(mm_ctx* ctx, const float* in[2]) {
+  const int which[2] = {0, 1};
+  const int what[2] = {3, 3};
+  Dir* dirs[2] = {&ctx->mag[0].dir, &ctx->mag[1].dir};
+  CKS(run_source_passes(ctx, in, which, 2, what, dirs));
+  const int srcs[2] = {0, 1};
+  // H_stray of the slider comes from source 0, of the base from source 1
+  float* H[2] = {ctx->mag[1].Hstray, ctx->mag[0].Hstray};
+  CKS(run_gathers(ctx, in, srcs, 2, H));
+  return MM_OK;
+}
+
+StageJob stage_job(mm_ctx* ctx, int g, const float* ys, float* ys_next, int stage, int mode, double dt,
+                   float* const* kptr, float* Heff) {
+  const Magnet& M = ctx->mag[g];
+  StageJob J{};
+  J.ys = ys;
+  J.y = M.m;
+  J.ys_next = ys_next;
+  for (int i = 0; i < 7; ++i) J.k[i] = kptr[i];
+  J.Hself = M.Hself;
+  J.Hstray = M.Hstray;
+  J.Heff = Heff;
+  J.nx = M.nx; J.ny = M.ny; J.nz = M.nz;
+  for (int a = 0; a < 3; ++a) {
+    J.ex[a] = (float)(2.0 * M.Aex / (kMu0 * M.Ms * M.d[a] * M.d[a]));
+    J.hext[a] = (float)ctx->Hext[a];
+  }
+  const double kn = sqrt(M.ku[0] * M.ku[0] + M.ku[1] * M.ku[1] + M.ku[2] * M.ku[2]);
+  for (int a = 0; a < 3; ++a) J.ku[a] = (float)(kn > 0 ? M.ku[a] / kn : 0.0);
+  J.an = (float)(2.0 * M.Ku / (kMu0 * M.Ms));
+  J.pref = (float)(-kMu0 * kGammaLL / (1.0 + M.alpha * M.alpha));
+  J.alpha = (float)M.alpha;
+  J.stage = stage;
+  J.mode = mode;
+  if (mode == 0 && stage < 7)
+    for (int j = 0; j < stage; ++j) J.comb[j] = (float)(dt * DP_A[stage][j]);
+  if (mode == 0 && stage == 7)
+    for (int j = 0; j < 7; ++j) J.ecoef[j] = (float)(dt * (DP_B5[j] - DP_B4[j]));
+  J.err_partial = M.err_partial;
+  return J;
+}
+
+mm_status run_stage(mm_ctx* ctx, const float* ys[2], float* ys_next[2], int stage, double dt) {
+  Launch<StageJob> L{};
+  L.njobs = 2;
+  int tiles = 0;
+  for (int g = 0; g < 2; ++g) {
+    L.job[g] = stage_job(ctx, g, ys[g], ys_next[g], stage, 0, dt, ctx->mag[g].k, nullptr);
+    L.tile_start[g] = tiles;
+    tiles += ctx->mag[g].nerr;
+  }
+  L.tile_start[2] = tiles;
+  Timer t(ctx, 4);
+  CK(launch_stage(L, ctx->st));
+  return MM_OK;
+}
+
+mm_status check_device_error(mm_ctx* ctx) {
+  int e = 0;
+  CK(cudaMemcpyAsync(&e, ctx->err_flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  if (e) {
+    CK(cudaMemsetAsync(ctx->err_flag, 0, sizeof(int), ctx->st));
+    return fail(ctx, MM_ERANGE, "slider displacement left the planned potential box during a step");
+  }
+  return MM_OK;
+}
+
+// One step attempt of size dt; returns the error norm in *err.
+mm_status attempt_step(mm_ctx* ctx, double dt, double* err) {
+  Magnet* M = ctx->mag;
+  if (!ctx->k1_valid) {
+    CKS(run_mech(ctx, mech_params(ctx, 4, 0, dt, false, false)));
+    const float* in[2] = {M[0].m, M[1].m};
+    CKS(evaluate_fields(ctx, in));
+    float* nxt[2] = {M[0].ys[0], M[1].ys[0]};
+    CKS(run_stage(ctx, in, nxt, 1, dt));
+    CKS(run_mech(ctx, mech_params(ctx, 0, 1, dt, true, true)));
+  } else {
+    Launch<CombineJob> L{};
+    L.njobs = 2;
+    int tiles = 0;
+    for (int g = 0; g < 2; ++g) {
+      CombineJob& J = L.job[g];
+      J.y = M[g].m;
+      J.out = M[g].ys[0];
+      J.k[0] = M[g].k[0];
+      J.comb[0] = (float)(dt * DP_A[1][0]);
+      J.nk = 1;
+      J.n = M[g].N;
+      L.tile_start[g] = tiles;
+      tiles += (int)((3 * M[g].N + 255) / 256);
+    }
+    L.tile_start[2] = tiles;
+    {
+      Timer t(ctx, 6);
+      CK(launch_combine(L, ctx->st));
+    }
+    CKS(run_mech(ctx, mech_params(ctx, 2, 1, dt, false, false)));
+  }
+  int cur = 0;
+  for (int i = 2; i <= 7; ++i) {
+    const float* in[2] = {M[0].ys[cur], M[1].ys[cur]};
+    CKS(evaluate_fields(ctx, in));
+    float* nxt[2] = {M[0].ys[1 - cur], M[1].ys[1 - cur]};
+    CKS(run_stage(ctx, in, nxt, i, dt));
+    CKS(run_mech(ctx, mech_params(ctx, 0, i, dt, true, true)));
+    if (i < 7) cur = 1 - cur;
+  }
+  // stages 2..7 alternate the two stage buffers, so the stage-7 input (the
+  // 5th-order solution) always ends in ys[1]
+  (void)cur;
+  CK(cudaMemcpyAsync(&ctx->host_mech, ctx->mech, sizeof(MechState), cudaMemcpyDeviceToHost, ctx->st));
+  CKS(check_device_error(ctx));
+  *err = ctx->host_mech.err;
+  return MM_OK;
+}
+
+}  // namespace
+
+// ============================================================ C ABI
+extern "C" {
+
+void mm_default_options(mm_options* o) {
+  if (!o) return;
+  o->precision = MM_FP32;
+  o->margin = 4;
+  o->adaptive = 1;
+  o->rtol = 1e-5;
+  o->dt_min = 1e-16;
+  o->dt_max = 1e-11;
+  o->stream = nullptr;
+}
+
+const char* mm_status_string(mm_status s) {
+  switch (s) {
+    case MM_OK: return "ok";
+    case MM_EINVAL: return "invalid argument";
+    case MM_ENOMEM: return "out of device memory";
+    case MM_ECUDA: return "CUDA error";
+    case MM_ERANGE: return "displacement outside planned box";
+    case MM_ETIMEOUT: return "timeout";
+    case MM_ESTATE: return "bad state buffer";
+    case MM_ENOTSUP: return "not supported";
+  }
+  return "unknown";
+}
+
+mm_status mm_create(mm_ctx** out, const mm_options* opt) {
+  if (!out) return MM_EINVAL;
+  *out = nullptr;
+  mm_ctx* ctx = new mm_ctx();
+  if (opt) ctx->opt = *opt;
+  else mm_default_options(&ctx->opt);
+  if (ctx->opt.precision != MM_FP32) {
+    delete ctx;
+    return MM_ENOTSUP;
+  }
+  if (ctx->opt.margin < 0 || ctx->opt.margin > 64) {
+    delete ctx;
+    return MM_EINVAL;
+  }
+  ctx->st = (cudaStream_t)ctx->opt.stream;
+  cudaError_t e = cudaMalloc((void**)&ctx->mech, sizeof(MechState));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->err_flag, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(ctx->err_flag, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(ctx->mech, 0, sizeof(MechState));
+  if (e == cudaSuccess) {
+    float taps[kFirHalf + 1];
+    double h[kFirHalf + 1];
+    fir_taps(h);
+    for (int i = 0; i <= kFirHalf; ++i) taps[i] = (float)h[i];
+    e = set_fir_taps(taps);
+  }
+  if (e != cudaSuccess) {
+    mm_destroy(ctx);
+    return e == cudaErrorMemoryAllocation ? MM_ENOMEM : MM_ECUDA;
+  }
+  *out = ctx;
+  return MM_OK;
+}
+
+static void free_dir(Dir& D) {
+  cudaFree(D.Tq); cudaFree(D.YC); cudaFree(D.C); cudaFree(D.partial);
+  D = Dir();
+}
+
+void mm_destroy(mm_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->st) cudaStreamSynchronize(ctx->st);
+  else cudaDeviceSynchronize();
+  for (auto& M : ctx->mag) {
+    cudaFree(M.m);
+    for (auto p : M.ys) cudaFree(p);
+    for (auto p : M.k) cudaFree(p);
+    cudaFree(M.Hself); cudaFree(M.Hstray); cudaFree(M.scratch3); cudaFree(M.err_partial);
+    cudaFree(M.X1); cudaFree(M.YH); cudaFree(M.Nq);
+    free_dir(M.dir);
+    free_dir(M.aux);
+  }
+  for (auto& kv : ctx->ffts) {
+    cudaFree(kv.second.tw_f); cudaFree(kv.second.tw_d); cudaFree(kv.second.pos); cudaFree(kv.second.freq);
+  }
+  cudaFree(ctx->gen_work); cudaFree(ctx->gen_q); cudaFree(ctx->W_dev);
+  cudaFree(ctx->mech); cudaFree(ctx->err_flag);
+  for (auto& p : ctx->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+  for (auto e : ctx->free_events) cudaEventDestroy(e);
+  delete ctx;
+}
+
+const char* mm_last_error(const mm_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+static bool bad_mag(int mag) { return mag != 0 && mag != 1; }
+
+mm_status mm_set_grid(mm_ctx* ctx, int mag, int nx, int ny, int nz, double dx, double dy, double dz,
+                      const long long offset_cells[3]) {
+  if (!ctx) return MM_EINVAL;
+  if (bad_mag(mag) || nx < 1 || ny < 1 || nz < 1 || !(dx > 0) || !(dy > 0) || !(dz > 0) || !offset_cells)
+    return fail(ctx, MM_EINVAL, "mm_set_grid: bad argument");
+  if (nz > kMaxNz) return fail(ctx, MM_ENOTSUP, "mm_set_grid: nz > 4 is not supported by this build");
+  const Magnet& O = ctx->mag[1 - mag];
+  if (O.grid && (O.d[0] != dx || O.d[1] != dy || O.d[2] != dz))
+    return fail(ctx, MM_EINVAL, "mm_set_grid: both magnets must share the cell size");
+  Magnet& M = ctx->mag[mag];
+  if (M.grid && (M.nx != nx || M.ny != ny || M.nz != nz))
+    return fail(ctx, MM_EINVAL, "mm_set_grid: grid size is fixed once set");
+  M.nx = nx; M.ny = ny; M.nz = nz;
+  M.N = (size_t)nx * ny * nz;
+  M.d[0] = dx; M.d[1] = dy; M.d[2] = dz;
+  for (int a = 0; a < 3; ++a) M.off[a] = offset_cells[a];
+  M.grid = true;
+  CKS(alloc_magnet(ctx, M));
+  ctx->planned = false;
+  ctx->k1_valid = false;
+  return MM_OK;
+}
+
+mm_status mm_set_material(mm_ctx* ctx, int mag, double Ms, double Aex, double Ku, const double ku_axis[3],
+                          double alpha) {
+  if (!ctx) return MM_EINVAL;
+  if (bad_mag(mag) || !(Ms > 0) || Aex < 0 || alpha < 0 || !ku_axis)
+    return fail(ctx, MM_EINVAL, "mm_set_material: bad argument");
+  Magnet& M = ctx->mag[mag];
+  M.Ms = Ms; M.Aex = Aex; M.Ku = Ku; M.alpha = alpha;
+  for (int a = 0; a < 3; ++a) M.ku[a] = ku_axis[a];
+  M.mat = true;
+  ctx->planned = false;
+  ctx->k1_valid = false;
+  // spectra carry Ms: force a rebuild of this source's kernels
+  M.Nq_Ms = 0;
+  M.dir.Tq_prefilter = -1;
+  M.aux.Tq_prefilter = -1;
+  return MM_OK;
+}
+
+mm_status mm_set_external_field(mm_ctx* ctx, const double H[3]) {
+  if (!ctx || !H) return MM_EINVAL;
+  for (int a = 0; a < 3; ++a) ctx->Hext[a] = H[a];
+  ctx->k1_valid = false;
+  return MM_OK;
+}
+
+mm_status mm_set_mechanics(mm_ctx* ctx, double mass, double k_spring, double v_drive, double gamma_visc,
+                           const double drive_dir[3], double x0_spring) {
+  if (!ctx || !drive_dir) return MM_EINVAL;
+  const double n = sqrt(drive_dir[0] * drive_dir[0] + drive_dir[1] * drive_dir[1] + drive_dir[2] * drive_dir[2]);
+  if (!(n > 0)) return fail(ctx, MM_EINVAL, "mm_set_mechanics: zero drive direction");
+  ctx->move = mass > 0;
+  ctx->mass = mass; ctx->k_spring = k_spring; ctx->v_drive = v_drive; ctx->gamma_v = gamma_visc;
+  ctx->x0_spring = x0_spring;
+  for (int a = 0; a < 3; ++a) ctx->e[a] = drive_dir[a] / n;
+  ctx->planned = false;
+  ctx->k1_valid = false;
+  return MM_OK;
+}
+
+mm_status mm_set_magnetization(mm_ctx* ctx, int mag, const float* m_dev) {
+  if (!ctx || bad_mag(mag) || !m_dev) return ctx ? fail(ctx, MM_EINVAL, "mm_set_magnetization") : MM_EINVAL;
+  Magnet& M = ctx->mag[mag];
+  if (!M.grid) return fail(ctx, MM_EINVAL, "mm_set_magnetization: grid not set");
+  CK(cudaMemcpyAsync(M.m, m_dev, sizeof(float) * 3 * M.N, cudaMemcpyDeviceToDevice, ctx->st));
+  M.mset = true;
+  ctx->k1_valid = false;
+  return MM_OK;
+}
+
+mm_status mm_get_magnetization(mm_ctx* ctx, int mag, float* m_dev) {
+  if (!ctx || bad_mag(mag) || !m_dev) return ctx ? fail(ctx, MM_EINVAL, "mm_get_magnetization") : MM_EINVAL;
+  Magnet& M = ctx->mag[mag];
+  if (!M.grid) return fail(ctx, MM_EINVAL, "mm_get_magnetization: grid not set");
+  CK(cudaMemcpyAsync(m_dev, M.m, sizeof(float) * 3 * M.N, cudaMemcpyDeviceToDevice, ctx->st));
+  return MM_OK;
+}
+
+mm_status mm_upload_magnetization(mm_ctx* ctx, int mag, const float* m_host) {
+  if (!ctx || bad_mag(mag) || !m_host) return ctx ? fail(ctx, MM_EINVAL, "mm_upload_magnetization") : MM_EINVAL;
+  Magnet& M = ctx->mag[mag];
+  if (!M.grid) return fail(ctx, MM_EINVAL, "mm_upload_magnetization: grid not set");
+  CK(cudaMemcpyAsync(M.m, m_host, sizeof(float) * 3 * M.N, cudaMemcpyHostToDevice, ctx->st));
+  M.mset = true;
+  ctx->k1_valid = false;
+  return MM_OK;
+}
+
+mm_status mm_download_magnetization(mm_ctx* ctx, int mag, float* m_host) {
+  if (!ctx || bad_mag(mag) || !m_host) return ctx ? fail(ctx, MM_EINVAL, "mm_download_magnetization") : MM_EINVAL;
+  Magnet& M = ctx->mag[mag];
+  if (!M.grid) return fail(ctx, MM_EINVAL, "mm_download_magnetization: grid not set");
+  CK(cudaMemcpyAsync(m_host, M.m, sizeof(float) * 3 * M.N, cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  return MM_OK;
+}
+
+mm_status mm_set_displacement(mm_ctx* ctx, const double u_m[3]) {
+  if (!ctx || !u_m) return MM_EINVAL;
+  for (int a = 0; a < 3; ++a) {
+    if (!isfinite(u_m[a])) return fail(ctx, MM_EINVAL, "mm_set_displacement: non-finite");
+    ctx->u_base[a] = u_m[a];
+  }
+  ctx->host_mech.x = 0.0;
+  ctx->k1_valid = false;
+  if (ctx->planned) CKS(replan_if_needed(ctx));
+  return MM_OK;
+}
+
+mm_status mm_set_slider_state(mm_ctx* ctx, double x, double v, double t) {
+  if (!ctx) return MM_EINVAL;
+  ctx->host_mech.x = x; ctx->host_mech.v = v; ctx->host_mech.t = t;
+  ctx->k1_valid = false;
+  if (ctx->planned) CKS(replan_if_needed(ctx));
+  return MM_OK;
+}
+
+mm_status mm_get_slider_state(mm_ctx* ctx, double* x, double* v, double* t) {
+  if (!ctx) return MM_EINVAL;
+  if (x) *x = ctx->host_mech.x;
+  if (v) *v = ctx->host_mech.v;
+  if (t) *t = ctx->host_mech.t;
+  return MM_OK;
+}
+
+static mm_status prepare(mm_ctx* ctx) {
+  if (!ctx->mag[0].mset || !ctx->mag[1].mset) return fail(ctx, MM_EINVAL, "magnetisation not set");
+  CKS(replan_if_needed(ctx));
+  // while a first-same-as-last k1 is held the device slider state is the
+  // authoritative one; any set_* call clears k1_valid and re-uploads
+  if (!ctx->k1_valid) CKS(upload_mech(ctx));
+  return MM_OK;
+}
+
+mm_status mm_compute_fields(mm_ctx* ctx) {
+  if (!ctx) return MM_EINVAL;
+  CKS(prepare(ctx));
+  const float* in[2] = {ctx->mag[0].m, ctx->mag[1].m};
+  CKS(evaluate_fields(ctx, in));
+  CKS(run_mech(ctx, mech_params(ctx, 1, 0, 0.0, true, true)));
+  return MM_OK;
+}
+
+mm_status mm_compute_stray_field(mm_ctx* ctx, int src, float* H_dev) {
+  if (!ctx || bad_mag(src)) return ctx ? fail(ctx, MM_EINVAL, "mm_compute_stray_field") : MM_EINVAL;
+  CKS(prepare(ctx));
+  const float* in[2] = {ctx->mag[0].m, ctx->mag[1].m};
+  const int which[1] = {src};
+  const int what[1] = {2};
+  Dir* dirs[1] = {&ctx->mag[src].dir};
+  CKS(run_source_passes(ctx, in, which, 1, what, dirs));
+  float* H[1] = {H_dev ? H_dev : ctx->mag[1 - src].Hstray};
+  CKS(run_gathers(ctx, in, which, 1, H));
+  CKS(run_mech(ctx, mech_params(ctx, 1, 0, 0.0, src == 0, src == 1)));
+  return MM_OK;
+}
+
+mm_status mm_compute_demag(mm_ctx* ctx, int mag, float* H_dev) {
+  if (!ctx || bad_mag(mag)) return ctx ? fail(ctx, MM_EINVAL, "mm_compute_demag") : MM_EINVAL;
+  CKS(prepare(ctx));
+  const float* in[2] = {ctx->mag[0].m, ctx->mag[1].m};
+  const int which[1] = {mag};
+  const int what[1] = {1};
+  Dir* dirs[1] = {&ctx->mag[mag].dir};
+  CKS(run_source_passes(ctx, in, which, 1, what, dirs));
+  if (H_dev)
+    CK(cudaMemcpyAsync(H_dev, ctx->mag[mag].Hself, sizeof(float) * 3 * ctx->mag[mag].N,
+                       cudaMemcpyDeviceToDevice, ctx->st));
+  return MM_OK;
+}
+
+mm_status mm_compute_potential(mm_ctx* ctx, int src, int prefiltered, float* out_dev, size_t capacity,
+                               int dims[3], long long lo[3]) {
+  if (!ctx || bad_mag(src)) return ctx ? fail(ctx, MM_EINVAL, "mm_compute_potential") : MM_EINVAL;
+  if (!ctx->mag[0].grid || !ctx->mag[1].grid) return fail(ctx, MM_EINVAL, "grids not set");
+  if (!ctx->mag[0].mat || !ctx->mag[1].mat) return fail(ctx, MM_EINVAL, "materials not set");
+  CKS(replan_if_needed(ctx));
+  Magnet& S = ctx->mag[src];
+  Dir& D = S.aux;
+  dir_geometry(ctx, src, true, &D);
+  D.prefilter = prefiltered ? 1 : 0;
+  if (dims)
+    for (int a = 0; a < 3; ++a) dims[a] = D.box_len[a];
+  if (lo)
+    for (int a = 0; a < 3; ++a) lo[a] = D.box_lo[a];
+  if (!out_dev) return MM_OK;
+  const size_t need = (size_t)D.box_len[0] * D.box_len[1] * D.box_len[2];
+  if (capacity < need) return fail(ctx, MM_EINVAL, "mm_compute_potential: output too small");
+  if (!S.mset) return fail(ctx, MM_EINVAL, "magnetisation not set");
+  if ((size_t)std::max(3 * S.nz, D.r[2]) * S.Qy * sizeof(float2) > 220 * 1024)
+    return fail(ctx, MM_ENOTSUP, "box too tall for the fused y pass");
+  CKS(build_T(ctx, src, &D));
+  CKS(ensure_buf(ctx, &D.YC, &D.YC_bytes, sizeof(float2) * (size_t)D.r[2] * S.kxh * D.r[1]));
+  const float* in[2] = {ctx->mag[0].m, ctx->mag[1].m};
+  const int which[1] = {src};
+  const int what[1] = {2};
+  float* saveC = D.C;
+  D.C = out_dev;  // x pass writes the box straight into the caller's buffer
+  Dir* dirs[1] = {&D};
+  mm_status s = run_source_passes(ctx, in, which, 1, what, dirs);
+  D.C = saveC;
+  D.valid = true;
+  return s;
+}
+
+mm_status mm_get_force(mm_ctx* ctx, int on_mag, double F_out[3], double* E_int_out) {
+  if (!ctx || bad_mag(on_mag)) return ctx ? fail(ctx, MM_EINVAL, "mm_get_force") : MM_EINVAL;
+  CK(cudaMemcpyAsync(&ctx->host_mech, ctx->mech, sizeof(MechState), cudaMemcpyDeviceToHost, ctx->st));
+  CKS(check_device_error(ctx));
+  const MechState& H = ctx->host_mech;
+  for (int a = 0; a < 3; ++a)
+    if (F_out) F_out[a] = on_mag == 1 ? H.F_slider[a] : H.F_base[a];
+  if (E_int_out) *E_int_out = on_mag == 1 ? H.E_slider : H.E_base;
+  return MM_OK;
+}
+
+mm_status mm_compute_torque(mm_ctx* ctx, int mag, float* dmdt_dev, float* Heff_dev) {
+  if (!ctx || bad_mag(mag)) return ctx ? fail(ctx, MM_EINVAL, "mm_compute_torque") : MM_EINVAL;
+  CKS(mm_compute_fields(ctx));
+  Magnet& M = ctx->mag[mag];
+  float* kp[7];
+  for (int i = 0; i < 7; ++i) kp[i] = M.k[i];
+  kp[0] = dmdt_dev ? dmdt_dev : M.scratch3;
+  Launch<StageJob> L{};
+  L.njobs = 1;
+  L.job[0] = stage_job(ctx, mag, M.m, nullptr, 1, 1, 0.0, kp, Heff_dev);
+  L.tile_start[0] = 0;
+  L.tile_start[1] = M.nerr;
+  {
+    Timer t(ctx, 4);
+    CK(launch_stage(L, ctx->st));
+  }
+  ctx->k1_valid = false;
+  return MM_OK;
+}
+
+mm_status mm_step(mm_ctx* ctx, int nsteps, double* t_out, double* dt_inout) {
+  if (!ctx || !dt_inout || nsteps < 0) return ctx ? fail(ctx, MM_EINVAL, "mm_step") : MM_EINVAL;
+  if (!(*dt_inout > 0)) return fail(ctx, MM_EINVAL, "mm_step: dt must be positive");
+  CKS(prepare(ctx));
+  double dt = *dt_inout;
+  int done = 0;
+  int guard_iter = 0;
+  while (done < nsteps) {
+    if (++guard_iter > 100 * (nsteps + 1) + 1000)
+      return fail(ctx, MM_EINVAL, "mm_step: step size control did not converge");
+    double err = 0.0;
+    CKS(attempt_step(ctx, dt, &err));
+    // after attempt_step the 5th-order solution is in ys[1] (stages 2..7 alternate 0,1,0,1,0,1)
+    const bool accept = !ctx->opt.adaptive || err <= ctx->opt.rtol || dt <= ctx->opt.dt_min;
+    double fac = 5.0;
+    if (err > 0.0) fac = std::min(5.0, std::max(0.2, 0.9 * pow(ctx->opt.rtol / err, 0.2)));
+    if (accept) {
+      Launch<CombineJob> L{};
+      L.njobs = 2;
+      int tiles = 0;
+      for (int g = 0; g < 2; ++g) {
+        CombineJob& J = L.job[g];
+        J.y = ctx->mag[g].ys[1];
+        J.out = ctx->mag[g].m;
+        J.n = ctx->mag[g].N;
+        L.tile_start[g] = tiles;
+        tiles += (int)((ctx->mag[g].N + 255) / 256);
+      }
+      L.tile_start[2] = tiles;
+      {
+        Timer t(ctx, 6);
+        CK(launch_normalise(L, ctx->st));
+      }
+      for (int g = 0; g < 2; ++g) std::swap(ctx->mag[g].k[0], ctx->mag[g].k[6]);
+      CKS(run_mech(ctx, mech_params(ctx, 3, 7, dt, false, false)));
+      ctx->host_mech.x = ctx->host_mech.xs;
+      ctx->host_mech.v = ctx->host_mech.vs;
+      ctx->host_mech.t = ctx->host_mech.t + dt;
+      ctx->host_mech.kx[0] = ctx->host_mech.kx[6];
+      ctx->host_mech.kv[0] = ctx->host_mech.kv[6];
+      ctx->k1_valid = true;
+      ctx->accepted++;
+      ++done;
+      // a whole-cell move beyond the guard needs new boxes (and a fresh k1)
+      bool moved = false;
+      for (int s = 0; s < 2 && !moved; ++s)
+        for (int a = 0; a < 3; ++a) {
+          const double sigma = s == 0 ? 1.0 : -1.0;
+          if ((int)floor(sigma * u_cells(ctx, a, ctx->host_mech.x)) != ctx->mag[s].dir.U0[a]) moved = true;
+        }
+      if (moved) {
+        CKS(ensure_plan(ctx));
+        CKS(upload_mech(ctx));
+        ctx->k1_valid = false;
+      }
+    } else {
+      ctx->rejected++;
+    }
+    if (ctx->opt.adaptive) dt = std::min(std::max(dt * fac, ctx->opt.dt_min), ctx->opt.dt_max);
+  }
+  *dt_inout = dt;
+  if (t_out) *t_out = ctx->host_mech.t;
+  return MM_OK;
+}
+
+mm_status mm_get_step_stats(mm_ctx* ctx, long long* accepted, long long* rejected) {
+  if (!ctx) return MM_EINVAL;
+  if (accepted) *accepted = ctx->accepted;
+  if (rejected) *rejected = ctx->rejected;
+  return MM_OK;
+}
+
+struct StateHeader {
+  unsigned magic, version;
+  unsigned long long n0, n1;
+  double x, v, t, u_base[3];
+};
+
+mm_status mm_get_state(mm_ctx* ctx, void* buf, size_t* bytes) {
+  if (!ctx || !bytes) return MM_EINVAL;
+  const size_t need = sizeof(StateHeader) + sizeof(float) * 3 * (ctx->mag[0].N + ctx->mag[1].N);
+  if (!buf) {
+    *bytes = need;
+    return MM_OK;
+  }
+  if (*bytes < need) return fail(ctx, MM_ESTATE, "mm_get_state: buffer too small");
+  StateHeader h{0x4d4d5354u, 1u, ctx->mag[0].N, ctx->mag[1].N, ctx->host_mech.x, ctx->host_mech.v,
+                ctx->host_mech.t, {ctx->u_base[0], ctx->u_base[1], ctx->u_base[2]}};
+  memcpy(buf, &h, sizeof(h));
+  char* p = (char*)buf + sizeof(h);
+  for (int g = 0; g < 2; ++g) {
+    if (ctx->mag[g].N) CK(cudaMemcpyAsync(p, ctx->mag[g].m, sizeof(float) * 3 * ctx->mag[g].N,
+                                          cudaMemcpyDeviceToHost, ctx->st));
+    p += sizeof(float) * 3 * ctx->mag[g].N;
+  }
+  CK(cudaStreamSynchronize(ctx->st));
+  *bytes = need;
+  return MM_OK;
+}
+
+mm_status mm_set_state(mm_ctx* ctx, const void* buf, size_t bytes) {
+  if (!ctx || !buf) return MM_EINVAL;
+  if (bytes < sizeof(StateHeader)) return fail(ctx, MM_ESTATE, "mm_set_state: short buffer");
+  StateHeader h;
+  memcpy(&h, buf, sizeof(h));
+  if (h.magic != 0x4d4d5354u || h.version != 1u || h.n0 != ctx->mag[0].N || h.n1 != ctx->mag[1].N)
+    return fail(ctx, MM_ESTATE, "mm_set_state: header does not match this context");
+  const size_t need = sizeof(StateHeader) + sizeof(float) * 3 * (h.n0 + h.n1);
+  if (bytes < need) return fail(ctx, MM_ESTATE, "mm_set_state: short buffer");
+  const char* p = (const char*)buf + sizeof(h);
+  for (int g = 0; g < 2; ++g) {
+    CK(cudaMemcpyAsync(ctx->mag[g].m, p, sizeof(float) * 3 * ctx->mag[g].N, cudaMemcpyHostToDevice, ctx->st));
+    p += sizeof(float) * 3 * ctx->mag[g].N;
+    ctx->mag[g].mset = true;
+  }
+  CK(cudaStreamSynchronize(ctx->st));
+  for (int a = 0; a < 3; ++a) ctx->u_base[a] = h.u_base[a];
+  ctx->host_mech.x = h.x; ctx->host_mech.v = h.v; ctx->host_mech.t = h.t;
+  ctx->k1_valid = false;
+  if (ctx->planned) CKS(replan_if_needed(ctx));
+  return MM_OK;
+}
+
+mm_status mm_eval_kernel_fp64(int kind, int n, const double* offsets_dev, double dx, double dy, double dz,
+                              double* out_dev) {
+  if ((kind != 0 && kind != 1) || n < 0 || !offsets_dev || !out_dev || !(dx > 0) || !(dy > 0) || !(dz > 0))
+    return MM_EINVAL;
+  cudaError_t e = eval_points_fp64(kind, n, offsets_dev, dx, dy, dz, out_dev, nullptr);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  return e == cudaSuccess ? MM_OK : MM_ECUDA;
+}
+
+mm_status mm_get_plan_info(mm_ctx* ctx, int src, int fft_dims[2], int box_dims[3], long long box_lo[3],
+                           int coef_dims[3]) {
+  if (!ctx || bad_mag(src)) return MM_EINVAL;
+  if (!ctx->planned) CKS(ensure_plan(ctx));
+  const Magnet& S = ctx->mag[src];
+  if (fft_dims) { fft_dims[0] = S.Qx; fft_dims[1] = S.Qy; }
+  for (int a = 0; a < 3; ++a) {
+    if (box_dims) box_dims[a] = S.dir.box_len[a];
+    if (box_lo) box_lo[a] = S.dir.box_lo[a];
+    if (coef_dims) coef_dims[a] = S.dir.r[a];
+  }
+  return MM_OK;
+}
+
+mm_status mm_set_timing(mm_ctx* ctx, int on) {
+  if (!ctx) return MM_EINVAL;
+  ctx->timing = on != 0;
+  return MM_OK;
+}
+
+mm_status mm_get_timing(mm_ctx* ctx, int cls, double* total_ms, long long* launches) {
+  if (!ctx || cls < 0 || cls >= kTimingClasses) return MM_EINVAL;
+  drain_timing(ctx);
+  if (total_ms) *total_ms = ctx->t_ms[cls];
+  if (launches) *launches = ctx->t_n[cls];
+  return MM_OK;
+}
+
+mm_status mm_reset_timing(mm_ctx* ctx) {
+  if (!ctx) return MM_EINVAL;
+  drain_timing(ctx);
+  for (int i = 0; i < kTimingClasses; ++i) { ctx->t_ms[i] = 0; ctx->t_n[i] = 0; }
+  return MM_OK;
+}
+
+long long mm_launch_count(const mm_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+}  // extern "C"

@@ -1,0 +1,186 @@
+// Internal types shared by the CUDA translation units of libmm.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mm {
+
+constexpr int kMaxStages = 16;
+constexpr int kMaxJobs = 4;        // jobs per launch (two magnets / two directions)
+constexpr int kFirHalf = 14;       // B-spline prefilter FIR half-width, |z1|^15 ~ 2.6e-9
+constexpr int kMaxNz = 4;          // thin-film path: z handled by direct plane mixing
+constexpr int kMaxOut = kMaxNz + 5; // coefficient planes: nz + 3 + 2 guard
+constexpr int kRowsPerCta = 8;     // real rows per CTA in the x passes (4 complex lines)
+
+struct FftPlanDev {
+  int L;
+  int nstages;
+  int radix[kMaxStages];
+  int blocklen[kMaxStages];
+};
+
+// Length-L transform resources resident on the device.
+struct FftTables {
+  FftPlanDev plan;
+  const float2* tw_f;     // exp(-2 pi i t / L), t < L
+  const double2* tw_d;
+  const int* pos;         // frequency k -> position in DIF output
+  const int* freq;        // position -> frequency
+};
+
+// ---------------------------------------------------------------- x forward
+struct XFwdJob {
+  const float* m;         // [3][nz][ny][nx]
+  float2* out;            // [3 nz][kxh][ny]
+  int nx, ny, nz;
+  int kxh;
+  FftTables fx;
+};
+
+// ---------------------------------------------------------------- y pass
+struct YJob {
+  const float2* in;       // [3 nz][kxh][ny]
+  int nz, ny, kxh;
+  FftTables fy;
+  int kyq;                // Qy/2 + 1 stored ky values of the kernel spectra
+  // self-demag output
+  int do_H;
+  const float* Nq;        // [6][nz][kxh][kyq]  (xx yy zz xy xz yz; dz >= 0)
+  float2* outH;           // [3 nz][kxh][ny]
+  // potential / coefficient output
+  int do_C;
+  int n_out;
+  const float* Tq;        // [n_out][nz][3][kxh][kyq]
+  float2* outC;           // [n_out][kxh][r]
+  int box_lo, box_len, start, r, fir;
+};
+
+// ---------------------------------------------------------------- x inverse
+struct XInvJob {
+  const float2* in;       // [planes][kxh][rows_per_plane]
+  float* out;             // [planes][rows_per_plane][out_len]
+  int planes, rows_per_plane, kxh;
+  FftTables fx;
+  // output window along x: circular index (box_lo + j) mod Q for box-local j
+  int box_lo, box_len, start, out_len, fir;
+};
+
+// ---------------------------------------------------------------- gather
+struct GatherJob {
+  const float* C;         // coefficients [rz][ry][rx]
+  int rx, ry, rz;
+  int nx, ny, nz;         // target grid
+  const double* u;        // slider displacement, lattice cells (device)
+  double sigma;           // +1 target is the slider, -1 source is the slider
+  int U0[3];              // floor(sigma u) when the box was planned
+  int guard[3];           // extra coefficient nodes kept on each side
+  float inv_d[3];         // 1 / cell size (1/m)
+  const float* m;         // target unit magnetisation [3][N]
+  float* H;               // stray field out [3][N] (A/m), may be null
+  double* partial;        // [tiles][4]: sum m.Hess (3), sum m.grad
+  int* err;               // set to 1 when the displacement leaves the box
+};
+
+// ---------------------------------------------------------------- LLG / RK
+struct StageJob {
+  const float* ys;        // stage input m [3][N]
+  const float* y;         // accepted state [3][N]
+  float* ys_next;         // next stage input
+  float* k[7];            // stage derivatives
+  const float* Hself;
+  const float* Hstray;
+  float* Heff;            // optional effective field out
+  int nx, ny, nz;
+  float ex[3];            // 2 A / (mu0 Ms d_a^2)
+  float an;               // 2 Ku / (mu0 Ms)
+  float ku[3];            // unit easy axis
+  float hext[3];
+  float pref;             // -gamma0 / (1 + alpha^2)
+  float alpha;
+  int stage;              // 1..7
+  int mode;               // 0 RK stage, 1 right-hand side only
+  float comb[7];          // dt a_{stage+1, j}
+  float ecoef[7];         // dt (b5_j - b4_j)
+  float* err_partial;     // per-CTA max |error| (stage 7)
+};
+
+struct CombineJob {
+  const float* y;
+  float* out;
+  const float* k[7];
+  float comb[7];
+  int nk;
+  size_t n;               // cells
+};
+
+struct MechState {
+  double x, v, t;         // accepted slider position (m), velocity, time
+  double xs, vs, ts;      // current stage values
+  double kx[7], kv[7];
+  double u[3];            // displacement (lattice cells) seen by the gathers
+  double F_slider[3], E_slider, F_base[3], E_base;
+  double err;
+};
+
+struct MechParams {
+  MechState* state;
+  const double* partial[2];   // gather partials: [0] base -> slider, [1] slider -> base
+  int ntiles[2];
+  double Fscale[2], Escale[2];
+  const float* err_partial[2];
+  int nerr[2];
+  int mode;               // 0 RK stage, 1 forces only, 2 stage-2 input from k1, 3 accept, 4 restart
+  int stage;
+  double dt;
+  double a[7];            // a_{stage+1, j}
+  double c_next;
+  int move;               // slider equation of motion active
+  double mass, k_spring, v_drive, x0_spring, gamma_v;
+  double e[3], inv_d[3], u_base[3];
+};
+
+template <typename J> struct Launch {
+  int njobs;
+  int tile_start[kMaxJobs + 1];
+  J job[kMaxJobs];
+};
+
+__device__ __forceinline__ int find_job(const int* tile_start, int njobs, int tile) {
+  int j = 0;
+  while (j + 1 < njobs && tile >= tile_start[j + 1]) ++j;
+  return j;
+}
+
+}  // namespace mm
+
+// ---------------------------------------------------------------- host entry points
+namespace mm {
+
+struct KernelPlan {
+  int Qx, Qy;             // circular grid
+  int Wx, Wy;             // kernel window |d| <= W (cells)
+  int nz;                 // source layers
+};
+
+cudaError_t set_fir_taps(const float* taps);
+cudaError_t launch_xfwd(const Launch<XFwdJob>& L, int Qmax, cudaStream_t st);
+cudaError_t launch_ypass(const Launch<YJob>& L, size_t smem, cudaStream_t st);
+cudaError_t launch_xinv(const Launch<XInvJob>& L, int Qmax, cudaStream_t st);
+int gather_tiles(int nx, int ny);
+size_t gather_smem(int nz);
+cudaError_t launch_gather(const Launch<GatherJob>& L, int nz_max, cudaStream_t st);
+cudaError_t launch_stage(const Launch<StageJob>& L, cudaStream_t st);
+cudaError_t launch_combine(const Launch<CombineJob>& L, cudaStream_t st);
+cudaError_t launch_normalise(const Launch<CombineJob>& L, cudaStream_t st);
+cudaError_t launch_mech(const MechParams& P, cudaStream_t st);
+cudaError_t eval_points_fp64(int kind, int n, const double* off_dev, double a, double b, double c,
+                             double* out_dev, cudaStream_t st);
+cudaError_t build_N_spectra(const KernelPlan& K, const FftTables& fx, const FftTables& fy, double a,
+                            double b, double c, double scale, float* Nq, double2* work, double* qbuf,
+                            cudaStream_t st);
+cudaError_t build_T_spectra(const KernelPlan& K, const FftTables& fx, const FftTables& fy, double a,
+                            double b, double c, double scale, int box_lo_z, int bz, int n_out,
+                            const double* W_dev, float* Tq, double2* work, double* Sq,
+                            cudaStream_t st);
+
+}  // namespace mm

@@ -1,0 +1,46 @@
+"""Shared set-up of a film pair on the CUDA path and on the CPU oracle (tests only)."""
+
+import numpy as np
+
+MU0 = 4e-7 * np.pi
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def gpu_pair(fp, m0, m1, margin=4, adaptive=False, rtol=1e-5, mech=True):
+    """MovingMagnets context for a workloads.FilmPair with the given unit m arrays."""
+    import torch
+    from paper_1801_04181_gb300 import MovingMagnets
+
+    mm = MovingMagnets(margin=margin, adaptive=adaptive, rtol=rtol)
+    for g, (n, mat, m) in enumerate(((fp.n_base, fp.mat_base, m0), (fp.n_slider, fp.mat_slider, m1))):
+        mm.set_grid(g, n, fp.cell, fp.offsets[g])
+        mm.set_material(g, mat.Ms, mat.Aex, mat.Ku, mat.ku_axis, mat.alpha)
+        mm.set_magnetization(g, torch.as_tensor(np.ascontiguousarray(m), dtype=torch.float32,
+                                                device="cuda"))
+    mm.set_external_field(fp.H_ext)
+    if mech:
+        me = fp.mech
+        mm.set_mechanics(me.mass, me.k, me.v_drive, me.gamma_v, me.dir, me.x0_spring)
+    mm.set_displacement(tuple(u * c for u, c in zip(fp.u0, fp.cell)))
+    return mm
+
+
+def oracle_system(fp):
+    from oracle.dynamics import System
+
+    return System([fp.n_base, fp.n_slider], fp.cell, fp.offsets,
+                  [fp.mat_base.as_dict(), fp.mat_slider.as_dict()], fp.mech.as_dict(), u0=fp.u0,
+                  H_ext=fp.H_ext)
+
+
+def force_scale(hess_n, M_t, cell):
+    """mu0 V sum_i |M_i| ||Hess_i||: the size of the terms that cancel in Eq. (EQForce)."""
+    d = np.asarray(cell, float)
+    hess = hess_n / d[:, None] / d[None, :]
+    Mt = np.moveaxis(M_t, 0, -1)
+    return MU0 * d.prod() * np.sum(np.linalg.norm(Mt, axis=-1) * np.linalg.norm(hess, axis=(-2, -1)))

@@ -1,0 +1,245 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerance: relative L2 error <= 1e-5 per field for the FP32 path; forces are
+compared against the size of the terms that cancel in Eq. (EQForce)
+(|F - F_ref| <= 1e-5 mu0 V sum |M| ||Hess||), energies relative.  Sizes span
+several CTA tiles and ragged edges (odd extents, nz = 1..4, partial 32 x 8
+gather tiles).
+"""
+
+import numpy as np
+import pytest
+
+import workloads
+from oracle import fields as OF
+from oracle import kernels as OK
+from oracle.interaction import stray_interaction
+from tests.pair_setup import force_scale, gpu_pair, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+def _pair(n0, n1, gap, seed, u_cells, Ms=8e5, lateral=(0, 0)):
+    fp, _, _ = workloads.film_pair_plain(n=n0, gap=gap, seed=seed)
+    fp.n_slider = n1
+    fp.u0 = u_cells
+    fp.lateral = lateral
+    m0 = workloads.random_unit(n0, seed)
+    m1 = workloads.random_unit(n1, seed + 7)
+    fp.mat_base.Ms = Ms
+    return fp, m0, m1, fp.offsets
+
+
+def _gpu(fp, m0, m1, offsets, **kw):
+    assert list(offsets) == list(fp.offsets)
+    return gpu_pair(fp, m0, m1, mech=False, **kw)
+
+
+def test_kernel_values_fp64_match_oracle():
+    from paper_1801_04181_gb300 import eval_kernel_fp64
+
+    cell = (4e-9, 3e-9, 2e-9)
+    rng = np.random.default_rng(0)
+    idx = np.concatenate([rng.integers(-6, 7, size=(40, 3)), rng.integers(-60, 61, size=(40, 3)),
+                          [[0, 0, 0], [1, 0, 0], [16, 3, 1], [17, 3, 1], [0, 0, 16], [0, 0, 17]]])
+    off = idx * np.array(cell)
+    S = eval_kernel_fp64(0, off, cell).cpu().numpy()
+    N = eval_kernel_fp64(1, off, cell).cpu().numpy()
+    S_ref = OK.S_kernel(off[:, 0], off[:, 1], off[:, 2], *cell)
+    N_ref = OK.N_kernel(off[:, 0], off[:, 1], off[:, 2], *cell)
+    for got, ref in ((S, S_ref), (N, N_ref)):
+        scale = np.abs(ref).max(axis=1, keepdims=True) + 1e-300
+        # the closed forms cancel ~1e6 at 16 cells: FP64 rounding order differs
+        assert np.max(np.abs(got - ref) / scale) < 1e-8
+
+
+@pytest.mark.parametrize("n0,n1,gap,u", [
+    ((40, 24, 1), (40, 24, 1), 1, (0.3125, 0.0, 0.0)),
+    ((37, 21, 2), (29, 26, 3), 2, (0.71, 0.45, 0.0)),
+    ((33, 17, 4), (33, 17, 1), 3, (1.6, -0.2, 0.3)),
+])
+def test_potential_box_matches_oracle(n0, n1, gap, u):
+    fp, m0, m1, offs = _pair(n0, n1, gap, 11, u)
+    mm = _gpu(fp, m0, m1, offs)
+    for src in (0, 1):
+        t = 1 - src
+        phi, lo = mm.compute_potential(src, prefiltered=False)
+        coef, lo2 = mm.compute_potential(src, prefiltered=True)
+        n_t = (fp.n_slider if t == 1 else fp.n_base)
+        box_lo, box_dims = OF.box_for_target(n_t, offs[t], offs[src], u, t == 1)
+        assert tuple(lo) == tuple(box_lo) and tuple(lo2) == tuple(box_lo)
+        assert tuple(phi.shape) == tuple(reversed(box_dims))
+        Ms = fp.mat_base.Ms if src == 0 else fp.mat_slider.Ms
+        m_s = m0 if src == 0 else m1
+        ref = OF.potential_conv(Ms * m_s, fp.cell, box_lo, box_dims)
+        assert rel_l2(phi.double().cpu().numpy(), ref) < TOL
+        from oracle.spline import prefilter_3d
+        assert rel_l2(coef.double().cpu().numpy(), prefilter_3d(ref)) < TOL
+    mm.close()
+
+
+@pytest.mark.parametrize("n0,n1,gap,u", [
+    ((40, 24, 1), (40, 24, 1), 1, (0.3125, 0.0, 0.0)),
+    ((37, 21, 2), (29, 26, 3), 2, (0.71, 0.45, 0.0)),
+    ((70, 19, 4), (45, 33, 2), 3, (2.6, -1.2, 0.3)),
+    ((64, 64, 1), (64, 64, 1), 1, (0.0, 0.0, 0.0)),
+])
+@pytest.mark.parametrize("lateral", [(0, 0), (9, -5)])
+def test_stray_field_force_energy_match_oracle(n0, n1, gap, u, lateral):
+    fp, m0, m1, offs = _pair(n0, n1, gap, 5, u, lateral=lateral)
+    mm = _gpu(fp, m0, m1, offs)
+    for src in (0, 1):
+        t = 1 - src
+        Hg = mm.compute_stray_field(src).double().cpu().numpy()
+        F, E = mm.get_force(t)
+        Ms_s = fp.mat_base.Ms if src == 0 else fp.mat_slider.Ms
+        Ms_t = fp.mat_slider.Ms if t == 1 else fp.mat_base.Ms
+        M_s = Ms_s * (m0 if src == 0 else m1)
+        M_t = Ms_t * (m1 if t == 1 else m0)
+        ref = stray_interaction(M_s, M_t, fp.cell, offs[src], offs[t], u, t == 1, return_box=True)
+        assert rel_l2(Hg, ref["H"]) < TOL
+        scale = force_scale(ref["hess_n"], M_t, fp.cell)
+        assert np.max(np.abs(np.array(F) - ref["F"])) < TOL * scale
+        assert abs(E - ref["E"]) < TOL * abs(ref["E"]) + 1e-6 * scale * fp.cell[0]
+    mm.close()
+
+
+@pytest.mark.parametrize("n", [(40, 24, 1), (37, 21, 2), (33, 17, 3), (19, 31, 4)])
+def test_demag_matches_oracle(n):
+    fp, m0, m1, offs = _pair(n, n, 2, 21, (0.0, 0.0, 0.0))
+    mm = _gpu(fp, m0, m1, offs)
+    for g, m in ((0, m0), (1, m1)):
+        H = mm.compute_demag(g).double().cpu().numpy()
+        ref = OF.demag_conv(fp.mat_base.Ms * m, fp.cell)
+        assert rel_l2(H, ref) < TOL
+    mm.close()
+
+
+def test_whole_cell_displacement_is_index_shift_bitwise():
+    fp, m0, m1, offs = _pair((36, 20, 2), (36, 20, 2), 2, 31, (1.0, 0.0, 0.0))
+    mm = _gpu(fp, m0, m1, offs)
+    H_a = mm.compute_stray_field(0).cpu().numpy()
+    F_a, _ = mm.get_force(1)
+    mm.close()
+    fp.lateral = (1, 0)
+    fp.u0 = (0.0, 0.0, 0.0)
+    mm = _gpu(fp, m0, m1, fp.offsets)
+    H_b = mm.compute_stray_field(0).cpu().numpy()
+    F_b, _ = mm.get_force(1)
+    mm.close()
+    assert np.array_equal(H_a, H_b)
+    assert F_a == F_b
+
+
+def test_offset_sweep_plain_films():
+    """64x64x1 films, gap 1 cell, 16 offsets in [0, 1): field and x-force per offset."""
+    fp, m0, m1 = workloads.film_pair_plain(n=(64, 64, 1), gap=1, seed=0)
+    mm = gpu_pair(fp, m0, m1, mech=False)
+    M0 = fp.mat_base.Ms * m0
+    M1 = fp.mat_slider.Ms * m1
+    cache = {}
+    for k in range(16):
+        u = (k / 16.0, 0.0, 0.0)
+        mm.set_displacement(tuple(v * c for v, c in zip(u, fp.cell)))
+        mm.compute_fields()
+        F, E = mm.get_force(1)
+        Hg = mm.compute_stray_field(0).double().cpu().numpy()
+        ref = stray_interaction(M0, M1, fp.cell, fp.offsets[0], fp.offsets[1], u, True,
+                                kernel_cache=cache, return_box=True)
+        assert rel_l2(Hg, ref["H"]) < TOL
+        scale = force_scale(ref["hess_n"], M1, fp.cell)
+        assert abs(F[0] - ref["F"][0]) < TOL * scale
+    mm.close()
+
+
+def test_torque_matches_oracle():
+    fp, m0, m1 = workloads.film_pair_stick_slip(n=(48, 20, 2), gap=5, seed=2)
+    fp.u0 = (0.4, 0.0, 0.0)
+    fp.H_ext = (1e4, -2e4, 5e4)
+    mm = gpu_pair(fp, m0, m1)
+    from tests.pair_setup import oracle_system
+    from oracle.dynamics import llg_rhs
+
+    sysm = oracle_system(fp)
+    H_ref, _, _ = sysm.fields(m0, m1, 0.0)
+    for g, m in ((0, m0), (1, m1)):
+        dm, H = mm.compute_torque(g)
+        assert rel_l2(H.double().cpu().numpy(), H_ref[g]) < TOL
+        ref = llg_rhs(m, H_ref[g], fp.mat_base.alpha)
+        assert rel_l2(dm.double().cpu().numpy(), ref) < TOL
+    mm.close()
+
+
+def test_fixed_dt_steps_match_oracle():
+    """Five fixed-dt Dormand-Prince steps of spring-pulled PMA films (shrunk)."""
+    fp, m0, m1 = workloads.film_pair_stick_slip(n=(40, 24, 2), gap=5, seed=4)
+    fp.u0 = (0.25, 0.0, 0.0)
+    fp.mech.x0_spring = 2e-9
+    fp.mech.v_drive = 50.0
+    mm = gpu_pair(fp, m0, m1)
+    from tests.pair_setup import oracle_system
+    from oracle import dynamics as D
+
+    sysm = oracle_system(fp)
+    dt = 5e-14
+    t_ref, y = D.run_fixed(sysm, [m0, m1, 0.0, 0.0], dt, 5)
+    t, _ = mm.step(5, dt)
+    x, v, tt = mm.get_slider_state()
+    for g in (0, 1):
+        got = mm.get_magnetization(g).double().cpu().numpy()
+        assert rel_l2(got, y[g]) < TOL
+        # the per-step change is what the stepper computes: compare it too
+        init = m0 if g == 0 else m1
+        assert rel_l2(got - init, y[g] - init) < 1e-3
+    assert abs(tt - t_ref) < 1e-20
+    assert abs(x - y[2]) <= 1e-5 * abs(y[2])
+    assert abs(v - y[3]) <= 1e-5 * abs(y[3])
+    mm.close()
+
+
+def test_checkpoint_resume_is_bitwise():
+    fp, m0, m1 = workloads.film_pair_stick_slip(n=(32, 16, 2), gap=5, seed=8)
+    fp.mech.x0_spring = 1e-9
+    mm = gpu_pair(fp, m0, m1)
+    mm.step(2, 5e-14)
+    blob = mm.get_state()
+    mm.step(3, 5e-14)
+    a = [mm.get_magnetization(g).cpu().numpy() for g in (0, 1)]
+    sa = mm.get_slider_state()
+    mm.set_state(blob)
+    mm.step(3, 5e-14)
+    b = [mm.get_magnetization(g).cpu().numpy() for g in (0, 1)]
+    sb = mm.get_slider_state()
+    assert all(np.array_equal(p, q) for p, q in zip(a, b))
+    assert sa == sb
+    mm.close()
+
+
+def test_adaptive_steps_accept_and_stay_normalised():
+    fp, m0, m1 = workloads.film_pair_stick_slip(n=(48, 24, 2), gap=5, seed=9)
+    mm = gpu_pair(fp, m0, m1, adaptive=True, rtol=1e-5)
+    t, dt = mm.step(10, 1e-14)
+    acc, rej = mm.step_stats()
+    assert acc == 10 and t > 0 and dt > 0
+    for g in (0, 1):
+        m = mm.get_magnetization(g).double().cpu().numpy()
+        assert np.max(np.abs(np.sqrt((m ** 2).sum(axis=0)) - 1)) < 1e-6
+    mm.close()
+
+
+def test_bad_arguments_are_rejected():
+    from paper_1801_04181_gb300 import MMError, MovingMagnets
+
+    mm = MovingMagnets()
+    with pytest.raises(MMError):
+        mm.set_grid(0, (8, 8, 5), (1e-9, 1e-9, 1e-9))   # nz > 4
+    with pytest.raises(MMError):
+        mm.set_grid(2, (8, 8, 1), (1e-9, 1e-9, 1e-9))   # no magnet 2
+    mm.set_grid(0, (8, 8, 1), (1e-9, 1e-9, 1e-9))
+    with pytest.raises(MMError):
+        mm.set_grid(1, (8, 8, 1), (2e-9, 1e-9, 1e-9))   # different cell
+    with pytest.raises(MMError):
+        mm.compute_fields()                             # nothing else set
+    mm.close()

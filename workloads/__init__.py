@@ -95,10 +95,11 @@ class FilmPair:
     mech: Mechanics = field(default_factory=Mechanics)
     u0: tuple = (0.0, 0.0, 0.0)
     H_ext: tuple = (0.0, 0.0, 0.0)
+    lateral: tuple = (0, 0)      # slider lattice offset in x, y (cells)
 
     @property
     def offsets(self):
-        return [(0, 0, 0), (0, 0, self.n_base[2] + self.gap)]
+        return [(0, 0, 0), (self.lateral[0], self.lateral[1], self.n_base[2] + self.gap)]
 
     def cells(self):
         return int(np.prod(self.n_base)) + int(np.prod(self.n_slider))
