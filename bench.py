@@ -1,0 +1,384 @@
+"""Benchmark: stray-field + LLG cell-updates/s of spring-pulled PMA film pairs.
+
+Workload: two PMA films of 1024 x 256 x 2 cells (4 nm), gap 5 cells,
+Ms = 1.1e6 A/m, Aex = 1.5e-11 J/m, Ku = 1e6 J/m^3 along z, alpha = 0.5, seeded
+~20-cell up/down domains, slider on a spring k = 1e-3 N/m pulled at 1 m/s,
+adaptive Dormand-Prince 5(4) with the displacement updated every stage.
+One bench step = one accepted RK45 step of the whole path (both demag fields,
+both stray fields with prefilter and tricubic gather, forces, LLG stages, slider).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 runs under torch.distributed.run: independent replicas, one per GPU
+(a single film pair does not shard), timing = max over ranks.
+"""
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "stray-field+LLG cell-updates/s, FP32 vs mixed-prec at <=1e-4 rel L2; % HBM roof"
+UNIT = "cell-updates/s"
+WORKLOAD = "stick-slip PMA film pair 1024x256x2 (4 nm), gap 5, spring-pulled, adaptive DP45"
+TIMING_CLASSES = ["fft_x_forward", "fft_y_pass_mix_prefilter", "fft_x_inverse_prefilter",
+                  "spline_gather_force", "llg_stage", "slider_reduce", "combine_normalise"]
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--seed", type=int, default=0)
+    return p.parse_args()
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names[1:], parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ algorithmic bytes
+def algorithmic_bytes(mm, fp):
+    """Bytes each kernel class must move per launch (both magnets), FP32 path."""
+    n = [fp.n_base, fp.n_slider]
+    N = [int(np.prod(x)) for x in n]
+    info = [mm.plan_info(0), mm.plan_info(1)]
+    xf = yp = xi = ga = 0
+    for s in (0, 1):
+        nx, ny, nz = n[s]
+        Qx, Qy = info[s]["fft"]
+        kxh, kyq = Qx // 2 + 1, Qy // 2 + 1
+        rx, ry, rz = info[s]["coef"]
+        t = 1 - s
+        x1 = 3 * nz * kxh * ny * 8
+        yc = rz * kxh * ry * 8
+        coef = rz * ry * rx * 4
+        xf += 3 * N[s] * 4 + x1
+        yp += x1 + 6 * nz * kxh * kyq * 4 + rz * nz * 3 * kxh * kyq * 4 + x1 + yc
+        xi += x1 + yc + 3 * N[s] * 4 + coef
+        ga += coef + 3 * N[t] * 4 + 3 * N[t] * 4
+    # LLG stage i reads ys, y, Hself, Hstray and k_1..k_{i-1}, writes k_i and
+    # (i < 7) the next stage input; stage 7 reads k_1..k_6 for the error norm
+    per_stage = []
+    for i in range(1, 8):
+        arrays = 4 + (i - 1) + 1 + (1 if i < 7 else 0)
+        if i == 7:
+            arrays = 3 + 6 + 1
+        per_stage.append(arrays)
+    st = sum(3 * x * 4 for x in N) * float(np.mean(per_stage[1:]))
+    return {0: xf, 1: yp, 2: xi, 3: ga, 4: st}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            P = json.load(f)
+        return float(P["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ CPU oracle sample
+def _S_chunk(args):
+    from oracle.kernels import S_kernel
+    X, Y, Z, cell = args
+    return S_kernel(X, Y, Z, *cell)
+
+
+def _N_chunk(args):
+    from oracle.kernels import N_kernel
+    X, Y, Z, cell = args
+    return N_kernel(X, Y, Z, *cell)
+
+
+def _window(fun, lo, length, cell, pool):
+    """Oracle kernel over an offset window, evaluated in z-plane chunks by a spawn pool."""
+    dx, dy, dz = cell
+    jobs = []
+    for iz in range(length[2]):
+        Y, X = np.meshgrid(np.arange(length[1]) + lo[1], np.arange(length[0]) + lo[0], indexing="ij")
+        Z = np.full_like(X, iz + lo[2])
+        jobs.append((X * dx, Y * dy, Z * dz, cell))
+    return np.stack(pool.map(fun, jobs))
+
+
+def cpu_oracle_sample(fp, m0, m1, pool=None):
+    """Time the oracle on a bounded sample of one RK45 step and scale to cell-updates/s.
+
+    Sample: one stray-field direction (potential on the box by linear
+    convolution, banded prefilter, 64-term evaluation, force) plus one
+    self-demag field, i.e. half of one field evaluation; a DP45 step makes six.
+    The kernel windows are set-up, computed beforehand by a process pool.
+    """
+    from oracle import fields as OF
+    from oracle.interaction import stray_interaction
+    import multiprocessing as mp
+
+    own = pool is None
+    if own:
+        pool = mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1)))
+    n_s = fp.n_base
+    box_lo, box_dims = OF.box_for_target(fp.n_slider, fp.offsets[1], fp.offsets[0], fp.u0, True)
+    d_lo = [box_lo[a] - (n_s[a] - 1) for a in range(3)]
+    d_len = [box_dims[a] + n_s[a] - 1 for a in range(3)]
+    S = _window(_S_chunk, d_lo, d_len, fp.cell, pool)
+    N = _window(_N_chunk, [-(n - 1) for n in n_s], [2 * n - 1 for n in n_s], fp.cell, pool)
+    if own:
+        pool.close()
+        pool.join()
+    key = ("S", (3,) + tuple(reversed(n_s)), tuple(fp.cell), tuple(box_lo), tuple(box_dims))
+    cache = {key: S}
+    M0 = fp.mat_base.Ms * m0
+    M1 = fp.mat_slider.Ms * m1
+    t0 = time.perf_counter()
+    stray_interaction(M0, M1, fp.cell, fp.offsets[0], fp.offsets[1], fp.u0, True, kernel_cache=cache)
+    OF.demag_conv(M0, fp.cell, kernel=N)
+    t = time.perf_counter() - t0
+    cells = fp.cells()
+    step_time = t * 2 * 6  # two halves per evaluation, six evaluations per DP45 step
+    return {"value": cells / step_time, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "one stray-field direction + one self-demag of the 1024x256x2 pair "
+                      "(1/12 of a DP45 step: 6 field evaluations x 2 halves), %.1f s on 1 "
+                      "thread; kernel windows precomputed as set-up" % t,
+            "sample_seconds": t}
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args):
+    import torch
+    import workloads
+    from tests.pair_setup import gpu_pair
+
+    rank, world, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    cpu_base = None
+    pool = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # start the oracle's process pool before the first GPU call
+        import multiprocessing as mp
+        pool = mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1)))
+
+    fp, m0, m1 = workloads.film_pair_stick_slip(seed=args.seed + 101 * rank)
+    mm = gpu_pair(fp, m0, m1, adaptive=True, rtol=1e-5)
+    cells = fp.cells()
+    stream = torch.cuda.current_stream()
+    dt = 1e-13
+    for _ in range(max(args.warmup, 3)):
+        _, dt = mm.step(1, dt)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    mm.reset_timing()
+    mm.set_timing(True)
+    launches0 = mm.launch_count()
+    acc0, rej0 = mm.step_stats()
+    barrier()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        _, dt = mm.step(1, dt)
+    ev1.record(stream)
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    launches = mm.launch_count() - launches0
+    acc1, rej1 = mm.step_stats()
+    mm.set_timing(False)
+    clk = clocks.stop()
+    kt = {c: mm.timing(c) for c in range(len(TIMING_CLASSES))}
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = cells * args.steps * world / (ms / 1e3)
+
+    # end to end through the public API with host buffers: upload m, step, read m + force
+    pin = [torch.empty(mm.shapes[g], dtype=torch.float32).pin_memory() for g in (0, 1)]
+    out = [torch.empty(mm.shapes[g], dtype=torch.float32).pin_memory() for g in (0, 1)]
+    for g in (0, 1):
+        mm.download_magnetization(g, pin[g])
+    k_e2e = max(1, min(args.steps, 50))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        for g in (0, 1):
+            mm.upload_magnetization(g, pin[g])
+        _, dt = mm.step(1, dt)
+        for g in (0, 1):
+            mm.download_magnetization(g, out[g])
+        mm.get_force(1)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = cells * k_e2e * world / e2e_s
+    h2d = sum(int(np.prod(mm.shapes[g])) * 4 for g in (0, 1))
+
+    # roofline of the dominant kernel class
+    ab = algorithmic_bytes(mm, fp)
+    dom = max(ab.keys(), key=lambda c: kt[c][0])
+    tot_ms, nl = kt[dom]
+    avg_s = tot_ms / max(nl, 1) / 1e3
+    peak, src = measured_peaks()
+    achieved = ab[dom] / avg_s / 1e9
+    roof = {"bound": "hbm", "kernel": TIMING_CLASSES[dom], "achieved": round(achieved, 1),
+            "peak": peak, "peak_source": src, "unit": "GB/s", "frac": round(achieved / peak, 4),
+            "algorithmic_bytes_per_launch": int(ab[dom]), "avg_launch_ms": round(avg_s * 1e3, 5),
+            "traffic": None}
+    ktab = {TIMING_CLASSES[c]: {"ms": round(kt[c][0], 3), "launches": kt[c][1]} for c in kt}
+    if pool is not None:
+        try:
+            cpu_base = cpu_oracle_sample(fp, m0, m1, pool)
+        finally:
+            pool.close()
+            pool.join()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "cells": cells, "fft": [mm.plan_info(0)["fft"]],
+                       "adaptive_rtol": 1e-5, "accepted": acc1 - acc0, "rejected": rej1 - rej0,
+                       "dt_final_s": dt, "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "no flush: per-step working set (~0.4 GB of spectra, kernels and RK "
+                             "arrays) exceeds the 129 MB L2"},
+            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d + 32,
+                    "steps": k_e2e},
+            "gpu_launches": int(launches),
+            "roofline": roof,
+            "kernel_times": ktab,
+            "clocks": clk,
+            "cpu_baseline": cpu_base,
+        }
+        print(json.dumps(line))
+    mm.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return
+    import workloads
+
+    fp, m0, m1 = workloads.film_pair_stick_slip(seed=args.seed)
+    samples = []
+    nw = min(args.warmup, 1)
+    ns = max(1, min(args.steps, 2))
+    import multiprocessing as mp
+    pool = mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1)))
+    try:
+        for i in range(nw + ns):
+            r = cpu_oracle_sample(fp, m0, m1, pool)
+            if i >= nw:
+                samples.append(r)
+    finally:
+        pool.close()
+        pool.join()
+    v = float(np.median([s["value"] for s in samples]))
+    step_s = fp.cells() / v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": ns, "warmup": nw, "ms_per_step": step_s * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "cells": fp.cells()},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": samples[0]["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -188,6 +188,29 @@ int smooth_even_at_least(int n) {
   }
 }
 
+// Fewest register-blocked stages whose radices (<= 16, as fft.cuh implements)
+// multiply to L; largest radices first.
+void radix_search(int L, int max_r, std::vector<int>& cur, std::vector<int>& best) {
+  static const int kRadices[] = {16, 15, 12, 10, 9, 8, 6, 5, 4, 3, 2};
+  if (L == 1) {
+    if (best.empty() || cur.size() < best.size()) best = cur;
+    return;
+  }
+  if (!best.empty() && cur.size() + 1 >= best.size()) return;
+  for (int r : kRadices) {
+    if (r > max_r || L % r) continue;
+    cur.push_back(r);
+    radix_search(L / r, r, cur, best);
+    cur.pop_back();
+  }
+}
+
+std::vector<int> plan_radices(int L) {
+  std::vector<int> cur, best;
+  radix_search(L, 16, cur, best);
+  return best;
+}
+
 mm_status get_fft(mm_ctx* ctx, int L, FftTables* out) {
   auto it = ctx->ffts.find(L);
   if (it != ctx->ffts.end()) {
@@ -200,13 +223,10 @@ mm_status get_fft(mm_ctx* ctx, int L, FftTables* out) {
   while (r % 3 == 0) { r /= 3; ++p3; }
   while (r % 5 == 0) { r /= 5; ++p5; }
   if (r != 1) return fail(ctx, MM_EINVAL, "FFT length is not 2^a 3^b 5^c");
-  std::vector<int> radix;
-  while (p2 >= 3) { radix.push_back(8); p2 -= 3; }
-  if (p2 == 2) radix.push_back(4);
-  if (p2 == 1) radix.push_back(2);
-  for (int i = 0; i < p5; ++i) radix.push_back(5);
-  for (int i = 0; i < p3; ++i) radix.push_back(3);
-  if ((int)radix.size() > kMaxStages) return fail(ctx, MM_ENOTSUP, "FFT length has too many factors");
+  (void)p2; (void)p3; (void)p5;
+  std::vector<int> radix = plan_radices(L);
+  if (radix.empty() || (int)radix.size() > kMaxStages)
+    return fail(ctx, MM_ENOTSUP, "FFT length has too many factors");
   FftPlanDev P{};
   P.L = L;
   P.nstages = (int)radix.size();
@@ -214,6 +234,12 @@ mm_status get_fft(mm_ctx* ctx, int L, FftTables* out) {
   for (int s = 0; s < P.nstages; ++s) {
     P.radix[s] = radix[s];
     P.blocklen[s] = Lb;
+    const unsigned per_line = (unsigned)(L / radix[s]);
+    const unsigned M = (unsigned)(Lb / radix[s]);
+    // 0 marks a divisor of 1 (the quotient is the dividend)
+    P.magic_per_line[s] = per_line == 1 ? 0u : (unsigned)(0xFFFFFFFFull / per_line) + 1u;
+    P.magic_M[s] = M == 1 ? 0u : (unsigned)(0xFFFFFFFFull / M) + 1u;
+    P.magic_r[s] = (unsigned)(0xFFFFFFFFull / (unsigned)radix[s]) + 1u;
     Lb /= radix[s];
   }
   std::vector<float2> twf(L);
@@ -567,7 +593,8 @@ mm_status run_source_passes(mm_ctx* ctx, const float* in[2], const int* which, i
       }
       const int Pout = (J.do_H ? 3 * S.nz : 0) + (J.do_C ? J.n_out : 0);
       const int P = std::max(3 * S.nz, Pout);
-      smem = std::max(smem, (size_t)P * S.Qy * sizeof(float2));
+      // spectra columns + the prefilter index table
+      smem = std::max(smem, (size_t)P * S.Qy * sizeof(float2) + ypass_table_bytes(J.do_C ? J.r : 0));
       L.tile_start[i] = tiles;
       tiles += S.kxh;
     }
@@ -869,13 +896,8 @@ mm_status mm_create(mm_ctx** out, const mm_options* opt) {
   if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->err_flag, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(ctx->err_flag, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(ctx->mech, 0, sizeof(MechState));
-  if (e == cudaSuccess) {
-    float taps[kFirHalf + 1];
-    double h[kFirHalf + 1];
-    fir_taps(h);
-    for (int i = 0; i <= kFirHalf; ++i) taps[i] = (float)h[i];
-    e = set_fir_taps(taps);
-  }
+  if (e == cudaSuccess) e = init_fft_constants_passes();
+  if (e == cudaSuccess) e = init_fft_constants_kgen();
   if (e != cudaSuccess) {
     mm_destroy(ctx);
     return e == cudaErrorMemoryAllocation ? MM_ENOMEM : MM_ECUDA;
@@ -1226,27 +1248,49 @@ mm_status mm_get_step_stats(mm_ctx* ctx, long long* accepted, long long* rejecte
   return MM_OK;
 }
 
+// Checkpoint layout: header, m of both magnets, then (when k1_valid) the
+// first-same-as-last derivative k1 of both magnets, so a resumed run repeats
+// the uninterrupted one bit for bit.
 struct StateHeader {
   unsigned magic, version;
   unsigned long long n0, n1;
   double x, v, t, u_base[3];
+  double kx1, kv1;
+  int k1_valid, pad;
 };
 
 mm_status mm_get_state(mm_ctx* ctx, void* buf, size_t* bytes) {
   if (!ctx || !bytes) return MM_EINVAL;
-  const size_t need = sizeof(StateHeader) + sizeof(float) * 3 * (ctx->mag[0].N + ctx->mag[1].N);
+  const size_t nm = sizeof(float) * 3 * (ctx->mag[0].N + ctx->mag[1].N);
+  const size_t need = sizeof(StateHeader) + 2 * nm;
   if (!buf) {
     *bytes = need;
     return MM_OK;
   }
   if (*bytes < need) return fail(ctx, MM_ESTATE, "mm_get_state: buffer too small");
-  StateHeader h{0x4d4d5354u, 1u, ctx->mag[0].N, ctx->mag[1].N, ctx->host_mech.x, ctx->host_mech.v,
-                ctx->host_mech.t, {ctx->u_base[0], ctx->u_base[1], ctx->u_base[2]}};
+  StateHeader h{};
+  h.magic = 0x4d4d5354u;
+  h.version = 2u;
+  h.n0 = ctx->mag[0].N;
+  h.n1 = ctx->mag[1].N;
+  h.x = ctx->host_mech.x; h.v = ctx->host_mech.v; h.t = ctx->host_mech.t;
+  for (int a = 0; a < 3; ++a) h.u_base[a] = ctx->u_base[a];
+  h.kx1 = ctx->host_mech.kx[0];
+  h.kv1 = ctx->host_mech.kv[0];
+  h.k1_valid = ctx->k1_valid ? 1 : 0;
   memcpy(buf, &h, sizeof(h));
   char* p = (char*)buf + sizeof(h);
   for (int g = 0; g < 2; ++g) {
     if (ctx->mag[g].N) CK(cudaMemcpyAsync(p, ctx->mag[g].m, sizeof(float) * 3 * ctx->mag[g].N,
                                           cudaMemcpyDeviceToHost, ctx->st));
+    p += sizeof(float) * 3 * ctx->mag[g].N;
+  }
+  for (int g = 0; g < 2; ++g) {
+    if (ctx->mag[g].N && ctx->k1_valid)
+      CK(cudaMemcpyAsync(p, ctx->mag[g].k[0], sizeof(float) * 3 * ctx->mag[g].N, cudaMemcpyDeviceToHost,
+                         ctx->st));
+    else
+      memset(p, 0, sizeof(float) * 3 * ctx->mag[g].N);
     p += sizeof(float) * 3 * ctx->mag[g].N;
   }
   CK(cudaStreamSynchronize(ctx->st));
@@ -1259,21 +1303,33 @@ mm_status mm_set_state(mm_ctx* ctx, const void* buf, size_t bytes) {
   if (bytes < sizeof(StateHeader)) return fail(ctx, MM_ESTATE, "mm_set_state: short buffer");
   StateHeader h;
   memcpy(&h, buf, sizeof(h));
-  if (h.magic != 0x4d4d5354u || h.version != 1u || h.n0 != ctx->mag[0].N || h.n1 != ctx->mag[1].N)
+  if (h.magic != 0x4d4d5354u || h.version != 2u || h.n0 != ctx->mag[0].N || h.n1 != ctx->mag[1].N)
     return fail(ctx, MM_ESTATE, "mm_set_state: header does not match this context");
-  const size_t need = sizeof(StateHeader) + sizeof(float) * 3 * (h.n0 + h.n1);
-  if (bytes < need) return fail(ctx, MM_ESTATE, "mm_set_state: short buffer");
+  const size_t nm = sizeof(float) * 3 * (h.n0 + h.n1);
+  if (bytes < sizeof(StateHeader) + 2 * nm) return fail(ctx, MM_ESTATE, "mm_set_state: short buffer");
   const char* p = (const char*)buf + sizeof(h);
   for (int g = 0; g < 2; ++g) {
     CK(cudaMemcpyAsync(ctx->mag[g].m, p, sizeof(float) * 3 * ctx->mag[g].N, cudaMemcpyHostToDevice, ctx->st));
     p += sizeof(float) * 3 * ctx->mag[g].N;
     ctx->mag[g].mset = true;
   }
+  if (h.k1_valid)
+    for (int g = 0; g < 2; ++g) {
+      CK(cudaMemcpyAsync(ctx->mag[g].k[0], p, sizeof(float) * 3 * ctx->mag[g].N, cudaMemcpyHostToDevice,
+                         ctx->st));
+      p += sizeof(float) * 3 * ctx->mag[g].N;
+    }
   CK(cudaStreamSynchronize(ctx->st));
   for (int a = 0; a < 3; ++a) ctx->u_base[a] = h.u_base[a];
   ctx->host_mech.x = h.x; ctx->host_mech.v = h.v; ctx->host_mech.t = h.t;
+  ctx->host_mech.kx[0] = h.kx1;
+  ctx->host_mech.kv[0] = h.kv1;
   ctx->k1_valid = false;
   if (ctx->planned) CKS(replan_if_needed(ctx));
+  if (h.k1_valid) {
+    CKS(upload_mech(ctx));  // carries kx[0], kv[0]
+    ctx->k1_valid = true;
+  }
   return MM_OK;
 }
 

@@ -1,18 +1,22 @@
-// Shared-memory mixed-radix FFT core (radix 2, 3, 4, 5, 8), in place.
+// Shared-memory mixed-radix FFT core, in place, register-blocked stages.
 //
 // Forward transforms run decimation-in-frequency stages: natural-order input,
 // output left in the mixed-radix digit-reversed order of the plan (frequency k
-// sits at position pos[k]).  Inverse transforms run the exact stage inverses
-// in reverse order: digit-reversed input, natural-order output, unnormalised
-// (sum_k X[k] e^{+2 pi i n k / L}).  A forward + pointwise + inverse sequence
-// therefore never needs a reordering pass.
+// sits at position fft_pos(k)).  Inverse transforms run the exact stage
+// inverses in reverse order: digit-reversed input, natural-order output,
+// unnormalised (sum_k X[k] e^{+2 pi i n k / L}).  A forward + pointwise +
+// inverse sequence therefore never needs a reordering pass.
 //
-// One stage of block length Lb = r * M maps, for every n1 < M,
-//   x[n1 + M n2] -> y[k2] = W_Lb^{n1 k2} sum_n2 x[n1 + M n2] W_r^{n2 k2}
-// stored back at n1 + M k2; twiddles come from a per-length table
+// One stage of block length Lb = R * M maps, for every n1 < M,
+//   x[n1 + M n2] -> y[k2] = W_Lb^{n1 k2} sum_n2 x[n1 + M n2] W_R^{n2 k2}
+// stored back at n1 + M k2.  Each thread keeps the R points of a butterfly in
+// registers, so a stage is one shared-memory round trip; radices up to 16
+// (composite ones as two register levels) keep lengths such as 2160 = 16 15 9
+// to three stages.  Stage twiddles come from a per-length table
 // W_L[t] = exp(-2 pi i t / L) (index n1 k2 L / Lb < L).
 #pragma once
 #include <cuda_runtime.h>
+#include <math.h>
 
 #include "mm_internal.h"
 
@@ -42,118 +46,241 @@ template <typename C> __device__ __forceinline__ C cmul_is(C a, int s) {
   return s > 0 ? cmake<C>(-a.y, a.x) : cmake<C>(a.y, -a.x);
 }
 
-// Small DFTs y[k] = sum_n x[n] exp(s 2 pi i n k / r), s = -1 forward, +1 inverse.
-template <typename C> __device__ __forceinline__ void dft2(C* x) {
-  C a = x[0], b = x[1];
-  x[0] = cadd(a, b); x[1] = csub(a, b);
-}
-template <typename C> __device__ __forceinline__ void dft3(C* x, int s) {
-  typedef typename cplx_traits<C>::real R;
-  const R h = (R)0.86602540378443864676;  // sqrt(3)/2
-  C t = cadd(x[1], x[2]);
-  C m = csub(x[0], cscale(t, (R)0.5));
-  C d = cscale(csub(x[1], x[2]), h);
-  C id = cmul_is(d, s);
-  x[0] = cadd(x[0], t);
-  x[1] = cadd(m, id);
-  x[2] = csub(m, id);
-}
-template <typename C> __device__ __forceinline__ void dft4(C* x, int s) {
-  C a = cadd(x[0], x[2]), b = csub(x[0], x[2]);
-  C c = cadd(x[1], x[3]), d = cmul_is(csub(x[1], x[3]), s);
-  x[0] = cadd(a, c); x[2] = csub(a, c);
-  x[1] = cadd(b, d); x[3] = csub(b, d);
-}
-template <typename C> __device__ __forceinline__ void dft5(C* x, int s) {
-  typedef typename cplx_traits<C>::real R;
-  const R c1 = (R)0.30901699437494742410;   // cos(2 pi / 5)
-  const R c2 = (R)-0.80901699437494742410;  // cos(4 pi / 5)
-  const R s1 = (R)0.95105651629515357212;   // sin(2 pi / 5)
-  const R s2 = (R)0.58778525229247312917;   // sin(4 pi / 5)
-  C t1 = cadd(x[1], x[4]), t2 = cadd(x[2], x[3]);
-  C d1 = csub(x[1], x[4]), d2 = csub(x[2], x[3]);
-  C a1 = cadd(x[0], cadd(cscale(t1, c1), cscale(t2, c2)));
-  C a2 = cadd(x[0], cadd(cscale(t1, c2), cscale(t2, c1)));
-  C b1 = cmul_is(cadd(cscale(d1, s1), cscale(d2, s2)), s);
-  C b2 = cmul_is(csub(cscale(d1, s2), cscale(d2, s1)), s);
-  x[0] = cadd(x[0], cadd(t1, t2));
-  x[1] = cadd(a1, b1); x[4] = csub(a1, b1);
-  x[2] = cadd(a2, b2); x[3] = csub(a2, b2);
-}
-template <typename C> __device__ __forceinline__ void dft8(C* x, int s) {
-  typedef typename cplx_traits<C>::real R;
-  const R q = (R)0.70710678118654752440;  // 1/sqrt(2)
-  C e[4] = {x[0], x[2], x[4], x[6]};
-  C o[4] = {x[1], x[3], x[5], x[7]};
-  dft4(e, s);
-  dft4(o, s);
-  // W8^k = exp(s 2 pi i k / 8)
-  C w1o = cscale(cadd(o[1], cmul_is(o[1], s)), q);          // (1 + i s)/sqrt2
-  C w2o = cmul_is(o[2], s);                                  // i s
-  C w3o = cscale(csub(cmul_is(o[3], s), o[3]), q);          // (-1 + i s)/sqrt2
-  x[0] = cadd(e[0], o[0]); x[4] = csub(e[0], o[0]);
-  x[1] = cadd(e[1], w1o); x[5] = csub(e[1], w1o);
-  x[2] = cadd(e[2], w2o); x[6] = csub(e[2], w2o);
-  x[3] = cadd(e[3], w3o); x[7] = csub(e[3], w3o);
+// cos / sin of 2 pi j / 720 for j < 720 (720 is a multiple of every radix),
+// one copy per translation unit, filled by upload_roots();
+// W_R^j = (c[j * 720/R], s[j * 720/R]).
+constexpr int kRootN = 720;
+static __constant__ float c_root_f[2][kRootN];
+static __constant__ double c_root_d[2][kRootN];
+
+static inline cudaError_t upload_roots() {
+  static float rf[2][kRootN];
+  static double rd[2][kRootN];
+  for (int j = 0; j < kRootN; ++j) {
+    const double a = 2.0 * 3.14159265358979323846 * (double)j / (double)kRootN;
+    rd[0][j] = cos(a);
+    rd[1][j] = sin(a);
+    rf[0][j] = (float)rd[0][j];
+    rf[1][j] = (float)rd[1][j];
+  }
+  cudaError_t e = cudaMemcpyToSymbol(c_root_f, rf, sizeof(rf));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_root_d, rd, sizeof(rd));
+  return e;
 }
 
-template <typename C> __device__ __forceinline__ void dft_small(C* x, int r, int s) {
-  switch (r) {
-    case 2: dft2(x); break;
-    case 3: dft3(x, s); break;
-    case 4: dft4(x, s); break;
-    case 5: dft5(x, s); break;
-    case 8: dft8(x, s); break;
-    default: break;
+template <typename C> __device__ __forceinline__ C root(int j);  // exp(+2 pi i j / 240)
+template <> __device__ __forceinline__ float2 root<float2>(int j) {
+  return make_float2(c_root_f[0][j], c_root_f[1][j]);
+}
+template <> __device__ __forceinline__ double2 root<double2>(int j) {
+  return make_double2(c_root_d[0][j], c_root_d[1][j]);
+}
+
+// Small DFTs y[k] = sum_n x[n] exp(s 2 pi i n k / R) in registers.
+template <int R, typename C> struct Dft;
+
+template <typename C> struct Dft<2, C> {
+  static __device__ __forceinline__ void run(C* x, int) {
+    C a = x[0], b = x[1];
+    x[0] = cadd(a, b); x[1] = csub(a, b);
+  }
+};
+template <typename C> struct Dft<3, C> {
+  static __device__ __forceinline__ void run(C* x, int s) {
+    typedef typename cplx_traits<C>::real R;
+    const R h = (R)0.86602540378443864676;  // sqrt(3)/2
+    C t = cadd(x[1], x[2]);
+    C m = csub(x[0], cscale(t, (R)0.5));
+    C id = cmul_is(cscale(csub(x[1], x[2]), h), s);
+    x[0] = cadd(x[0], t);
+    x[1] = cadd(m, id);
+    x[2] = csub(m, id);
+  }
+};
+template <typename C> struct Dft<4, C> {
+  static __device__ __forceinline__ void run(C* x, int s) {
+    C a = cadd(x[0], x[2]), b = csub(x[0], x[2]);
+    C c = cadd(x[1], x[3]), d = cmul_is(csub(x[1], x[3]), s);
+    x[0] = cadd(a, c); x[2] = csub(a, c);
+    x[1] = cadd(b, d); x[3] = csub(b, d);
+  }
+};
+template <typename C> struct Dft<5, C> {
+  static __device__ __forceinline__ void run(C* x, int s) {
+    typedef typename cplx_traits<C>::real R;
+    const R c1 = (R)0.30901699437494742410;   // cos(2 pi / 5)
+    const R c2 = (R)-0.80901699437494742410;  // cos(4 pi / 5)
+    const R s1 = (R)0.95105651629515357212;   // sin(2 pi / 5)
+    const R s2 = (R)0.58778525229247312917;   // sin(4 pi / 5)
+    C t1 = cadd(x[1], x[4]), t2 = cadd(x[2], x[3]);
+    C d1 = csub(x[1], x[4]), d2 = csub(x[2], x[3]);
+    C a1 = cadd(x[0], cadd(cscale(t1, c1), cscale(t2, c2)));
+    C a2 = cadd(x[0], cadd(cscale(t1, c2), cscale(t2, c1)));
+    C b1 = cmul_is(cadd(cscale(d1, s1), cscale(d2, s2)), s);
+    C b2 = cmul_is(csub(cscale(d1, s2), cscale(d2, s1)), s);
+    x[0] = cadd(x[0], cadd(t1, t2));
+    x[1] = cadd(a1, b1); x[4] = csub(a1, b1);
+    x[2] = cadd(a2, b2); x[3] = csub(a2, b2);
+  }
+};
+
+// Composite R = A * B: n = B n1 + n2, k = k1 + A k2,
+//   y[k1 + A k2] = sum_n2 W_B^{n2 k2} W_R^{n2 k1} sum_n1 x[B n1 + n2] W_A^{n1 k1}
+template <int A, int B, typename C> struct DftComp {
+  static __device__ __forceinline__ void run(C* x, int s) {
+    constexpr int R = A * B;
+    C t[B][A];
+#pragma unroll
+    for (int n2 = 0; n2 < B; ++n2) {
+#pragma unroll
+      for (int n1 = 0; n1 < A; ++n1) t[n2][n1] = x[B * n1 + n2];
+      Dft<A, C>::run(t[n2], s);
+#pragma unroll
+      for (int k1 = 1; k1 < A; ++k1) {
+        if (n2 == 0) continue;
+        const int j = (n2 * k1) % R * (kRootN / R);
+        C w = root<C>(j);
+        if (s < 0) w.y = -w.y;
+        t[n2][k1] = cmul(t[n2][k1], w);
+      }
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < A; ++k1) {
+      C u[B];
+#pragma unroll
+      for (int n2 = 0; n2 < B; ++n2) u[n2] = t[n2][k1];
+      Dft<B, C>::run(u, s);
+#pragma unroll
+      for (int k2 = 0; k2 < B; ++k2) x[k1 + A * k2] = u[k2];
+    }
+  }
+};
+template <typename C> struct Dft<6, C> : DftComp<2, 3, C> {};
+template <typename C> struct Dft<8, C> : DftComp<2, 4, C> {};
+template <typename C> struct Dft<9, C> : DftComp<3, 3, C> {};
+template <typename C> struct Dft<10, C> : DftComp<2, 5, C> {};
+template <typename C> struct Dft<12, C> : DftComp<4, 3, C> {};
+template <typename C> struct Dft<15, C> : DftComp<3, 5, C> {};
+template <typename C> struct Dft<16, C> : DftComp<4, 4, C> {};
+
+template <int R, bool INV, typename C>
+__device__ __forceinline__ void fft_stage(C* buf, int ldl, int nlines, int L, int Lb, unsigned mpl,
+                                          unsigned mM, const C* __restrict__ tw, int tid, int nthr) {
+  const int M = Lb / R;
+  const int tstride = L / Lb;
+  const int per_line = L / R;
+  const int nb = nlines * per_line;
+  for (int b = tid; b < nb; b += nthr) {
+    const int line = mpl ? (int)__umulhi((unsigned)b, mpl) : b;
+    const int rem = b - line * per_line;
+    const int blk = mM ? (int)__umulhi((unsigned)rem, mM) : rem;
+    const int n1 = rem - blk * M;
+    C* base = buf + (size_t)line * ldl + blk * Lb + n1;
+    C v[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) v[k] = base[k * M];
+    if (!INV) {
+      Dft<R, C>::run(v, -1);
+      if (n1)
+#pragma unroll
+        for (int k = 1; k < R; ++k) v[k] = cmul(v[k], tw[n1 * k * tstride]);
+    } else {
+      if (n1)
+#pragma unroll
+        for (int k = 1; k < R; ++k) v[k] = cmulconj(v[k], tw[n1 * k * tstride]);
+      Dft<R, C>::run(v, +1);
+    }
+#pragma unroll
+    for (int k = 0; k < R; ++k) base[k * M] = v[k];
   }
 }
+
+// Decimation-in-frequency stage with the inverse sign: natural-order input,
+// digit-reversed output of sum_k X[k] e^{+2 pi i n k / L}.
+template <int R, typename C>
+__device__ __forceinline__ void fft_stage_dif_inv(C* buf, int ldl, int nlines, int L, int Lb, unsigned mpl,
+                                                  unsigned mM, const C* __restrict__ tw, int tid, int nthr) {
+  const int M = Lb / R;
+  const int tstride = L / Lb;
+  const int per_line = L / R;
+  const int nb = nlines * per_line;
+  for (int b = tid; b < nb; b += nthr) {
+    const int line = mpl ? (int)__umulhi((unsigned)b, mpl) : b;
+    const int rem = b - line * per_line;
+    const int blk = mM ? (int)__umulhi((unsigned)rem, mM) : rem;
+    const int n1 = rem - blk * M;
+    C* base = buf + (size_t)line * ldl + blk * Lb + n1;
+    C v[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) v[k] = base[k * M];
+    Dft<R, C>::run(v, +1);
+    if (n1)
+#pragma unroll
+      for (int k = 1; k < R; ++k) v[k] = cmulconj(v[k], tw[n1 * k * tstride]);
+#pragma unroll
+    for (int k = 0; k < R; ++k) base[k * M] = v[k];
+  }
+}
+
+// Stage orders of fft_smem.
+enum FftMode { kFwdDif = 0, kInvDit = 1, kInvDif = 2 };
 
 // Runs all stages of one transform on `nlines` lines of buf (line stride ldl),
 // using the threads [tid0, tid0 + nthr) of the block.  The caller syncs before.
+//   kFwdDif: forward, natural in, digit-reversed out
+//   kInvDit: inverse, digit-reversed in, natural out
+//   kInvDif: inverse, natural in, digit-reversed out
 template <typename C>
 __device__ void fft_smem(C* buf, int ldl, int nlines, const FftPlanDev& P, const C* __restrict__ tw,
-                         bool inverse, int tid0, int nthr) {
+                         int mode, int tid0, int nthr) {
   const int L = P.L;
   const int tid = (int)threadIdx.x - tid0;
+  const bool mine = tid >= 0 && tid < nthr;
   for (int si = 0; si < P.nstages; ++si) {
-    const int st = inverse ? P.nstages - 1 - si : si;
-    const int r = P.radix[st];
+    const int st = mode == kInvDit ? P.nstages - 1 - si : si;
     const int Lb = P.blocklen[st];
-    const int M = Lb / r;
-    const int tstride = L / Lb;
-    const int per_line = L / r;
-    const int nb = nlines * per_line;
-    if (tid >= 0 && tid < nthr) {
-      for (int b = tid; b < nb; b += nthr) {
-        const int line = b / per_line;
-        const int rem = b - line * per_line;
-        const int blk = rem / M;
-        const int n1 = rem - blk * M;
-        C* base = buf + (size_t)line * ldl + blk * Lb + n1;
-        C v[8];
-        if (!inverse) {
-#pragma unroll
-          for (int k = 0; k < 8; ++k) if (k < r) v[k] = base[k * M];
-          dft_small(v, r, -1);
-#pragma unroll
-          for (int k = 1; k < 8; ++k)
-            if (k < r) v[k] = cmul(v[k], tw[n1 * k * tstride]);
-#pragma unroll
-          for (int k = 0; k < 8; ++k) if (k < r) base[k * M] = v[k];
-        } else {
-#pragma unroll
-          for (int k = 0; k < 8; ++k) if (k < r) v[k] = base[k * M];
-#pragma unroll
-          for (int k = 1; k < 8; ++k)
-            if (k < r) v[k] = cmulconj(v[k], tw[n1 * k * tstride]);
-          dft_small(v, r, +1);
-#pragma unroll
-          for (int k = 0; k < 8; ++k) if (k < r) base[k * M] = v[k];
-        }
+    const unsigned mpl = P.magic_per_line[st], mM = P.magic_M[st];
+    if (mine) {
+#define MM_STAGE(R)                                                                                 \
+  case R:                                                                                           \
+    if (mode == kInvDit) fft_stage<R, true, C>(buf, ldl, nlines, L, Lb, mpl, mM, tw, tid, nthr);     \
+    else if (mode == kFwdDif) fft_stage<R, false, C>(buf, ldl, nlines, L, Lb, mpl, mM, tw, tid, nthr); \
+    else fft_stage_dif_inv<R, C>(buf, ldl, nlines, L, Lb, mpl, mM, tw, tid, nthr);                 \
+    break;
+      switch (P.radix[st]) {
+        MM_STAGE(2) MM_STAGE(3) MM_STAGE(4) MM_STAGE(5) MM_STAGE(6) MM_STAGE(8) MM_STAGE(9)
+        MM_STAGE(10) MM_STAGE(12) MM_STAGE(15) MM_STAGE(16)
+        default: break;
       }
+#undef MM_STAGE
     }
     __syncthreads();
   }
+}
+
+// Position of frequency k in the DIF output: sum_s M_s digit_s(k).
+__device__ __forceinline__ int fft_pos(int k, const FftPlanDev& P) {
+  int p = 0;
+  for (int s = 0; s < P.nstages; ++s) {
+    const int r = P.radix[s];
+    const int q = (int)__umulhi((unsigned)k, P.magic_r[s]);
+    p += (P.blocklen[s] / r) * (k - q * r);
+    k = q;
+  }
+  return p;
+}
+
+// Frequency held at DIF position p (inverse of fft_pos).
+__device__ __forceinline__ int fft_freq(int p, const FftPlanDev& P) {
+  int k = 0, mult = 1;
+  for (int s = 0; s < P.nstages; ++s) {
+    const int M = P.blocklen[s] / P.radix[s];
+    const int d = P.magic_M[s] ? (int)__umulhi((unsigned)p, P.magic_M[s]) : p;
+    p -= d * M;
+    k += mult * d;
+    mult *= P.radix[s];
+  }
+  return k;
 }
 
 // Mirror (whole-sample symmetric) reflection of index j into [0, b).

@@ -12,17 +12,66 @@
 // Kernel spectra are real quarter planes (kx <= Qx/2, ky <= Qy/2): every
 // component of S and N is even or odd in x and y, so its spectrum is purely
 // real or purely imaginary and even or odd in ky.  Signs and the factor i are
-// restored here.
+// restored here; one thread handles the pair (ky, Qy - ky), which shares the
+// stored values, and walks ky in natural order so those loads coalesce.
+//
+// Prefilter (Sec. III.A, cubic B-spline coefficients with mirror ends): the
+// inverse of (q + 4 + 1/q)/6 factors into a causal and an anticausal
+// first-order recursion with pole z1 = sqrt(3) - 2 and gain -6 z1.  On the
+// mirror-extended samples each thread runs both recursions over a chunk of
+// outputs plus kPrefWarm samples of warm-up on either side; the warm-up error
+// is |z1|^14 ~ 1e-8 relative.
 #include "fft.cuh"
 #include "mm_internal.h"
 
 namespace mm {
 
-// Cubic B-spline prefilter taps h_i = sqrt(3) z1^|i|, z1 = sqrt(3) - 2: the
-// impulse response of the inverse of (z + 4 + 1/z)/6 (Sec. III.A prefilter),
-// truncated at |i| <= kFirHalf; applied to the mirror-extended samples this is
-// the mirror-end spline to ~1e-8 relative.
-__constant__ float c_fir[kFirHalf + 1];
+constexpr int kPrefWarm = 14;
+constexpr float kZ1 = -0.26794919243112270f;    // sqrt(3) - 2
+constexpr float kPrefGain = 1.6076951545867362f; // -6 z1
+constexpr int kYChunk = 8;   // prefilter outputs per thread in the y pass (complex)
+constexpr int kXChunk = 16;  // ... in the x pass (real)
+constexpr int kBatch = 4;    // independent global loads in flight per thread
+
+cudaError_t init_fft_constants_passes() { return upload_roots(); }
+
+// Shared-memory index of the samples the prefilter reads: entry j holds the
+// position, in a line of `Q` transformed by `P` (natural order when P is
+// null), of box-local node mirror(start - kPrefWarm + j).
+__device__ __forceinline__ void build_pref_table(int* tab, int n, int box_lo, int box_len, int start, int Q,
+                                                 const FftPlanDev* P) {
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const int g = wrap_index((long long)box_lo + mirror_index(start - kPrefWarm + j, box_len), Q);
+    tab[j] = P ? fft_pos(g, *P) : g;
+  }
+}
+
+// Prefilter outputs [k0, k0 + CH) of one line: src(j) = sample at table entry j.
+template <int CH, typename T, typename Src, typename Out>
+__device__ __forceinline__ void prefilter_chunk(int k0, int r, Src src, Out out) {
+  T ybuf[CH + kPrefWarm];
+  T y = T();
+#pragma unroll
+  for (int j = 0; j < CH + 2 * kPrefWarm; ++j) {
+    y = src(k0 + j) + kZ1 * y;
+    if (j >= kPrefWarm) ybuf[j - kPrefWarm] = y;
+  }
+  T c = T();
+#pragma unroll
+  for (int i = CH + kPrefWarm - 1; i >= 0; --i) {
+    c = ybuf[i] + kZ1 * c;
+    if (i < CH && k0 + i < r) out(k0 + i, kPrefGain * c);
+  }
+}
+
+struct f2 {  // float2 with the arithmetic the recursion needs
+  float x, y;
+  __device__ f2() : x(0.f), y(0.f) {}
+  __device__ f2(float2 v) : x(v.x), y(v.y) {}
+  __device__ f2(float a, float b) : x(a), y(b) {}
+};
+__device__ __forceinline__ f2 operator+(f2 a, f2 b) { return f2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ f2 operator*(float s, f2 a) { return f2(s * a.x, s * a.y); }
 
 // ------------------------------------------------------------------ x forward
 __global__ void __launch_bounds__(256) k_xfwd(const Launch<XFwdJob> Lc) {
@@ -35,44 +84,150 @@ __global__ void __launch_bounds__(256) k_xfwd(const Launch<XFwdJob> Lc) {
   const int r0 = tile * kRowsPerCta;
   const int nrows = min(kRowsPerCta, rows - r0);
   const int nlines = (nrows + 1) >> 1;
+  const int nx = J.nx;
 
-  for (int idx = threadIdx.x; idx < nlines * Q; idx += blockDim.x) {
-    const int line = idx / Q;
-    const int x = idx - line * Q;
-    float a = 0.f, b = 0.f;
-    if (x < J.nx) {
-      const int ra = r0 + 2 * line;
-      a = __ldg(J.m + (size_t)ra * J.nx + x);
-      if (2 * line + 1 < nrows) b = __ldg(J.m + (size_t)(ra + 1) * J.nx + x);
+  if ((nx & 3) == 0) {
+    const int n4 = nx >> 2;
+    const int n = nlines * n4;
+    for (int base = threadIdx.x; base < n; base += kBatch * blockDim.x) {
+      float4 a[kBatch], b[kBatch];
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) {
+        const int idx = base + u * blockDim.x;
+        a[u] = b[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (idx < n) {
+          const int line = idx / n4, x4 = idx - line * n4;
+          const int ra = r0 + 2 * line;
+          a[u] = __ldg(reinterpret_cast<const float4*>(J.m + (size_t)ra * nx) + x4);
+          if (2 * line + 1 < nrows) b[u] = __ldg(reinterpret_cast<const float4*>(J.m + (size_t)(ra + 1) * nx) + x4);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) {
+        const int idx = base + u * blockDim.x;
+        if (idx < n) {
+          const int line = idx / n4, x4 = idx - line * n4;
+          float2* d = sm + line * Q + 4 * x4;
+          d[0] = make_float2(a[u].x, b[u].x);
+          d[1] = make_float2(a[u].y, b[u].y);
+          d[2] = make_float2(a[u].z, b[u].z);
+          d[3] = make_float2(a[u].w, b[u].w);
+        }
+      }
     }
-    sm[line * Q + x] = make_float2(a, b);
+  } else {
+    for (int idx = threadIdx.x; idx < nlines * nx; idx += blockDim.x) {
+      const int line = idx / nx;
+      const int x = idx - line * nx;
+      const int ra = r0 + 2 * line;
+      const float a = __ldg(J.m + (size_t)ra * nx + x);
+      const float b = (2 * line + 1 < nrows) ? __ldg(J.m + (size_t)(ra + 1) * nx + x) : 0.f;
+      sm[line * Q + x] = make_float2(a, b);
+    }
+  }
+  const int pad = Q - nx;
+  for (int idx = threadIdx.x; idx < nlines * pad; idx += blockDim.x) {
+    const int line = idx / pad;
+    sm[line * Q + nx + (idx - line * pad)] = make_float2(0.f, 0.f);
   }
   __syncthreads();
-  fft_smem<float2>(sm, Q, nlines, J.fx.plan, J.fx.tw_f, false, 0, blockDim.x);
+  fft_smem<float2>(sm, Q, nlines, J.fx.plan, J.fx.tw_f, kFwdDif, 0, blockDim.x);
 
   // Z = A + iB:  A_k = (Z_k + conj Z_{Q-k}) / 2,  B_k = (Z_k - conj Z_{Q-k}) / (2i)
-  for (int idx = threadIdx.x; idx < J.kxh * nrows; idx += blockDim.x) {
-    const int kx = idx / nrows;
-    const int rl = idx - kx * nrows;
-    const int line = rl >> 1;
-    const float2 Zk = sm[line * Q + J.fx.pos[kx]];
-    const float2 Zm = sm[line * Q + J.fx.pos[kx == 0 ? 0 : Q - kx]];
-    float2 v;
-    if ((rl & 1) == 0) {
-      v = make_float2(0.5f * (Zk.x + Zm.x), 0.5f * (Zk.y - Zm.y));
-    } else {
-      v = make_float2(0.5f * (Zk.y + Zm.y), -0.5f * (Zk.x - Zm.x));
+  for (int idx = threadIdx.x; idx < J.kxh * nlines; idx += blockDim.x) {
+    const int kx = idx / nlines;
+    const int line = idx - kx * nlines;
+    const float2 Zk = sm[line * Q + fft_pos(kx, J.fx.plan)];
+    const float2 Zm = sm[line * Q + fft_pos(kx == 0 ? 0 : Q - kx, J.fx.plan)];
+    const int ra = r0 + 2 * line;
+    const int pa = ra / J.ny, ya = ra - pa * J.ny;
+    J.out[((size_t)pa * J.kxh + kx) * J.ny + ya] = make_float2(0.5f * (Zk.x + Zm.x), 0.5f * (Zk.y - Zm.y));
+    if (2 * line + 1 < nrows) {
+      const int rb = ra + 1;
+      const int pb = rb / J.ny, yb = rb - pb * J.ny;
+      J.out[((size_t)pb * J.kxh + kx) * J.ny + yb] =
+          make_float2(0.5f * (Zk.y + Zm.y), -0.5f * (Zk.x - Zm.x));
     }
-    const int row = r0 + rl;
-    const int plane = row / J.ny;
-    const int y = row - plane * J.ny;
-    J.out[((size_t)plane * J.kxh + kx) * J.ny + y] = v;
   }
 }
 
 // ------------------------------------------------------------------ y pass
 __device__ __forceinline__ float2 kmul(float v, bool imag, float2 m) {
   return imag ? make_float2(-v * m.y, v * m.x) : make_float2(v * m.x, v * m.y);
+}
+__device__ __forceinline__ void cacc(float2& a, float2 b) { a.x += b.x; a.y += b.y; }
+
+template <int NZ>
+__device__ __forceinline__ void ypass_mix(const YJob& J, float2* sm, int kx, int Q, int nH) {
+  const size_t kstride = (size_t)J.kxh * J.kyq;  // one stored kernel plane
+  const int half = Q >> 1;
+  for (int kyq = threadIdx.x; kyq <= half; kyq += blockDim.x) {
+    // the two frequencies ky = kyq and Qy - kyq share every stored kernel value;
+    // the second has the odd-in-y components negated
+    const bool two = kyq != 0 && 2 * kyq != Q;
+    const int p0 = fft_pos(kyq, J.fy.plan);
+    const int p1 = two ? fft_pos(Q - kyq, J.fy.plan) : p0;
+    const size_t koff = (size_t)kx * J.kyq + kyq;
+    float2 mh[2][3][NZ];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int z = 0; z < NZ; ++z) {
+        mh[0][c][z] = sm[(c * NZ + z) * Q + p0];
+        mh[1][c][z] = sm[(c * NZ + z) * Q + p1];
+      }
+    if (J.do_H) {
+      // H_a(iz) = sum_jz sum_b Ns_ab(iz - jz) m_b(jz); Ns = -Ms N / (Qx Qy)
+      float nv[6][NZ];
+#pragma unroll
+      for (int comp = 0; comp < 6; ++comp)
+#pragma unroll
+        for (int dz = 0; dz < NZ; ++dz) nv[comp][dz] = __ldg(J.Nq + (size_t)(comp * NZ + dz) * kstride + koff);
+#pragma unroll
+      for (int side = 0; side < 2; ++side) {
+        const float fy = side ? -1.f : 1.f;
+        const int p = side ? p1 : p0;
+        if (side == 1 && !two) break;
+#pragma unroll
+        for (int iz = 0; iz < NZ; ++iz) {
+          float2 a0 = make_float2(0.f, 0.f), a1 = a0, a2 = a0;
+#pragma unroll
+          for (int jz = 0; jz < NZ; ++jz) {
+            const int adz = iz >= jz ? iz - jz : jz - iz;
+            const float sz = iz >= jz ? 1.f : -1.f;
+            const float nxx = nv[0][adz], nyy = nv[1][adz], nzz = nv[2][adz];
+            const float nxy = nv[3][adz] * fy, nxz = nv[4][adz] * sz, nyz = nv[5][adz] * sz * fy;
+            const float2 mx = mh[side][0][jz], my = mh[side][1][jz], mz = mh[side][2][jz];
+            cacc(a0, kmul(nxx, false, mx)); cacc(a0, kmul(nxy, false, my)); cacc(a0, kmul(nxz, true, mz));
+            cacc(a1, kmul(nxy, false, mx)); cacc(a1, kmul(nyy, false, my)); cacc(a1, kmul(nyz, true, mz));
+            cacc(a2, kmul(nxz, true, mx));  cacc(a2, kmul(nyz, true, my));  cacc(a2, kmul(nzz, false, mz));
+          }
+          sm[(0 * NZ + iz) * Q + p] = a0;
+          sm[(1 * NZ + iz) * Q + p] = a1;
+          sm[(2 * NZ + iz) * Q + p] = a2;
+        }
+      }
+    }
+    if (J.do_C) {
+      // c(o) = sum_jz sum_c T_c(o, jz) m_c(jz); T = Ms W (S spectra) / (Qx Qy)
+      for (int o = 0; o < J.n_out; ++o) {
+        float2 acc0 = make_float2(0.f, 0.f), acc1 = acc0;
+#pragma unroll
+        for (int jz = 0; jz < NZ; ++jz) {
+          const float* base = J.Tq + (size_t)((o * NZ + jz) * 3) * kstride + koff;
+          const float tx = __ldg(base), ty = __ldg(base + kstride), tz = __ldg(base + 2 * kstride);
+          cacc(acc0, kmul(tx, true, mh[0][0][jz]));
+          cacc(acc0, kmul(ty, true, mh[0][1][jz]));
+          cacc(acc0, kmul(tz, false, mh[0][2][jz]));
+          cacc(acc1, kmul(tx, true, mh[1][0][jz]));
+          cacc(acc1, kmul(-ty, true, mh[1][1][jz]));
+          cacc(acc1, kmul(tz, false, mh[1][2][jz]));
+        }
+        sm[(nH + o) * Q + p0] = acc0;
+        if (two) sm[(nH + o) * Q + p1] = acc1;
+      }
+    }
+  }
 }
 
 __global__ void __launch_bounds__(256) k_ypass(const Launch<YJob> Lc) {
@@ -85,171 +240,183 @@ __global__ void __launch_bounds__(256) k_ypass(const Launch<YJob> Lc) {
   const int Pin = 3 * nz;
   const int nH = J.do_H ? 3 * nz : 0;
   const int Pout = nH + (J.do_C ? J.n_out : 0);
+  int* tab = reinterpret_cast<int*>(sm + (size_t)max(Pin, Pout) * Q);
+  const int ny = J.ny;
 
-  for (int idx = threadIdx.x; idx < Pin * Q; idx += blockDim.x) {
-    const int p = idx / Q;
-    const int y = idx - p * Q;
-    float2 v = make_float2(0.f, 0.f);
-    if (y < J.ny) v = J.in[((size_t)p * J.kxh + kx) * J.ny + y];
-    sm[p * Q + y] = v;
-  }
-  __syncthreads();
-  fft_smem<float2>(sm, Q, Pin, J.fy.plan, J.fy.tw_f, false, 0, blockDim.x);
-
-  const size_t kstride = (size_t)J.kxh * J.kyq;  // one stored kernel plane
-  for (int q = threadIdx.x; q < Q; q += blockDim.x) {
-    const int ky = J.fy.freq[q];
-    const bool upper = 2 * ky > Q;
-    const int kyq = upper ? Q - ky : ky;
-    const float fy = upper ? -1.f : 1.f;     // sign of odd-in-y spectra above Qy/2
-    const size_t koff = (size_t)kx * J.kyq + kyq;
-    float2 mh[3 * kMaxNz];
-    for (int p = 0; p < Pin; ++p) mh[p] = sm[p * Q + q];
-    if (J.do_H) {
-      // H_a(iz) = sum_jz sum_b Ns_ab(iz - jz) m_b(jz); Ns = -Ms N / (Qx Qy)
-      for (int iz = 0; iz < nz; ++iz) {
-        float2 acc[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-        for (int jz = 0; jz < nz; ++jz) {
-          const int dz = iz - jz;
-          const int adz = dz < 0 ? -dz : dz;
-          const float sz = dz < 0 ? -1.f : 1.f;
-          const float* base = J.Nq + (size_t)adz * kstride + koff;
-          const float nxx = __ldg(base + 0 * nz * kstride);
-          const float nyy = __ldg(base + 1 * nz * kstride);
-          const float nzz = __ldg(base + 2 * nz * kstride);
-          const float nxy = __ldg(base + 3 * nz * kstride) * fy;
-          const float nxz = __ldg(base + 4 * nz * kstride) * sz;
-          const float nyz = __ldg(base + 5 * nz * kstride) * sz * fy;
-          const float2 mx = mh[0 * nz + jz], my = mh[1 * nz + jz], mz = mh[2 * nz + jz];
-          float2 t;
-          t = kmul(nxx, false, mx); acc[0].x += t.x; acc[0].y += t.y;
-          t = kmul(nxy, false, my); acc[0].x += t.x; acc[0].y += t.y;
-          t = kmul(nxz, true, mz);  acc[0].x += t.x; acc[0].y += t.y;
-          t = kmul(nxy, false, mx); acc[1].x += t.x; acc[1].y += t.y;
-          t = kmul(nyy, false, my); acc[1].x += t.x; acc[1].y += t.y;
-          t = kmul(nyz, true, mz);  acc[1].x += t.x; acc[1].y += t.y;
-          t = kmul(nxz, true, mx);  acc[2].x += t.x; acc[2].y += t.y;
-          t = kmul(nyz, true, my);  acc[2].x += t.x; acc[2].y += t.y;
-          t = kmul(nzz, false, mz); acc[2].x += t.x; acc[2].y += t.y;
+  if ((ny & 1) == 0) {
+    const int n2 = ny >> 1;
+    const int n = Pin * n2;
+    for (int base = threadIdx.x; base < n; base += kBatch * blockDim.x) {
+      float4 v[kBatch];
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) {
+        const int idx = base + u * blockDim.x;
+        if (idx < n) {
+          const int p = idx / n2, y2 = idx - p * n2;
+          v[u] = *(reinterpret_cast<const float4*>(J.in + ((size_t)p * J.kxh + kx) * ny) + y2);
         }
-        for (int a = 0; a < 3; ++a) sm[(a * nz + iz) * Q + q] = acc[a];
+      }
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) {
+        const int idx = base + u * blockDim.x;
+        if (idx < n) {
+          const int p = idx / n2, y2 = idx - p * n2;
+          sm[p * Q + 2 * y2] = make_float2(v[u].x, v[u].y);
+          sm[p * Q + 2 * y2 + 1] = make_float2(v[u].z, v[u].w);
+        }
       }
     }
-    if (J.do_C) {
-      // c(o) = sum_jz sum_c T_c(o, jz) m_c(jz); T = Ms W (S spectra) / (Qx Qy)
-      for (int o = 0; o < J.n_out; ++o) {
-        float2 acc = make_float2(0.f, 0.f);
-        for (int jz = 0; jz < nz; ++jz) {
-          const float* base = J.Tq + (size_t)((o * nz + jz) * 3) * kstride + koff;
-          const float tx = __ldg(base);
-          const float ty = __ldg(base + kstride) * fy;
-          const float tz = __ldg(base + 2 * kstride);
-          float2 t;
-          t = kmul(tx, true, mh[0 * nz + jz]);  acc.x += t.x; acc.y += t.y;
-          t = kmul(ty, true, mh[1 * nz + jz]);  acc.x += t.x; acc.y += t.y;
-          t = kmul(tz, false, mh[2 * nz + jz]); acc.x += t.x; acc.y += t.y;
-        }
-        sm[(nH + o) * Q + q] = acc;
-      }
+  } else {
+    for (int idx = threadIdx.x; idx < Pin * ny; idx += blockDim.x) {
+      const int p = idx / ny;
+      const int y = idx - p * ny;
+      sm[p * Q + y] = J.in[((size_t)p * J.kxh + kx) * ny + y];
     }
   }
+  const int pad = Q - ny;
+  for (int idx = threadIdx.x; idx < Pin * pad; idx += blockDim.x) {
+    const int p = idx / pad;
+    sm[p * Q + ny + (idx - p * pad)] = make_float2(0.f, 0.f);
+  }
+  if (J.do_C) build_pref_table(tab, J.r + 2 * kPrefWarm + kYChunk, J.box_lo, J.box_len, J.start, Q, nullptr);
   __syncthreads();
-  fft_smem<float2>(sm, Q, Pout, J.fy.plan, J.fy.tw_f, true, 0, blockDim.x);
+  fft_smem<float2>(sm, Q, Pin, J.fy.plan, J.fy.tw_f, kFwdDif, 0, blockDim.x);
+
+  switch (nz) {
+    case 1: ypass_mix<1>(J, sm, kx, Q, nH); break;
+    case 2: ypass_mix<2>(J, sm, kx, Q, nH); break;
+    case 3: ypass_mix<3>(J, sm, kx, Q, nH); break;
+    default: ypass_mix<4>(J, sm, kx, Q, nH); break;
+  }
+  __syncthreads();
+  fft_smem<float2>(sm, Q, Pout, J.fy.plan, J.fy.tw_f, kInvDit, 0, blockDim.x);
 
   if (J.do_H) {
-    for (int idx = threadIdx.x; idx < nH * J.ny; idx += blockDim.x) {
-      const int p = idx / J.ny;
-      const int y = idx - p * J.ny;
-      J.outH[((size_t)p * J.kxh + kx) * J.ny + y] = sm[p * Q + y];
+    for (int idx = threadIdx.x; idx < nH * ny; idx += blockDim.x) {
+      const int p = idx / ny;
+      const int y = idx - p * ny;
+      J.outH[((size_t)p * J.kxh + kx) * ny + y] = sm[p * Q + y];
     }
   }
   if (J.do_C) {
-    for (int idx = threadIdx.x; idx < J.n_out * J.r; idx += blockDim.x) {
-      const int o = idx / J.r;
-      const int k = idx - o * J.r;
-      const float2* col = sm + (size_t)(nH + o) * Q;
-      float2 v;
-      if (J.fir) {
-        v = make_float2(0.f, 0.f);
-        const int c = J.start + k;
-#pragma unroll
-        for (int i = -kFirHalf; i <= kFirHalf; ++i) {
-          const float h = c_fir[i < 0 ? -i : i];
-          const float2 s = col[wrap_index((long long)J.box_lo + mirror_index(c - i, J.box_len), Q)];
-          v.x += h * s.x;
-          v.y += h * s.y;
-        }
-      } else {
-        v = col[wrap_index((long long)J.box_lo + J.start + k, Q)];
+    float2* outC = J.outC;
+    const int r = J.r;
+    if (J.fir) {
+      const int nch = (r + kYChunk - 1) / kYChunk;
+      for (int idx = threadIdx.x; idx < J.n_out * nch; idx += blockDim.x) {
+        const int o = idx / nch;
+        const int k0 = (idx - o * nch) * kYChunk;
+        const float2* col = sm + (size_t)(nH + o) * Q;
+        float2* dst = outC + ((size_t)o * J.kxh + kx) * r;
+        prefilter_chunk<kYChunk, f2>(
+            k0, r, [&](int jj) { return f2(col[tab[jj]]); },
+            [&](int k, f2 v) { dst[k] = make_float2(v.x, v.y); });
       }
-      J.outC[((size_t)o * J.kxh + kx) * J.r + k] = v;
+    } else {
+      for (int idx = threadIdx.x; idx < J.n_out * r; idx += blockDim.x) {
+        const int o = idx / r;
+        const int k = idx - o * r;
+        outC[((size_t)o * J.kxh + kx) * r + k] = sm[(size_t)(nH + o) * Q + tab[k + kPrefWarm]];
+      }
     }
   }
 }
 
 // ------------------------------------------------------------------ x inverse
+__device__ __forceinline__ void xinv_put(float2* sm, int line, int Q, int kx, float2 A, float2 B) {
+  // Z_k = A_k + i B_k and Z_{Q-k} = conj(A_k) + i conj(B_k), natural order
+  sm[line * Q + kx] = make_float2(A.x - B.y, A.y + B.x);
+  if (kx > 0 && 2 * kx != Q) sm[line * Q + Q - kx] = make_float2(A.x + B.y, B.x - A.y);
+}
+
 __global__ void __launch_bounds__(256) k_xinv(const Launch<XInvJob> Lc) {
   extern __shared__ float2 sm[];
   const int j = find_job(Lc.tile_start, Lc.njobs, blockIdx.x);
   const XInvJob& J = Lc.job[j];
   const int tile = blockIdx.x - Lc.tile_start[j];
   const int Q = J.fx.plan.L;
-  const int rows = J.planes * J.rows_per_plane;
+  const int rpp = J.rows_per_plane;
+  const int rows = J.planes * rpp;
   const int r0 = tile * kRowsPerCta;
   const int nrows = min(kRowsPerCta, rows - r0);
   const int nlines = (nrows + 1) >> 1;
+  int* tab = reinterpret_cast<int*>(sm + (size_t)(kRowsPerCta / 2) * Q);
 
-  // Z_k = A_k + i B_k and Z_{Q-k} = conj(A_k) + i conj(B_k), scattered to DIF order
-  for (int idx = threadIdx.x; idx < J.kxh * nlines; idx += blockDim.x) {
-    const int kx = idx / nlines;
-    const int line = idx - kx * nlines;
-    const int ra = r0 + 2 * line;
-    const int pa = ra / J.rows_per_plane, ya = ra - pa * J.rows_per_plane;
-    const float2 A = J.in[((size_t)pa * J.kxh + kx) * J.rows_per_plane + ya];
-    float2 B = make_float2(0.f, 0.f);
-    if (2 * line + 1 < nrows) {
-      const int rb = ra + 1;
-      const int pb = rb / J.rows_per_plane, yb = rb - pb * J.rows_per_plane;
-      B = J.in[((size_t)pb * J.kxh + kx) * J.rows_per_plane + yb];
-    }
-    sm[line * Q + J.fx.pos[kx]] = make_float2(A.x - B.y, A.y + B.x);
-    if (kx > 0 && 2 * kx != Q) sm[line * Q + J.fx.pos[Q - kx]] = make_float2(A.x + B.y, B.x - A.y);
-  }
-  __syncthreads();
-  fft_smem<float2>(sm, Q, nlines, J.fx.plan, J.fx.tw_f, true, 0, blockDim.x);
-
-  for (int idx = threadIdx.x; idx < nrows * J.out_len; idx += blockDim.x) {
-    const int rl = idx / J.out_len;
-    const int k = idx - rl * J.out_len;
-    const float2* line = sm + (size_t)(rl >> 1) * Q;
-    const bool im = rl & 1;
-    float v;
-    if (J.fir) {
-      v = 0.f;
-      const int c = J.start + k;
+  const int n = J.kxh * nlines;
+  if ((rpp & 1) == 0 && (nrows & 1) == 0) {
+    // row pairs are adjacent in memory and 16-byte aligned: one float4 per (kx, line)
+    for (int base = threadIdx.x; base < n; base += kBatch * blockDim.x) {
+      float4 v[kBatch];
 #pragma unroll
-      for (int i = -kFirHalf; i <= kFirHalf; ++i) {
-        const float2 s = line[wrap_index((long long)J.box_lo + mirror_index(c - i, J.box_len), Q)];
-        v += c_fir[i < 0 ? -i : i] * (im ? s.y : s.x);
+      for (int u = 0; u < kBatch; ++u) {
+        const int idx = base + u * blockDim.x;
+        if (idx < n) {
+          const int kx = idx / nlines, line = idx - kx * nlines;
+          const int ra = r0 + 2 * line;
+          const int pa = ra / rpp, ya = ra - pa * rpp;
+          v[u] = *reinterpret_cast<const float4*>(J.in + ((size_t)pa * J.kxh + kx) * rpp + ya);
+        }
       }
-    } else {
-      const float2 s = line[wrap_index((long long)J.box_lo + J.start + k, Q)];
-      v = im ? s.y : s.x;
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) {
+        const int idx = base + u * blockDim.x;
+        if (idx < n) {
+          const int kx = idx / nlines, line = idx - kx * nlines;
+          xinv_put(sm, line, Q, kx, make_float2(v[u].x, v[u].y), make_float2(v[u].z, v[u].w));
+        }
+      }
     }
-    const int row = r0 + rl;
-    J.out[(size_t)row * J.out_len + k] = v;
+  } else {
+    for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
+      const int kx = idx / nlines, line = idx - kx * nlines;
+      const int ra = r0 + 2 * line;
+      const int pa = ra / rpp, ya = ra - pa * rpp;
+      const float2 A = J.in[((size_t)pa * J.kxh + kx) * rpp + ya];
+      float2 B = make_float2(0.f, 0.f);
+      if (2 * line + 1 < nrows) {
+        const int rb = ra + 1;
+        const int pb = rb / rpp, yb = rb - pb * rpp;
+        B = J.in[((size_t)pb * J.kxh + kx) * rpp + yb];
+      }
+      xinv_put(sm, line, Q, kx, A, B);
+    }
+  }
+  build_pref_table(tab, J.out_len + 2 * kPrefWarm + kXChunk, J.box_lo, J.box_len, J.start, Q, &J.fx.plan);
+  __syncthreads();
+  // natural-order input, digit-reversed output: the table above maps through it
+  fft_smem<float2>(sm, Q, nlines, J.fx.plan, J.fx.tw_f, kInvDif, 0, blockDim.x);
+
+  const int r = J.out_len;
+  if (J.fir) {
+    const int nch = (r + kXChunk - 1) / kXChunk;
+    for (int idx = threadIdx.x; idx < nrows * nch; idx += blockDim.x) {
+      const int rl = idx / nch;
+      const int k0 = (idx - rl * nch) * kXChunk;
+      const float* line = reinterpret_cast<const float*>(sm + (size_t)(rl >> 1) * Q) + (rl & 1);
+      float* dst = J.out + (size_t)(r0 + rl) * r;
+      prefilter_chunk<kXChunk, float>(
+          k0, r, [&](int jj) { return line[2 * tab[jj]]; }, [&](int k, float v) { dst[k] = v; });
+    }
+  } else {
+    for (int idx = threadIdx.x; idx < nrows * r; idx += blockDim.x) {
+      const int rl = idx / r;
+      const int k = idx - rl * r;
+      const float* line = reinterpret_cast<const float*>(sm + (size_t)(rl >> 1) * Q) + (rl & 1);
+      J.out[(size_t)(r0 + rl) * r + k] = line[2 * tab[k + kPrefWarm]];
+    }
   }
 }
 
 // ------------------------------------------------------------------ host side
-static size_t xpass_smem(int Qmax) { return (size_t)(kRowsPerCta / 2) * Qmax * sizeof(float2); }
+size_t ypass_table_bytes(int r) { return sizeof(int) * (size_t)(r + 2 * kPrefWarm + kYChunk); }
 
-cudaError_t set_fir_taps(const float* taps) {
-  return cudaMemcpyToSymbol(c_fir, taps, sizeof(float) * (kFirHalf + 1));
+static size_t xinv_smem(int Qmax, int out_max) {
+  return (size_t)(kRowsPerCta / 2) * Qmax * sizeof(float2) +
+         sizeof(int) * (size_t)(out_max + 2 * kPrefWarm + kXChunk);
 }
 
 cudaError_t launch_xfwd(const Launch<XFwdJob>& L, int Qmax, cudaStream_t st) {
-  const size_t smem = xpass_smem(Qmax);
+  const size_t smem = (size_t)(kRowsPerCta / 2) * Qmax * sizeof(float2);
   cudaError_t e = cudaFuncSetAttribute(k_xfwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int grid = L.tile_start[L.njobs];
@@ -268,7 +435,9 @@ cudaError_t launch_ypass(const Launch<YJob>& L, size_t smem, cudaStream_t st) {
 }
 
 cudaError_t launch_xinv(const Launch<XInvJob>& L, int Qmax, cudaStream_t st) {
-  const size_t smem = xpass_smem(Qmax);
+  int out_max = 0;
+  for (int i = 0; i < L.njobs; ++i) out_max = max(out_max, L.job[i].out_len);
+  const size_t smem = xinv_smem(Qmax, out_max);
   cudaError_t e = cudaFuncSetAttribute(k_xinv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int grid = L.tile_start[L.njobs];

@@ -44,6 +44,81 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// y and z stages for one target column (x, y), all NZ layers.
+template <int NZ>
+__device__ __forceinline__ void gather_column(const GatherJob& J, const float* A, int a_n,
+                                              const float (*w_s)[12], int tx, int ty, int x, int y,
+                                              double* acc) {
+  constexpr int CZ = NZ + 3;
+  float B[6][CZ];
+  const float* wy = w_s[1];
+#pragma unroll
+  for (int zz = 0; zz < CZ; ++zz) {
+    float a0[4], a1[4], a2[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int o = (zz * (TY + 3) + ty + k) * TX + tx;
+      a0[k] = A[o];
+      a1[k] = A[a_n + o];
+      a2[k] = A[2 * a_n + o];
+    }
+    float b00 = 0.f, b10 = 0.f, b01 = 0.f, b20 = 0.f, b02 = 0.f, b11 = 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      b00 += wy[k] * a0[k];
+      b10 += wy[k] * a1[k];
+      b01 += wy[4 + k] * a0[k];
+      b20 += wy[k] * a2[k];
+      b02 += wy[8 + k] * a0[k];
+      b11 += wy[4 + k] * a1[k];
+    }
+    B[0][zz] = b00; B[1][zz] = b10; B[2][zz] = b01;
+    B[3][zz] = b20; B[4][zz] = b02; B[5][zz] = b11;
+  }
+  const float* wz = w_s[2];
+  const float ix = J.inv_d[0], iy = J.inv_d[1], iz = J.inv_d[2];
+  const size_t N = (size_t)J.nx * J.ny * NZ;
+  float m[3][NZ];
+#pragma unroll
+  for (int zl = 0; zl < NZ; ++zl) {
+    const size_t cell = ((size_t)zl * J.ny + y) * J.nx + x;
+    m[0][zl] = __ldg(J.m + cell);
+    m[1][zl] = __ldg(J.m + N + cell);
+    m[2][zl] = __ldg(J.m + 2 * N + cell);
+  }
+#pragma unroll
+  for (int zl = 0; zl < NZ; ++zl) {
+    float gx = 0.f, gy = 0.f, gz = 0.f, hxx = 0.f, hyy = 0.f, hzz = 0.f, hxy = 0.f, hxz = 0.f, hyz = 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int zz = zl + k;
+      gx += wz[k] * B[1][zz];
+      gy += wz[k] * B[2][zz];
+      gz += wz[4 + k] * B[0][zz];
+      hxx += wz[k] * B[3][zz];
+      hyy += wz[k] * B[4][zz];
+      hzz += wz[8 + k] * B[0][zz];
+      hxy += wz[k] * B[5][zz];
+      hxz += wz[4 + k] * B[1][zz];
+      hyz += wz[4 + k] * B[2][zz];
+    }
+    gx *= ix; gy *= iy; gz *= iz;
+    hxx *= ix * ix; hyy *= iy * iy; hzz *= iz * iz;
+    hxy *= ix * iy; hxz *= ix * iz; hyz *= iy * iz;
+    const size_t cell = ((size_t)zl * J.ny + y) * J.nx + x;
+    if (J.H) {
+      J.H[cell] = -gx;
+      J.H[N + cell] = -gy;
+      J.H[2 * N + cell] = -gz;
+    }
+    const float mx = m[0][zl], my = m[1][zl], mz = m[2][zl];
+    acc[0] += (double)(mx * hxx + my * hxy + mz * hxz);
+    acc[1] += (double)(mx * hxy + my * hyy + mz * hyz);
+    acc[2] += (double)(mx * hxz + my * hyz + mz * hzz);
+    acc[3] += (double)(mx * gx + my * gy + mz * gz);
+  }
+}
+
 __global__ void __launch_bounds__(TX * TY) k_gather(const Launch<GatherJob> Lc) {
   extern __shared__ float gsm[];
   __shared__ float w_s[3][12];
@@ -82,19 +157,29 @@ __global__ void __launch_bounds__(TX * TY) k_gather(const Launch<GatherJob> Lc) 
   float* ct = gsm;
   float* A = gsm + cz * (TY + 3) * (TX + 3);  // [3][cz][TY+3][TX]
   const int tile_n = cz * (TY + 3) * (TX + 3);
-  for (int idx = threadIdx.x; idx < tile_n; idx += blockDim.x) {
-    const int xx = idx % (TX + 3);
-    const int rest = idx / (TX + 3);
-    const int yy = rest % (TY + 3);
-    const int zz = rest / (TY + 3);
-    float v = 0.f;
-    if (!bad) {
-      const int gx = x0 + xx + shift_s[0];
-      const int gy = y0 + yy + shift_s[1];
-      const int gz = zz + shift_s[2];
-      if (gx < J.rx && gy < J.ry && gz < J.rz) v = __ldg(J.C + ((size_t)gz * J.ry + gy) * J.rx + gx);
+  if (!bad) {
+    const int sx = shift_s[0], sy = shift_s[1], sz = shift_s[2];
+    for (int base = threadIdx.x; base < tile_n; base += 4 * blockDim.x) {
+      float v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int idx = base + u * blockDim.x;
+        v[u] = 0.f;
+        if (idx < tile_n) {
+          const int xx = idx % (TX + 3);
+          const int rest = idx / (TX + 3);
+          const int yy = rest % (TY + 3);
+          const int zz = rest / (TY + 3);
+          const int gx = x0 + xx + sx, gy = y0 + yy + sy, gz = zz + sz;
+          if (gx < J.rx && gy < J.ry && gz < J.rz) v[u] = __ldg(J.C + ((size_t)gz * J.ry + gy) * J.rx + gx);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int idx = base + u * blockDim.x;
+        if (idx < tile_n) ct[idx] = v[u];
+      }
     }
-    ct[idx] = v;
   }
   __syncthreads();
   const int a_n = cz * (TY + 3) * TX;
@@ -116,64 +201,11 @@ __global__ void __launch_bounds__(TX * TY) k_gather(const Launch<GatherJob> Lc) 
   const int x = x0 + tx, y = y0 + ty;
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
   if (!bad && x < J.nx && y < J.ny) {
-    // B_{dx,dy}(z') for (dx,dy) in {00, 10, 01, 20, 02, 11}
-    float B[6][kMaxNz + 3];
-    const float* wy = w_s[1];
-    for (int zz = 0; zz < cz; ++zz) {
-      float a0[4], a1[4], a2[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int o = (zz * (TY + 3) + ty + k) * TX + tx;
-        a0[k] = A[o];
-        a1[k] = A[a_n + o];
-        a2[k] = A[2 * a_n + o];
-      }
-      float b00 = 0.f, b10 = 0.f, b01 = 0.f, b20 = 0.f, b02 = 0.f, b11 = 0.f;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        b00 += wy[k] * a0[k];
-        b10 += wy[k] * a1[k];
-        b01 += wy[4 + k] * a0[k];
-        b20 += wy[k] * a2[k];
-        b02 += wy[8 + k] * a0[k];
-        b11 += wy[4 + k] * a1[k];
-      }
-      B[0][zz] = b00; B[1][zz] = b10; B[2][zz] = b01;
-      B[3][zz] = b20; B[4][zz] = b02; B[5][zz] = b11;
-    }
-    const float* wz = w_s[2];
-    const float ix = J.inv_d[0], iy = J.inv_d[1], iz = J.inv_d[2];
-    const size_t N = (size_t)J.nx * J.ny * nz;
-    for (int zl = 0; zl < nz; ++zl) {
-      float gx = 0.f, gy = 0.f, gz = 0.f, hxx = 0.f, hyy = 0.f, hzz = 0.f, hxy = 0.f, hxz = 0.f,
-            hyz = 0.f;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int zz = zl + k;
-        gx += wz[k] * B[1][zz];
-        gy += wz[k] * B[2][zz];
-        gz += wz[4 + k] * B[0][zz];
-        hxx += wz[k] * B[3][zz];
-        hyy += wz[k] * B[4][zz];
-        hzz += wz[8 + k] * B[0][zz];
-        hxy += wz[k] * B[5][zz];
-        hxz += wz[4 + k] * B[1][zz];
-        hyz += wz[4 + k] * B[2][zz];
-      }
-      gx *= ix; gy *= iy; gz *= iz;
-      hxx *= ix * ix; hyy *= iy * iy; hzz *= iz * iz;
-      hxy *= ix * iy; hxz *= ix * iz; hyz *= iy * iz;
-      const size_t cell = ((size_t)zl * J.ny + y) * J.nx + x;
-      if (J.H) {
-        J.H[cell] = -gx;
-        J.H[N + cell] = -gy;
-        J.H[2 * N + cell] = -gz;
-      }
-      const float mx = __ldg(J.m + cell), my = __ldg(J.m + N + cell), mz = __ldg(J.m + 2 * N + cell);
-      acc[0] += (double)(mx * hxx + my * hxy + mz * hxz);
-      acc[1] += (double)(mx * hxy + my * hyy + mz * hyz);
-      acc[2] += (double)(mx * hxz + my * hyz + mz * hzz);
-      acc[3] += (double)(mx * gx + my * gy + mz * gz);
+    switch (nz) {
+      case 1: gather_column<1>(J, A, a_n, w_s, tx, ty, x, y, acc); break;
+      case 2: gather_column<2>(J, A, a_n, w_s, tx, ty, x, y, acc); break;
+      case 3: gather_column<3>(J, A, a_n, w_s, tx, ty, x, y, acc); break;
+      default: gather_column<4>(J, A, a_n, w_s, tx, ty, x, y, acc); break;
     }
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;

@@ -28,6 +28,8 @@ namespace mm {
 constexpr int kFarCells = 16;
 constexpr double kPi = 3.14159265358979323846;
 
+cudaError_t init_fft_constants_kgen() { return upload_roots(); }
+
 // 3-point Gauss-Legendre on [-1, 1]
 __constant__ double c_gl_x[3] = {-0.77459666924148337704, 0.0, 0.77459666924148337704};
 __constant__ double c_gl_w[3] = {0.55555555555555555556, 0.88888888888888888889,
@@ -231,7 +233,7 @@ __global__ void __launch_bounds__(256) k_fft_lines_d(double2* data, int nlines, 
   double2* g = data + (size_t)line * L;
   for (int i = threadIdx.x; i < L; i += blockDim.x) smd[i] = g[i];
   __syncthreads();
-  fft_smem<double2>(smd, L, 1, T.plan, T.tw_d, false, 0, blockDim.x);
+  fft_smem<double2>(smd, L, 1, T.plan, T.tw_d, kFwdDif, 0, blockDim.x);
   for (int k = threadIdx.x; k < L; k += blockDim.x) g[k] = smd[T.pos[k]];
 }
 

@@ -145,33 +145,44 @@ __device__ double block_sum(double v, double* sh) {
 }
 
 __global__ void __launch_bounds__(256) k_mech(const MechParams P) {
-  __shared__ double sh[8];
+  __shared__ double sh[8][9];
   MechState* S = P.state;
   // Eq. (EQForce) reductions in a fixed order: thread t sums tiles t, t+256, ...
-  double red[2][4];
+  // then a fixed warp-shuffle and cross-warp order (deterministic)
+  double v[9];
   for (int d = 0; d < 2; ++d) {
-    for (int c = 0; c < 4; ++c) {
-      double v = 0.0;
-      if (P.partial[d])
-        for (int t = threadIdx.x; t < P.ntiles[d]; t += blockDim.x) v += P.partial[d][(size_t)t * 4 + c];
-      red[d][c] = block_sum(v, sh);
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    if (P.partial[d]) {
+      const double4* pp = reinterpret_cast<const double4*>(P.partial[d]);
+      for (int t = threadIdx.x; t < P.ntiles[d]; t += blockDim.x) {
+        const double4 q = pp[t];
+        a0 += q.x; a1 += q.y; a2 += q.z; a3 += q.w;
+      }
     }
+    v[4 * d + 0] = a0; v[4 * d + 1] = a1; v[4 * d + 2] = a2; v[4 * d + 3] = a3;
   }
   float emax = 0.f;
-  if (P.mode == 0 && P.stage == 7) {
+  if (P.mode == 0 && P.stage == 7)
     for (int d = 0; d < 2; ++d)
       if (P.err_partial[d])
         for (int t = threadIdx.x; t < P.nerr[d]; t += blockDim.x) emax = fmaxf(emax, P.err_partial[d][t]);
-    emax = warp_max(emax);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = emax;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      float v = 0.f;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v = fmaxf(v, (float)sh[w]);
-      emax = v;
-    }
-  }
+  v[8] = emax;
+#pragma unroll
+  for (int c = 0; c < 8; ++c)
+    for (int o = 16; o > 0; o >>= 1) v[c] += __shfl_down_sync(0xffffffffu, v[c], o);
+  for (int o = 16; o > 0; o >>= 1) v[8] = fmax(v[8], __shfl_down_sync(0xffffffffu, v[8], o));
+  if ((threadIdx.x & 31) == 0)
+#pragma unroll
+    for (int c = 0; c < 9; ++c) sh[threadIdx.x >> 5][c] = v[c];
+  __syncthreads();
   if (threadIdx.x != 0) return;
+  double red[2][4];
+  for (int c = 0; c < 8; ++c) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w][c];
+    red[c / 4][c % 4] = s;
+  }
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) emax = fmaxf(emax, (float)sh[w][8]);
 
   if (P.mode == 0 || P.mode == 1) {
     for (int c = 0; c < 3; ++c) {

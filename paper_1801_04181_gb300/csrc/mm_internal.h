@@ -17,6 +17,11 @@ struct FftPlanDev {
   int nstages;
   int radix[kMaxStages];
   int blocklen[kMaxStages];
+  // n / d = __umulhi(n, magic) for the two per-stage divisors (L / r and
+  // Lb / r); exact while n * d < 2^32, which holds for every launch here
+  unsigned magic_per_line[kMaxStages];
+  unsigned magic_M[kMaxStages];
+  unsigned magic_r[kMaxStages];
 };
 
 // Length-L transform resources resident on the device.
@@ -162,7 +167,9 @@ struct KernelPlan {
   int nz;                 // source layers
 };
 
-cudaError_t set_fir_taps(const float* taps);
+cudaError_t init_fft_constants_passes();
+cudaError_t init_fft_constants_kgen();
+size_t ypass_table_bytes(int r);
 cudaError_t launch_xfwd(const Launch<XFwdJob>& L, int Qmax, cudaStream_t st);
 cudaError_t launch_ypass(const Launch<YJob>& L, size_t smem, cudaStream_t st);
 cudaError_t launch_xinv(const Launch<XInvJob>& L, int Qmax, cudaStream_t st);
