@@ -44,7 +44,8 @@ typedef enum {
   MM_ERANGE = -4,   /* displacement left the planned potential box */
   MM_ETIMEOUT = -5, /* reserved */
   MM_ESTATE = -6,   /* state buffer of the wrong size or version */
-  MM_ENOTSUP = -7   /* geometry outside what this build supports */
+  MM_ENOTSUP = -7,  /* geometry outside what this build supports */
+  MM_ETOOBIG = -8   /* larger than the fixed scratch of mm_spline_field_noalloc */
 } mm_status;
 
 enum { MM_FP32 = 0 };
@@ -188,6 +189,38 @@ mm_status mm_reset_timing(mm_ctx* ctx);
 
 /* Number of kernel launches this context has issued (all classes). */
 long long mm_launch_count(const mm_ctx* ctx);
+
+/*
+ * Stray field, force and interaction energy from a caller-held coefficient
+ * box, with no device memory allocated by the call.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate while
+ * they drive the library -- an application whose device memory is owned by its
+ * own pool allocator and forbids raw cudaMalloc, or a stepping loop that
+ * cannot afford the device synchronisation of cudaMalloc / cudaFree.
+ *
+ * Inputs (all caller-owned): coef_dev, B-spline coefficients of a source
+ * potential on a box, dims (x, y, z) floats x fastest, whose node [0][0][0]
+ * is source lattice node coef_lo (e.g. mm_compute_potential with
+ * prefiltered = 1); pos0_nodes, position of target cell (0,0,0) in source
+ * lattice nodes (target offset - source offset +- slider displacement, in
+ * cells); m_dev, unit magnetisation of the nx x ny x nz target (nz <= 4); cell
+ * size dx, dy, dz (m); Ms of the target (A/m).
+ * Outputs (caller-owned device memory): H_dev, 3 N floats of H = -grad phi
+ * (A/m), may be NULL; FE_dev, 4 doubles: Eq. (EQForce) force F (N) on the
+ * target and its interaction energy E (J).  Asynchronous on `stream`
+ * (cudaStream_t, NULL = default stream).
+ *
+ * Scratch: a fixed 2 MiB array inside the library (resident on every GPU that
+ * loads it until exit), good for targets of up to 65536 tiles of 32 x 8 cell
+ * columns; larger targets return MM_ETOOBIG.  A target whose spline support
+ * leaves the box returns MM_ERANGE.  The first call on each device looks up the
+ * array's address; make that first call before any stream capture.  All calls
+ * share the array: calls that overlap on the GPU race and must be serialised.
+ */
+mm_status mm_spline_field_noalloc(const float* coef_dev, const int coef_dims[3],
+                                  const long long coef_lo[3], const double pos0_nodes[3],
+                                  const float* m_dev, int nx, int ny, int nz, double dx, double dy,
+                                  double dz, double Ms, float* H_dev, double* FE_dev, void* stream);
 
 #ifdef __cplusplus
 }

@@ -201,6 +201,35 @@ class MovingMagnets:
         return self.lib.mm_launch_count(self.ctx)
 
 
+def spline_field_noalloc(coef, coef_lo, pos0_nodes, m_target, cell, Ms, H_out=None, FE_out=None,
+                         stream=None):
+    """mm_spline_field_noalloc: stray field / force / energy from a coefficient box, no allocation.
+
+    coef: (bz, by, bx) float32 CUDA tensor of B-spline coefficients whose node
+    [0, 0, 0] is source lattice node coef_lo; pos0_nodes: source-lattice
+    position of target cell (0, 0, 0); m_target: (3, nz, ny, nx) float32 CUDA.
+    H_out (3, nz, ny, nx) float32 and FE_out (4,) float64 are caller-provided
+    CUDA tensors (FE_out = [Fx, Fy, Fz, E]); nothing is allocated here.
+    """
+    lib = _native.load()
+    _need_cuda_f32(coef)
+    _need_cuda_f32(m_target)
+    if H_out is not None:
+        _need_cuda_f32(H_out, tuple(m_target.shape))
+    if not (FE_out.is_cuda and FE_out.dtype == torch.float64 and FE_out.numel() == 4):
+        raise ValueError("FE_out must be a (4,) float64 CUDA tensor")
+    bz, by, bx = coef.shape
+    _, nz, ny, nx = m_target.shape
+    st = stream if stream is not None else torch.cuda.current_stream()
+    s = lib.mm_spline_field_noalloc(_ptr(coef), _native._i3(bx, by, bz), _native._ll3(*coef_lo),
+                                    _native._d3(*pos0_nodes), _ptr(m_target), nx, ny, nz,
+                                    *[float(c) for c in cell], float(Ms), _ptr(H_out), _ptr(FE_out),
+                                    C.c_void_p(st.cuda_stream))
+    if s != 0:
+        raise MMError(s, "mm_spline_field_noalloc")
+    return H_out, FE_out
+
+
 def eval_kernel_fp64(kind, offsets_m, cell):
     """S (kind 0) or N (kind 1) at target-minus-source offsets (n, 3) metres, FP64 on the GPU."""
     lib = _native.load()

@@ -10,6 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "lib", "libmm.so")
 
 MM_OK, MM_EINVAL, MM_ENOMEM, MM_ECUDA, MM_ERANGE, MM_ETIMEOUT, MM_ESTATE, MM_ENOTSUP = 0, -1, -2, -3, -4, -5, -6, -7
+MM_ETOOBIG = -8
 
 
 class mm_options(C.Structure):
@@ -63,6 +64,10 @@ SIGNATURES = [
     ("mm_get_timing", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
     ("mm_reset_timing", C.c_int, [C.c_void_p]),
     ("mm_launch_count", C.c_longlong, [C.c_void_p]),
+    ("mm_spline_field_noalloc", C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_longlong),
+                                          C.POINTER(C.c_double), C.c_void_p, C.c_int, C.c_int, C.c_int,
+                                          C.c_double, C.c_double, C.c_double, C.c_double, C.c_void_p,
+                                          C.c_void_p, C.c_void_p]),
 ]
 
 _lib = None
@@ -92,4 +97,4 @@ class MMError(RuntimeError):
 
 def status_name(s):
     return {0: "MM_OK", -1: "MM_EINVAL", -2: "MM_ENOMEM", -3: "MM_ECUDA", -4: "MM_ERANGE",
-            -5: "MM_ETIMEOUT", -6: "MM_ESTATE", -7: "MM_ENOTSUP"}.get(s, "MM_?")
+            -5: "MM_ETIMEOUT", -6: "MM_ESTATE", -7: "MM_ENOTSUP", -8: "MM_ETOOBIG"}.get(s, "MM_?")

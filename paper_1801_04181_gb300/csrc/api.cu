@@ -873,6 +873,7 @@ const char* mm_status_string(mm_status s) {
     case MM_ETIMEOUT: return "timeout";
     case MM_ESTATE: return "bad state buffer";
     case MM_ENOTSUP: return "not supported";
+    case MM_ETOOBIG: return "larger than the fixed scratch of the no-allocation entry point";
   }
   return "unknown";
 }
