@@ -138,6 +138,38 @@ def algorithmic_bytes(mm, fp):
     return {0: xf, 1: yp, 2: xi, 3: ga, 4: st}
 
 
+KERNEL_OF_CLASS = {0: ("k_xfwd", ["fft_passes.cu", "fft.cuh", "mm_internal.h"]),
+                   1: ("k_ypass", ["fft_passes.cu", "fft.cuh", "mm_internal.h"]),
+                   2: ("k_xinv", ["fft_passes.cu", "fft.cuh", "mm_internal.h"]),
+                   3: ("k_gather", ["gather.cu", "mm_internal.h"]),
+                   4: ("k_stage", ["llg.cu", "mm_internal.h"])}
+
+
+def profiled_traffic(cls):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel is unchanged since."""
+    import hashlib
+    import re
+    if cls not in KERNEL_OF_CLASS:
+        return None, None
+    name, files = KERNEL_OF_CLASS[cls]
+    path = os.path.join(ROOT, "profiles", "%s_stick_slip_1024x256x2.md" % name)
+    try:
+        text = open(path).read()
+    except OSError:
+        return None, None
+    t = re.search(r"traffic_bytes_per_launch:\s*(\d+)", text)
+    s = re.search(r"source_sha256:\s*([0-9a-f]+)", text)
+    if not t or not s:
+        return None, None
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_1801_04181_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest() != s.group(1):
+        return None, os.path.relpath(path, ROOT) + " (stale: kernel changed since the capture)"
+    return int(t.group(1)), os.path.relpath(path, ROOT)
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -148,29 +180,6 @@ def measured_peaks():
 
 
 # ------------------------------------------------------------------ CPU oracle sample
-def _S_chunk(args):
-    from oracle.kernels import S_kernel
-    X, Y, Z, cell = args
-    return S_kernel(X, Y, Z, *cell)
-
-
-def _N_chunk(args):
-    from oracle.kernels import N_kernel
-    X, Y, Z, cell = args
-    return N_kernel(X, Y, Z, *cell)
-
-
-def _window(fun, lo, length, cell, pool):
-    """Oracle kernel over an offset window, evaluated in z-plane chunks by a spawn pool."""
-    dx, dy, dz = cell
-    jobs = []
-    for iz in range(length[2]):
-        Y, X = np.meshgrid(np.arange(length[1]) + lo[1], np.arange(length[0]) + lo[0], indexing="ij")
-        Z = np.full_like(X, iz + lo[2])
-        jobs.append((X * dx, Y * dy, Z * dz, cell))
-    return np.stack(pool.map(fun, jobs))
-
-
 def cpu_oracle_sample(fp, m0, m1, pool=None):
     """Time the oracle on a bounded sample of one RK45 step and scale to cell-updates/s.
 
@@ -186,12 +195,11 @@ def cpu_oracle_sample(fp, m0, m1, pool=None):
     own = pool is None
     if own:
         pool = mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1)))
+    from tests.pair_setup import oracle_kernel_windows
+
     n_s = fp.n_base
     box_lo, box_dims = OF.box_for_target(fp.n_slider, fp.offsets[1], fp.offsets[0], fp.u0, True)
-    d_lo = [box_lo[a] - (n_s[a] - 1) for a in range(3)]
-    d_len = [box_dims[a] + n_s[a] - 1 for a in range(3)]
-    S = _window(_S_chunk, d_lo, d_len, fp.cell, pool)
-    N = _window(_N_chunk, [-(n - 1) for n in n_s], [2 * n - 1 for n in n_s], fp.cell, pool)
+    S, N = oracle_kernel_windows(n_s, fp.cell, box_lo, box_dims, pool)
     if own:
         pool.close()
         pool.join()
@@ -304,10 +312,11 @@ def run_gpu(args):
     avg_s = tot_ms / max(nl, 1) / 1e3
     peak, src = measured_peaks()
     achieved = ab[dom] / avg_s / 1e9
+    traffic, traffic_src = profiled_traffic(dom)
     roof = {"bound": "hbm", "kernel": TIMING_CLASSES[dom], "achieved": round(achieved, 1),
             "peak": peak, "peak_source": src, "unit": "GB/s", "frac": round(achieved / peak, 4),
             "algorithmic_bytes_per_launch": int(ab[dom]), "avg_launch_ms": round(avg_s * 1e3, 5),
-            "traffic": None}
+            "traffic": traffic, "traffic_source": traffic_src}
     ktab = {TIMING_CLASSES[c]: {"ms": round(kt[c][0], 3), "launches": kt[c][1]} for c in kt}
     if pool is not None:
         try:

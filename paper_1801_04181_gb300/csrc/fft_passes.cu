@@ -29,8 +29,10 @@ namespace mm {
 constexpr int kPrefWarm = 14;
 constexpr float kZ1 = -0.26794919243112270f;    // sqrt(3) - 2
 constexpr float kPrefGain = 1.6076951545867362f; // -6 z1
-constexpr int kYChunk = 8;   // prefilter outputs per thread in the y pass (complex)
-constexpr int kXChunk = 16;  // ... in the x pass (real)
+// prefilter outputs per thread; odd, so neighbouring threads' table reads
+// fall in different shared-memory banks
+constexpr int kYChunk = 9;   // y pass (complex)
+constexpr int kXChunk = 17;  // x pass (real)
 constexpr int kBatch = 4;    // independent global loads in flight per thread
 
 cudaError_t init_fft_constants_passes() { return upload_roots(); }
@@ -125,20 +127,22 @@ __global__ void __launch_bounds__(256) k_xfwd(const Launch<XFwdJob> Lc) {
       sm[line * Q + x] = make_float2(a, b);
     }
   }
-  const int pad = Q - nx;
-  for (int idx = threadIdx.x; idx < nlines * pad; idx += blockDim.x) {
-    const int line = idx / pad;
-    sm[line * Q + nx + (idx - line * pad)] = make_float2(0.f, 0.f);
-  }
+  for (int line = 0; line < nlines; ++line)
+    for (int x = nx + threadIdx.x; x < Q; x += blockDim.x) sm[line * Q + x] = make_float2(0.f, 0.f);
+  // DIF positions of k and Q - k for every kx <= Q/2
+  int2* ptab = reinterpret_cast<int2*>(sm + (size_t)(kRowsPerCta / 2) * Q);
+  for (int kx = threadIdx.x; kx < J.kxh; kx += blockDim.x)
+    ptab[kx] = make_int2(fft_pos(kx, J.fx.plan), fft_pos(kx == 0 ? 0 : Q - kx, J.fx.plan));
   __syncthreads();
   fft_smem<float2>(sm, Q, nlines, J.fx.plan, J.fx.tw_f, kFwdDif, 0, blockDim.x);
 
   // Z = A + iB:  A_k = (Z_k + conj Z_{Q-k}) / 2,  B_k = (Z_k - conj Z_{Q-k}) / (2i)
   for (int idx = threadIdx.x; idx < J.kxh * nlines; idx += blockDim.x) {
-    const int kx = idx / nlines;
+    const int kx = nlines == 4 ? idx >> 2 : idx / nlines;
     const int line = idx - kx * nlines;
-    const float2 Zk = sm[line * Q + fft_pos(kx, J.fx.plan)];
-    const float2 Zm = sm[line * Q + fft_pos(kx == 0 ? 0 : Q - kx, J.fx.plan)];
+    const int2 pp = ptab[kx];
+    const float2 Zk = sm[line * Q + pp.x];
+    const float2 Zm = sm[line * Q + pp.y];
     const int ra = r0 + 2 * line;
     const int pa = ra / J.ny, ya = ra - pa * J.ny;
     J.out[((size_t)pa * J.kxh + kx) * J.ny + ya] = make_float2(0.5f * (Zk.x + Zm.x), 0.5f * (Zk.y - Zm.y));
@@ -415,8 +419,13 @@ static size_t xinv_smem(int Qmax, int out_max) {
          sizeof(int) * (size_t)(out_max + 2 * kPrefWarm + kXChunk);
 }
 
+static void max_carveout(const void* f) {
+  cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+}
+
 cudaError_t launch_xfwd(const Launch<XFwdJob>& L, int Qmax, cudaStream_t st) {
-  const size_t smem = (size_t)(kRowsPerCta / 2) * Qmax * sizeof(float2);
+  const size_t smem = (size_t)(kRowsPerCta / 2) * Qmax * sizeof(float2) + sizeof(int2) * (size_t)(Qmax / 2 + 1);
+  max_carveout((const void*)k_xfwd);
   cudaError_t e = cudaFuncSetAttribute(k_xfwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int grid = L.tile_start[L.njobs];
@@ -426,6 +435,7 @@ cudaError_t launch_xfwd(const Launch<XFwdJob>& L, int Qmax, cudaStream_t st) {
 }
 
 cudaError_t launch_ypass(const Launch<YJob>& L, size_t smem, cudaStream_t st) {
+  max_carveout((const void*)k_ypass);
   cudaError_t e = cudaFuncSetAttribute(k_ypass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int grid = L.tile_start[L.njobs];
@@ -438,6 +448,7 @@ cudaError_t launch_xinv(const Launch<XInvJob>& L, int Qmax, cudaStream_t st) {
   int out_max = 0;
   for (int i = 0; i < L.njobs; ++i) out_max = max(out_max, L.job[i].out_len);
   const size_t smem = xinv_smem(Qmax, out_max);
+  max_carveout((const void*)k_xinv);
   cudaError_t e = cudaFuncSetAttribute(k_xinv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int grid = L.tile_start[L.njobs];

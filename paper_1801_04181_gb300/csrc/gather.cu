@@ -231,6 +231,8 @@ size_t gather_smem(int nz) {
 
 cudaError_t launch_gather(const Launch<GatherJob>& L, int nz_max, cudaStream_t st) {
   const size_t smem = gather_smem(nz_max);
+  cudaFuncSetAttribute((const void*)k_gather, cudaFuncAttributePreferredSharedMemoryCarveout,
+                       cudaSharedmemCarveoutMaxShared);
   cudaError_t e = cudaFuncSetAttribute(k_gather, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int grid = L.tile_start[L.njobs];

@@ -38,6 +38,41 @@ def oracle_system(fp):
                   H_ext=fp.H_ext)
 
 
+def _S_chunk(args):
+    from oracle.kernels import S_kernel
+    X, Y, Z, cell = args
+    return S_kernel(X, Y, Z, *cell)
+
+
+def _N_chunk(args):
+    from oracle.kernels import N_kernel
+    X, Y, Z, cell = args
+    return N_kernel(X, Y, Z, *cell)
+
+
+def _window(fun, lo, length, cell, pool):
+    dx, dy, dz = cell
+    jobs = []
+    for iz in range(length[2]):
+        Y, X = np.meshgrid(np.arange(length[1]) + lo[1], np.arange(length[0]) + lo[0], indexing="ij")
+        Z = np.full_like(X, iz + lo[2])
+        jobs.append((X * dx, Y * dy, Z * dz, cell))
+    return np.stack(pool.map(fun, jobs))
+
+
+def oracle_kernel_windows(n_s, cell, box_lo, box_dims, pool):
+    """The oracle's S window of a box and N window of a source grid, one z plane per pool task.
+
+    Same values as oracle.fields.potential_kernel_window / demag_kernel_window,
+    computed in parallel; pass a multiprocessing pool made with 'spawn'.
+    """
+    d_lo = [box_lo[a] - (n_s[a] - 1) for a in range(3)]
+    d_len = [box_dims[a] + n_s[a] - 1 for a in range(3)]
+    S = _window(_S_chunk, d_lo, d_len, cell, pool)
+    N = _window(_N_chunk, [-(n - 1) for n in n_s], [2 * n - 1 for n in n_s], cell, pool)
+    return S, N
+
+
 def force_scale(hess_n, M_t, cell):
     """mu0 V sum_i |M_i| ||Hess_i||: the size of the terms that cancel in Eq. (EQForce)."""
     d = np.asarray(cell, float)
