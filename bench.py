@@ -51,6 +51,22 @@ def dist_info():
     return rank, world, local
 
 
+def max_over_ranks(x, world, device):
+    """Largest value of x over all ranks (the job's time is its slowest rank's)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, steps, seconds, world):
+    """Units processed by all ranks per second of the slowest rank (weak scaling)."""
+    return units_per_rank * steps * world / seconds
+
+
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -214,9 +230,9 @@ def cpu_oracle_sample(fp, m0, m1, pool=None):
     cells = fp.cells()
     step_time = t * 2 * 6  # two halves per evaluation, six evaluations per DP45 step
     return {"value": cells / step_time, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "one stray-field direction + one self-demag of the 1024x256x2 pair "
+            "sample": "one stray-field direction + one self-demag of the %dx%dx%d pair "
                       "(1/12 of a DP45 step: 6 field evaluations x 2 halves), %.1f s on 1 "
-                      "thread; kernel windows precomputed as set-up" % t,
+                      "thread; kernel windows precomputed as set-up" % (tuple(fp.n_base) + (t,)),
             "sample_seconds": t}
 
 
@@ -273,12 +289,8 @@ def run_gpu(args):
     mm.set_timing(False)
     clk = clocks.stop()
     kt = {c: mm.timing(c) for c in range(len(TIMING_CLASSES))}
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = cells * args.steps * world / (ms / 1e3)
+    ms = max_over_ranks(ms, world, "cuda")
+    value = whole_job_rate(cells, args.steps, ms / 1e3, world)
 
     # end to end through the public API with host buffers: upload m, step, read m + force
     pin = [torch.empty(mm.shapes[g], dtype=torch.float32).pin_memory() for g in (0, 1)]
@@ -296,13 +308,8 @@ def run_gpu(args):
             mm.download_magnetization(g, out[g])
         mm.get_force(1)
     barrier()
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = cells * k_e2e * world / e2e_s
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, "cuda")
+    e2e = whole_job_rate(cells, k_e2e, e2e_s, world)
     h2d = sum(int(np.prod(mm.shapes[g])) * 4 for g in (0, 1))
 
     # roofline of the dominant kernel class

@@ -23,7 +23,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/mm.h"
+#include "mm.h"
 #include "mm_internal.h"
 
 using namespace mm;
@@ -119,6 +119,7 @@ struct mm_ctx {
   MechState host_mech{};
   MechState* mech = nullptr;          // device
   int* err_flag = nullptr;            // device
+  int* tickets = nullptr;             // device: last-block counters of the gather and stage launches
   bool k1_valid = false;
   long long accepted = 0, rejected = 0;
   bool planned = false;
@@ -665,7 +666,9 @@ GatherJob gather_job(mm_ctx* ctx, int s, const float* m_t, float* H) {
   return J;
 }
 
-mm_status run_gathers(mm_ctx* ctx, const float* in[2], const int* srcs, int n, float* const* Hout) {
+// P: reduction / slider update done by the gather's last block (null: none)
+mm_status run_gathers(mm_ctx* ctx, const float* in[2], const int* srcs, int n, float* const* Hout,
+                      const MechParams* P) {
   Launch<GatherJob> L{};
   L.njobs = n;
   int tiles = 0, nzmax = 1;
@@ -677,8 +680,9 @@ mm_status run_gathers(mm_ctx* ctx, const float* in[2], const int* srcs, int n, f
     nzmax = std::max(nzmax, ctx->mag[1 - s].nz);
   }
   L.tile_start[n] = tiles;
+  const MechParams none{};
   Timer t(ctx, 3);
-  CK(launch_gather(L, nzmax, ctx->st));
+  CK(launch_gather(L, nzmax, P ? *P : none, ctx->tickets, ctx->st));
   return MM_OK;
 }
 
@@ -696,8 +700,10 @@ MechParams mech_params(mm_ctx* ctx, int mode, int stage, double dt, bool dir0, b
     const double V = T.d[0] * T.d[1] * T.d[2];
     P.Fscale[s] = -kMu0 * V * T.Ms;
     P.Escale[s] = kMu0 * V * T.Ms;
-    P.err_partial[s] = ctx->mag[s].err_partial;
-    P.nerr[s] = ctx->mag[s].nerr;
+    if (mode == 5) {  // only the error-norm reduction reads the stage partials
+      P.err_partial[s] = ctx->mag[s].err_partial;
+      P.nerr[s] = ctx->mag[s].nerr;
+    }
   }
   P.mode = mode;
   P.stage = stage;
@@ -727,8 +733,9 @@ mm_status run_mech(mm_ctx* ctx, const MechParams& P) {
   return MM_OK;
 }
 
-// All fields of both magnets for stage inputs `in` (demag, stray, forces).
-mm_status evaluate_fields(mm_ctx* ctx, const float* in[2]) {
+// All fields of both magnets for stage inputs `in` (demag, stray, forces);
+// P: force reduction / slider update fused into the gather.
+mm_status evaluate_fields(mm_ctx* ctx, const float* in[2], const MechParams& P) {
   const int which[2] = {0, 1};
   const int what[2] = {3, 3};
   Dir* dirs[2] = {&ctx->mag[0].dir, &ctx->mag[1].dir};
@@ -736,7 +743,7 @@ mm_status evaluate_fields(mm_ctx* ctx, const float* in[2]) {
   const int srcs[2] = {0, 1};
   // H_stray of the slider comes from source 0, of the base from source 1
   float* H[2] = {ctx->mag[1].Hstray, ctx->mag[0].Hstray};
-  CKS(run_gathers(ctx, in, srcs, 2, H));
+  CKS(run_gathers(ctx, in, srcs, 2, H, &P));
   return MM_OK;
 }
 
@@ -781,8 +788,10 @@ mm_status run_stage(mm_ctx* ctx, const float* ys[2], float* ys_next[2], int stag
     tiles += ctx->mag[g].nerr;
   }
   L.tile_start[2] = tiles;
+  // the last stage's last block reduces the embedded error norm
+  const MechParams Perr = stage == 7 ? mech_params(ctx, 5, 7, dt, false, false) : MechParams{};
   Timer t(ctx, 4);
-  CK(launch_stage(L, ctx->st));
+  CK(launch_stage(L, Perr, ctx->tickets + 1, ctx->st));
   return MM_OK;
 }
 
@@ -803,10 +812,9 @@ mm_status attempt_step(mm_ctx* ctx, double dt, double* err) {
   if (!ctx->k1_valid) {
     CKS(run_mech(ctx, mech_params(ctx, 4, 0, dt, false, false)));
     const float* in[2] = {M[0].m, M[1].m};
-    CKS(evaluate_fields(ctx, in));
+    CKS(evaluate_fields(ctx, in, mech_params(ctx, 0, 1, dt, true, true)));
     float* nxt[2] = {M[0].ys[0], M[1].ys[0]};
     CKS(run_stage(ctx, in, nxt, 1, dt));
-    CKS(run_mech(ctx, mech_params(ctx, 0, 1, dt, true, true)));
   } else {
     Launch<CombineJob> L{};
     L.njobs = 2;
@@ -832,10 +840,10 @@ mm_status attempt_step(mm_ctx* ctx, double dt, double* err) {
   int cur = 0;
   for (int i = 2; i <= 7; ++i) {
     const float* in[2] = {M[0].ys[cur], M[1].ys[cur]};
-    CKS(evaluate_fields(ctx, in));
+    // the gather's last block reduces the forces and advances the slider stage
+    CKS(evaluate_fields(ctx, in, mech_params(ctx, 0, i, dt, true, true)));
     float* nxt[2] = {M[0].ys[1 - cur], M[1].ys[1 - cur]};
     CKS(run_stage(ctx, in, nxt, i, dt));
-    CKS(run_mech(ctx, mech_params(ctx, 0, i, dt, true, true)));
     if (i < 7) cur = 1 - cur;
   }
   // stages 2..7 alternate the two stage buffers, so the stage-7 input (the
@@ -895,6 +903,8 @@ mm_status mm_create(mm_ctx** out, const mm_options* opt) {
   ctx->st = (cudaStream_t)ctx->opt.stream;
   cudaError_t e = cudaMalloc((void**)&ctx->mech, sizeof(MechState));
   if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->err_flag, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->tickets, 2 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(ctx->tickets, 0, 2 * sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(ctx->err_flag, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(ctx->mech, 0, sizeof(MechState));
   if (e == cudaSuccess) e = init_fft_constants_passes();
@@ -929,7 +939,7 @@ void mm_destroy(mm_ctx* ctx) {
     cudaFree(kv.second.tw_f); cudaFree(kv.second.tw_d); cudaFree(kv.second.pos); cudaFree(kv.second.freq);
   }
   cudaFree(ctx->gen_work); cudaFree(ctx->gen_q); cudaFree(ctx->W_dev);
-  cudaFree(ctx->mech); cudaFree(ctx->err_flag);
+  cudaFree(ctx->mech); cudaFree(ctx->err_flag); cudaFree(ctx->tickets);
   for (auto& p : ctx->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
   for (auto e : ctx->free_events) cudaEventDestroy(e);
   delete ctx;
@@ -1079,8 +1089,7 @@ mm_status mm_compute_fields(mm_ctx* ctx) {
   if (!ctx) return MM_EINVAL;
   CKS(prepare(ctx));
   const float* in[2] = {ctx->mag[0].m, ctx->mag[1].m};
-  CKS(evaluate_fields(ctx, in));
-  CKS(run_mech(ctx, mech_params(ctx, 1, 0, 0.0, true, true)));
+  CKS(evaluate_fields(ctx, in, mech_params(ctx, 1, 0, 0.0, true, true)));
   return MM_OK;
 }
 
@@ -1093,8 +1102,8 @@ mm_status mm_compute_stray_field(mm_ctx* ctx, int src, float* H_dev) {
   Dir* dirs[1] = {&ctx->mag[src].dir};
   CKS(run_source_passes(ctx, in, which, 1, what, dirs));
   float* H[1] = {H_dev ? H_dev : ctx->mag[1 - src].Hstray};
-  CKS(run_gathers(ctx, in, which, 1, H));
-  CKS(run_mech(ctx, mech_params(ctx, 1, 0, 0.0, src == 0, src == 1)));
+  const MechParams P = mech_params(ctx, 1, 0, 0.0, src == 0, src == 1);
+  CKS(run_gathers(ctx, in, which, 1, H, &P));
   return MM_OK;
 }
 
@@ -1171,7 +1180,7 @@ mm_status mm_compute_torque(mm_ctx* ctx, int mag, float* dmdt_dev, float* Heff_d
   L.tile_start[1] = M.nerr;
   {
     Timer t(ctx, 4);
-    CK(launch_stage(L, ctx->st));
+    CK(launch_stage(L, MechParams{}, nullptr, ctx->st));
   }
   ctx->k1_valid = false;
   return MM_OK;

@@ -163,6 +163,22 @@ template <typename C> struct Dft<12, C> : DftComp<4, 3, C> {};
 template <typename C> struct Dft<15, C> : DftComp<3, 5, C> {};
 template <typename C> struct Dft<16, C> : DftComp<4, 4, C> {};
 
+// Stage twiddles w[k] = W^k (W = W_Lb^{n1}), k = 1..R-1: the power-of-two
+// ones are read from the table (log2 R loads instead of R - 1), every other
+// one is the product of the table values of its set bits, so no twiddle is
+// more than 2 popcount(k) - 1 <= 7 roundings away from exact.
+template <int R, typename C>
+__device__ __forceinline__ void twiddle_powers(const C* __restrict__ tw, int idx1, C* w) {
+#pragma unroll
+  for (int k = 1; k < R; k *= 2) w[k] = tw[idx1 * k];
+#pragma unroll
+  for (int k = 3; k < R; ++k) {
+    if ((k & (k - 1)) == 0) continue;
+    const int low = k & -k;
+    w[k] = cmul(w[k - low], w[low]);
+  }
+}
+
 template <int R, bool INV, typename C>
 __device__ __forceinline__ void fft_stage(C* buf, int ldl, int nlines, int L, int Lb, unsigned mpl,
                                           unsigned mM, const C* __restrict__ tw, int tid, int nthr) {
@@ -175,19 +191,25 @@ __device__ __forceinline__ void fft_stage(C* buf, int ldl, int nlines, int L, in
     const int rem = b - line * per_line;
     const int blk = mM ? (int)__umulhi((unsigned)rem, mM) : rem;
     const int n1 = rem - blk * M;
-    C* base = buf + (size_t)line * ldl + blk * Lb + n1;
+    C* base = buf + (line * ldl + blk * Lb + n1);  // shared memory: 32-bit offsets
     C v[R];
 #pragma unroll
     for (int k = 0; k < R; ++k) v[k] = base[k * M];
     if (!INV) {
       Dft<R, C>::run(v, -1);
-      if (n1)
+      if (n1) {
+        C w[R];
+        twiddle_powers<R, C>(tw, n1 * tstride, w);
 #pragma unroll
-        for (int k = 1; k < R; ++k) v[k] = cmul(v[k], tw[n1 * k * tstride]);
+        for (int k = 1; k < R; ++k) v[k] = cmul(v[k], w[k]);
+      }
     } else {
-      if (n1)
+      if (n1) {
+        C w[R];
+        twiddle_powers<R, C>(tw, n1 * tstride, w);
 #pragma unroll
-        for (int k = 1; k < R; ++k) v[k] = cmulconj(v[k], tw[n1 * k * tstride]);
+        for (int k = 1; k < R; ++k) v[k] = cmulconj(v[k], w[k]);
+      }
       Dft<R, C>::run(v, +1);
     }
 #pragma unroll
@@ -209,14 +231,17 @@ __device__ __forceinline__ void fft_stage_dif_inv(C* buf, int ldl, int nlines, i
     const int rem = b - line * per_line;
     const int blk = mM ? (int)__umulhi((unsigned)rem, mM) : rem;
     const int n1 = rem - blk * M;
-    C* base = buf + (size_t)line * ldl + blk * Lb + n1;
+    C* base = buf + (line * ldl + blk * Lb + n1);
     C v[R];
 #pragma unroll
     for (int k = 0; k < R; ++k) v[k] = base[k * M];
     Dft<R, C>::run(v, +1);
-    if (n1)
+    if (n1) {
+      C w[R];
+      twiddle_powers<R, C>(tw, n1 * tstride, w);
 #pragma unroll
-      for (int k = 1; k < R; ++k) v[k] = cmulconj(v[k], tw[n1 * k * tstride]);
+      for (int k = 1; k < R; ++k) v[k] = cmulconj(v[k], w[k]);
+    }
 #pragma unroll
     for (int k = 0; k < R; ++k) base[k * M] = v[k];
   }
@@ -296,5 +321,8 @@ __device__ __forceinline__ int wrap_index(long long j, int Q) {
   long long m = j % Q;
   return (int)(m < 0 ? m + Q : m);
 }
+
+// j mod Q for -Q <= j < 2Q (box-local nodes never wrap more than once)
+__device__ __forceinline__ int wrap_once(int j, int Q) { return j < 0 ? j + Q : (j >= Q ? j - Q : j); }
 
 }  // namespace mm

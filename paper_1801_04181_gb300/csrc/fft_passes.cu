@@ -33,7 +33,7 @@ constexpr float kPrefGain = 1.6076951545867362f; // -6 z1
 // fall in different shared-memory banks
 constexpr int kYChunk = 9;   // y pass (complex)
 constexpr int kXChunk = 17;  // x pass (real)
-constexpr int kBatch = 4;    // independent global loads in flight per thread
+constexpr int kLines = kRowsPerCta / 2;  // complex lines per CTA in the x passes
 
 cudaError_t init_fft_constants_passes() { return upload_roots(); }
 
@@ -43,7 +43,7 @@ cudaError_t init_fft_constants_passes() { return upload_roots(); }
 __device__ __forceinline__ void build_pref_table(int* tab, int n, int box_lo, int box_len, int start, int Q,
                                                  const FftPlanDev* P) {
   for (int j = threadIdx.x; j < n; j += blockDim.x) {
-    const int g = wrap_index((long long)box_lo + mirror_index(start - kPrefWarm + j, box_len), Q);
+    const int g = wrap_once(box_lo + mirror_index(start - kPrefWarm + j, box_len), Q);
     tab[j] = P ? fft_pos(g, *P) : g;
   }
 }
@@ -76,7 +76,7 @@ __device__ __forceinline__ f2 operator+(f2 a, f2 b) { return f2(a.x + b.x, a.y +
 __device__ __forceinline__ f2 operator*(float s, f2 a) { return f2(s * a.x, s * a.y); }
 
 // ------------------------------------------------------------------ x forward
-__global__ void __launch_bounds__(256) k_xfwd(const Launch<XFwdJob> Lc) {
+__global__ void __launch_bounds__(256, 3) k_xfwd(const Launch<XFwdJob> Lc) {
   extern __shared__ float2 sm[];
   const int j = find_job(Lc.tile_start, Lc.njobs, blockIdx.x);
   const XFwdJob& J = Lc.job[j];
@@ -87,70 +87,74 @@ __global__ void __launch_bounds__(256) k_xfwd(const Launch<XFwdJob> Lc) {
   const int nrows = min(kRowsPerCta, rows - r0);
   const int nlines = (nrows + 1) >> 1;
   const int nx = J.nx;
+  const float* row0 = J.m + (size_t)r0 * nx;
 
   if ((nx & 3) == 0) {
+    // all rows of the CTA per thread and step: 2 kLines float4 loads in flight
     const int n4 = nx >> 2;
-    const int n = nlines * n4;
-    for (int base = threadIdx.x; base < n; base += kBatch * blockDim.x) {
-      float4 a[kBatch], b[kBatch];
+    for (int x4 = threadIdx.x; x4 < n4; x4 += blockDim.x) {
+      float4 v[kRowsPerCta];
 #pragma unroll
-      for (int u = 0; u < kBatch; ++u) {
-        const int idx = base + u * blockDim.x;
-        a[u] = b[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (idx < n) {
-          const int line = idx / n4, x4 = idx - line * n4;
-          const int ra = r0 + 2 * line;
-          a[u] = __ldg(reinterpret_cast<const float4*>(J.m + (size_t)ra * nx) + x4);
-          if (2 * line + 1 < nrows) b[u] = __ldg(reinterpret_cast<const float4*>(J.m + (size_t)(ra + 1) * nx) + x4);
-        }
-      }
+      for (int r = 0; r < kRowsPerCta; ++r)
+        v[r] = r < nrows ? __ldg(reinterpret_cast<const float4*>(row0 + r * nx) + x4)
+                         : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-      for (int u = 0; u < kBatch; ++u) {
-        const int idx = base + u * blockDim.x;
-        if (idx < n) {
-          const int line = idx / n4, x4 = idx - line * n4;
-          float2* d = sm + line * Q + 4 * x4;
-          d[0] = make_float2(a[u].x, b[u].x);
-          d[1] = make_float2(a[u].y, b[u].y);
-          d[2] = make_float2(a[u].z, b[u].z);
-          d[3] = make_float2(a[u].w, b[u].w);
+      for (int l = 0; l < kLines; ++l) {
+        if (l < nlines) {
+          float2* d = sm + l * Q + 4 * x4;
+          const float4 a = v[2 * l], b = v[2 * l + 1];
+          d[0] = make_float2(a.x, b.x);
+          d[1] = make_float2(a.y, b.y);
+          d[2] = make_float2(a.z, b.z);
+          d[3] = make_float2(a.w, b.w);
         }
       }
     }
   } else {
-    for (int idx = threadIdx.x; idx < nlines * nx; idx += blockDim.x) {
-      const int line = idx / nx;
-      const int x = idx - line * nx;
-      const int ra = r0 + 2 * line;
-      const float a = __ldg(J.m + (size_t)ra * nx + x);
-      const float b = (2 * line + 1 < nrows) ? __ldg(J.m + (size_t)(ra + 1) * nx + x) : 0.f;
-      sm[line * Q + x] = make_float2(a, b);
+    for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+      float v[kRowsPerCta];
+#pragma unroll
+      for (int r = 0; r < kRowsPerCta; ++r) v[r] = r < nrows ? __ldg(row0 + r * nx + x) : 0.f;
+#pragma unroll
+      for (int l = 0; l < kLines; ++l)
+        if (l < nlines) sm[l * Q + x] = make_float2(v[2 * l], v[2 * l + 1]);
     }
   }
-  for (int line = 0; line < nlines; ++line)
-    for (int x = nx + threadIdx.x; x < Q; x += blockDim.x) sm[line * Q + x] = make_float2(0.f, 0.f);
+  for (int l = 0; l < nlines; ++l)
+    for (int x = nx + threadIdx.x; x < Q; x += blockDim.x) sm[l * Q + x] = make_float2(0.f, 0.f);
   // DIF positions of k and Q - k for every kx <= Q/2
-  int2* ptab = reinterpret_cast<int2*>(sm + (size_t)(kRowsPerCta / 2) * Q);
+  int2* ptab = reinterpret_cast<int2*>(sm + kLines * Q);
   for (int kx = threadIdx.x; kx < J.kxh; kx += blockDim.x)
     ptab[kx] = make_int2(fft_pos(kx, J.fx.plan), fft_pos(kx == 0 ? 0 : Q - kx, J.fx.plan));
   __syncthreads();
   fft_smem<float2>(sm, Q, nlines, J.fx.plan, J.fx.tw_f, kFwdDif, 0, blockDim.x);
 
   // Z = A + iB:  A_k = (Z_k + conj Z_{Q-k}) / 2,  B_k = (Z_k - conj Z_{Q-k}) / (2i)
-  for (int idx = threadIdx.x; idx < J.kxh * nlines; idx += blockDim.x) {
-    const int kx = nlines == 4 ? idx >> 2 : idx / nlines;
-    const int line = idx - kx * nlines;
+  // thread -> (kx, line) with the line fastest: a warp writes 8 runs of 64 bytes
+  const int ny = J.ny;
+  const int pa0 = r0 / ny;
+  const bool pairs = (ny & 1) == 0 && (nrows & 1) == 0;  // both rows of a line in one plane, 16-B aligned
+  const int n = J.kxh * nlines;
+  for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
+    const int kx = nlines == kLines ? idx / kLines : idx / nlines;
+    const int l = idx - kx * nlines;
     const int2 pp = ptab[kx];
-    const float2 Zk = sm[line * Q + pp.x];
-    const float2 Zm = sm[line * Q + pp.y];
-    const int ra = r0 + 2 * line;
-    const int pa = ra / J.ny, ya = ra - pa * J.ny;
-    J.out[((size_t)pa * J.kxh + kx) * J.ny + ya] = make_float2(0.5f * (Zk.x + Zm.x), 0.5f * (Zk.y - Zm.y));
-    if (2 * line + 1 < nrows) {
-      const int rb = ra + 1;
-      const int pb = rb / J.ny, yb = rb - pb * J.ny;
-      J.out[((size_t)pb * J.kxh + kx) * J.ny + yb] =
-          make_float2(0.5f * (Zk.y + Zm.y), -0.5f * (Zk.x - Zm.x));
+    const float2 Zk = sm[l * Q + pp.x];
+    const float2 Zm = sm[l * Q + pp.y];
+    const float2 A = make_float2(0.5f * (Zk.x + Zm.x), 0.5f * (Zk.y - Zm.y));
+    const float2 B = make_float2(0.5f * (Zk.y + Zm.y), -0.5f * (Zk.x - Zm.x));
+    int pa = pa0, ya = r0 + 2 * l - pa0 * ny;
+    while (ya >= ny) { ++pa; ya -= ny; }
+    float2* dst = J.out + ((size_t)pa * J.kxh + kx) * ny + ya;
+    if (pairs) {
+      *reinterpret_cast<float4*>(dst) = make_float4(A.x, A.y, B.x, B.y);
+    } else {
+      *dst = A;
+      if (2 * l + 1 < nrows) {
+        int pb = pa, yb = ya + 1;
+        if (yb >= ny) { ++pb; yb -= ny; }
+        J.out[((size_t)pb * J.kxh + kx) * ny + yb] = B;
+      }
     }
   }
 }
@@ -162,31 +166,83 @@ __device__ __forceinline__ float2 kmul(float v, bool imag, float2 m) {
 __device__ __forceinline__ void cacc(float2& a, float2 b) { a.x += b.x; a.y += b.y; }
 
 template <int NZ>
+__device__ __forceinline__ void load_pair(const float2* sm, int Q, int p0, int p1, float2 (*mh)[3][NZ]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int z = 0; z < NZ; ++z) {
+      mh[0][c][z] = sm[(c * NZ + z) * Q + p0];
+      mh[1][c][z] = sm[(c * NZ + z) * Q + p1];
+    }
+}
+
+// Spectral products at every (ky, Qy - ky) pair of one kx column.  The
+// potential planes go first: they land beyond the input planes whenever the
+// demag planes are produced too, which then overwrite the inputs in place.
+// Each thread issues all of its kernel-spectrum loads before it computes.
+template <int NZ>
 __device__ __forceinline__ void ypass_mix(const YJob& J, float2* sm, int kx, int Q, int nH) {
+  // output planes per batch of kernel loads (about 40 values in flight)
+  constexpr int OB = 40 / (3 * NZ) > 0 ? 40 / (3 * NZ) : 1;
   const size_t kstride = (size_t)J.kxh * J.kyq;  // one stored kernel plane
   const int half = Q >> 1;
+  if (J.do_C) {
+    for (int kyq = threadIdx.x; kyq <= half; kyq += blockDim.x) {
+      const bool two = kyq != 0 && 2 * kyq != Q;
+      const size_t koff = (size_t)kx * J.kyq + kyq;
+      const int p0 = fft_pos(kyq, J.fy.plan);
+      const int p1 = two ? fft_pos(Q - kyq, J.fy.plan) : p0;
+      float2 mh[2][3][NZ];
+      load_pair<NZ>(sm, Q, p0, p1, mh);  // before any output overwrites an input plane
+      for (int ob = 0; ob < J.n_out; ob += OB) {
+        float tv[OB][NZ][3];
+#pragma unroll
+        for (int o = 0; o < OB; ++o)
+#pragma unroll
+          for (int jz = 0; jz < NZ; ++jz)
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+              tv[o][jz][c] = ob + o < J.n_out
+                                 ? __ldg(J.Tq + (size_t)(((ob + o) * NZ + jz) * 3 + c) * kstride + koff)
+                                 : 0.f;
+        // c(o) = sum_jz sum_c T_c(o, jz) m_c(jz); T = Ms W (S spectra) / (Qx Qy)
+#pragma unroll
+        for (int o = 0; o < OB; ++o) {
+          if (ob + o >= J.n_out) break;
+          float2 acc0 = make_float2(0.f, 0.f), acc1 = acc0;
+#pragma unroll
+          for (int jz = 0; jz < NZ; ++jz) {
+            const float tx = tv[o][jz][0], ty = tv[o][jz][1], tz = tv[o][jz][2];
+            cacc(acc0, kmul(tx, true, mh[0][0][jz]));
+            cacc(acc0, kmul(ty, true, mh[0][1][jz]));
+            cacc(acc0, kmul(tz, false, mh[0][2][jz]));
+            cacc(acc1, kmul(tx, true, mh[1][0][jz]));
+            cacc(acc1, kmul(-ty, true, mh[1][1][jz]));
+            cacc(acc1, kmul(tz, false, mh[1][2][jz]));
+          }
+          sm[(nH + ob + o) * Q + p0] = acc0;
+          if (two) sm[(nH + ob + o) * Q + p1] = acc1;
+        }
+      }
+    }
+  }
+  if (!J.do_H) return;
   for (int kyq = threadIdx.x; kyq <= half; kyq += blockDim.x) {
     // the two frequencies ky = kyq and Qy - kyq share every stored kernel value;
     // the second has the odd-in-y components negated
     const bool two = kyq != 0 && 2 * kyq != Q;
+    const size_t koff = (size_t)kx * J.kyq + kyq;
     const int p0 = fft_pos(kyq, J.fy.plan);
     const int p1 = two ? fft_pos(Q - kyq, J.fy.plan) : p0;
-    const size_t koff = (size_t)kx * J.kyq + kyq;
-    float2 mh[2][3][NZ];
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-      for (int z = 0; z < NZ; ++z) {
-        mh[0][c][z] = sm[(c * NZ + z) * Q + p0];
-        mh[1][c][z] = sm[(c * NZ + z) * Q + p1];
-      }
-    if (J.do_H) {
+    {
       // H_a(iz) = sum_jz sum_b Ns_ab(iz - jz) m_b(jz); Ns = -Ms N / (Qx Qy)
       float nv[6][NZ];
 #pragma unroll
       for (int comp = 0; comp < 6; ++comp)
 #pragma unroll
         for (int dz = 0; dz < NZ; ++dz) nv[comp][dz] = __ldg(J.Nq + (size_t)(comp * NZ + dz) * kstride + koff);
+      float2 mh[2][3][NZ];
+      load_pair<NZ>(sm, Q, p0, p1, mh);
 #pragma unroll
       for (int side = 0; side < 2; ++side) {
         const float fy = side ? -1.f : 1.f;
@@ -212,115 +268,82 @@ __device__ __forceinline__ void ypass_mix(const YJob& J, float2* sm, int kx, int
         }
       }
     }
-    if (J.do_C) {
-      // c(o) = sum_jz sum_c T_c(o, jz) m_c(jz); T = Ms W (S spectra) / (Qx Qy)
-      for (int o = 0; o < J.n_out; ++o) {
-        float2 acc0 = make_float2(0.f, 0.f), acc1 = acc0;
-#pragma unroll
-        for (int jz = 0; jz < NZ; ++jz) {
-          const float* base = J.Tq + (size_t)((o * NZ + jz) * 3) * kstride + koff;
-          const float tx = __ldg(base), ty = __ldg(base + kstride), tz = __ldg(base + 2 * kstride);
-          cacc(acc0, kmul(tx, true, mh[0][0][jz]));
-          cacc(acc0, kmul(ty, true, mh[0][1][jz]));
-          cacc(acc0, kmul(tz, false, mh[0][2][jz]));
-          cacc(acc1, kmul(tx, true, mh[1][0][jz]));
-          cacc(acc1, kmul(-ty, true, mh[1][1][jz]));
-          cacc(acc1, kmul(tz, false, mh[1][2][jz]));
-        }
-        sm[(nH + o) * Q + p0] = acc0;
-        if (two) sm[(nH + o) * Q + p1] = acc1;
-      }
-    }
   }
 }
 
-__global__ void __launch_bounds__(256) k_ypass(const Launch<YJob> Lc) {
+// One CTA per kx; every job of a launch has NZ layers.
+template <int NZ>
+__global__ void __launch_bounds__(256, NZ <= 2 ? 3 : 2) k_ypass(const Launch<YJob> Lc) {
+  constexpr int Pin = 3 * NZ;
   extern __shared__ float2 sm[];
   const int j = find_job(Lc.tile_start, Lc.njobs, blockIdx.x);
   const YJob& J = Lc.job[j];
   const int kx = blockIdx.x - Lc.tile_start[j];
   const int Q = J.fy.plan.L;
-  const int nz = J.nz;
-  const int Pin = 3 * nz;
-  const int nH = J.do_H ? 3 * nz : 0;
+  const int nH = J.do_H ? Pin : 0;
   const int Pout = nH + (J.do_C ? J.n_out : 0);
-  int* tab = reinterpret_cast<int*>(sm + (size_t)max(Pin, Pout) * Q);
+  int* tab = reinterpret_cast<int*>(sm + max(Pin, Pout) * Q);
   const int ny = J.ny;
+  const float2* col0 = J.in + (size_t)kx * ny;
+  const size_t pstride = (size_t)J.kxh * ny;  // one input plane
 
   if ((ny & 1) == 0) {
+    // one float4 (two complex rows) of every plane per thread and step
     const int n2 = ny >> 1;
-    const int n = Pin * n2;
-    for (int base = threadIdx.x; base < n; base += kBatch * blockDim.x) {
-      float4 v[kBatch];
+    for (int y2 = threadIdx.x; y2 < n2; y2 += blockDim.x) {
+      float4 v[Pin];
 #pragma unroll
-      for (int u = 0; u < kBatch; ++u) {
-        const int idx = base + u * blockDim.x;
-        if (idx < n) {
-          const int p = idx / n2, y2 = idx - p * n2;
-          v[u] = *(reinterpret_cast<const float4*>(J.in + ((size_t)p * J.kxh + kx) * ny) + y2);
-        }
-      }
+      for (int p = 0; p < Pin; ++p) v[p] = *(reinterpret_cast<const float4*>(col0 + p * pstride) + y2);
 #pragma unroll
-      for (int u = 0; u < kBatch; ++u) {
-        const int idx = base + u * blockDim.x;
-        if (idx < n) {
-          const int p = idx / n2, y2 = idx - p * n2;
-          sm[p * Q + 2 * y2] = make_float2(v[u].x, v[u].y);
-          sm[p * Q + 2 * y2 + 1] = make_float2(v[u].z, v[u].w);
-        }
+      for (int p = 0; p < Pin; ++p) {
+        sm[p * Q + 2 * y2] = make_float2(v[p].x, v[p].y);
+        sm[p * Q + 2 * y2 + 1] = make_float2(v[p].z, v[p].w);
       }
     }
   } else {
-    for (int idx = threadIdx.x; idx < Pin * ny; idx += blockDim.x) {
-      const int p = idx / ny;
-      const int y = idx - p * ny;
-      sm[p * Q + y] = J.in[((size_t)p * J.kxh + kx) * ny + y];
+    for (int y = threadIdx.x; y < ny; y += blockDim.x) {
+      float2 v[Pin];
+#pragma unroll
+      for (int p = 0; p < Pin; ++p) v[p] = col0[p * pstride + y];
+#pragma unroll
+      for (int p = 0; p < Pin; ++p) sm[p * Q + y] = v[p];
     }
   }
-  const int pad = Q - ny;
-  for (int idx = threadIdx.x; idx < Pin * pad; idx += blockDim.x) {
-    const int p = idx / pad;
-    sm[p * Q + ny + (idx - p * pad)] = make_float2(0.f, 0.f);
-  }
+  for (int y = ny + threadIdx.x; y < Q; y += blockDim.x)
+#pragma unroll
+    for (int p = 0; p < Pin; ++p) sm[p * Q + y] = make_float2(0.f, 0.f);
   if (J.do_C) build_pref_table(tab, J.r + 2 * kPrefWarm + kYChunk, J.box_lo, J.box_len, J.start, Q, nullptr);
   __syncthreads();
   fft_smem<float2>(sm, Q, Pin, J.fy.plan, J.fy.tw_f, kFwdDif, 0, blockDim.x);
-
-  switch (nz) {
-    case 1: ypass_mix<1>(J, sm, kx, Q, nH); break;
-    case 2: ypass_mix<2>(J, sm, kx, Q, nH); break;
-    case 3: ypass_mix<3>(J, sm, kx, Q, nH); break;
-    default: ypass_mix<4>(J, sm, kx, Q, nH); break;
-  }
+  ypass_mix<NZ>(J, sm, kx, Q, nH);
   __syncthreads();
   fft_smem<float2>(sm, Q, Pout, J.fy.plan, J.fy.tw_f, kInvDit, 0, blockDim.x);
 
   if (J.do_H) {
-    for (int idx = threadIdx.x; idx < nH * ny; idx += blockDim.x) {
-      const int p = idx / ny;
-      const int y = idx - p * ny;
-      J.outH[((size_t)p * J.kxh + kx) * ny + y] = sm[p * Q + y];
-    }
+    float2* out0 = J.outH + (size_t)kx * ny;
+    for (int y = threadIdx.x; y < ny; y += blockDim.x)
+#pragma unroll
+      for (int p = 0; p < Pin; ++p) out0[p * pstride + y] = sm[p * Q + y];
   }
   if (J.do_C) {
-    float2* outC = J.outC;
     const int r = J.r;
+    float2* out0 = J.outC + (size_t)kx * r;
+    const size_t ostride = (size_t)J.kxh * r;
     if (J.fir) {
       const int nch = (r + kYChunk - 1) / kYChunk;
       for (int idx = threadIdx.x; idx < J.n_out * nch; idx += blockDim.x) {
         const int o = idx / nch;
         const int k0 = (idx - o * nch) * kYChunk;
-        const float2* col = sm + (size_t)(nH + o) * Q;
-        float2* dst = outC + ((size_t)o * J.kxh + kx) * r;
+        const float2* col = sm + (nH + o) * Q;
+        float2* dst = out0 + o * ostride;
         prefilter_chunk<kYChunk, f2>(
             k0, r, [&](int jj) { return f2(col[tab[jj]]); },
             [&](int k, f2 v) { dst[k] = make_float2(v.x, v.y); });
       }
     } else {
-      for (int idx = threadIdx.x; idx < J.n_out * r; idx += blockDim.x) {
-        const int o = idx / r;
-        const int k = idx - o * r;
-        outC[((size_t)o * J.kxh + kx) * r + k] = sm[(size_t)(nH + o) * Q + tab[k + kPrefWarm]];
+      for (int k = threadIdx.x; k < r; k += blockDim.x) {
+        const int t = tab[k + kPrefWarm];
+        for (int o = 0; o < J.n_out; ++o) out0[o * ostride + k] = sm[(nH + o) * Q + t];
       }
     }
   }
@@ -333,7 +356,7 @@ __device__ __forceinline__ void xinv_put(float2* sm, int line, int Q, int kx, fl
   if (kx > 0 && 2 * kx != Q) sm[line * Q + Q - kx] = make_float2(A.x + B.y, B.x - A.y);
 }
 
-__global__ void __launch_bounds__(256) k_xinv(const Launch<XInvJob> Lc) {
+__global__ void __launch_bounds__(256, 3) k_xinv(const Launch<XInvJob> Lc) {
   extern __shared__ float2 sm[];
   const int j = find_job(Lc.tile_start, Lc.njobs, blockIdx.x);
   const XInvJob& J = Lc.job[j];
@@ -344,45 +367,47 @@ __global__ void __launch_bounds__(256) k_xinv(const Launch<XInvJob> Lc) {
   const int r0 = tile * kRowsPerCta;
   const int nrows = min(kRowsPerCta, rows - r0);
   const int nlines = (nrows + 1) >> 1;
-  int* tab = reinterpret_cast<int*>(sm + (size_t)(kRowsPerCta / 2) * Q);
+  int* tab = reinterpret_cast<int*>(sm + kLines * Q);
 
+  // input row r of this CTA (its kx = 0 element)
+  const int pa0 = r0 / rpp;
+  auto rowptr = [&](int r) {
+    int p = pa0, y = min(r0 + r, rows - 1) - pa0 * rpp;
+    while (y >= rpp) { ++p; y -= rpp; }
+    return J.in + (size_t)p * J.kxh * rpp + y;
+  };
+  const bool paired = (rpp & 1) == 0 && (nrows & 1) == 0;  // row pairs adjacent, 16-byte aligned
   const int n = J.kxh * nlines;
-  if ((rpp & 1) == 0 && (nrows & 1) == 0) {
-    // row pairs are adjacent in memory and 16-byte aligned: one float4 per (kx, line)
-    for (int base = threadIdx.x; base < n; base += kBatch * blockDim.x) {
-      float4 v[kBatch];
+  if (paired) {
+    // thread -> (kx, line), line fastest: a warp reads 8 runs of 64 bytes;
+    // kBatchX such reads in flight per thread
+    constexpr int kBatchX = 4;
+    for (int base = threadIdx.x; base < n; base += kBatchX * blockDim.x) {
+      float4 v[kBatchX];
 #pragma unroll
-      for (int u = 0; u < kBatch; ++u) {
+      for (int u = 0; u < kBatchX; ++u) {
         const int idx = base + u * blockDim.x;
         if (idx < n) {
-          const int kx = idx / nlines, line = idx - kx * nlines;
-          const int ra = r0 + 2 * line;
-          const int pa = ra / rpp, ya = ra - pa * rpp;
-          v[u] = *reinterpret_cast<const float4*>(J.in + ((size_t)pa * J.kxh + kx) * rpp + ya);
+          const int kx = idx / nlines, l = idx - kx * nlines;
+          v[u] = *reinterpret_cast<const float4*>(rowptr(2 * l) + (size_t)kx * rpp);
         }
       }
 #pragma unroll
-      for (int u = 0; u < kBatch; ++u) {
+      for (int u = 0; u < kBatchX; ++u) {
         const int idx = base + u * blockDim.x;
         if (idx < n) {
-          const int kx = idx / nlines, line = idx - kx * nlines;
-          xinv_put(sm, line, Q, kx, make_float2(v[u].x, v[u].y), make_float2(v[u].z, v[u].w));
+          const int kx = idx / nlines, l = idx - kx * nlines;
+          xinv_put(sm, l, Q, kx, make_float2(v[u].x, v[u].y), make_float2(v[u].z, v[u].w));
         }
       }
     }
   } else {
     for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
-      const int kx = idx / nlines, line = idx - kx * nlines;
-      const int ra = r0 + 2 * line;
-      const int pa = ra / rpp, ya = ra - pa * rpp;
-      const float2 A = J.in[((size_t)pa * J.kxh + kx) * rpp + ya];
-      float2 B = make_float2(0.f, 0.f);
-      if (2 * line + 1 < nrows) {
-        const int rb = ra + 1;
-        const int pb = rb / rpp, yb = rb - pb * rpp;
-        B = J.in[((size_t)pb * J.kxh + kx) * rpp + yb];
-      }
-      xinv_put(sm, line, Q, kx, A, B);
+      const int kx = idx / nlines, l = idx - kx * nlines;
+      const size_t off = (size_t)kx * rpp;
+      const float2 a = rowptr(2 * l)[off];
+      const float2 b = 2 * l + 1 < nrows ? rowptr(2 * l + 1)[off] : make_float2(0.f, 0.f);
+      xinv_put(sm, l, Q, kx, a, b);
     }
   }
   build_pref_table(tab, J.out_len + 2 * kPrefWarm + kXChunk, J.box_lo, J.box_len, J.start, Q, &J.fx.plan);
@@ -391,22 +416,24 @@ __global__ void __launch_bounds__(256) k_xinv(const Launch<XInvJob> Lc) {
   fft_smem<float2>(sm, Q, nlines, J.fx.plan, J.fx.tw_f, kInvDif, 0, blockDim.x);
 
   const int r = J.out_len;
+  float* out0 = J.out + (size_t)r0 * r;
   if (J.fir) {
     const int nch = (r + kXChunk - 1) / kXChunk;
     for (int idx = threadIdx.x; idx < nrows * nch; idx += blockDim.x) {
       const int rl = idx / nch;
       const int k0 = (idx - rl * nch) * kXChunk;
-      const float* line = reinterpret_cast<const float*>(sm + (size_t)(rl >> 1) * Q) + (rl & 1);
-      float* dst = J.out + (size_t)(r0 + rl) * r;
+      const float* line = reinterpret_cast<const float*>(sm + (rl >> 1) * Q) + (rl & 1);
+      float* dst = out0 + rl * r;
       prefilter_chunk<kXChunk, float>(
           k0, r, [&](int jj) { return line[2 * tab[jj]]; }, [&](int k, float v) { dst[k] = v; });
     }
   } else {
-    for (int idx = threadIdx.x; idx < nrows * r; idx += blockDim.x) {
-      const int rl = idx / r;
-      const int k = idx - rl * r;
-      const float* line = reinterpret_cast<const float*>(sm + (size_t)(rl >> 1) * Q) + (rl & 1);
-      J.out[(size_t)(r0 + rl) * r + k] = line[2 * tab[k + kPrefWarm]];
+    for (int k = threadIdx.x; k < r; k += blockDim.x) {
+      const int t = 2 * tab[k + kPrefWarm];
+      const float* base = reinterpret_cast<const float*>(sm) + t;
+#pragma unroll
+      for (int rl = 0; rl < kRowsPerCta; ++rl)
+        if (rl < nrows) out0[rl * r + k] = base[(rl >> 1) * 2 * Q + (rl & 1)];
     }
   }
 }
@@ -415,8 +442,7 @@ __global__ void __launch_bounds__(256) k_xinv(const Launch<XInvJob> Lc) {
 size_t ypass_table_bytes(int r) { return sizeof(int) * (size_t)(r + 2 * kPrefWarm + kYChunk); }
 
 static size_t xinv_smem(int Qmax, int out_max) {
-  return (size_t)(kRowsPerCta / 2) * Qmax * sizeof(float2) +
-         sizeof(int) * (size_t)(out_max + 2 * kPrefWarm + kXChunk);
+  return (size_t)kLines * Qmax * sizeof(float2) + sizeof(int) * (size_t)(out_max + 2 * kPrefWarm + kXChunk);
 }
 
 static void max_carveout(const void* f) {
@@ -424,7 +450,7 @@ static void max_carveout(const void* f) {
 }
 
 cudaError_t launch_xfwd(const Launch<XFwdJob>& L, int Qmax, cudaStream_t st) {
-  const size_t smem = (size_t)(kRowsPerCta / 2) * Qmax * sizeof(float2) + sizeof(int2) * (size_t)(Qmax / 2 + 1);
+  const size_t smem = (size_t)kLines * Qmax * sizeof(float2) + sizeof(int2) * (size_t)(Qmax / 2 + 1);
   max_carveout((const void*)k_xfwd);
   cudaError_t e = cudaFuncSetAttribute(k_xfwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -434,14 +460,38 @@ cudaError_t launch_xfwd(const Launch<XFwdJob>& L, int Qmax, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_ypass(const Launch<YJob>& L, size_t smem, cudaStream_t st) {
-  max_carveout((const void*)k_ypass);
-  cudaError_t e = cudaFuncSetAttribute(k_ypass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+template <int NZ>
+static cudaError_t launch_ypass_nz(const Launch<YJob>& L, size_t smem, cudaStream_t st) {
+  max_carveout((const void*)k_ypass<NZ>);
+  cudaError_t e = cudaFuncSetAttribute(k_ypass<NZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int grid = L.tile_start[L.njobs];
   if (grid == 0) return cudaSuccess;
-  k_ypass<<<grid, 256, smem, st>>>(L);
+  k_ypass<NZ><<<grid, 256, smem, st>>>(L);
   return cudaGetLastError();
+}
+
+// Jobs of different layer counts go to separate launches of the matching kernel.
+cudaError_t launch_ypass(const Launch<YJob>& L, size_t smem, cudaStream_t st) {
+  for (int nz = 1; nz <= kMaxNz; ++nz) {
+    Launch<YJob> S{};
+    int tiles = 0;
+    for (int i = 0; i < L.njobs; ++i) {
+      if (L.job[i].nz != nz) continue;
+      S.job[S.njobs] = L.job[i];
+      S.tile_start[S.njobs] = tiles;
+      tiles += L.tile_start[i + 1] - L.tile_start[i];
+      ++S.njobs;
+    }
+    if (S.njobs == 0) continue;
+    S.tile_start[S.njobs] = tiles;
+    cudaError_t e = nz == 1   ? launch_ypass_nz<1>(S, smem, st)
+                    : nz == 2 ? launch_ypass_nz<2>(S, smem, st)
+                    : nz == 3 ? launch_ypass_nz<3>(S, smem, st)
+                              : launch_ypass_nz<4>(S, smem, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_xinv(const Launch<XInvJob>& L, int Qmax, cudaStream_t st) {

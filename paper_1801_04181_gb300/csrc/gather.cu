@@ -15,6 +15,7 @@
 // and F (F_t = -mu0 V Ms_t sum Hess(phi) m).
 #include <cuda_runtime.h>
 
+#include "mech.cuh"
 #include "mm_internal.h"
 
 namespace mm {
@@ -119,7 +120,7 @@ __device__ __forceinline__ void gather_column(const GatherJob& J, const float* A
   }
 }
 
-__global__ void __launch_bounds__(TX * TY) k_gather(const Launch<GatherJob> Lc) {
+__global__ void __launch_bounds__(TX * TY, 3) k_gather(const Launch<GatherJob> Lc, const MechParams P, int* ticket) {
   extern __shared__ float gsm[];
   __shared__ float w_s[3][12];
   __shared__ int shift_s[3];
@@ -220,6 +221,8 @@ __global__ void __launch_bounds__(TX * TY) k_gather(const Launch<GatherJob> Lc) 
     for (int w = 0; w < TX * TY / 32; ++w) s += red_s[w][threadIdx.x];
     J.partial[(size_t)tile * 4 + threadIdx.x] = s;
   }
+  // the last block reduces the forces and, during a step, advances the slider
+  if (P.state && last_block(ticket, (int)gridDim.x)) mech_block(P);
 }
 
 int gather_tiles(int nx, int ny) { return ((nx + TX - 1) / TX) * ((ny + TY - 1) / TY); }
@@ -229,7 +232,8 @@ size_t gather_smem(int nz) {
   return sizeof(float) * ((size_t)cz * (TY + 3) * (TX + 3) + 3 * (size_t)cz * (TY + 3) * TX);
 }
 
-cudaError_t launch_gather(const Launch<GatherJob>& L, int nz_max, cudaStream_t st) {
+cudaError_t launch_gather(const Launch<GatherJob>& L, int nz_max, const MechParams& P, int* ticket,
+                          cudaStream_t st) {
   const size_t smem = gather_smem(nz_max);
   cudaFuncSetAttribute((const void*)k_gather, cudaFuncAttributePreferredSharedMemoryCarveout,
                        cudaSharedmemCarveoutMaxShared);
@@ -237,7 +241,7 @@ cudaError_t launch_gather(const Launch<GatherJob>& L, int nz_max, cudaStream_t s
   if (e != cudaSuccess) return e;
   const int grid = L.tile_start[L.njobs];
   if (grid == 0) return cudaSuccess;
-  k_gather<<<grid, TX * TY, smem, st>>>(L);
+  k_gather<<<grid, TX * TY, smem, st>>>(L, P, ticket);
   return cudaGetLastError();
 }
 

@@ -12,6 +12,7 @@
 // state m x'' = k (v_d t + x0 - x) - gamma_v m x' + F . e with the same tableau.
 #include <cuda_runtime.h>
 
+#include "mech.cuh"
 #include "mm_internal.h"
 
 namespace mm {
@@ -21,7 +22,7 @@ __device__ __forceinline__ float warp_max(float v) {
   return v;
 }
 
-__global__ void __launch_bounds__(256) k_stage(const Launch<StageJob> Lc) {
+__global__ void __launch_bounds__(256) k_stage(const Launch<StageJob> Lc, const MechParams Perr, int* ticket) {
   __shared__ float red[8];
   const int j = find_job(Lc.tile_start, Lc.njobs, blockIdx.x);
   const StageJob& J = Lc.job[j];
@@ -107,6 +108,8 @@ __global__ void __launch_bounds__(256) k_stage(const Launch<StageJob> Lc) {
       for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v = fmaxf(v, red[w]);
       J.err_partial[tile] = v;
     }
+    // the last block reduces the error norm of the attempt
+    if (Perr.state && last_block(ticket, (int)gridDim.x)) mech_block(Perr);
   }
 }
 
@@ -133,106 +136,12 @@ __global__ void __launch_bounds__(256) k_normalise(const Launch<CombineJob> Lc) 
   J.out[i] = a * inv; J.out[J.n + i] = b * inv; J.out[2 * J.n + i] = c * inv;
 }
 
-__device__ double block_sum(double v, double* sh) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
-  __syncthreads();
-  double s = 0.0;
-  if (threadIdx.x == 0)
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
-  __syncthreads();
-  return s;  // valid in thread 0
-}
+__global__ void __launch_bounds__(256) k_mech(const MechParams P) { mech_block(P); }
 
-__global__ void __launch_bounds__(256) k_mech(const MechParams P) {
-  __shared__ double sh[8][9];
-  MechState* S = P.state;
-  // Eq. (EQForce) reductions in a fixed order: thread t sums tiles t, t+256, ...
-  // then a fixed warp-shuffle and cross-warp order (deterministic)
-  double v[9];
-  for (int d = 0; d < 2; ++d) {
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-    if (P.partial[d]) {
-      const double4* pp = reinterpret_cast<const double4*>(P.partial[d]);
-      for (int t = threadIdx.x; t < P.ntiles[d]; t += blockDim.x) {
-        const double4 q = pp[t];
-        a0 += q.x; a1 += q.y; a2 += q.z; a3 += q.w;
-      }
-    }
-    v[4 * d + 0] = a0; v[4 * d + 1] = a1; v[4 * d + 2] = a2; v[4 * d + 3] = a3;
-  }
-  float emax = 0.f;
-  if (P.mode == 0 && P.stage == 7)
-    for (int d = 0; d < 2; ++d)
-      if (P.err_partial[d])
-        for (int t = threadIdx.x; t < P.nerr[d]; t += blockDim.x) emax = fmaxf(emax, P.err_partial[d][t]);
-  v[8] = emax;
-#pragma unroll
-  for (int c = 0; c < 8; ++c)
-    for (int o = 16; o > 0; o >>= 1) v[c] += __shfl_down_sync(0xffffffffu, v[c], o);
-  for (int o = 16; o > 0; o >>= 1) v[8] = fmax(v[8], __shfl_down_sync(0xffffffffu, v[8], o));
-  if ((threadIdx.x & 31) == 0)
-#pragma unroll
-    for (int c = 0; c < 9; ++c) sh[threadIdx.x >> 5][c] = v[c];
-  __syncthreads();
-  if (threadIdx.x != 0) return;
-  double red[2][4];
-  for (int c = 0; c < 8; ++c) {
-    double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w][c];
-    red[c / 4][c % 4] = s;
-  }
-  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) emax = fmaxf(emax, (float)sh[w][8]);
-
-  if (P.mode == 0 || P.mode == 1) {
-    for (int c = 0; c < 3; ++c) {
-      if (P.partial[0]) S->F_slider[c] = P.Fscale[0] * red[0][c];
-      if (P.partial[1]) S->F_base[c] = P.Fscale[1] * red[1][c];
-    }
-    if (P.partial[0]) S->E_slider = P.Escale[0] * red[0][3];
-    if (P.partial[1]) S->E_base = P.Escale[1] * red[1][3];
-  }
-  const double dt = P.dt;
-  if (P.mode == 0) {
-    const int i = P.stage;
-    const double Fe = S->F_slider[0] * P.e[0] + S->F_slider[1] * P.e[1] + S->F_slider[2] * P.e[2];
-    if (P.move) {
-      S->kx[i - 1] = S->vs;
-      S->kv[i - 1] = (P.k_spring * (P.v_drive * S->ts + P.x0_spring - S->xs) -
-                      P.gamma_v * P.mass * S->vs + Fe) / P.mass;
-    } else {
-      S->kx[i - 1] = 0.0;
-      S->kv[i - 1] = 0.0;
-    }
-    if (i < 7) {
-      double xs = S->x, vs = S->v;
-      for (int jj = 0; jj < i; ++jj) {
-        xs += dt * P.a[jj] * S->kx[jj];
-        vs += dt * P.a[jj] * S->kv[jj];
-      }
-      S->xs = xs; S->vs = vs; S->ts = S->t + P.c_next * dt;
-    } else {
-      S->err = emax;
-    }
-  } else if (P.mode == 2) {  // stage 2 input from a stored k1
-    S->xs = S->x + dt * P.a[0] * S->kx[0];
-    S->vs = S->v + dt * P.a[0] * S->kv[0];
-    S->ts = S->t + P.c_next * dt;
-  } else if (P.mode == 3) {  // accept: stage-7 input is the 5th-order solution
-    S->x = S->xs; S->v = S->vs; S->t = S->t + dt;
-    S->kx[0] = S->kx[6]; S->kv[0] = S->kv[6];
-    S->xs = S->x; S->vs = S->v; S->ts = S->t;
-  } else if (P.mode == 4) {  // restart an attempt from the accepted state
-    S->xs = S->x; S->vs = S->v; S->ts = S->t;
-  }
-  if (P.mode != 1)
-    for (int c = 0; c < 3; ++c) S->u[c] = P.u_base[c] + S->xs * P.e[c] * P.inv_d[c];
-}
-
-cudaError_t launch_stage(const Launch<StageJob>& L, cudaStream_t st) {
+cudaError_t launch_stage(const Launch<StageJob>& L, const MechParams& Perr, int* ticket, cudaStream_t st) {
   const int grid = L.tile_start[L.njobs];
   if (grid == 0) return cudaSuccess;
-  k_stage<<<grid, 256, 0, st>>>(L);
+  k_stage<<<grid, 256, 0, st>>>(L, Perr, ticket);
   return cudaGetLastError();
 }
 cudaError_t launch_combine(const Launch<CombineJob>& L, cudaStream_t st) {

@@ -134,7 +134,8 @@ struct MechParams {
   double Fscale[2], Escale[2];
   const float* err_partial[2];
   int nerr[2];
-  int mode;               // 0 RK stage, 1 forces only, 2 stage-2 input from k1, 3 accept, 4 restart
+  int mode;               // 0 RK stage, 1 forces only, 2 stage-2 input from k1, 3 accept,
+                          // 4 restart, 5 error norm of the attempt
   int stage;
   double dt;
   double a[7];            // a_{stage+1, j}
@@ -175,8 +176,9 @@ cudaError_t launch_ypass(const Launch<YJob>& L, size_t smem, cudaStream_t st);
 cudaError_t launch_xinv(const Launch<XInvJob>& L, int Qmax, cudaStream_t st);
 int gather_tiles(int nx, int ny);
 size_t gather_smem(int nz);
-cudaError_t launch_gather(const Launch<GatherJob>& L, int nz_max, cudaStream_t st);
-cudaError_t launch_stage(const Launch<StageJob>& L, cudaStream_t st);
+cudaError_t launch_gather(const Launch<GatherJob>& L, int nz_max, const MechParams& P, int* ticket,
+                          cudaStream_t st);
+cudaError_t launch_stage(const Launch<StageJob>& L, const MechParams& Perr, int* ticket, cudaStream_t st);
 cudaError_t launch_combine(const Launch<CombineJob>& L, cudaStream_t st);
 cudaError_t launch_normalise(const Launch<CombineJob>& L, cudaStream_t st);
 cudaError_t launch_mech(const MechParams& P, cudaStream_t st);

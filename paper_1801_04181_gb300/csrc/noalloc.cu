@@ -20,7 +20,7 @@
 
 #include <mutex>
 
-#include "../../include/mm.h"
+#include "mm.h"
 #include "mm_internal.h"
 
 namespace mm {
@@ -136,7 +136,8 @@ extern "C" mm_status mm_spline_field_noalloc(const float* coef_dev, const int co
   L.tile_start[0] = 0;
   L.tile_start[1] = ntiles;
   L.job[0] = J;
-  if (launch_gather(L, nz, st) != cudaSuccess) return MM_ECUDA;
+  const MechParams none{};  // reduction done by k_noalloc_reduce below
+  if (launch_gather(L, nz, none, nullptr, st) != cudaSuccess) return MM_ECUDA;
   const double mu0 = 4e-7 * 3.14159265358979323846;
   const double V = dx * dy * dz;
   k_noalloc_reduce<<<1, 256, 0, st>>>(ntiles, -mu0 * V * Ms, mu0 * V * Ms, FE_dev);
