@@ -34,6 +34,7 @@ constexpr float kPrefGain = 1.6076951545867362f; // -6 z1
 constexpr int kYChunk = 9;   // y pass (complex)
 constexpr int kXChunk = 17;  // x pass (real)
 constexpr int kLines = kRowsPerCta / 2;  // complex lines per CTA in the x passes
+constexpr int kLinePad = 4;              // float2 between lines of an x-pass CTA
 
 cudaError_t init_fft_constants_passes() { return upload_roots(); }
 
@@ -82,6 +83,7 @@ __global__ void __launch_bounds__(256, 3) k_xfwd(const Launch<XFwdJob> Lc) {
   const XFwdJob& J = Lc.job[j];
   const int tile = blockIdx.x - Lc.tile_start[j];
   const int Q = J.fx.plan.L;
+  const int ldl = Q + kLinePad;  // padded line stride: the lines start in different banks
   const int rows = 3 * J.nz * J.ny;
   const int r0 = tile * kRowsPerCta;
   const int nrows = min(kRowsPerCta, rows - r0);
@@ -101,7 +103,7 @@ __global__ void __launch_bounds__(256, 3) k_xfwd(const Launch<XFwdJob> Lc) {
 #pragma unroll
       for (int l = 0; l < kLines; ++l) {
         if (l < nlines) {
-          float2* d = sm + l * Q + 4 * x4;
+          float2* d = sm + l * ldl + 4 * x4;
           const float4 a = v[2 * l], b = v[2 * l + 1];
           d[0] = make_float2(a.x, b.x);
           d[1] = make_float2(a.y, b.y);
@@ -117,17 +119,18 @@ __global__ void __launch_bounds__(256, 3) k_xfwd(const Launch<XFwdJob> Lc) {
       for (int r = 0; r < kRowsPerCta; ++r) v[r] = r < nrows ? __ldg(row0 + r * nx + x) : 0.f;
 #pragma unroll
       for (int l = 0; l < kLines; ++l)
-        if (l < nlines) sm[l * Q + x] = make_float2(v[2 * l], v[2 * l + 1]);
+        if (l < nlines) sm[l * ldl + x] = make_float2(v[2 * l], v[2 * l + 1]);
     }
   }
   for (int l = 0; l < nlines; ++l)
-    for (int x = nx + threadIdx.x; x < Q; x += blockDim.x) sm[l * Q + x] = make_float2(0.f, 0.f);
+    for (int x = nx + threadIdx.x; x < Q; x += blockDim.x) sm[l * ldl + x] = make_float2(0.f, 0.f);
   // DIF positions of k and Q - k for every kx <= Q/2
-  int2* ptab = reinterpret_cast<int2*>(sm + kLines * Q);
+  ushort2* ptab = reinterpret_cast<ushort2*>(sm + kLines * ldl);  // Q < 65536
   for (int kx = threadIdx.x; kx < J.kxh; kx += blockDim.x)
-    ptab[kx] = make_int2(fft_pos(kx, J.fx.plan), fft_pos(kx == 0 ? 0 : Q - kx, J.fx.plan));
+    ptab[kx] = make_ushort2((unsigned short)fft_pos(kx, J.fx.plan),
+                            (unsigned short)fft_pos(kx == 0 ? 0 : Q - kx, J.fx.plan));
   __syncthreads();
-  fft_smem<float2>(sm, Q, nlines, J.fx.plan, J.fx.tw_f, kFwdDif, 0, blockDim.x);
+  fft_smem<float2>(sm, ldl, nlines, J.fx.plan, J.fx.tw_f, kFwdDif, 0, blockDim.x);
 
   // Z = A + iB:  A_k = (Z_k + conj Z_{Q-k}) / 2,  B_k = (Z_k - conj Z_{Q-k}) / (2i)
   // thread -> (kx, line) with the line fastest: a warp writes 8 runs of 64 bytes
@@ -138,9 +141,9 @@ __global__ void __launch_bounds__(256, 3) k_xfwd(const Launch<XFwdJob> Lc) {
   for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
     const int kx = nlines == kLines ? idx / kLines : idx / nlines;
     const int l = idx - kx * nlines;
-    const int2 pp = ptab[kx];
-    const float2 Zk = sm[l * Q + pp.x];
-    const float2 Zm = sm[l * Q + pp.y];
+    const ushort2 pp = ptab[kx];
+    const float2 Zk = sm[l * ldl + pp.x];
+    const float2 Zm = sm[l * ldl + pp.y];
     const float2 A = make_float2(0.5f * (Zk.x + Zm.x), 0.5f * (Zk.y - Zm.y));
     const float2 B = make_float2(0.5f * (Zk.y + Zm.y), -0.5f * (Zk.x - Zm.x));
     int pa = pa0, ya = r0 + 2 * l - pa0 * ny;
@@ -287,6 +290,20 @@ __global__ void __launch_bounds__(256, NZ <= 2 ? 3 : 2) k_ypass(const Launch<YJo
   const float2* col0 = J.in + (size_t)kx * ny;
   const size_t pstride = (size_t)J.kxh * ny;  // one input plane
 
+  // The kernel spectra of this kx column are read only after the forward FFT:
+  // start moving their lines into L2 now (one prefetch per 128-byte line).
+  {
+    const size_t kstride = (size_t)J.kxh * J.kyq;
+    const int lines = (J.kyq + 31) / 32;
+    const int nN = J.do_H ? 6 * NZ : 0;
+    const int nT = J.do_C ? 3 * NZ * J.n_out : 0;
+    for (int i = threadIdx.x; i < (nN + nT) * lines; i += blockDim.x) {
+      const int row = i / lines, ln = i - row * lines;
+      const float* p = row < nN ? J.Nq + (size_t)row * kstride : J.Tq + (size_t)(row - nN) * kstride;
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(p + (size_t)kx * J.kyq + 32 * ln));
+    }
+  }
+
   if ((ny & 1) == 0) {
     // one float4 (two complex rows) of every plane per thread and step
     const int n2 = ny >> 1;
@@ -350,10 +367,10 @@ __global__ void __launch_bounds__(256, NZ <= 2 ? 3 : 2) k_ypass(const Launch<YJo
 }
 
 // ------------------------------------------------------------------ x inverse
-__device__ __forceinline__ void xinv_put(float2* sm, int line, int Q, int kx, float2 A, float2 B) {
-  // Z_k = A_k + i B_k and Z_{Q-k} = conj(A_k) + i conj(B_k), natural order
-  sm[line * Q + kx] = make_float2(A.x - B.y, A.y + B.x);
-  if (kx > 0 && 2 * kx != Q) sm[line * Q + Q - kx] = make_float2(A.x + B.y, B.x - A.y);
+__device__ __forceinline__ void xinv_put(float2* sm, int off, int Q, int kx, float2 A, float2 B) {
+  // Z_k = A_k + i B_k and Z_{Q-k} = conj(A_k) + i conj(B_k), natural order; off = line start
+  sm[off + kx] = make_float2(A.x - B.y, A.y + B.x);
+  if (kx > 0 && 2 * kx != Q) sm[off + Q - kx] = make_float2(A.x + B.y, B.x - A.y);
 }
 
 __global__ void __launch_bounds__(256, 3) k_xinv(const Launch<XInvJob> Lc) {
@@ -362,12 +379,13 @@ __global__ void __launch_bounds__(256, 3) k_xinv(const Launch<XInvJob> Lc) {
   const XInvJob& J = Lc.job[j];
   const int tile = blockIdx.x - Lc.tile_start[j];
   const int Q = J.fx.plan.L;
+  const int ldl = Q + kLinePad;  // padded line stride: the lines start in different banks
   const int rpp = J.rows_per_plane;
   const int rows = J.planes * rpp;
   const int r0 = tile * kRowsPerCta;
   const int nrows = min(kRowsPerCta, rows - r0);
   const int nlines = (nrows + 1) >> 1;
-  int* tab = reinterpret_cast<int*>(sm + kLines * Q);
+  int* tab = reinterpret_cast<int*>(sm + kLines * ldl);
 
   // input row r of this CTA (its kx = 0 element)
   const int pa0 = r0 / rpp;
@@ -397,7 +415,7 @@ __global__ void __launch_bounds__(256, 3) k_xinv(const Launch<XInvJob> Lc) {
         const int idx = base + u * blockDim.x;
         if (idx < n) {
           const int kx = idx / nlines, l = idx - kx * nlines;
-          xinv_put(sm, l, Q, kx, make_float2(v[u].x, v[u].y), make_float2(v[u].z, v[u].w));
+          xinv_put(sm, l * ldl, Q, kx, make_float2(v[u].x, v[u].y), make_float2(v[u].z, v[u].w));
         }
       }
     }
@@ -407,13 +425,13 @@ __global__ void __launch_bounds__(256, 3) k_xinv(const Launch<XInvJob> Lc) {
       const size_t off = (size_t)kx * rpp;
       const float2 a = rowptr(2 * l)[off];
       const float2 b = 2 * l + 1 < nrows ? rowptr(2 * l + 1)[off] : make_float2(0.f, 0.f);
-      xinv_put(sm, l, Q, kx, a, b);
+      xinv_put(sm, l * ldl, Q, kx, a, b);
     }
   }
   build_pref_table(tab, J.out_len + 2 * kPrefWarm + kXChunk, J.box_lo, J.box_len, J.start, Q, &J.fx.plan);
   __syncthreads();
   // natural-order input, digit-reversed output: the table above maps through it
-  fft_smem<float2>(sm, Q, nlines, J.fx.plan, J.fx.tw_f, kInvDif, 0, blockDim.x);
+  fft_smem<float2>(sm, ldl, nlines, J.fx.plan, J.fx.tw_f, kInvDif, 0, blockDim.x);
 
   const int r = J.out_len;
   float* out0 = J.out + (size_t)r0 * r;
@@ -422,7 +440,7 @@ __global__ void __launch_bounds__(256, 3) k_xinv(const Launch<XInvJob> Lc) {
     for (int idx = threadIdx.x; idx < nrows * nch; idx += blockDim.x) {
       const int rl = idx / nch;
       const int k0 = (idx - rl * nch) * kXChunk;
-      const float* line = reinterpret_cast<const float*>(sm + (rl >> 1) * Q) + (rl & 1);
+      const float* line = reinterpret_cast<const float*>(sm + (rl >> 1) * ldl) + (rl & 1);
       float* dst = out0 + rl * r;
       prefilter_chunk<kXChunk, float>(
           k0, r, [&](int jj) { return line[2 * tab[jj]]; }, [&](int k, float v) { dst[k] = v; });
@@ -433,7 +451,7 @@ __global__ void __launch_bounds__(256, 3) k_xinv(const Launch<XInvJob> Lc) {
       const float* base = reinterpret_cast<const float*>(sm) + t;
 #pragma unroll
       for (int rl = 0; rl < kRowsPerCta; ++rl)
-        if (rl < nrows) out0[rl * r + k] = base[(rl >> 1) * 2 * Q + (rl & 1)];
+        if (rl < nrows) out0[rl * r + k] = base[(rl >> 1) * 2 * ldl + (rl & 1)];
     }
   }
 }
@@ -442,7 +460,8 @@ __global__ void __launch_bounds__(256, 3) k_xinv(const Launch<XInvJob> Lc) {
 size_t ypass_table_bytes(int r) { return sizeof(int) * (size_t)(r + 2 * kPrefWarm + kYChunk); }
 
 static size_t xinv_smem(int Qmax, int out_max) {
-  return (size_t)kLines * Qmax * sizeof(float2) + sizeof(int) * (size_t)(out_max + 2 * kPrefWarm + kXChunk);
+  return (size_t)kLines * (Qmax + kLinePad) * sizeof(float2) +
+         sizeof(int) * (size_t)(out_max + 2 * kPrefWarm + kXChunk);
 }
 
 static void max_carveout(const void* f) {
@@ -450,7 +469,8 @@ static void max_carveout(const void* f) {
 }
 
 cudaError_t launch_xfwd(const Launch<XFwdJob>& L, int Qmax, cudaStream_t st) {
-  const size_t smem = (size_t)kLines * Qmax * sizeof(float2) + sizeof(int2) * (size_t)(Qmax / 2 + 1);
+  const size_t smem =
+      (size_t)kLines * (Qmax + kLinePad) * sizeof(float2) + sizeof(ushort2) * (size_t)(Qmax / 2 + 1);
   max_carveout((const void*)k_xfwd);
   cudaError_t e = cudaFuncSetAttribute(k_xfwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

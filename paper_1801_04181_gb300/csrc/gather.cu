@@ -10,9 +10,9 @@
 // memory, filters it along x for the three derivative orders, then each thread
 // finishes y and z for one (x, y) column of the target.
 //
-// Per cell it writes H (A/m) and accumulates, in FP64, sum m . grad phi and
-// sum_a m_a d_a d_b phi; the host-side constants mu0 V Ms_t turn them into E
-// and F (F_t = -mu0 V Ms_t sum Hess(phi) m).
+// Per cell it writes H (A/m) and accumulates sum m . grad phi and
+// sum_a m_a d_a d_b phi (FP32 within a warp, FP64 across warps and tiles);
+// the constants mu0 V Ms_t turn them into E and F (F_t = -mu0 V Ms_t sum Hess(phi) m).
 #include <cuda_runtime.h>
 
 #include "mech.cuh"
@@ -49,7 +49,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 template <int NZ>
 __device__ __forceinline__ void gather_column(const GatherJob& J, const float* A, int a_n,
                                               const float (*w_s)[12], int tx, int ty, int x, int y,
-                                              double* acc) {
+                                              float* acc) {
   constexpr int CZ = NZ + 3;
   float B[6][CZ];
   const float* wy = w_s[1];
@@ -113,10 +113,10 @@ __device__ __forceinline__ void gather_column(const GatherJob& J, const float* A
       J.H[2 * N + cell] = -gz;
     }
     const float mx = m[0][zl], my = m[1][zl], mz = m[2][zl];
-    acc[0] += (double)(mx * hxx + my * hxy + mz * hxz);
-    acc[1] += (double)(mx * hxy + my * hyy + mz * hyz);
-    acc[2] += (double)(mx * hxz + my * hyz + mz * hzz);
-    acc[3] += (double)(mx * gx + my * gy + mz * gz);
+    acc[0] += mx * hxx + my * hxy + mz * hxz;
+    acc[1] += mx * hxy + my * hyy + mz * hyz;
+    acc[2] += mx * hxz + my * hyz + mz * hzz;
+    acc[3] += mx * gx + my * gy + mz * gz;
   }
 }
 
@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(TX * TY, 3) k_gather(const Launch<GatherJob> L
   const int tx = threadIdx.x % TX;
   const int ty = threadIdx.x / TX;
   const int x = x0 + tx, y = y0 + ty;
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
   if (!bad && x < J.nx && y < J.ny) {
     switch (nz) {
       case 1: gather_column<1>(J, A, a_n, w_s, tx, ty, x, y, acc); break;
@@ -209,11 +209,15 @@ __global__ void __launch_bounds__(TX * TY, 3) k_gather(const Launch<GatherJob> L
       default: gather_column<4>(J, A, a_n, w_s, tx, ty, x, y, acc); break;
     }
   }
+  // FP32 within a warp (at most 32 x nz cells), FP64 from there on: the FP64
+  // pipe of this GPU is narrow, and a warp's partial sum keeps ~1e-6 of the
+  // magnitude of its terms, well inside the force tolerance
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
-    const double s = warp_sum(acc[c]);
-    if (lane == 0) red_s[warp][c] = s;
+    float s = acc[c];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) red_s[warp][c] = (double)s;
   }
   __syncthreads();
   if (threadIdx.x < 4) {
