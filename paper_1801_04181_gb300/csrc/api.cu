@@ -68,7 +68,7 @@ struct Dir {
   float* Tq = nullptr;
   float2* YC = nullptr;
   float* C = nullptr;
-  double* partial = nullptr;
+  float2* partial = nullptr;   // gather tile partials [ntiles][4], double-float
   int ntiles = 0;
   size_t Tq_bytes = 0, YC_bytes = 0, C_bytes = 0, partial_bytes = 0;
 };
@@ -108,6 +108,12 @@ struct TimedLaunch {
 struct mm_ctx {
   mm_options opt{};
   cudaStream_t st = nullptr;
+  // the slider update of a step stage runs on `side` beside the LLG stage
+  // launch; ev_fork / ev_join order it after the gather and before the next
+  // reader of the state
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  bool mech_pending = false;
   std::string err;
   Magnet mag[2];
   std::map<int, FftRes> ffts;
@@ -243,13 +249,25 @@ mm_status get_fft(mm_ctx* ctx, int L, FftTables* out) {
     P.magic_r[s] = (unsigned)(0xFFFFFFFFull / (unsigned)radix[s]) + 1u;
     Lb /= radix[s];
   }
-  std::vector<float2> twf(L);
-  std::vector<double2> twd(L);
-  for (int t = 0; t < L; ++t) {
-    const double ang = -2.0 * 3.14159265358979323846 * (double)t / (double)L;
-    twd[t] = make_double2(cos(ang), sin(ang));
-    twf[t] = make_float2((float)twd[t].x, (float)twd[t].y);
+  // stage twiddle tables: W_Lb^{n1 k} at (k - 1) M + n1, k = 1 .. R-1, n1 < M = Lb / R
+  std::vector<float2> twf;
+  std::vector<double2> twd;
+  for (int s = 0; s < P.nstages; ++s) {
+    const int R = P.radix[s], Lbs = P.blocklen[s], M = Lbs / R;
+    P.stw_off[s] = (int)twf.size();
+    for (int k = 1; k < R; ++k)
+      for (int n1 = 0; n1 < M; ++n1) {
+        const long long t = ((long long)n1 * k) % Lbs;
+        const double ang = -2.0 * 3.14159265358979323846 * (double)t / (double)Lbs;
+        twd.push_back(make_double2(cos(ang), sin(ang)));
+        twf.push_back(make_float2((float)twd.back().x, (float)twd.back().y));
+      }
   }
+  if (twf.empty()) {  // a single-stage plan reads no table
+    twf.push_back(make_float2(1.f, 0.f));
+    twd.push_back(make_double2(1.0, 0.0));
+  }
+  const size_t ntw = twf.size();
   std::vector<int> pos(L), freq(L);
   for (int k = 0; k < L; ++k) {
     int p = 0, rem = k, B = L;
@@ -262,12 +280,12 @@ mm_status get_fft(mm_ctx* ctx, int L, FftTables* out) {
     pos[k] = p;
     freq[p] = k;
   }
-  CKS(alloc(ctx, (void**)&R.tw_f, sizeof(float2) * L));
-  CKS(alloc(ctx, (void**)&R.tw_d, sizeof(double2) * L));
+  CKS(alloc(ctx, (void**)&R.tw_f, sizeof(float2) * ntw));
+  CKS(alloc(ctx, (void**)&R.tw_d, sizeof(double2) * ntw));
   CKS(alloc(ctx, (void**)&R.pos, sizeof(int) * L));
   CKS(alloc(ctx, (void**)&R.freq, sizeof(int) * L));
-  CK(cudaMemcpy(R.tw_f, twf.data(), sizeof(float2) * L, cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(R.tw_d, twd.data(), sizeof(double2) * L, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(R.tw_f, twf.data(), sizeof(float2) * ntw, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(R.tw_d, twd.data(), sizeof(double2) * ntw, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(R.pos, pos.data(), sizeof(int) * L, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(R.freq, freq.data(), sizeof(int) * L, cudaMemcpyHostToDevice));
   R.t.plan = P;
@@ -432,7 +450,7 @@ mm_status alloc_dir_outputs(mm_ctx* ctx, int s, Dir* D) {
   CKS(ensure_buf(ctx, &D->YC, &D->YC_bytes, sizeof(float2) * (size_t)D->r[2] * S.kxh * D->r[1]));
   CKS(ensure_buf(ctx, &D->C, &D->C_bytes, sizeof(float) * (size_t)D->r[2] * D->r[1] * D->r[0]));
   D->ntiles = gather_tiles(T.nx, T.ny);
-  CKS(ensure_buf(ctx, &D->partial, &D->partial_bytes, sizeof(double) * 4 * (size_t)D->ntiles));
+  CKS(ensure_buf(ctx, &D->partial, &D->partial_bytes, sizeof(float2) * 4 * (size_t)D->ntiles));
   return MM_OK;
 }
 
@@ -527,7 +545,16 @@ mm_status replan_if_needed(mm_ctx* ctx) {
   return MM_OK;
 }
 
+// The context stream waits for a slider update still running on the side stream.
+mm_status join_mech(mm_ctx* ctx) {
+  if (!ctx->mech_pending) return MM_OK;
+  CK(cudaStreamWaitEvent(ctx->st, ctx->ev_join, 0));
+  ctx->mech_pending = false;
+  return MM_OK;
+}
+
 mm_status upload_mech(mm_ctx* ctx) {
+  CKS(join_mech(ctx));
   MechState& H = ctx->host_mech;
   H.xs = H.x; H.vs = H.v; H.ts = H.t;
   for (int a = 0; a < 3; ++a) H.u[a] = u_cells(ctx, a, H.x);
@@ -667,8 +694,8 @@ GatherJob gather_job(mm_ctx* ctx, int s, const float* m_t, float* H) {
 }
 
 // P: reduction / slider update done by the gather's last block (null: none)
-mm_status run_gathers(mm_ctx* ctx, const float* in[2], const int* srcs, int n, float* const* Hout,
-                      const MechParams* P) {
+mm_status run_gathers(mm_ctx* ctx, const float* in[2], const int* srcs, int n, float* const* Hout) {
+  CKS(join_mech(ctx));  // the gathers read the displacement
   Launch<GatherJob> L{};
   L.njobs = n;
   int tiles = 0, nzmax = 1;
@@ -680,9 +707,8 @@ mm_status run_gathers(mm_ctx* ctx, const float* in[2], const int* srcs, int n, f
     nzmax = std::max(nzmax, ctx->mag[1 - s].nz);
   }
   L.tile_start[n] = tiles;
-  const MechParams none{};
   Timer t(ctx, 3);
-  CK(launch_gather(L, nzmax, P ? *P : none, ctx->tickets, ctx->st));
+  CK(launch_gather(L, nzmax, ctx->st));
   return MM_OK;
 }
 
@@ -695,7 +721,7 @@ MechParams mech_params(mm_ctx* ctx, int mode, int stage, double dt, bool dir0, b
     // direction s -> t: partial index s (0: base -> slider, 1: slider -> base)
     if (use[s]) {
       P.partial[s] = ctx->mag[s].dir.partial;
-      P.ntiles[s] = ctx->mag[s].dir.ntiles;
+      P.nparts[s] = ctx->mag[s].dir.ntiles;
     }
     const double V = T.d[0] * T.d[1] * T.d[2];
     P.Fscale[s] = -kMu0 * V * T.Ms;
@@ -715,6 +741,7 @@ MechParams mech_params(mm_ctx* ctx, int mode, int stage, double dt, bool dir0, b
   P.c_next = (mode == 2) ? DP_C[1] : (stage >= 1 && stage < 7 ? DP_C[stage] : 0.0);
   P.move = ctx->move ? 1 : 0;
   P.mass = ctx->mass;
+  P.inv_mass = ctx->mass > 0 ? 1.0 / ctx->mass : 0.0;
   P.k_spring = ctx->k_spring;
   P.v_drive = ctx->v_drive;
   P.x0_spring = ctx->x0_spring;
@@ -728,13 +755,28 @@ MechParams mech_params(mm_ctx* ctx, int mode, int stage, double dt, bool dir0, b
 }
 
 mm_status run_mech(mm_ctx* ctx, const MechParams& P) {
+  CKS(join_mech(ctx));
   Timer t(ctx, 5);
   CK(launch_mech(P, ctx->st));
   return MM_OK;
 }
 
-// All fields of both magnets for stage inputs `in` (demag, stray, forces);
-// P: force reduction / slider update fused into the gather.
+// The same update on the side stream, after the work queued so far on the
+// context stream, which goes on without waiting for it (join_mech waits).
+mm_status fork_mech(mm_ctx* ctx, const MechParams& P) {
+  CKS(join_mech(ctx));
+  CK(cudaEventRecord(ctx->ev_fork, ctx->st));
+  CK(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
+  CK(launch_mech(P, ctx->side));
+  CK(cudaEventRecord(ctx->ev_join, ctx->side));
+  ctx->mech_pending = true;
+  ctx->launches++;
+  return MM_OK;
+}
+
+// All fields of both magnets for stage inputs `in` (demag, stray, force
+// partials), then the force reduction P: for a step stage (mode 0) on the side
+// stream beside the LLG stage launch, otherwise in line.
 mm_status evaluate_fields(mm_ctx* ctx, const float* in[2], const MechParams& P) {
   const int which[2] = {0, 1};
   const int what[2] = {3, 3};
@@ -743,7 +785,9 @@ mm_status evaluate_fields(mm_ctx* ctx, const float* in[2], const MechParams& P) 
   const int srcs[2] = {0, 1};
   // H_stray of the slider comes from source 0, of the base from source 1
   float* H[2] = {ctx->mag[1].Hstray, ctx->mag[0].Hstray};
-  CKS(run_gathers(ctx, in, srcs, 2, H, &P));
+  CKS(run_gathers(ctx, in, srcs, 2, H));
+  if (P.mode == 0) CKS(fork_mech(ctx, P));
+  else CKS(run_mech(ctx, P));
   return MM_OK;
 }
 
@@ -840,7 +884,7 @@ mm_status attempt_step(mm_ctx* ctx, double dt, double* err) {
   int cur = 0;
   for (int i = 2; i <= 7; ++i) {
     const float* in[2] = {M[0].ys[cur], M[1].ys[cur]};
-    // the gather's last block reduces the forces and advances the slider stage
+    // the side stream reduces the forces and advances the slider stage
     CKS(evaluate_fields(ctx, in, mech_params(ctx, 0, i, dt, true, true)));
     float* nxt[2] = {M[0].ys[1 - cur], M[1].ys[1 - cur]};
     CKS(run_stage(ctx, in, nxt, i, dt));
@@ -849,6 +893,7 @@ mm_status attempt_step(mm_ctx* ctx, double dt, double* err) {
   // stages 2..7 alternate the two stage buffers, so the stage-7 input (the
   // 5th-order solution) always ends in ys[1]
   (void)cur;
+  CKS(join_mech(ctx));
   CK(cudaMemcpyAsync(&ctx->host_mech, ctx->mech, sizeof(MechState), cudaMemcpyDeviceToHost, ctx->st));
   CKS(check_device_error(ctx));
   *err = ctx->host_mech.err;
@@ -901,7 +946,10 @@ mm_status mm_create(mm_ctx** out, const mm_options* opt) {
     return MM_EINVAL;
   }
   ctx->st = (cudaStream_t)ctx->opt.stream;
-  cudaError_t e = cudaMalloc((void**)&ctx->mech, sizeof(MechState));
+  cudaError_t e = cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->mech, sizeof(MechState));
   if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->err_flag, sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->tickets, 2 * sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(ctx->tickets, 0, 2 * sizeof(int));
@@ -924,6 +972,7 @@ static void free_dir(Dir& D) {
 
 void mm_destroy(mm_ctx* ctx) {
   if (!ctx) return;
+  if (ctx->side) cudaStreamSynchronize(ctx->side);
   if (ctx->st) cudaStreamSynchronize(ctx->st);
   else cudaDeviceSynchronize();
   for (auto& M : ctx->mag) {
@@ -941,6 +990,9 @@ void mm_destroy(mm_ctx* ctx) {
   cudaFree(ctx->gen_work); cudaFree(ctx->gen_q); cudaFree(ctx->W_dev);
   cudaFree(ctx->mech); cudaFree(ctx->err_flag); cudaFree(ctx->tickets);
   for (auto& p : ctx->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+  if (ctx->side) cudaStreamDestroy(ctx->side);
   for (auto e : ctx->free_events) cudaEventDestroy(e);
   delete ctx;
 }
@@ -1103,7 +1155,8 @@ mm_status mm_compute_stray_field(mm_ctx* ctx, int src, float* H_dev) {
   CKS(run_source_passes(ctx, in, which, 1, what, dirs));
   float* H[1] = {H_dev ? H_dev : ctx->mag[1 - src].Hstray};
   const MechParams P = mech_params(ctx, 1, 0, 0.0, src == 0, src == 1);
-  CKS(run_gathers(ctx, in, which, 1, H, &P));
+  CKS(run_gathers(ctx, in, which, 1, H));
+  CKS(run_mech(ctx, P));
   return MM_OK;
 }
 
@@ -1157,6 +1210,7 @@ mm_status mm_compute_potential(mm_ctx* ctx, int src, int prefiltered, float* out
 
 mm_status mm_get_force(mm_ctx* ctx, int on_mag, double F_out[3], double* E_int_out) {
   if (!ctx || bad_mag(on_mag)) return ctx ? fail(ctx, MM_EINVAL, "mm_get_force") : MM_EINVAL;
+  CKS(join_mech(ctx));
   CK(cudaMemcpyAsync(&ctx->host_mech, ctx->mech, sizeof(MechState), cudaMemcpyDeviceToHost, ctx->st));
   CKS(check_device_error(ctx));
   const MechState& H = ctx->host_mech;

@@ -12,8 +12,8 @@
 // stored back at n1 + M k2.  Each thread keeps the R points of a butterfly in
 // registers, so a stage is one shared-memory round trip; radices up to 16
 // (composite ones as two register levels) keep lengths such as 2160 = 16 15 9
-// to three stages.  Stage twiddles come from a per-length table
-// W_L[t] = exp(-2 pi i t / L) (index n1 k2 L / Lb < L).
+// to three stages.  Stage twiddles W_Lb^{n1 k} (k = 1 .. R-1, n1 < Lb / R)
+// come from per-stage tables, each value rounded once from FP64.
 #pragma once
 #include <cuda_runtime.h>
 #include <math.h>
@@ -155,35 +155,58 @@ template <int A, int B, typename C> struct DftComp {
     }
   }
 };
-template <typename C> struct Dft<6, C> : DftComp<2, 3, C> {};
+// Coprime R = A * B (Good-Thomas prime-factor mapping): with
+// n = (B n1 + A n2) mod R and k = the k' < R with k' = k1 (mod A), k' = k2 (mod B),
+//   y[k] = sum_n2 W_B^{n2 k2} sum_n1 x[(B n1 + A n2) mod R] W_A^{n1 k1},
+// with no twiddle factors between the two levels.
+__host__ __device__ constexpr int inv_mod(int a, int m) {
+  int r = 1;
+  while ((a * r) % m != 1) ++r;
+  return r;
+}
+template <int A, int B, typename C> struct DftPfa {
+  static __device__ __forceinline__ void run(C* x, int s) {
+    constexpr int R = A * B;
+    constexpr int eA = B * inv_mod(B % A, A);  // = 1 (mod A), = 0 (mod B)
+    constexpr int eB = A * inv_mod(A % B, B);  // = 0 (mod A), = 1 (mod B)
+    C t[B][A];
+#pragma unroll
+    for (int n2 = 0; n2 < B; ++n2) {
+#pragma unroll
+      for (int n1 = 0; n1 < A; ++n1) t[n2][n1] = x[(B * n1 + A * n2) % R];
+      Dft<A, C>::run(t[n2], s);
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < A; ++k1) {
+      C u[B];
+#pragma unroll
+      for (int n2 = 0; n2 < B; ++n2) u[n2] = t[n2][k1];
+      Dft<B, C>::run(u, s);
+#pragma unroll
+      for (int k2 = 0; k2 < B; ++k2) x[(k1 * eA + k2 * eB) % R] = u[k2];
+    }
+  }
+};
+template <typename C> struct Dft<6, C> : DftPfa<2, 3, C> {};
 template <typename C> struct Dft<8, C> : DftComp<2, 4, C> {};
 template <typename C> struct Dft<9, C> : DftComp<3, 3, C> {};
-template <typename C> struct Dft<10, C> : DftComp<2, 5, C> {};
-template <typename C> struct Dft<12, C> : DftComp<4, 3, C> {};
-template <typename C> struct Dft<15, C> : DftComp<3, 5, C> {};
+template <typename C> struct Dft<10, C> : DftPfa<2, 5, C> {};
+template <typename C> struct Dft<12, C> : DftPfa<4, 3, C> {};
+template <typename C> struct Dft<15, C> : DftPfa<3, 5, C> {};
 template <typename C> struct Dft<16, C> : DftComp<4, 4, C> {};
 
-// Stage twiddles w[k] = W^k (W = W_Lb^{n1}), k = 1..R-1: the power-of-two
-// ones are read from the table (log2 R loads instead of R - 1), every other
-// one is the product of the table values of its set bits, so no twiddle is
-// more than 2 popcount(k) - 1 <= 7 roundings away from exact.
+// Stage twiddles w[k] = W_Lb^{n1 k}, k = 1..R-1: entry (k - 1) M + n1 of the
+// stage table, so the lanes of a warp (consecutive n1) read consecutive words.
 template <int R, typename C>
-__device__ __forceinline__ void twiddle_powers(const C* __restrict__ tw, int idx1, C* w) {
+__device__ __forceinline__ void stage_twiddles(const C* __restrict__ col, int M, C* w) {
 #pragma unroll
-  for (int k = 1; k < R; k *= 2) w[k] = tw[idx1 * k];
-#pragma unroll
-  for (int k = 3; k < R; ++k) {
-    if ((k & (k - 1)) == 0) continue;
-    const int low = k & -k;
-    w[k] = cmul(w[k - low], w[low]);
-  }
+  for (int k = 1; k < R; ++k) w[k] = col[(k - 1) * M];
 }
 
 template <int R, bool INV, typename C>
 __device__ __forceinline__ void fft_stage(C* buf, int ldl, int nlines, int L, int Lb, unsigned mpl,
-                                          unsigned mM, const C* __restrict__ tw, int tid, int nthr) {
+                                          unsigned mM, const C* __restrict__ stw, int tid, int nthr) {
   const int M = Lb / R;
-  const int tstride = L / Lb;
   const int per_line = L / R;
   const int nb = nlines * per_line;
   for (int b = tid; b < nb; b += nthr) {
@@ -199,14 +222,14 @@ __device__ __forceinline__ void fft_stage(C* buf, int ldl, int nlines, int L, in
       Dft<R, C>::run(v, -1);
       if (n1) {
         C w[R];
-        twiddle_powers<R, C>(tw, n1 * tstride, w);
+        stage_twiddles<R, C>(stw + n1, M, w);
 #pragma unroll
         for (int k = 1; k < R; ++k) v[k] = cmul(v[k], w[k]);
       }
     } else {
       if (n1) {
         C w[R];
-        twiddle_powers<R, C>(tw, n1 * tstride, w);
+        stage_twiddles<R, C>(stw + n1, M, w);
 #pragma unroll
         for (int k = 1; k < R; ++k) v[k] = cmulconj(v[k], w[k]);
       }
@@ -221,9 +244,8 @@ __device__ __forceinline__ void fft_stage(C* buf, int ldl, int nlines, int L, in
 // digit-reversed output of sum_k X[k] e^{+2 pi i n k / L}.
 template <int R, typename C>
 __device__ __forceinline__ void fft_stage_dif_inv(C* buf, int ldl, int nlines, int L, int Lb, unsigned mpl,
-                                                  unsigned mM, const C* __restrict__ tw, int tid, int nthr) {
+                                                  unsigned mM, const C* __restrict__ stw, int tid, int nthr) {
   const int M = Lb / R;
-  const int tstride = L / Lb;
   const int per_line = L / R;
   const int nb = nlines * per_line;
   for (int b = tid; b < nb; b += nthr) {
@@ -238,7 +260,7 @@ __device__ __forceinline__ void fft_stage_dif_inv(C* buf, int ldl, int nlines, i
     Dft<R, C>::run(v, +1);
     if (n1) {
       C w[R];
-      twiddle_powers<R, C>(tw, n1 * tstride, w);
+      stage_twiddles<R, C>(stw + n1, M, w);
 #pragma unroll
       for (int k = 1; k < R; ++k) v[k] = cmulconj(v[k], w[k]);
     }
@@ -255,22 +277,25 @@ enum FftMode { kFwdDif = 0, kInvDit = 1, kInvDif = 2 };
 //   kFwdDif: forward, natural in, digit-reversed out
 //   kInvDit: inverse, digit-reversed in, natural out
 //   kInvDif: inverse, natural in, digit-reversed out
-template <typename C>
-__device__ void fft_smem(C* buf, int ldl, int nlines, const FftPlanDev& P, const C* __restrict__ tw,
-                         int mode, int tid0, int nthr) {
+// stw: the stage twiddle tables of the plan (stage s at P.stw_off[s]).
+template <int MODE, typename C>
+__device__ __forceinline__ void fft_smem(C* buf, int ldl, int nlines, const FftPlanDev& P,
+                                         const C* __restrict__ stw, int tid0, int nthr) {
   const int L = P.L;
   const int tid = (int)threadIdx.x - tid0;
   const bool mine = tid >= 0 && tid < nthr;
   for (int si = 0; si < P.nstages; ++si) {
-    const int st = mode == kInvDit ? P.nstages - 1 - si : si;
+    const int st = MODE == kInvDit ? P.nstages - 1 - si : si;
     const int Lb = P.blocklen[st];
     const unsigned mpl = P.magic_per_line[st], mM = P.magic_M[st];
+    const C* tws = stw + P.stw_off[st];
     if (mine) {
-#define MM_STAGE(R)                                                                                 \
-  case R:                                                                                           \
-    if (mode == kInvDit) fft_stage<R, true, C>(buf, ldl, nlines, L, Lb, mpl, mM, tw, tid, nthr);     \
-    else if (mode == kFwdDif) fft_stage<R, false, C>(buf, ldl, nlines, L, Lb, mpl, mM, tw, tid, nthr); \
-    else fft_stage_dif_inv<R, C>(buf, ldl, nlines, L, Lb, mpl, mM, tw, tid, nthr);                 \
+#define MM_STAGE(R)                                                                                  \
+  case R:                                                                                            \
+    if (MODE == kInvDit) fft_stage<R, true, C>(buf, ldl, nlines, L, Lb, mpl, mM, tws, tid, nthr); \
+    else if (MODE == kFwdDif)                                                                        \
+      fft_stage<R, false, C>(buf, ldl, nlines, L, Lb, mpl, mM, tws, tid, nthr);                 \
+    else fft_stage_dif_inv<R, C>(buf, ldl, nlines, L, Lb, mpl, mM, tws, tid, nthr);             \
     break;
       switch (P.radix[st]) {
         MM_STAGE(2) MM_STAGE(3) MM_STAGE(4) MM_STAGE(5) MM_STAGE(6) MM_STAGE(8) MM_STAGE(9)

@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(256, 3) k_xfwd(const Launch<XFwdJob> Lc) {
     ptab[kx] = make_ushort2((unsigned short)fft_pos(kx, J.fx.plan),
                             (unsigned short)fft_pos(kx == 0 ? 0 : Q - kx, J.fx.plan));
   __syncthreads();
-  fft_smem<float2>(sm, ldl, nlines, J.fx.plan, J.fx.tw_f, kFwdDif, 0, blockDim.x);
+  fft_smem<kFwdDif, float2>(sm, ldl, nlines, J.fx.plan, J.fx.tw_f, 0, blockDim.x);
 
   // Z = A + iB:  A_k = (Z_k + conj Z_{Q-k}) / 2,  B_k = (Z_k - conj Z_{Q-k}) / (2i)
   // thread -> (kx, line) with the line fastest: a warp writes 8 runs of 64 bytes
@@ -180,23 +180,28 @@ __device__ __forceinline__ void load_pair(const float2* sm, int Q, int p0, int p
 }
 
 // Spectral products at every (ky, Qy - ky) pair of one kx column.  The
-// potential planes go first: they land beyond the input planes whenever the
-// demag planes are produced too, which then overwrite the inputs in place.
-// Each thread issues all of its kernel-spectrum loads before it computes.
+// potential planes land beyond the input planes whenever the demag planes are
+// produced too; those overwrite the inputs in place.  A thread owns the two
+// positions of its pair in every plane, so it reads the inputs once and writes
+// both products without any barrier.  Kernel-spectrum loads are issued in
+// batches before the arithmetic that uses them.
 template <int NZ>
 __device__ __forceinline__ void ypass_mix(const YJob& J, float2* sm, int kx, int Q, int nH) {
-  // output planes per batch of kernel loads (about 40 values in flight)
-  constexpr int OB = 40 / (3 * NZ) > 0 ? 40 / (3 * NZ) : 1;
-  const size_t kstride = (size_t)J.kxh * J.kyq;  // one stored kernel plane
+  // output planes per batch of kernel loads (about 30 values in flight)
+  constexpr int OB = 30 / (3 * NZ) > 0 ? 30 / (3 * NZ) : 1;
+  const int kstride = J.kxh * J.kyq;  // one stored kernel plane (< 2^31 values in all)
   const int half = Q >> 1;
-  if (J.do_C) {
-    for (int kyq = threadIdx.x; kyq <= half; kyq += blockDim.x) {
-      const bool two = kyq != 0 && 2 * kyq != Q;
-      const size_t koff = (size_t)kx * J.kyq + kyq;
-      const int p0 = fft_pos(kyq, J.fy.plan);
-      const int p1 = two ? fft_pos(Q - kyq, J.fy.plan) : p0;
-      float2 mh[2][3][NZ];
-      load_pair<NZ>(sm, Q, p0, p1, mh);  // before any output overwrites an input plane
+  for (int kyq = threadIdx.x; kyq <= half; kyq += blockDim.x) {
+    // the two frequencies ky = kyq and Qy - kyq share every stored kernel value;
+    // the second has the odd-in-y components negated
+    const bool two = kyq != 0 && 2 * kyq != Q;
+    const int koff = kx * J.kyq + kyq;
+    const int p0 = fft_pos(kyq, J.fy.plan);
+    const int p1 = two ? fft_pos(Q - kyq, J.fy.plan) : p0;
+    float2 mh[2][3][NZ];
+    load_pair<NZ>(sm, Q, p0, p1, mh);
+    if (J.do_C) {
+      const float* Tk = J.Tq + koff;
       for (int ob = 0; ob < J.n_out; ob += OB) {
         float tv[OB][NZ][3];
 #pragma unroll
@@ -205,9 +210,7 @@ __device__ __forceinline__ void ypass_mix(const YJob& J, float2* sm, int kx, int
           for (int jz = 0; jz < NZ; ++jz)
 #pragma unroll
             for (int c = 0; c < 3; ++c)
-              tv[o][jz][c] = ob + o < J.n_out
-                                 ? __ldg(J.Tq + (size_t)(((ob + o) * NZ + jz) * 3 + c) * kstride + koff)
-                                 : 0.f;
+              tv[o][jz][c] = ob + o < J.n_out ? __ldg(Tk + (((ob + o) * NZ + jz) * 3 + c) * kstride) : 0.f;
         // c(o) = sum_jz sum_c T_c(o, jz) m_c(jz); T = Ms W (S spectra) / (Qx Qy)
 #pragma unroll
         for (int o = 0; o < OB; ++o) {
@@ -228,24 +231,14 @@ __device__ __forceinline__ void ypass_mix(const YJob& J, float2* sm, int kx, int
         }
       }
     }
-  }
-  if (!J.do_H) return;
-  for (int kyq = threadIdx.x; kyq <= half; kyq += blockDim.x) {
-    // the two frequencies ky = kyq and Qy - kyq share every stored kernel value;
-    // the second has the odd-in-y components negated
-    const bool two = kyq != 0 && 2 * kyq != Q;
-    const size_t koff = (size_t)kx * J.kyq + kyq;
-    const int p0 = fft_pos(kyq, J.fy.plan);
-    const int p1 = two ? fft_pos(Q - kyq, J.fy.plan) : p0;
-    {
+    if (J.do_H) {
       // H_a(iz) = sum_jz sum_b Ns_ab(iz - jz) m_b(jz); Ns = -Ms N / (Qx Qy)
+      const float* Nk = J.Nq + koff;
       float nv[6][NZ];
 #pragma unroll
       for (int comp = 0; comp < 6; ++comp)
 #pragma unroll
-        for (int dz = 0; dz < NZ; ++dz) nv[comp][dz] = __ldg(J.Nq + (size_t)(comp * NZ + dz) * kstride + koff);
-      float2 mh[2][3][NZ];
-      load_pair<NZ>(sm, Q, p0, p1, mh);
+        for (int dz = 0; dz < NZ; ++dz) nv[comp][dz] = __ldg(Nk + (comp * NZ + dz) * kstride);
 #pragma unroll
       for (int side = 0; side < 2; ++side) {
         const float fy = side ? -1.f : 1.f;
@@ -331,10 +324,10 @@ __global__ void __launch_bounds__(256, NZ <= 2 ? 3 : 2) k_ypass(const Launch<YJo
     for (int p = 0; p < Pin; ++p) sm[p * Q + y] = make_float2(0.f, 0.f);
   if (J.do_C) build_pref_table(tab, J.r + 2 * kPrefWarm + kYChunk, J.box_lo, J.box_len, J.start, Q, nullptr);
   __syncthreads();
-  fft_smem<float2>(sm, Q, Pin, J.fy.plan, J.fy.tw_f, kFwdDif, 0, blockDim.x);
+  fft_smem<kFwdDif, float2>(sm, Q, Pin, J.fy.plan, J.fy.tw_f, 0, blockDim.x);
   ypass_mix<NZ>(J, sm, kx, Q, nH);
   __syncthreads();
-  fft_smem<float2>(sm, Q, Pout, J.fy.plan, J.fy.tw_f, kInvDit, 0, blockDim.x);
+  fft_smem<kInvDit, float2>(sm, Q, Pout, J.fy.plan, J.fy.tw_f, 0, blockDim.x);
 
   if (J.do_H) {
     float2* out0 = J.outH + (size_t)kx * ny;
@@ -431,7 +424,7 @@ __global__ void __launch_bounds__(256, 3) k_xinv(const Launch<XInvJob> Lc) {
   build_pref_table(tab, J.out_len + 2 * kPrefWarm + kXChunk, J.box_lo, J.box_len, J.start, Q, &J.fx.plan);
   __syncthreads();
   // natural-order input, digit-reversed output: the table above maps through it
-  fft_smem<float2>(sm, ldl, nlines, J.fx.plan, J.fx.tw_f, kInvDif, 0, blockDim.x);
+  fft_smem<kInvDif, float2>(sm, ldl, nlines, J.fx.plan, J.fx.tw_f, 0, blockDim.x);
 
   const int r = J.out_len;
   float* out0 = J.out + (size_t)r0 * r;

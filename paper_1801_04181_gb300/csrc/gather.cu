@@ -6,16 +6,16 @@
 // position f in the source lattice: the 64 weights (cubic B-spline w, w', w''
 // per axis at f, full float precision as in Sec. IV.D) are shared by all
 // cells and the evaluation is a separable 4-tap filter of the coefficient box.
-// A CTA stages a (32 + 3) x (8 + 3) x (nz + 3) coefficient tile in shared
-// memory, filters it along x for the three derivative orders, then each thread
-// finishes y and z for one (x, y) column of the target.
+// A CTA filters the (32 + 3) x (8 + 3) x (nz + 3) coefficient tile of its
+// 32 x 8 target columns along x for the three derivative orders (into shared
+// memory), then each thread finishes y and z for one (x, y) column.
 //
 // Per cell it writes H (A/m) and accumulates sum m . grad phi and
-// sum_a m_a d_a d_b phi (FP32 within a warp, FP64 across warps and tiles);
+// sum_a m_a d_a d_b phi (FP32 within a warp, double-float across warps and tiles);
 // the constants mu0 V Ms_t turn them into E and F (F_t = -mu0 V Ms_t sum Hess(phi) m).
 #include <cuda_runtime.h>
 
-#include "mech.cuh"
+#include "dfloat.cuh"
 #include "mm_internal.h"
 
 namespace mm {
@@ -38,11 +38,6 @@ __device__ __forceinline__ void bspline_w(float t, float* w) {
   w[9] = 3.f * t - 2.f;
   w[10] = -3.f * t + 1.f;
   w[11] = t;
-}
-
-__device__ __forceinline__ double warp_sum(double v) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  return v;
 }
 
 // y and z stages for one target column (x, y), all NZ layers.
@@ -120,11 +115,11 @@ __device__ __forceinline__ void gather_column(const GatherJob& J, const float* A
   }
 }
 
-__global__ void __launch_bounds__(TX * TY, 3) k_gather(const Launch<GatherJob> Lc, const MechParams P, int* ticket) {
+__global__ void __launch_bounds__(TX * TY, 3) k_gather(const Launch<GatherJob> Lc) {
   extern __shared__ float gsm[];
   __shared__ float w_s[3][12];
   __shared__ int shift_s[3];
-  __shared__ double red_s[TX * TY / 32][4];
+  __shared__ float red_s[TX * TY / 32][4];
 
   const int j = find_job(Lc.tile_start, Lc.njobs, blockIdx.x);
   const GatherJob& J = Lc.job[j];
@@ -154,45 +149,43 @@ __global__ void __launch_bounds__(TX * TY, 3) k_gather(const Launch<GatherJob> L
   __syncthreads();
   const bool bad = shift_s[0] == 0x7fffffff || shift_s[1] == 0x7fffffff || shift_s[2] == 0x7fffffff;
 
-  // coefficient tile [cz][TY+3][TX+3]
-  float* ct = gsm;
-  float* A = gsm + cz * (TY + 3) * (TX + 3);  // [3][cz][TY+3][TX]
-  const int tile_n = cz * (TY + 3) * (TX + 3);
+  // x-filtered coefficient rows A[d][zz][yy][x] (d: w, w', w''), one warp per
+  // (zz, yy) row, filtered straight from global memory: a warp's four tap
+  // loads are four coalesced 128-byte reads of one coefficient row (L1 hits
+  // after the first).  Lanes past the target's edge read clamped, in-box
+  // positions and their results are never used.
+  float* A = gsm;
+  const int a_n = cz * (TY + 3) * TX;
   if (!bad) {
     const int sx = shift_s[0], sy = shift_s[1], sz = shift_s[2];
-    for (int base = threadIdx.x; base < tile_n; base += 4 * blockDim.x) {
-      float v[4];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const float* colp = J.C + (min(x0 + lane, J.nx - 1) + sx);
+    const float w0 = w_s[0][0], w1 = w_s[0][1], w2 = w_s[0][2], w3 = w_s[0][3];
+    const float d0 = w_s[0][4], d1 = w_s[0][5], d2 = w_s[0][6], d3 = w_s[0][7];
+    const float e0 = w_s[0][8], e1 = w_s[0][9], e2 = w_s[0][10], e3 = w_s[0][11];
+    const int nrow = cz * (TY + 3);
+    constexpr int kRowBatch = 2;
+    for (int r0 = warp; r0 < nrow; r0 += kRowBatch * (TX * TY / 32)) {
+      float c[kRowBatch][4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int idx = base + u * blockDim.x;
-        v[u] = 0.f;
-        if (idx < tile_n) {
-          const int xx = idx % (TX + 3);
-          const int rest = idx / (TX + 3);
-          const int yy = rest % (TY + 3);
-          const int zz = rest / (TY + 3);
-          const int gx = x0 + xx + sx, gy = y0 + yy + sy, gz = zz + sz;
-          if (gx < J.rx && gy < J.ry && gz < J.rz) v[u] = __ldg(J.C + ((size_t)gz * J.ry + gy) * J.rx + gx);
-        }
+      for (int b = 0; b < kRowBatch; ++b) {
+        const int r = min(r0 + b * (TX * TY / 32), nrow - 1);
+        const int zz = r / (TY + 3), yy = r - zz * (TY + 3);
+        // rows past the target's last support row are clamped in the box
+        const int gy = min(y0 + yy, J.ny + 2) + sy;
+        const float* src = colp + ((size_t)(zz + sz) * J.ry + gy) * J.rx;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) c[b][k] = __ldg(src + k);
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int idx = base + u * blockDim.x;
-        if (idx < tile_n) ct[idx] = v[u];
+      for (int b = 0; b < kRowBatch; ++b) {
+        const int r = r0 + b * (TX * TY / 32);
+        if (r >= nrow) break;
+        const int o = r * TX + lane;
+        A[o] = w0 * c[b][0] + w1 * c[b][1] + w2 * c[b][2] + w3 * c[b][3];
+        A[a_n + o] = d0 * c[b][0] + d1 * c[b][1] + d2 * c[b][2] + d3 * c[b][3];
+        A[2 * a_n + o] = e0 * c[b][0] + e1 * c[b][1] + e2 * c[b][2] + e3 * c[b][3];
       }
-    }
-  }
-  __syncthreads();
-  const int a_n = cz * (TY + 3) * TX;
-  for (int idx = threadIdx.x; idx < a_n; idx += blockDim.x) {
-    const int x = idx % TX;
-    const int zy = idx / TX;  // zz * (TY+3) + yy
-    const float* row = ct + zy * (TX + 3) + x;
-    const float c0 = row[0], c1 = row[1], c2 = row[2], c3 = row[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      const float* w = w_s[0] + 4 * d;
-      A[d * a_n + idx] = w[0] * c0 + w[1] * c1 + w[2] * c2 + w[3] * c3;
     }
   }
   __syncthreads();
@@ -217,27 +210,27 @@ __global__ void __launch_bounds__(TX * TY, 3) k_gather(const Launch<GatherJob> L
   for (int c = 0; c < 4; ++c) {
     float s = acc[c];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (lane == 0) red_s[warp][c] = (double)s;
+    if (lane == 0) red_s[warp][c] = s;
   }
   __syncthreads();
-  if (threadIdx.x < 4) {
-    double s = 0.0;
-    for (int w = 0; w < TX * TY / 32; ++w) s += red_s[w][threadIdx.x];
-    J.partial[(size_t)tile * 4 + threadIdx.x] = s;
+  if (warp != 0) return;
+  // the tile's four sums: lane c adds the warps in a fixed order in
+  // double-float; the fixed-order reduction over tiles runs in a later launch
+  if (lane < 4) {
+    dfloat s = {0.f, 0.f};
+    for (int w = 0; w < TX * TY / 32; ++w) s = df_add(s, dfloat{red_s[w][lane], 0.f});
+    J.partial[(size_t)tile * 4 + lane] = make_float2(s.hi, s.lo);
   }
-  // the last block reduces the forces and, during a step, advances the slider
-  if (P.state && last_block(ticket, (int)gridDim.x)) mech_block(P);
 }
 
 int gather_tiles(int nx, int ny) { return ((nx + TX - 1) / TX) * ((ny + TY - 1) / TY); }
 
 size_t gather_smem(int nz) {
   const int cz = nz + 3;
-  return sizeof(float) * ((size_t)cz * (TY + 3) * (TX + 3) + 3 * (size_t)cz * (TY + 3) * TX);
+  return sizeof(float) * 3 * (size_t)cz * (TY + 3) * TX;
 }
 
-cudaError_t launch_gather(const Launch<GatherJob>& L, int nz_max, const MechParams& P, int* ticket,
-                          cudaStream_t st) {
+cudaError_t launch_gather(const Launch<GatherJob>& L, int nz_max, cudaStream_t st) {
   const size_t smem = gather_smem(nz_max);
   cudaFuncSetAttribute((const void*)k_gather, cudaFuncAttributePreferredSharedMemoryCarveout,
                        cudaSharedmemCarveoutMaxShared);
@@ -245,7 +238,7 @@ cudaError_t launch_gather(const Launch<GatherJob>& L, int nz_max, const MechPara
   if (e != cudaSuccess) return e;
   const int grid = L.tile_start[L.njobs];
   if (grid == 0) return cudaSuccess;
-  k_gather<<<grid, TX * TY, smem, st>>>(L, P, ticket);
+  k_gather<<<grid, TX * TY, smem, st>>>(L);
   return cudaGetLastError();
 }
 

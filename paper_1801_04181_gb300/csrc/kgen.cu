@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(256) k_fft_lines_d(double2* data, int nlines, 
   double2* g = data + (size_t)line * L;
   for (int i = threadIdx.x; i < L; i += blockDim.x) smd[i] = g[i];
   __syncthreads();
-  fft_smem<double2>(smd, L, 1, T.plan, T.tw_d, kFwdDif, 0, blockDim.x);
+  fft_smem<kFwdDif, double2>(smd, L, 1, T.plan, T.tw_d, 0, blockDim.x);
   for (int k = threadIdx.x; k < L; k += blockDim.x) g[k] = smd[T.pos[k]];
 }
 

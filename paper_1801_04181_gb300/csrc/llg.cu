@@ -7,9 +7,10 @@
 // form  dm/dt = -gamma0/(1+alpha^2) [m x H + alpha m x (m x H)];  then the
 // next stage input y + dt sum_j a_{i+1,j} k_j (or, at the last stage, the
 // max-norm of the embedded 5(4) error).
-// k_mech: one block.  Reduces the Eq. (EQForce) partial sums of both
-// directions in a fixed order (deterministic, FP64) and advances the slider
-// state m x'' = k (v_d t + x0 - x) - gamma_v m x' + F . e with the same tableau.
+// k_mech: one block.  Reduces the Eq. (EQForce) tile partials of both
+// directions in a fixed order (deterministic, double-float) and advances the
+// slider state
+// m x'' = k (v_d t + x0 - x) - gamma_v m x' + F . e with the same tableau.
 #include <cuda_runtime.h>
 
 #include "mech.cuh"
@@ -109,7 +110,7 @@ __global__ void __launch_bounds__(256) k_stage(const Launch<StageJob> Lc, const 
       J.err_partial[tile] = v;
     }
     // the last block reduces the error norm of the attempt
-    if (Perr.state && last_block(ticket, (int)gridDim.x)) mech_block(Perr);
+    if (Perr.state && last_block(ticket, (int)gridDim.x)) err_block(Perr);
   }
 }
 

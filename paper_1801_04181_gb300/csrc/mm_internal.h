@@ -22,12 +22,15 @@ struct FftPlanDev {
   unsigned magic_per_line[kMaxStages];
   unsigned magic_M[kMaxStages];
   unsigned magic_r[kMaxStages];
+  // stage twiddle table s starts at entry stw_off[s] of FftTables::tw_f / tw_d:
+  // W_Lb^{n1 k} at (k - 1) M + n1, M = blocklen / radix, k = 1 .. radix - 1
+  int stw_off[kMaxStages];
 };
 
 // Length-L transform resources resident on the device.
 struct FftTables {
   FftPlanDev plan;
-  const float2* tw_f;     // exp(-2 pi i t / L), t < L
+  const float2* tw_f;     // stage twiddle tables, W_Lb^{n1 k} (see FftPlanDev)
   const double2* tw_d;
   const int* pos;         // frequency k -> position in DIF output
   const int* freq;        // position -> frequency
@@ -82,7 +85,7 @@ struct GatherJob {
   float inv_d[3];         // 1 / cell size (1/m)
   const float* m;         // target unit magnetisation [3][N]
   float* H;               // stray field out [3][N] (A/m), may be null
-  double* partial;        // [tiles][4]: sum m.Hess (3), sum m.grad
+  float2* partial;        // [tiles][4] double-float (hi, lo): sum m.Hess (3), sum m.grad
   int* err;               // set to 1 when the displacement leaves the box
 };
 
@@ -129,8 +132,8 @@ struct MechState {
 
 struct MechParams {
   MechState* state;
-  const double* partial[2];   // gather partials: [0] base -> slider, [1] slider -> base
-  int ntiles[2];
+  const float2* partial[2];   // gather tile partials [nparts][4] (hi, lo): [0] base -> slider, [1] slider -> base
+  int nparts[2];
   double Fscale[2], Escale[2];
   const float* err_partial[2];
   int nerr[2];
@@ -141,7 +144,7 @@ struct MechParams {
   double a[7];            // a_{stage+1, j}
   double c_next;
   int move;               // slider equation of motion active
-  double mass, k_spring, v_drive, x0_spring, gamma_v;
+  double mass, inv_mass, k_spring, v_drive, x0_spring, gamma_v;
   double e[3], inv_d[3], u_base[3];
 };
 
@@ -176,8 +179,7 @@ cudaError_t launch_ypass(const Launch<YJob>& L, size_t smem, cudaStream_t st);
 cudaError_t launch_xinv(const Launch<XInvJob>& L, int Qmax, cudaStream_t st);
 int gather_tiles(int nx, int ny);
 size_t gather_smem(int nz);
-cudaError_t launch_gather(const Launch<GatherJob>& L, int nz_max, const MechParams& P, int* ticket,
-                          cudaStream_t st);
+cudaError_t launch_gather(const Launch<GatherJob>& L, int nz_max, cudaStream_t st);
 cudaError_t launch_stage(const Launch<StageJob>& L, const MechParams& Perr, int* ticket, cudaStream_t st);
 cudaError_t launch_combine(const Launch<CombineJob>& L, cudaStream_t st);
 cudaError_t launch_normalise(const Launch<CombineJob>& L, cudaStream_t st);

@@ -6,7 +6,7 @@
 // forbids raw cudaMalloc, or a time-stepping loop in which the implicit device
 // synchronisation of cudaMalloc / cudaFree would stall other streams.  For them
 // mm_spline_field_noalloc runs the tricubic gather of the stray field and the
-// force / energy reduction with its scratch (the per-tile FP64 partial sums,
+// force / energy reduction with its scratch (the per-tile partial sums,
 // the displacement and an error flag) in the fixed array below, which every
 // GPU that loads the library holds until the process exits.
 //
@@ -20,6 +20,7 @@
 
 #include <mutex>
 
+#include "dfloat.cuh"
 #include "mm.h"
 #include "mm_internal.h"
 
@@ -45,20 +46,27 @@ __global__ void k_noalloc_begin(double p0, double p1, double p2) {
 // Fixed-order reduction of the tile partials into F[3], E (caller memory).
 __global__ void __launch_bounds__(256) k_noalloc_reduce(int ntiles, double Fscale, double Escale,
                                                         double* FE_out) {
-  __shared__ double sh[8][4];
-  const double* part = g_noalloc_scratch + kNoAllocHeader;
-  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  __shared__ dfloat sh[8][4];
+  // tile partials: [tile][4] double-float pairs
+  const float2* part = reinterpret_cast<const float2*>(g_noalloc_scratch + kNoAllocHeader);
+  dfloat v[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
   for (int t = threadIdx.x; t < ntiles; t += blockDim.x)
-    for (int c = 0; c < 4; ++c) v[c] += part[(size_t)t * 4 + c];
+    for (int c = 0; c < 4; ++c) {
+      const float2 q = part[(size_t)t * 4 + c];
+      v[c] = df_add(v[c], dfloat{q.x, q.y});
+    }
   for (int c = 0; c < 4; ++c)
-    for (int o = 16; o > 0; o >>= 1) v[c] += __shfl_down_sync(0xffffffffu, v[c], o);
+    for (int o = 16; o > 0; o >>= 1) v[c] = df_add(v[c], df_shfl_down(v[c], o));
   if ((threadIdx.x & 31) == 0)
     for (int c = 0; c < 4; ++c) sh[threadIdx.x >> 5][c] = v[c];
   __syncthreads();
   if (threadIdx.x == 0) {
-    double s[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
-      for (int c = 0; c < 4; ++c) s[c] += sh[w][c];
+    double s[4];
+    for (int c = 0; c < 4; ++c) {
+      dfloat a = {0.f, 0.f};
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a = df_add(a, sh[w][c]);
+      s[c] = df_to_double(a);
+    }
     const int err = reinterpret_cast<const int*>(g_noalloc_scratch)[0];
     const double nan = __longlong_as_double(0x7ff8000000000000ll);
     for (int c = 0; c < 3; ++c) FE_out[c] = err ? nan : Fscale * s[c];
@@ -129,15 +137,15 @@ extern "C" mm_status mm_spline_field_noalloc(const float* coef_dev, const int co
   J.inv_d[2] = (float)(1.0 / dz);
   J.m = m_dev;
   J.H = H_dev;
-  J.partial = scratch + kNoAllocHeader;
+  J.partial = reinterpret_cast<float2*>(scratch + kNoAllocHeader);
   J.err = reinterpret_cast<int*>(scratch);
   Launch<GatherJob> L{};
   L.njobs = 1;
   L.tile_start[0] = 0;
   L.tile_start[1] = ntiles;
   L.job[0] = J;
-  const MechParams none{};  // reduction done by k_noalloc_reduce below
-  if (launch_gather(L, nz, none, nullptr, st) != cudaSuccess) return MM_ECUDA;
+  // tile partials only; k_noalloc_reduce below sums them
+  if (launch_gather(L, nz, st) != cudaSuccess) return MM_ECUDA;
   const double mu0 = 4e-7 * 3.14159265358979323846;
   const double V = dx * dy * dz;
   k_noalloc_reduce<<<1, 256, 0, st>>>(ntiles, -mu0 * V * Ms, mu0 * V * Ms, FE_dev);
