@@ -267,9 +267,12 @@ __device__ __forceinline__ void ypass_mix(const YJob& J, float2* sm, int kx, int
   }
 }
 
-// One CTA per kx; every job of a launch has NZ layers.
+// One CTA per kx; every job of a launch has NZ layers.  kYThreads = 288 (nine
+// warps) covers the 271 frequency pairs of a 540-point line in one round of
+// the spectral products.
+constexpr int kYThreads = 288;
 template <int NZ>
-__global__ void __launch_bounds__(256, NZ <= 2 ? 3 : 2) k_ypass(const Launch<YJob> Lc) {
+__global__ void __launch_bounds__(kYThreads, NZ <= 2 ? 3 : 2) k_ypass(const Launch<YJob> Lc) {
   constexpr int Pin = 3 * NZ;
   extern __shared__ float2 sm[];
   const int j = find_job(Lc.tile_start, Lc.njobs, blockIdx.x);
@@ -480,7 +483,7 @@ static cudaError_t launch_ypass_nz(const Launch<YJob>& L, size_t smem, cudaStrea
   if (e != cudaSuccess) return e;
   const int grid = L.tile_start[L.njobs];
   if (grid == 0) return cudaSuccess;
-  k_ypass<NZ><<<grid, 256, smem, st>>>(L);
+  k_ypass<NZ><<<grid, kYThreads, smem, st>>>(L);
   return cudaGetLastError();
 }
 
