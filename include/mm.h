@@ -72,7 +72,10 @@ const char* mm_status_string(mm_status s);
  * Grid of magnet `mag` (0 base, 1 slider): nx x ny x nz cuboid cells of size
  * dx x dy x dz metres (Sec. II: uniform M per cell at its centre) with lattice
  * offset `offset_cells` (x, y, z).  Both magnets must use the same cell size.
- * This build supports nz <= 4 (thin films; z by direct plane mixing).
+ * Sources with nz <= 4 take z by a direct sum over planes (thin films);
+ * thicker sources, or sources whose box around a thick target is tall, take z
+ * by FFT (Sec. III.A on a three-dimensional grid).  Grids whose FFT lines do
+ * not fit one shared-memory pass return MM_ENOTSUP when planned.
  */
 mm_status mm_set_grid(mm_ctx* ctx, int mag, int nx, int ny, int nz, double dx, double dy, double dz,
                       const long long offset_cells[3]);
@@ -176,8 +179,9 @@ mm_status mm_set_state(mm_ctx* ctx, const void* buf, size_t bytes);
 mm_status mm_eval_kernel_fp64(int kind, int n, const double* offsets_dev, double dx, double dy,
                               double dz, double* out_dev);
 
-/* FFT grid and potential box of the path from `src` (for reporting). */
-mm_status mm_get_plan_info(mm_ctx* ctx, int src, int fft_dims[2], int box_dims[3],
+/* FFT grid and potential box of the path from `src` (for reporting).
+ * fft_dims: Qx, Qy and Qz (0 for a thin source, whose z is summed directly). */
+mm_status mm_get_plan_info(mm_ctx* ctx, int src, int fft_dims[3], int box_dims[3],
                            long long box_lo[3], int coef_dims[3]);
 
 /* Per-kernel timing with CUDA events on the context stream (off by default).

@@ -177,12 +177,12 @@ class MovingMagnets:
         self._c(self.lib.mm_set_state(self.ctx, buf, len(blob)))
 
     def plan_info(self, src):
-        q = (C.c_int * 2)()
+        q = (C.c_int * 3)()
         b = _native._i3()
         lo = _native._ll3()
         cd = _native._i3()
         self._c(self.lib.mm_get_plan_info(self.ctx, src, q, b, lo, cd))
-        return dict(fft=(q[0], q[1]), box=(b[0], b[1], b[2]), box_lo=(lo[0], lo[1], lo[2]),
+        return dict(fft=(q[0], q[1]), Qz=q[2], box=(b[0], b[1], b[2]), box_lo=(lo[0], lo[1], lo[2]),
                     coef=(cd[0], cd[1], cd[2]))
 
     # ---------------------------------------------------------------- timing

@@ -70,7 +70,8 @@ struct Dir {
   float* C = nullptr;
   float2* partial = nullptr;   // gather tile partials [ntiles][4], double-float
   int ntiles = 0;
-  size_t Tq_bytes = 0, YC_bytes = 0, C_bytes = 0, partial_bytes = 0;
+  float2* Z3C = nullptr;       // thick sources: z-pass coefficient planes [r_z][kxh][Qy]
+  size_t Tq_bytes = 0, YC_bytes = 0, C_bytes = 0, partial_bytes = 0, Z3C_bytes = 0;
 };
 
 struct Magnet {
@@ -94,6 +95,13 @@ struct Magnet {
   float2* X1 = nullptr;
   float2* YH = nullptr;
   float* Nq = nullptr;
+  // thick sources (z by FFT): grid depth, spectra and the y / z pass buffers
+  bool thick = false;
+  int Qz = 0, Wz = 0, kzq = 0;
+  float* N3 = nullptr;     // [6][kxh][kyq][kzq]
+  float* S3 = nullptr;     // [3][kxh][kyq][kzq]
+  float2* Y3 = nullptr;    // [kxh][Qy][3 nz]
+  float2* Z3H = nullptr;   // [3 nz][kxh][Qy]
   Dir dir;   // hot path: coefficients around the other magnet
   Dir aux;   // mm_compute_potential output
 };
@@ -391,7 +399,7 @@ void dir_geometry(const mm_ctx* ctx, int s, bool full_box, Dir* D) {
 }
 
 int window_needed(const Magnet& S, const Dir& D, int a) {
-  const int n = a == 0 ? S.nx : S.ny;
+  const int n = a == 0 ? S.nx : (a == 1 ? S.ny : S.nz);
   int w = n - 1;  // self-demag offsets
   w = std::max(w, std::abs(D.box_lo[a] - (n - 1)));
   w = std::max(w, std::abs(D.box_lo[a] + D.box_len[a] - 1));
@@ -449,8 +457,10 @@ mm_status alloc_dir_outputs(mm_ctx* ctx, int s, Dir* D) {
   const Magnet& T = ctx->mag[1 - s];
   CKS(ensure_buf(ctx, &D->YC, &D->YC_bytes, sizeof(float2) * (size_t)D->r[2] * S.kxh * D->r[1]));
   CKS(ensure_buf(ctx, &D->C, &D->C_bytes, sizeof(float) * (size_t)D->r[2] * D->r[1] * D->r[0]));
-  D->ntiles = gather_tiles(T.nx, T.ny);
+  D->ntiles = gather_tiles(T.nx, T.ny, T.nz);
   CKS(ensure_buf(ctx, &D->partial, &D->partial_bytes, sizeof(float2) * 4 * (size_t)D->ntiles));
+  if (S.thick)
+    CKS(ensure_buf(ctx, &D->Z3C, &D->Z3C_bytes, sizeof(float2) * (size_t)D->r[2] * S.kxh * S.Qy));
   return MM_OK;
 }
 
@@ -469,6 +479,32 @@ mm_status alloc_magnet(mm_ctx* ctx, Magnet& M) {
   return MM_OK;
 }
 
+// FP64 generation of the 3D N and S spectra of a thick source (one-time set-up).
+mm_status build_spectra_3d_all(mm_ctx* ctx, Magnet& S, const FftTables& fx, const FftTables& fy) {
+  FftTables fz;
+  CKS(get_fft(ctx, S.Qz, &fz));
+  const size_t qsize = (size_t)S.kxh * S.kyq;
+  double* q2 = nullptr;
+  double* qtmp = nullptr;
+  double2* zl = nullptr;
+  CKS(alloc(ctx, (void**)&q2, sizeof(double) * 6 * (size_t)S.Qz * qsize));
+  mm_status st = alloc(ctx, (void**)&qtmp, sizeof(double) * 6 * qsize);
+  if (st == MM_OK) st = alloc(ctx, (void**)&zl, sizeof(double2) * qsize * S.Qz);
+  if (st == MM_OK) {
+    const KernelPlan3 K{S.Qx, S.Qy, S.Qz, S.Wx, S.Wy, S.Wz};
+    const double norm = (double)S.Qx * S.Qy * S.Qz;
+    cudaError_t e = build_spectra_3d(1, K, fx, fy, fz, S.d[0], S.d[1], S.d[2], -S.Ms / norm, S.N3,
+                                     ctx->gen_work, q2, qtmp, zl, ctx->st);
+    if (e == cudaSuccess)
+      e = build_spectra_3d(0, K, fx, fy, fz, S.d[0], S.d[1], S.d[2], S.Ms / norm, S.S3, ctx->gen_work, q2,
+                           qtmp, zl, ctx->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->st);
+    if (e != cudaSuccess) st = fail(ctx, MM_ECUDA, std::string("3D spectra: ") + cudaGetErrorString(e));
+  }
+  cudaFree(q2); cudaFree(qtmp); cudaFree(zl);
+  return st;
+}
+
 // (Re)plan both sources for the current displacement; rebuild spectra as needed.
 mm_status ensure_plan(mm_ctx* ctx) {
   for (int g = 0; g < 2; ++g) {
@@ -480,9 +516,13 @@ mm_status ensure_plan(mm_ctx* ctx) {
     Dir& D = S.dir;
     dir_geometry(ctx, s, false, &D);
     D.prefilter = 1;
-    const int wx = window_needed(S, D, 0), wy = window_needed(S, D, 1);
-    const bool regrid = S.Qx == 0 || 2 * wx + 2 > S.Qx || 2 * wy + 2 > S.Qy;
+    // z by FFT when the source is thick or the box around the target is tall
+    const bool thick = S.nz > kMaxNz || ctx->mag[1 - s].nz > kMaxNz;
+    const int wx = window_needed(S, D, 0), wy = window_needed(S, D, 1), wz = window_needed(S, D, 2);
+    const bool regrid = S.Qx == 0 || 2 * wx + 2 > S.Qx || 2 * wy + 2 > S.Qy || thick != S.thick ||
+                        (thick && 2 * wz + 2 > S.Qz);
     if (regrid) {
+      S.thick = thick;
       S.Wx = wx + kWindowSlack;
       S.Wy = wy + kWindowSlack;
       S.Qx = smooth_even_at_least(2 * S.Wx + 2);
@@ -492,22 +532,45 @@ mm_status ensure_plan(mm_ctx* ctx) {
       S.Wy = (S.Qy - 2) / 2;
       S.kxh = S.Qx / 2 + 1;
       S.kyq = S.Qy / 2 + 1;
+      if (thick) {
+        S.Wz = wz + kWindowSlack;
+        S.Qz = smooth_even_at_least(2 * S.Wz + 2);
+        S.Wz = (S.Qz - 2) / 2;
+        S.kzq = S.Qz / 2 + 1;
+      } else {
+        S.Qz = S.Wz = S.kzq = 0;
+      }
       if ((size_t)(kRowsPerCta / 2) * S.Qx * sizeof(float2) > 220 * 1024)
         return fail(ctx, MM_ENOTSUP, "x extent too large for one shared-memory line");
-      const int P = std::max(3 * S.nz, 3 * S.nz + D.r[2]);
-      if ((size_t)P * S.Qy * sizeof(float2) > 220 * 1024)
-        return fail(ctx, MM_ENOTSUP, "y extent x planes too large for the fused y pass");
-      S.Nq_Ms = 0;  // force N rebuild
-      if (S.X1) { cudaFree(S.X1); S.X1 = nullptr; }
-      if (S.YH) { cudaFree(S.YH); S.YH = nullptr; }
-      if (S.Nq) { cudaFree(S.Nq); S.Nq = nullptr; }
+      if (!thick) {
+        const int P = std::max(3 * S.nz, 3 * S.nz + D.r[2]);
+        if ((size_t)P * S.Qy * sizeof(float2) > 220 * 1024)
+          return fail(ctx, MM_ENOTSUP, "y extent x planes too large for the fused y pass");
+      } else {
+        if ((size_t)(S.Qy + 1) * sizeof(float2) + 4096 > 220 * 1024)
+          return fail(ctx, MM_ENOTSUP, "y extent too large for one shared-memory line");
+        if ((size_t)32 * (S.Qz + 1) * sizeof(float2) + 8192 > 220 * 1024)
+          return fail(ctx, MM_ENOTSUP, "z extent too large for the z pass");
+      }
+      S.Nq_Ms = 0;  // force a spectra rebuild
+      cudaFree(S.X1); cudaFree(S.YH); cudaFree(S.Nq);
+      cudaFree(S.N3); cudaFree(S.S3); cudaFree(S.Y3); cudaFree(S.Z3H);
+      S.X1 = S.YH = S.Y3 = S.Z3H = nullptr;
+      S.Nq = S.N3 = S.S3 = nullptr;
       S.aux.valid = false;
     }
     const size_t qsize = (size_t)S.kxh * S.kyq;
     if (!S.X1) {
       CKS(alloc(ctx, (void**)&S.X1, sizeof(float2) * 3 * S.nz * S.kxh * (size_t)S.ny));
       CKS(alloc(ctx, (void**)&S.YH, sizeof(float2) * 3 * S.nz * S.kxh * (size_t)S.ny));
-      CKS(alloc(ctx, (void**)&S.Nq, sizeof(float) * 6 * S.nz * qsize));
+      if (!S.thick) {
+        CKS(alloc(ctx, (void**)&S.Nq, sizeof(float) * 6 * S.nz * qsize));
+      } else {
+        CKS(alloc(ctx, (void**)&S.N3, sizeof(float) * 6 * qsize * S.kzq));
+        CKS(alloc(ctx, (void**)&S.S3, sizeof(float) * 3 * qsize * S.kzq));
+        CKS(alloc(ctx, (void**)&S.Y3, sizeof(float2) * (size_t)S.kxh * S.Qy * 3 * S.nz));
+        CKS(alloc(ctx, (void**)&S.Z3H, sizeof(float2) * (size_t)3 * S.nz * S.kxh * S.Qy));
+      }
     }
     if (S.Nq_Ms != S.Ms) {
       FftTables fx, fy;
@@ -515,15 +578,19 @@ mm_status ensure_plan(mm_ctx* ctx) {
       CKS(get_fft(ctx, S.Qy, &fy));
       const size_t plane = (size_t)S.Qx * S.Qy;
       CKS(ensure_buf(ctx, &ctx->gen_work, &ctx->gen_work_bytes, sizeof(double2) * 2 * 6 * plane));
-      CKS(ensure_buf(ctx, &ctx->gen_q, &ctx->gen_q_bytes,
-                     std::max(ctx->gen_q_bytes, sizeof(double) * 6 * qsize)));
-      KernelPlan K{S.Qx, S.Qy, S.Wx, S.Wy, S.nz};
-      CK(build_N_spectra(K, fx, fy, S.d[0], S.d[1], S.d[2], -S.Ms / ((double)S.Qx * S.Qy), S.Nq,
-                         ctx->gen_work, ctx->gen_q, ctx->st));
+      if (!S.thick) {
+        CKS(ensure_buf(ctx, &ctx->gen_q, &ctx->gen_q_bytes,
+                       std::max(ctx->gen_q_bytes, sizeof(double) * 6 * qsize)));
+        KernelPlan K{S.Qx, S.Qy, S.Wx, S.Wy, S.nz};
+        CK(build_N_spectra(K, fx, fy, S.d[0], S.d[1], S.d[2], -S.Ms / ((double)S.Qx * S.Qy), S.Nq,
+                           ctx->gen_work, ctx->gen_q, ctx->st));
+      } else {
+        CKS(build_spectra_3d_all(ctx, S, fx, fy));
+      }
       CK(cudaStreamSynchronize(ctx->st));
       S.Nq_Ms = S.Ms;
     }
-    CKS(build_T(ctx, s, &D));
+    if (!S.thick) CKS(build_T(ctx, s, &D));
     CKS(alloc_dir_outputs(ctx, s, &D));
     D.valid = true;
   }
@@ -593,15 +660,17 @@ mm_status run_source_passes(mm_ctx* ctx, const float* in[2], const int* which, i
     Timer t(ctx, 0);
     CK(launch_xfwd(L, Qmax, st));
   }
+  // y stage: thin sources in the fused y pass (z by plane mixing); thick
+  // sources through y forward, z pass and y inverse (z by FFT)
   {
     Launch<YJob> L{};
-    L.njobs = n;
-    int tiles = 0;
+    int tiles = 0, nj = 0;
     size_t smem = 0;
     for (int i = 0; i < n; ++i) {
       Magnet& S = ctx->mag[which[i]];
+      if (S.thick) continue;
       Dir* D = dirs[i];
-      YJob& J = L.job[i];
+      YJob& J = L.job[nj];
       J.in = S.X1;
       J.nz = S.nz; J.ny = S.ny; J.kxh = S.kxh; J.kyq = S.kyq;
       CKS(get_fft(ctx, S.Qy, &J.fy));
@@ -623,12 +692,81 @@ mm_status run_source_passes(mm_ctx* ctx, const float* in[2], const int* which, i
       const int P = std::max(3 * S.nz, Pout);
       // spectra columns + the prefilter index table
       smem = std::max(smem, (size_t)P * S.Qy * sizeof(float2) + ypass_table_bytes(J.do_C ? J.r : 0));
-      L.tile_start[i] = tiles;
+      L.tile_start[nj] = tiles;
       tiles += S.kxh;
+      ++nj;
     }
-    L.tile_start[n] = tiles;
-    Timer t(ctx, 1);
-    CK(launch_ypass(L, smem, st));
+    if (nj) {
+      L.njobs = nj;
+      L.tile_start[nj] = tiles;
+      Timer t(ctx, 1);
+      CK(launch_ypass(L, smem, st));
+    }
+  }
+  {
+    Launch<YFwdJob> Lf{};
+    Launch<ZJob> Lz{};
+    Launch<YInvJob> Li{};
+    int nf = 0, tf = 0, tz = 0, ni = 0, ti = 0;
+    for (int i = 0; i < n; ++i) {
+      Magnet& S = ctx->mag[which[i]];
+      if (!S.thick) continue;
+      Dir* D = dirs[i];
+      FftTables fy, fz;
+      CKS(get_fft(ctx, S.Qy, &fy));
+      CKS(get_fft(ctx, S.Qz, &fz));
+      // planes per y-pass CTA: about 48 KB of lines, at most 16
+      const int group = std::max(1, std::min(16, (int)((48 * 1024) / ((S.Qy + 1) * sizeof(float2)))));
+      const int P3 = 3 * S.nz;
+      YFwdJob& F = Lf.job[nf];
+      F.in = S.X1; F.out = S.Y3; F.planes = P3; F.ny = S.ny; F.kxh = S.kxh; F.group = group; F.fy = fy;
+      Lf.tile_start[nf] = tf;
+      tf += S.kxh * ((P3 + group - 1) / group);
+      ZJob& Z = Lz.job[nf];
+      Z.in = S.Y3; Z.nz = S.nz; Z.kxh = S.kxh; Z.fy = fy; Z.fz = fz; Z.kyq = S.kyq; Z.kzq = S.kzq;
+      Z.N3 = S.N3; Z.S3 = S.S3;
+      Z.do_H = (what[i] & 1) ? 1 : 0;
+      Z.do_C = (what[i] & 2) ? 1 : 0;
+      Z.outH = S.Z3H;
+      if (Z.do_C) {
+        Z.outC = D->Z3C;
+        Z.box_lo = D->box_lo[2]; Z.box_len = D->box_len[2]; Z.start = D->start[2]; Z.r = D->r[2];
+        Z.fir = D->prefilter;
+      }
+      Lz.tile_start[nf] = tz;
+      tz += S.kxh * zpass_tiles(S.Qy);
+      ++nf;
+      if (Z.do_H) {
+        YInvJob& J = Li.job[ni];
+        J = YInvJob{};
+        J.in = S.Z3H; J.planes = P3; J.kxh = S.kxh; J.group = group; J.fy = fy; J.is_C = 0;
+        J.ny = S.ny; J.outH = S.YH;
+        Li.tile_start[ni] = ti;
+        ti += S.kxh * ((P3 + group - 1) / group);
+        ++ni;
+      }
+      if (Z.do_C) {
+        YInvJob& J = Li.job[ni];
+        J = YInvJob{};
+        J.in = D->Z3C; J.planes = D->r[2]; J.kxh = S.kxh; J.group = group; J.fy = fy; J.is_C = 1;
+        J.outC = D->YC;
+        J.box_lo = D->box_lo[1]; J.box_len = D->box_len[1]; J.start = D->start[1]; J.r = D->r[1];
+        J.fir = D->prefilter;
+        Li.tile_start[ni] = ti;
+        ti += S.kxh * ((J.planes + group - 1) / group);
+        ++ni;
+      }
+    }
+    if (nf) {
+      Lf.njobs = nf; Lf.tile_start[nf] = tf;
+      Lz.njobs = nf; Lz.tile_start[nf] = tz;
+      Li.njobs = ni; Li.tile_start[ni] = ti;
+      Timer t(ctx, 1);
+      CK(launch_yfwd3(Lf, st));
+      CK(launch_zpass3(Lz, st));
+      CK(launch_yinv3(Li, st));
+      ctx->launches += 2;
+    }
   }
   {
     Launch<XInvJob> L{};
@@ -957,6 +1095,7 @@ mm_status mm_create(mm_ctx** out, const mm_options* opt) {
   if (e == cudaSuccess) e = cudaMemset(ctx->mech, 0, sizeof(MechState));
   if (e == cudaSuccess) e = init_fft_constants_passes();
   if (e == cudaSuccess) e = init_fft_constants_kgen();
+  if (e == cudaSuccess) e = init_fft_constants_3d();
   if (e != cudaSuccess) {
     mm_destroy(ctx);
     return e == cudaErrorMemoryAllocation ? MM_ENOMEM : MM_ECUDA;
@@ -966,7 +1105,7 @@ mm_status mm_create(mm_ctx** out, const mm_options* opt) {
 }
 
 static void free_dir(Dir& D) {
-  cudaFree(D.Tq); cudaFree(D.YC); cudaFree(D.C); cudaFree(D.partial);
+  cudaFree(D.Tq); cudaFree(D.YC); cudaFree(D.C); cudaFree(D.partial); cudaFree(D.Z3C);
   D = Dir();
 }
 
@@ -981,6 +1120,7 @@ void mm_destroy(mm_ctx* ctx) {
     for (auto p : M.k) cudaFree(p);
     cudaFree(M.Hself); cudaFree(M.Hstray); cudaFree(M.scratch3); cudaFree(M.err_partial);
     cudaFree(M.X1); cudaFree(M.YH); cudaFree(M.Nq);
+    cudaFree(M.N3); cudaFree(M.S3); cudaFree(M.Y3); cudaFree(M.Z3H);
     free_dir(M.dir);
     free_dir(M.aux);
   }
@@ -1006,7 +1146,6 @@ mm_status mm_set_grid(mm_ctx* ctx, int mag, int nx, int ny, int nz, double dx, d
   if (!ctx) return MM_EINVAL;
   if (bad_mag(mag) || nx < 1 || ny < 1 || nz < 1 || !(dx > 0) || !(dy > 0) || !(dz > 0) || !offset_cells)
     return fail(ctx, MM_EINVAL, "mm_set_grid: bad argument");
-  if (nz > kMaxNz) return fail(ctx, MM_ENOTSUP, "mm_set_grid: nz > 4 is not supported by this build");
   const Magnet& O = ctx->mag[1 - mag];
   if (O.grid && (O.d[0] != dx || O.d[1] != dy || O.d[2] != dz))
     return fail(ctx, MM_EINVAL, "mm_set_grid: both magnets must share the cell size");
@@ -1192,9 +1331,13 @@ mm_status mm_compute_potential(mm_ctx* ctx, int src, int prefiltered, float* out
   const size_t need = (size_t)D.box_len[0] * D.box_len[1] * D.box_len[2];
   if (capacity < need) return fail(ctx, MM_EINVAL, "mm_compute_potential: output too small");
   if (!S.mset) return fail(ctx, MM_EINVAL, "magnetisation not set");
-  if ((size_t)std::max(3 * S.nz, D.r[2]) * S.Qy * sizeof(float2) > 220 * 1024)
-    return fail(ctx, MM_ENOTSUP, "box too tall for the fused y pass");
-  CKS(build_T(ctx, src, &D));
+  if (!S.thick) {
+    if ((size_t)std::max(3 * S.nz, D.r[2]) * S.Qy * sizeof(float2) > 220 * 1024)
+      return fail(ctx, MM_ENOTSUP, "box too tall for the fused y pass");
+    CKS(build_T(ctx, src, &D));
+  } else {
+    CKS(ensure_buf(ctx, &D.Z3C, &D.Z3C_bytes, sizeof(float2) * (size_t)D.r[2] * S.kxh * S.Qy));
+  }
   CKS(ensure_buf(ctx, &D.YC, &D.YC_bytes, sizeof(float2) * (size_t)D.r[2] * S.kxh * D.r[1]));
   const float* in[2] = {ctx->mag[0].m, ctx->mag[1].m};
   const int which[1] = {src};
@@ -1406,12 +1549,12 @@ mm_status mm_eval_kernel_fp64(int kind, int n, const double* offsets_dev, double
   return e == cudaSuccess ? MM_OK : MM_ECUDA;
 }
 
-mm_status mm_get_plan_info(mm_ctx* ctx, int src, int fft_dims[2], int box_dims[3], long long box_lo[3],
+mm_status mm_get_plan_info(mm_ctx* ctx, int src, int fft_dims[3], int box_dims[3], long long box_lo[3],
                            int coef_dims[3]) {
   if (!ctx || bad_mag(src)) return MM_EINVAL;
   if (!ctx->planned) CKS(ensure_plan(ctx));
   const Magnet& S = ctx->mag[src];
-  if (fft_dims) { fft_dims[0] = S.Qx; fft_dims[1] = S.Qy; }
+  if (fft_dims) { fft_dims[0] = S.Qx; fft_dims[1] = S.Qy; fft_dims[2] = S.thick ? S.Qz : 0; }
   for (int a = 0; a < 3; ++a) {
     if (box_dims) box_dims[a] = S.dir.box_len[a];
     if (box_lo) box_lo[a] = S.dir.box_lo[a];

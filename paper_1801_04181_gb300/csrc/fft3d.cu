@@ -1,0 +1,273 @@
+// FFT passes for thick magnets (nz > 4): the convolution of Sec. III.A with z
+// by FFT, on a Qx x Qy x Qz circular grid.
+//
+//   x pass (k_xfwd, shared with thin films)          -> X1[plane][kx][y]
+//   y forward (k_yfwd3): y FFT of each column        -> Y3[kx][ypos][plane]
+//   z pass (k_zpass3): per (kx, y position) the z FFT of the three components,
+//       H = -N.M and phi = S.M against the 3D kernel spectra, the inverse z
+//       FFT, and the z prefilter of phi on the box  -> Z[plane][kx][ypos]
+//   y inverse (k_yinv3): inverse y FFT, demag rows and y prefilter
+//                                                    -> Y[plane][kx][row]
+//   x pass (k_xinv, shared)                          -> real rows
+//
+// Planes are (component, z layer) = c nz + z.  Y3 keeps the planes of one
+// (kx, y position) contiguous so the z pass reads them as whole runs, and Z
+// keeps y positions contiguous for the y inverse.  y positions stay in the
+// DIF order of the forward transform; the inverse (DIT) takes them back.
+//
+// Kernel spectra (FP32, generated once in FP64) are stored for kx <= Qx/2,
+// ky <= Qy/2, kz <= Qz/2.  Every component of N and S has a parity in each
+// axis: the six N spectra are real (each off-diagonal is odd in exactly two
+// axes), the three S spectra imaginary (each odd in one); mirrored ky or kz
+// flips the sign of the components odd in that axis.
+#include <algorithm>
+
+#include "fft.cuh"
+#include "mm_internal.h"
+#include "prefilter.cuh"
+
+namespace mm {
+
+constexpr int kZTile = 8;  // y positions per z-pass CTA
+
+// this translation unit's copy of the small-DFT roots (see fft.cuh)
+cudaError_t init_fft_constants_3d() { return upload_roots(); }
+
+// ------------------------------------------------------------------ y forward
+__global__ void __launch_bounds__(256) k_yfwd3(const Launch<YFwdJob> Lc) {
+  extern __shared__ float2 sm[];
+  const int j = find_job(Lc.tile_start, Lc.njobs, blockIdx.x);
+  const YFwdJob& J = Lc.job[j];
+  const int tile = blockIdx.x - Lc.tile_start[j];
+  const int ng = (J.planes + J.group - 1) / J.group;
+  const int kx = tile / ng;
+  const int p0 = (tile - kx * ng) * J.group;
+  const int np = min(J.group, J.planes - p0);
+  const int Q = J.fy.plan.L;
+  const int ldl = Q + 1;  // odd stride: the plane-fastest reads below spread over the banks
+  for (int l = 0; l < np; ++l) {
+    const float2* col = J.in + ((size_t)(p0 + l) * J.kxh + kx) * J.ny;
+    for (int y = threadIdx.x; y < Q; y += blockDim.x)
+      sm[l * ldl + y] = y < J.ny ? col[y] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  fft_smem<kFwdDif, float2>(sm, ldl, np, J.fy.plan, J.fy.tw_f, 0, blockDim.x);
+  float2* dst = J.out + (size_t)kx * Q * J.planes + p0;
+  for (int i = threadIdx.x; i < Q * np; i += blockDim.x) {
+    const int p = i / np, l = i - p * np;
+    dst[(size_t)p * J.planes + l] = sm[l * ldl + p];
+  }
+}
+
+// ------------------------------------------------------------------ z pass
+__device__ __forceinline__ float2 c_i_times(float2 m) { return make_float2(-m.y, m.x); }
+
+__global__ void __launch_bounds__(256) k_zpass3(const Launch<ZJob> Lc) {
+  extern __shared__ float2 sm[];
+  const int j = find_job(Lc.tile_start, Lc.njobs, blockIdx.x);
+  const ZJob& J = Lc.job[j];
+  const int tile = blockIdx.x - Lc.tile_start[j];
+  const int Qy = J.fy.plan.L, Qz = J.fz.plan.L;
+  const int npt = (Qy + kZTile - 1) / kZTile;
+  const int kx = tile / npt;
+  const int y0 = (tile - kx * npt) * kZTile;
+  const int nt = min(kZTile, Qy - y0);
+  const int nz = J.nz, P3 = 3 * nz;
+  const int ldz = Qz + 1;
+  // lines: t * 3 + c (input, then H in place) for t < nt; phi line t at 3 kZTile + t
+  float2* phi = sm + 3 * kZTile * ldz;
+  int* tab = reinterpret_cast<int*>(sm + 4 * kZTile * ldz);
+
+  const float2* src = J.in + ((size_t)kx * Qy + y0) * P3;
+  for (int i = threadIdx.x; i < nt * P3; i += blockDim.x) {
+    const int t = i / P3, q = i - t * P3;
+    const int c = q / nz, z = q - c * nz;
+    sm[(t * 3 + c) * ldz + z] = src[i];
+  }
+  const int pad = Qz - nz;
+  for (int i = threadIdx.x; i < nt * 3 * pad; i += blockDim.x) {
+    const int l = i / pad, z = nz + (i - l * pad);
+    sm[l * ldz + z] = make_float2(0.f, 0.f);
+  }
+  if (J.do_C) build_pref_table(tab, J.r + 2 * kPrefWarm + kZChunk, J.box_lo, J.box_len, J.start, Qz, nullptr);
+  __syncthreads();
+  fft_smem<kFwdDif, float2>(sm, ldz, 3 * nt, J.fz.plan, J.fz.tw_f, 0, blockDim.x);
+
+  // spectral products at the pair (kz, Qz - kz) of every y position of the tile
+  const int half = Qz >> 1;
+  const size_t kstride = (size_t)J.kxh * J.kyq * J.kzq;
+  for (int i = threadIdx.x; i < nt * (half + 1); i += blockDim.x) {
+    const int t = i / (half + 1), kz = i - t * (half + 1);
+    const int ky = fft_freq(y0 + t, J.fy.plan);
+    const bool ym = 2 * ky > Qy;
+    const int kys = ym ? Qy - ky : ky;
+    const bool two = kz != 0 && 2 * kz != Qz;
+    const int q0 = fft_pos(kz, J.fz.plan);
+    const int q1 = two ? fft_pos(Qz - kz, J.fz.plan) : q0;
+    const size_t koff = ((size_t)kx * J.kyq + kys) * J.kzq + kz;
+    float nv[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, sv[3] = {0.f, 0.f, 0.f};
+    if (J.do_H)
+#pragma unroll
+      for (int c = 0; c < 6; ++c) nv[c] = __ldg(J.N3 + c * kstride + koff);
+    if (J.do_C)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) sv[c] = __ldg(J.S3 + c * kstride + koff);
+    const float sy = ym ? -1.f : 1.f;
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      if (side == 1 && !two) break;
+      const int q = side ? q1 : q0;
+      const float sz = side ? -1.f : 1.f;
+      const float2 mx = sm[(t * 3 + 0) * ldz + q], my = sm[(t * 3 + 1) * ldz + q],
+                   mz = sm[(t * 3 + 2) * ldz + q];
+      if (J.do_C) {
+        // phi = i (Sx mx + Sy my + Sz mz); Sy odd in y, Sz odd in z
+        const float ax = sv[0], ay = sy * sv[1], az = sz * sv[2];
+        phi[t * ldz + q] = c_i_times(make_float2(ax * mx.x + ay * my.x + az * mz.x,
+                                                 ax * mx.y + ay * my.y + az * mz.y));
+      }
+      if (J.do_H) {
+        // N real: xy odd in y, xz odd in z, yz odd in both
+        const float nxx = nv[0], nyy = nv[1], nzz = nv[2];
+        const float nxy = sy * nv[3], nxz = sz * nv[4], nyz = sy * sz * nv[5];
+        sm[(t * 3 + 0) * ldz + q] = make_float2(nxx * mx.x + nxy * my.x + nxz * mz.x,
+                                                nxx * mx.y + nxy * my.y + nxz * mz.y);
+        sm[(t * 3 + 1) * ldz + q] = make_float2(nxy * mx.x + nyy * my.x + nyz * mz.x,
+                                                nxy * mx.y + nyy * my.y + nyz * mz.y);
+        sm[(t * 3 + 2) * ldz + q] = make_float2(nxz * mx.x + nyz * my.x + nzz * mz.x,
+                                                nxz * mx.y + nyz * my.y + nzz * mz.y);
+      }
+    }
+  }
+  __syncthreads();
+  if (J.do_H) fft_smem<kInvDit, float2>(sm, ldz, 3 * nt, J.fz.plan, J.fz.tw_f, 0, blockDim.x);
+  if (J.do_C) fft_smem<kInvDit, float2>(phi, ldz, nt, J.fz.plan, J.fz.tw_f, 0, blockDim.x);
+
+  if (J.do_H) {
+    for (int i = threadIdx.x; i < P3 * nt; i += blockDim.x) {
+      const int q = i / nt, t = i - q * nt;
+      const int c = q / nz, z = q - c * nz;
+      J.outH[((size_t)q * J.kxh + kx) * Qy + y0 + t] = sm[(t * 3 + c) * ldz + z];
+    }
+  }
+  if (J.do_C) {
+    const int r = J.r;
+    if (J.fir) {
+      const int nch = (r + kZChunk - 1) / kZChunk;
+      for (int i = threadIdx.x; i < nt * nch; i += blockDim.x) {
+        const int t = i / nch;
+        const int k0 = (i - t * nch) * kZChunk;
+        const float2* line = phi + t * ldz;
+        prefilter_chunk<kZChunk, f2>(
+            k0, r, [&](int jj) { return f2(line[tab[jj]]); },
+            [&](int k, f2 v) { J.outC[((size_t)k * J.kxh + kx) * Qy + y0 + t] = make_float2(v.x, v.y); });
+      }
+    } else {
+      for (int i = threadIdx.x; i < nt * r; i += blockDim.x) {
+        const int k = i / nt, t = i - k * nt;
+        J.outC[((size_t)k * J.kxh + kx) * Qy + y0 + t] = phi[t * ldz + tab[k + kPrefWarm]];
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ y inverse
+__global__ void __launch_bounds__(256) k_yinv3(const Launch<YInvJob> Lc) {
+  extern __shared__ float2 sm[];
+  const int j = find_job(Lc.tile_start, Lc.njobs, blockIdx.x);
+  const YInvJob& J = Lc.job[j];
+  const int tile = blockIdx.x - Lc.tile_start[j];
+  const int ng = (J.planes + J.group - 1) / J.group;
+  const int kx = tile / ng;
+  const int p0 = (tile - kx * ng) * J.group;
+  const int np = min(J.group, J.planes - p0);
+  const int Q = J.fy.plan.L;
+  const int ldl = Q + 1;
+  int* tab = reinterpret_cast<int*>(sm + J.group * ldl);
+  for (int l = 0; l < np; ++l) {
+    const float2* col = J.in + ((size_t)(p0 + l) * J.kxh + kx) * Q;
+    for (int p = threadIdx.x; p < Q; p += blockDim.x) sm[l * ldl + p] = col[p];
+  }
+  if (J.is_C) build_pref_table(tab, J.r + 2 * kPrefWarm + kYChunk, J.box_lo, J.box_len, J.start, Q, nullptr);
+  __syncthreads();
+  fft_smem<kInvDit, float2>(sm, ldl, np, J.fy.plan, J.fy.tw_f, 0, blockDim.x);
+  if (!J.is_C) {
+    for (int l = 0; l < np; ++l) {
+      float2* dst = J.outH + ((size_t)(p0 + l) * J.kxh + kx) * J.ny;
+      for (int y = threadIdx.x; y < J.ny; y += blockDim.x) dst[y] = sm[l * ldl + y];
+    }
+    return;
+  }
+  const int r = J.r;
+  if (J.fir) {
+    const int nch = (r + kYChunk - 1) / kYChunk;
+    for (int i = threadIdx.x; i < np * nch; i += blockDim.x) {
+      const int l = i / nch;
+      const int k0 = (i - l * nch) * kYChunk;
+      const float2* line = sm + l * ldl;
+      float2* dst = J.outC + ((size_t)(p0 + l) * J.kxh + kx) * r;
+      prefilter_chunk<kYChunk, f2>(
+          k0, r, [&](int jj) { return f2(line[tab[jj]]); },
+          [&](int k, f2 v) { dst[k] = make_float2(v.x, v.y); });
+    }
+  } else {
+    for (int l = 0; l < np; ++l) {
+      float2* dst = J.outC + ((size_t)(p0 + l) * J.kxh + kx) * r;
+      for (int k = threadIdx.x; k < r; k += blockDim.x) dst[k] = sm[l * ldl + tab[k + kPrefWarm]];
+    }
+  }
+}
+
+// ------------------------------------------------------------------ host side
+static cudaError_t prep(const void* f, size_t smem) {
+  cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+int zpass_tiles(int Qy) { return (Qy + kZTile - 1) / kZTile; }
+
+cudaError_t launch_yfwd3(const Launch<YFwdJob>& L, cudaStream_t st) {
+  size_t smem = 0;
+  for (int i = 0; i < L.njobs; ++i)
+    smem = std::max(smem, sizeof(float2) * (size_t)L.job[i].group * (L.job[i].fy.plan.L + 1));
+  cudaError_t e = prep((const void*)k_yfwd3, smem);
+  if (e != cudaSuccess) return e;
+  const int grid = L.tile_start[L.njobs];
+  if (grid == 0) return cudaSuccess;
+  k_yfwd3<<<grid, 256, smem, st>>>(L);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zpass3(const Launch<ZJob>& L, cudaStream_t st) {
+  size_t smem = 0;
+  for (int i = 0; i < L.njobs; ++i) {
+    const ZJob& J = L.job[i];
+    const size_t lines = sizeof(float2) * 4 * kZTile * (size_t)(J.fz.plan.L + 1);
+    const size_t tab = sizeof(int) * (size_t)(J.do_C ? J.r + 2 * kPrefWarm + kZChunk : 0);
+    smem = std::max(smem, lines + tab);
+  }
+  cudaError_t e = prep((const void*)k_zpass3, smem);
+  if (e != cudaSuccess) return e;
+  const int grid = L.tile_start[L.njobs];
+  if (grid == 0) return cudaSuccess;
+  k_zpass3<<<grid, 256, smem, st>>>(L);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_yinv3(const Launch<YInvJob>& L, cudaStream_t st) {
+  size_t smem = 0;
+  for (int i = 0; i < L.njobs; ++i) {
+    const YInvJob& J = L.job[i];
+    const size_t lines = sizeof(float2) * (size_t)J.group * (J.fy.plan.L + 1);
+    const size_t tab = sizeof(int) * (size_t)(J.is_C ? J.r + 2 * kPrefWarm + kYChunk : 0);
+    smem = std::max(smem, lines + tab);
+  }
+  cudaError_t e = prep((const void*)k_yinv3, smem);
+  if (e != cudaSuccess) return e;
+  const int grid = L.tile_start[L.njobs];
+  if (grid == 0) return cudaSuccess;
+  k_yinv3<<<grid, 256, smem, st>>>(L);
+  return cudaGetLastError();
+}
+
+}  // namespace mm

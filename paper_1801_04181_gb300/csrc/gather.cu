@@ -6,9 +6,10 @@
 // position f in the source lattice: the 64 weights (cubic B-spline w, w', w''
 // per axis at f, full float precision as in Sec. IV.D) are shared by all
 // cells and the evaluation is a separable 4-tap filter of the coefficient box.
-// A CTA filters the (32 + 3) x (8 + 3) x (nz + 3) coefficient tile of its
-// 32 x 8 target columns along x for the three derivative orders (into shared
-// memory), then each thread finishes y and z for one (x, y) column.
+// A CTA takes 32 x 8 target columns and up to four layers (thick targets
+// are split into chunks of four): it filters the (32 + 3) x (8 + 3) x
+// (layers + 3) coefficient tile along x for the three derivative orders (into
+// shared memory), then each thread finishes y and z for one (x, y) column.
 //
 // Per cell it writes H (A/m) and accumulates sum m . grad phi and
 // sum_a m_a d_a d_b phi (FP32 within a warp, double-float across warps and tiles);
@@ -40,10 +41,10 @@ __device__ __forceinline__ void bspline_w(float t, float* w) {
   w[11] = t;
 }
 
-// y and z stages for one target column (x, y), all NZ layers.
+// y and z stages for one target column (x, y), the NZ layers z0 .. z0 + NZ - 1.
 template <int NZ>
 __device__ __forceinline__ void gather_column(const GatherJob& J, const float* A, int a_n,
-                                              const float (*w_s)[12], int tx, int ty, int x, int y,
+                                              const float (*w_s)[12], int tx, int ty, int x, int y, int z0,
                                               float* acc) {
   constexpr int CZ = NZ + 3;
   float B[6][CZ];
@@ -73,11 +74,11 @@ __device__ __forceinline__ void gather_column(const GatherJob& J, const float* A
   }
   const float* wz = w_s[2];
   const float ix = J.inv_d[0], iy = J.inv_d[1], iz = J.inv_d[2];
-  const size_t N = (size_t)J.nx * J.ny * NZ;
+  const size_t N = (size_t)J.nx * J.ny * J.nz;
   float m[3][NZ];
 #pragma unroll
   for (int zl = 0; zl < NZ; ++zl) {
-    const size_t cell = ((size_t)zl * J.ny + y) * J.nx + x;
+    const size_t cell = ((size_t)(z0 + zl) * J.ny + y) * J.nx + x;
     m[0][zl] = __ldg(J.m + cell);
     m[1][zl] = __ldg(J.m + N + cell);
     m[2][zl] = __ldg(J.m + 2 * N + cell);
@@ -101,7 +102,7 @@ __device__ __forceinline__ void gather_column(const GatherJob& J, const float* A
     gx *= ix; gy *= iy; gz *= iz;
     hxx *= ix * ix; hyy *= iy * iy; hzz *= iz * iz;
     hxy *= ix * iy; hxz *= ix * iz; hyz *= iy * iz;
-    const size_t cell = ((size_t)zl * J.ny + y) * J.nx + x;
+    const size_t cell = ((size_t)(z0 + zl) * J.ny + y) * J.nx + x;
     if (J.H) {
       J.H[cell] = -gx;
       J.H[N + cell] = -gy;
@@ -124,10 +125,14 @@ __global__ void __launch_bounds__(TX * TY, 3) k_gather(const Launch<GatherJob> L
   const int j = find_job(Lc.tile_start, Lc.njobs, blockIdx.x);
   const GatherJob& J = Lc.job[j];
   const int tile = blockIdx.x - Lc.tile_start[j];
-  const int ntx = (J.nx + TX - 1) / TX;
-  const int x0 = (tile % ntx) * TX;
-  const int y0 = (tile / ntx) * TY;
-  const int nz = J.nz;
+  // tile -> (x tile, y tile, chunk of up to kMaxNz layers)
+  const int ntx = (J.nx + TX - 1) / TX, nty = (J.ny + TY - 1) / TY;
+  const int zc = tile / (ntx * nty);
+  const int txy = tile - zc * ntx * nty;
+  const int x0 = (txy % ntx) * TX;
+  const int y0 = (txy / ntx) * TY;
+  const int z0 = zc * kMaxNz;
+  const int nz = min(kMaxNz, J.nz - z0);
   const int cz = nz + 3;
 
   if (threadIdx.x < 3) {
@@ -173,7 +178,7 @@ __global__ void __launch_bounds__(TX * TY, 3) k_gather(const Launch<GatherJob> L
         const int zz = r / (TY + 3), yy = r - zz * (TY + 3);
         // rows past the target's last support row are clamped in the box
         const int gy = min(y0 + yy, J.ny + 2) + sy;
-        const float* src = colp + ((size_t)(zz + sz) * J.ry + gy) * J.rx;
+        const float* src = colp + ((size_t)(z0 + zz + sz) * J.ry + gy) * J.rx;
 #pragma unroll
         for (int k = 0; k < 4; ++k) c[b][k] = __ldg(src + k);
       }
@@ -196,10 +201,10 @@ __global__ void __launch_bounds__(TX * TY, 3) k_gather(const Launch<GatherJob> L
   float acc[4] = {0.f, 0.f, 0.f, 0.f};
   if (!bad && x < J.nx && y < J.ny) {
     switch (nz) {
-      case 1: gather_column<1>(J, A, a_n, w_s, tx, ty, x, y, acc); break;
-      case 2: gather_column<2>(J, A, a_n, w_s, tx, ty, x, y, acc); break;
-      case 3: gather_column<3>(J, A, a_n, w_s, tx, ty, x, y, acc); break;
-      default: gather_column<4>(J, A, a_n, w_s, tx, ty, x, y, acc); break;
+      case 1: gather_column<1>(J, A, a_n, w_s, tx, ty, x, y, z0, acc); break;
+      case 2: gather_column<2>(J, A, a_n, w_s, tx, ty, x, y, z0, acc); break;
+      case 3: gather_column<3>(J, A, a_n, w_s, tx, ty, x, y, z0, acc); break;
+      default: gather_column<4>(J, A, a_n, w_s, tx, ty, x, y, z0, acc); break;
     }
   }
   // FP32 within a warp (at most 32 x nz cells), FP64 from there on: the FP64
@@ -223,10 +228,12 @@ __global__ void __launch_bounds__(TX * TY, 3) k_gather(const Launch<GatherJob> L
   }
 }
 
-int gather_tiles(int nx, int ny) { return ((nx + TX - 1) / TX) * ((ny + TY - 1) / TY); }
+int gather_tiles(int nx, int ny, int nz) {
+  return ((nx + TX - 1) / TX) * ((ny + TY - 1) / TY) * ((nz + kMaxNz - 1) / kMaxNz);
+}
 
 size_t gather_smem(int nz) {
-  const int cz = nz + 3;
+  const int cz = min(nz, kMaxNz) + 3;  // one chunk of layers
   return sizeof(float) * 3 * (size_t)cz * (TY + 3) * TX;
 }
 

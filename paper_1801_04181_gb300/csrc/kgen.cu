@@ -20,6 +20,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <algorithm>
+
 #include "fft.cuh"
 #include "mm_internal.h"
 
@@ -362,6 +364,80 @@ cudaError_t build_T_spectra(const KernelPlan& K, const FftTables& fx, const FftT
   dim3 g((unsigned)((qsize + 255) / 256), 3, n_out * K.nz);
   k_mix_T<<<g, 256, 0, st>>>(Sq, W_dev, Tq, n_out, K.nz, bz, K.nz - 1, qsize, scale);
   return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ 3D spectra
+// q2 [Qz][qsize] (real) -> z lines [qsize][Qz] (complex; the 2D value was the
+// real or the imaginary part of the 2D spectrum)
+__global__ void k_zlines(const double* q2, double2* zl, int Qz, size_t qsize, int imag2d) {
+  __shared__ double tile[32][33];
+  const size_t i0 = (size_t)blockIdx.x * 32;
+  const int z0 = blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int z = z0 + r;
+    const size_t i = i0 + threadIdx.x;
+    tile[r][threadIdx.x] = (z < Qz && i < qsize) ? q2[(size_t)z * qsize + i] : 0.0;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const size_t i = i0 + r;
+    const int z = z0 + threadIdx.x;
+    if (i < qsize && z < Qz) {
+      const double v = tile[threadIdx.x][r];
+      zl[i * Qz + z] = imag2d ? make_double2(0.0, v) : make_double2(v, 0.0);
+    }
+  }
+}
+
+// z-transformed lines [qsize][Qz] -> out [qsize][kzq] (real or imaginary part, scaled)
+__global__ void k_extract_kz(const double2* zl, float* out, int Qz, int kzq, size_t qsize, int take_imag,
+                             double scale) {
+  const size_t n = qsize * kzq;
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const size_t q = i / kzq;
+  const int kz = (int)(i - q * kzq);
+  const double2 v = zl[q * Qz + kz];
+  out[i] = (float)(scale * (take_imag ? v.y : v.x));
+}
+
+// 3D spectra: the 2D quarter spectra of every z offset |dz| <= Wz (laid on
+// the circular z grid), transformed along z in FP64; kz <= Qz/2 is kept.
+cudaError_t build_spectra_3d(int kind, const KernelPlan3& K, const FftTables& fx, const FftTables& fy,
+                             const FftTables& fz, double a, double b, double c, double scale, float* out,
+                             double2* work, double* q2, double* qtmp, double2* zl, cudaStream_t st) {
+  const int ncomp = kind == 0 ? 3 : 6;
+  static const int imagS[3] = {1, 1, 0};           // 2D: S_x, S_y odd in-plane
+  static const int imagN[6] = {0, 0, 0, 0, 1, 1};  // 2D: N_xz, N_yz odd in x or y alone
+  const int* imag2d = kind == 0 ? imagS : imagN;
+  const int take_imag3 = kind == 0 ? 1 : 0;        // S imaginary, N real in 3D
+  const int kxh = K.Qx / 2 + 1, kyq = K.Qy / 2 + 1, kzq = K.Qz / 2 + 1;
+  const size_t qsize = (size_t)kxh * kyq;
+  cudaError_t e = cudaMemsetAsync(q2, 0, sizeof(double) * ncomp * (size_t)K.Qz * qsize, st);
+  if (e != cudaSuccess) return e;
+  for (int dz = -K.Wz; dz <= K.Wz; ++dz) {
+    e = plane_spectra(kind, ncomp, K.Qx, K.Qy, K.Wx, K.Wy, dz, a, b, c, fx, fy, work, qtmp, imag2d, st);
+    if (e != cudaSuccess) return e;
+    const int zs = dz < 0 ? dz + K.Qz : dz;
+    for (int q = 0; q < ncomp; ++q) {
+      e = cudaMemcpyAsync(q2 + ((size_t)q * K.Qz + zs) * qsize, qtmp + (size_t)q * qsize, sizeof(double) * qsize,
+                          cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  cudaFuncSetAttribute(k_fft_lines_d, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)(sizeof(double2) * std::max(K.Qz, std::max(K.Qx, K.Qy))));
+  for (int q = 0; q < ncomp; ++q) {
+    dim3 tg((unsigned)((qsize + 31) / 32), (K.Qz + 31) / 32);
+    k_zlines<<<tg, dim3(32, 8), 0, st>>>(q2 + (size_t)q * K.Qz * qsize, zl, K.Qz, qsize, imag2d[q]);
+    k_fft_lines_d<<<(unsigned)qsize, 256, sizeof(double2) * K.Qz, st>>>(zl, (int)qsize, fz);
+    const size_t n = qsize * kzq;
+    k_extract_kz<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(zl, out + (size_t)q * n, K.Qz, kzq, qsize,
+                                                              take_imag3, scale);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace mm

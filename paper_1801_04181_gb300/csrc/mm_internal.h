@@ -73,6 +73,43 @@ struct XInvJob {
   int box_lo, box_len, start, out_len, fir;
 };
 
+// ---------------------------------------------------------------- 3D sources (nz > kMaxNz)
+// y FFT of X1 columns; out[kx][pos][plane], positions in the plan's DIF order
+struct YFwdJob {
+  const float2* in;       // [planes][kxh][ny]
+  float2* out;            // [kxh][Qy][planes]
+  int planes, ny, kxh;
+  int group;              // planes per CTA
+  FftTables fy;
+};
+
+// z FFT, spectral products, inverse z FFT and z prefilter for a tile of y positions
+struct ZJob {
+  const float2* in;       // [kxh][Qy][3 nz]
+  int nz, kxh;
+  FftTables fy, fz;       // fy: frequency of a y position; fz: the z transforms
+  int kyq, kzq;           // stored ky <= Qy/2, kz <= Qz/2
+  const float* N3;        // [6][kxh][kyq][kzq], -Ms N / (Qx Qy Qz)
+  const float* S3;        // [3][kxh][kyq][kzq], imaginary parts of Ms S / (Qx Qy Qz)
+  int do_H, do_C;
+  float2* outH;           // [3 nz][kxh][Qy]
+  float2* outC;           // [r][kxh][Qy]
+  int box_lo, box_len, start, r, fir;  // z box of the coefficient planes
+};
+
+// inverse y FFT (DIF-order positions in, natural out) and the y outputs
+struct YInvJob {
+  const float2* in;       // [planes][kxh][Qy]
+  int planes, kxh;
+  int group;
+  FftTables fy;
+  int is_C;               // 0: demag rows y < ny -> outH; 1: coefficient rows -> outC
+  int ny;
+  float2* outH;           // [planes][kxh][ny]
+  float2* outC;           // [planes][kxh][r]
+  int box_lo, box_len, start, r, fir;  // y box
+};
+
 // ---------------------------------------------------------------- gather
 struct GatherJob {
   const float* C;         // coefficients [rz][ry][rx]
@@ -171,13 +208,23 @@ struct KernelPlan {
   int nz;                 // source layers
 };
 
+struct KernelPlan3 {
+  int Qx, Qy, Qz;
+  int Wx, Wy, Wz;
+};
+
 cudaError_t init_fft_constants_passes();
 cudaError_t init_fft_constants_kgen();
+cudaError_t init_fft_constants_3d();
 size_t ypass_table_bytes(int r);
 cudaError_t launch_xfwd(const Launch<XFwdJob>& L, int Qmax, cudaStream_t st);
 cudaError_t launch_ypass(const Launch<YJob>& L, size_t smem, cudaStream_t st);
 cudaError_t launch_xinv(const Launch<XInvJob>& L, int Qmax, cudaStream_t st);
-int gather_tiles(int nx, int ny);
+cudaError_t launch_yfwd3(const Launch<YFwdJob>& L, cudaStream_t st);
+cudaError_t launch_zpass3(const Launch<ZJob>& L, cudaStream_t st);
+cudaError_t launch_yinv3(const Launch<YInvJob>& L, cudaStream_t st);
+int zpass_tiles(int Qy);
+int gather_tiles(int nx, int ny, int nz);  // 32 x 8 columns x up to kMaxNz layers
 size_t gather_smem(int nz);
 cudaError_t launch_gather(const Launch<GatherJob>& L, int nz_max, cudaStream_t st);
 cudaError_t launch_stage(const Launch<StageJob>& L, const MechParams& Perr, int* ticket, cudaStream_t st);
@@ -189,6 +236,12 @@ cudaError_t eval_points_fp64(int kind, int n, const double* off_dev, double a, d
 cudaError_t build_N_spectra(const KernelPlan& K, const FftTables& fx, const FftTables& fy, double a,
                             double b, double c, double scale, float* Nq, double2* work, double* qbuf,
                             cudaStream_t st);
+// 3D spectra of S (kind 0, 3 comps) or N (kind 1, 6 comps): out [comp][kxh][kyq][kzq].
+// Scratch: work 2 * ncomp * Qx * Qy double2, q2 ncomp * Qz * kxh * kyq double,
+// qtmp ncomp * kxh * kyq double, zl kxh * kyq * Qz double2.
+cudaError_t build_spectra_3d(int kind, const KernelPlan3& K, const FftTables& fx, const FftTables& fy,
+                             const FftTables& fz, double a, double b, double c, double scale, float* out,
+                             double2* work, double* q2, double* qtmp, double2* zl, cudaStream_t st);
 cudaError_t build_T_spectra(const KernelPlan& K, const FftTables& fx, const FftTables& fy, double a,
                             double b, double c, double scale, int box_lo_z, int bz, int n_out,
                             const double* W_dev, float* Tq, double2* work, double* Sq,

@@ -109,7 +109,7 @@ extern "C" mm_status mm_spline_field_noalloc(const float* coef_dev, const int co
     return MM_EINVAL;
   for (int a = 0; a < 3; ++a)
     if (coef_dims[a] < 4 || !isfinite(pos0_nodes[a])) return MM_EINVAL;
-  const int ntiles = gather_tiles(nx, ny);
+  const int ntiles = gather_tiles(nx, ny, nz);
   if (ntiles > kNoAllocMaxTiles) return MM_ETOOBIG;
   // support of every target centre must lie inside the coefficient box
   const int n[3] = {nx, ny, nz};

@@ -234,7 +234,7 @@ def test_bad_arguments_are_rejected():
 
     mm = MovingMagnets()
     with pytest.raises(MMError):
-        mm.set_grid(0, (8, 8, 5), (1e-9, 1e-9, 1e-9))   # nz > 4
+        mm.set_grid(0, (8, 8, 0), (1e-9, 1e-9, 1e-9))   # empty grid
     with pytest.raises(MMError):
         mm.set_grid(2, (8, 8, 1), (1e-9, 1e-9, 1e-9))   # no magnet 2
     mm.set_grid(0, (8, 8, 1), (1e-9, 1e-9, 1e-9))

@@ -84,7 +84,9 @@ class Mechanics:
 
 @dataclass
 class FilmPair:
-    """Two magnets stacked along z: base at the origin, slider `gap` cells above."""
+    """Two magnets: base at the origin, slider `gap` cells beyond it along
+    `stack_axis` (z for films, x for side-by-side cubes), shifted by `lateral`
+    cells along the two other axes."""
     name: str
     n_base: tuple
     n_slider: tuple
@@ -95,11 +97,16 @@ class FilmPair:
     mech: Mechanics = field(default_factory=Mechanics)
     u0: tuple = (0.0, 0.0, 0.0)
     H_ext: tuple = (0.0, 0.0, 0.0)
-    lateral: tuple = (0, 0)      # slider lattice offset in x, y (cells)
+    lateral: tuple = (0, 0)      # slider lattice offset along the other two axes (cells)
+    stack_axis: int = 2
 
     @property
     def offsets(self):
-        return [(0, 0, 0), (self.lateral[0], self.lateral[1], self.n_base[2] + self.gap)]
+        o = [0, 0, 0]
+        others = [a for a in range(3) if a != self.stack_axis]
+        o[others[0]], o[others[1]] = self.lateral
+        o[self.stack_axis] = self.n_base[self.stack_axis] + self.gap
+        return [(0, 0, 0), tuple(o)]
 
     def cells(self):
         return int(np.prod(self.n_base)) + int(np.prod(self.n_slider))
@@ -120,3 +127,12 @@ def film_pair_stick_slip(n=(1024, 256, 2), gap=5, seed=0):
     fp = FilmPair("stick_slip_%dx%dx%d_gap%d" % (n + (gap,)), n, n, (4e-9, 4e-9, 4e-9), gap,
                   mat, mat, mech)
     return fp, pma_domains(n, seed), pma_domains(n, seed + 1)
+
+
+def cube_pair(n=(64, 64, 64), gap=3, seed=0):
+    """Two vortex-seeded cubes of 2 nm cells side by side along x, `gap` cells
+    apart; Ms=8e5 A/m, Aex=1.3e-11 J/m, no anisotropy, alpha=0.5."""
+    mat = Material(Ms=8e5, Aex=1.3e-11, Ku=0.0, alpha=0.5)
+    fp = FilmPair("cube_pair_%dx%dx%d_gap%d" % (n + (gap,)), n, n, (2e-9, 2e-9, 2e-9), gap, mat, mat,
+                  stack_axis=0)
+    return fp, vortex(n, seed), vortex(n, seed + 1)
