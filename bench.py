@@ -30,7 +30,8 @@ METRIC = "stray-field+LLG cell-updates/s, FP32 vs mixed-prec at <=1e-4 rel L2; %
 UNIT = "cell-updates/s"
 WORKLOAD = "stick-slip PMA film pair 1024x256x2 (4 nm), gap 5, spring-pulled, adaptive DP45"
 TIMING_CLASSES = ["fft_x_forward", "fft_y_pass_mix_prefilter", "fft_x_inverse_prefilter",
-                  "spline_gather_force", "llg_stage", "slider_reduce", "combine_normalise"]
+                  "spline_gather_force", "llg_stage", "slider_reduce", "combine_normalise",
+                  "fft_y_forward_thick", "fft_z_pass_thick", "fft_y_inverse_thick"]
 
 
 def parse():
@@ -324,7 +325,7 @@ def run_gpu(args):
             "peak": peak, "peak_source": src, "unit": "GB/s", "frac": round(achieved / peak, 4),
             "algorithmic_bytes_per_launch": int(ab[dom]), "avg_launch_ms": round(avg_s * 1e3, 5),
             "traffic": traffic, "traffic_source": traffic_src}
-    ktab = {TIMING_CLASSES[c]: {"ms": round(kt[c][0], 3), "launches": kt[c][1]} for c in kt}
+    ktab = {TIMING_CLASSES[c]: {"ms": round(kt[c][0], 3), "launches": kt[c][1]} for c in kt if kt[c][1]}
     if pool is not None:
         try:
             cpu_base = cpu_oracle_sample(fp, m0, m1, pool)

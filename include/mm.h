@@ -186,7 +186,8 @@ mm_status mm_get_plan_info(mm_ctx* ctx, int src, int fft_dims[3], int box_dims[3
 
 /* Per-kernel timing with CUDA events on the context stream (off by default).
  * Classes: 0 x-forward FFT, 1 y pass, 2 x-inverse FFT, 3 gather, 4 LLG stage,
- * 5 slider/reduction, 6 combine/normalise. */
+ * 5 slider/reduction, 6 combine/normalise; thick sources: 7 y forward,
+ * 8 z pass, 9 y inverse. */
 mm_status mm_set_timing(mm_ctx* ctx, int on);
 mm_status mm_get_timing(mm_ctx* ctx, int kernel_class, double* total_ms, long long* launches);
 mm_status mm_reset_timing(mm_ctx* ctx);

@@ -33,7 +33,7 @@ namespace {
 constexpr double kMu0 = 4e-7 * 3.14159265358979323846;
 constexpr double kGammaLL = 1.7595e11;  // rad / (s T)
 constexpr int kWindowSlack = 8;         // cells of displacement before the FFT grid is re-planned
-constexpr int kTimingClasses = 7;
+constexpr int kTimingClasses = 10;
 
 // Dormand-Prince 5(4)
 const double DP_C[7] = {0.0, 1.0 / 5, 3.0 / 10, 4.0 / 5, 8.0 / 9, 1.0, 1.0};
@@ -549,7 +549,7 @@ mm_status ensure_plan(mm_ctx* ctx) {
       } else {
         if ((size_t)(S.Qy + 1) * sizeof(float2) + 4096 > 220 * 1024)
           return fail(ctx, MM_ENOTSUP, "y extent too large for one shared-memory line");
-        if ((size_t)32 * (S.Qz + 1) * sizeof(float2) + 8192 > 220 * 1024)
+        if ((size_t)4 * zpass_tile(S.Qz) * (S.Qz + 1) * sizeof(float2) + 8192 > 220 * 1024)
           return fail(ctx, MM_ENOTSUP, "z extent too large for the z pass");
       }
       S.Nq_Ms = 0;  // force a spectra rebuild
@@ -733,8 +733,9 @@ mm_status run_source_passes(mm_ctx* ctx, const float* in[2], const int* which, i
         Z.box_lo = D->box_lo[2]; Z.box_len = D->box_len[2]; Z.start = D->start[2]; Z.r = D->r[2];
         Z.fir = D->prefilter;
       }
+      Z.ztile = zpass_tile(S.Qz);
       Lz.tile_start[nf] = tz;
-      tz += S.kxh * zpass_tiles(S.Qy);
+      tz += S.kxh * zpass_tiles(S.Qy, Z.ztile);
       ++nf;
       if (Z.do_H) {
         YInvJob& J = Li.job[ni];
@@ -761,11 +762,16 @@ mm_status run_source_passes(mm_ctx* ctx, const float* in[2], const int* which, i
       Lf.njobs = nf; Lf.tile_start[nf] = tf;
       Lz.njobs = nf; Lz.tile_start[nf] = tz;
       Li.njobs = ni; Li.tile_start[ni] = ti;
-      Timer t(ctx, 1);
-      CK(launch_yfwd3(Lf, st));
-      CK(launch_zpass3(Lz, st));
+      {
+        Timer t(ctx, 7);
+        CK(launch_yfwd3(Lf, st));
+      }
+      {
+        Timer t(ctx, 8);
+        CK(launch_zpass3(Lz, st));
+      }
+      Timer t(ctx, 9);
       CK(launch_yinv3(Li, st));
-      ctx->launches += 2;
     }
   }
   {

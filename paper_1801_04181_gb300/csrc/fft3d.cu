@@ -28,13 +28,11 @@
 
 namespace mm {
 
-constexpr int kZTile = 8;  // y positions per z-pass CTA
-
 // this translation unit's copy of the small-DFT roots (see fft.cuh)
 cudaError_t init_fft_constants_3d() { return upload_roots(); }
 
 // ------------------------------------------------------------------ y forward
-__global__ void __launch_bounds__(256) k_yfwd3(const Launch<YFwdJob> Lc) {
+__global__ void __launch_bounds__(256, 2) k_yfwd3(const Launch<YFwdJob> Lc) {
   extern __shared__ float2 sm[];
   const int j = find_job(Lc.tile_start, Lc.njobs, blockIdx.x);
   const YFwdJob& J = Lc.job[j];
@@ -62,21 +60,22 @@ __global__ void __launch_bounds__(256) k_yfwd3(const Launch<YFwdJob> Lc) {
 // ------------------------------------------------------------------ z pass
 __device__ __forceinline__ float2 c_i_times(float2 m) { return make_float2(-m.y, m.x); }
 
-__global__ void __launch_bounds__(256) k_zpass3(const Launch<ZJob> Lc) {
+__global__ void __launch_bounds__(256, 2) k_zpass3(const Launch<ZJob> Lc) {
   extern __shared__ float2 sm[];
   const int j = find_job(Lc.tile_start, Lc.njobs, blockIdx.x);
   const ZJob& J = Lc.job[j];
   const int tile = blockIdx.x - Lc.tile_start[j];
   const int Qy = J.fy.plan.L, Qz = J.fz.plan.L;
-  const int npt = (Qy + kZTile - 1) / kZTile;
+  const int zt = J.ztile;
+  const int npt = (Qy + zt - 1) / zt;
   const int kx = tile / npt;
-  const int y0 = (tile - kx * npt) * kZTile;
-  const int nt = min(kZTile, Qy - y0);
+  const int y0 = (tile - kx * npt) * zt;
+  const int nt = min(zt, Qy - y0);
   const int nz = J.nz, P3 = 3 * nz;
   const int ldz = Qz + 1;
-  // lines: t * 3 + c (input, then H in place) for t < nt; phi line t at 3 kZTile + t
-  float2* phi = sm + 3 * kZTile * ldz;
-  int* tab = reinterpret_cast<int*>(sm + 4 * kZTile * ldz);
+  // lines: t * 3 + c (input, then H in place) for t < nt; phi line t at 3 zt + t
+  float2* phi = sm + 3 * zt * ldz;
+  int* tab = reinterpret_cast<int*>(sm + 4 * zt * ldz);
 
   const float2* src = J.in + ((size_t)kx * Qy + y0) * P3;
   for (int i = threadIdx.x; i < nt * P3; i += blockDim.x) {
@@ -172,7 +171,7 @@ __global__ void __launch_bounds__(256) k_zpass3(const Launch<ZJob> Lc) {
 }
 
 // ------------------------------------------------------------------ y inverse
-__global__ void __launch_bounds__(256) k_yinv3(const Launch<YInvJob> Lc) {
+__global__ void __launch_bounds__(256, 3) k_yinv3(const Launch<YInvJob> Lc) {
   extern __shared__ float2 sm[];
   const int j = find_job(Lc.tile_start, Lc.njobs, blockIdx.x);
   const YInvJob& J = Lc.job[j];
@@ -224,7 +223,10 @@ static cudaError_t prep(const void* f, size_t smem) {
   return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-int zpass_tiles(int Qy) { return (Qy + kZTile - 1) / kZTile; }
+// about 80 KB of lines per CTA (two CTAs per SM), at least 8 y positions:
+// short z grids get many positions, which spreads the per-CTA set-up
+int zpass_tile(int Qz) { return std::max(8, (80 * 1024) / (4 * (Qz + 1) * (int)sizeof(float2))); }
+int zpass_tiles(int Qy, int ztile) { return (Qy + ztile - 1) / ztile; }
 
 cudaError_t launch_yfwd3(const Launch<YFwdJob>& L, cudaStream_t st) {
   size_t smem = 0;
@@ -242,7 +244,7 @@ cudaError_t launch_zpass3(const Launch<ZJob>& L, cudaStream_t st) {
   size_t smem = 0;
   for (int i = 0; i < L.njobs; ++i) {
     const ZJob& J = L.job[i];
-    const size_t lines = sizeof(float2) * 4 * kZTile * (size_t)(J.fz.plan.L + 1);
+    const size_t lines = sizeof(float2) * 4 * J.ztile * (size_t)(J.fz.plan.L + 1);
     const size_t tab = sizeof(int) * (size_t)(J.do_C ? J.r + 2 * kPrefWarm + kZChunk : 0);
     smem = std::max(smem, lines + tab);
   }

@@ -95,6 +95,7 @@ struct ZJob {
   float2* outH;           // [3 nz][kxh][Qy]
   float2* outC;           // [r][kxh][Qy]
   int box_lo, box_len, start, r, fir;  // z box of the coefficient planes
+  int ztile;              // y positions per CTA
 };
 
 // inverse y FFT (DIF-order positions in, natural out) and the y outputs
@@ -223,7 +224,8 @@ cudaError_t launch_xinv(const Launch<XInvJob>& L, int Qmax, cudaStream_t st);
 cudaError_t launch_yfwd3(const Launch<YFwdJob>& L, cudaStream_t st);
 cudaError_t launch_zpass3(const Launch<ZJob>& L, cudaStream_t st);
 cudaError_t launch_yinv3(const Launch<YInvJob>& L, cudaStream_t st);
-int zpass_tiles(int Qy);
+int zpass_tile(int Qz);                 // y positions per z-pass CTA for a z grid
+int zpass_tiles(int Qy, int ztile);
 int gather_tiles(int nx, int ny, int nz);  // 32 x 8 columns x up to kMaxNz layers
 size_t gather_smem(int nz);
 cudaError_t launch_gather(const Launch<GatherJob>& L, int nz_max, cudaStream_t st);
