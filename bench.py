@@ -29,6 +29,14 @@ sys.path.insert(0, ROOT)
 METRIC = "stray-field+LLG cell-updates/s, FP32 vs mixed-prec at <=1e-4 rel L2; % HBM roof"
 UNIT = "cell-updates/s"
 WORKLOAD = "stick-slip PMA film pair 1024x256x2 (4 nm), gap 5, spring-pulled, adaptive DP45"
+# name -> (description, builder); the thick ones plan z by FFT
+WORKLOADS = {
+    "stick_slip": (WORKLOAD, lambda seed: __import__("workloads").film_pair_stick_slip(seed=seed)),
+    "cubes64": ("vortex cube pair 64x64x64 (2 nm), gap 3 along x, spring-pulled, adaptive DP45",
+                lambda seed: __import__("workloads").cube_pair((64, 64, 64), 3, seed)),
+    "films512x512x8": ("random-unit film pair 512x512x8 (4 nm), gap 1, adaptive DP45",
+                       lambda seed: __import__("workloads").film_pair_plain((512, 512, 8), 1, seed)),
+}
 TIMING_CLASSES = ["fft_x_forward", "fft_y_pass_mix_prefilter", "fft_x_inverse_prefilter",
                   "spline_gather_force", "llg_stage", "slider_reduce", "combine_normalise",
                   "fft_y_forward_thick", "fft_z_pass_thick", "fft_y_inverse_thick"]
@@ -42,6 +50,8 @@ def parse():
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--seed", type=int, default=0)
+    p.add_argument("--workload", default="stick_slip", choices=sorted(WORKLOADS),
+                   help="stick_slip (the headline workload) or a thick-source workload")
     return p.parse_args()
 
 
@@ -155,10 +165,10 @@ def algorithmic_bytes(mm, fp):
     return {0: xf, 1: yp, 2: xi, 3: ga, 4: st}
 
 
-KERNEL_OF_CLASS = {0: ("k_xfwd", ["fft_passes.cu", "fft.cuh", "mm_internal.h"]),
-                   1: ("k_ypass", ["fft_passes.cu", "fft.cuh", "mm_internal.h"]),
-                   2: ("k_xinv", ["fft_passes.cu", "fft.cuh", "mm_internal.h"]),
-                   3: ("k_gather", ["gather.cu", "mm_internal.h"]),
+KERNEL_OF_CLASS = {0: ("k_xfwd", ["fft_passes.cu", "fft.cuh", "prefilter.cuh", "mm_internal.h"]),
+                   1: ("k_ypass", ["fft_passes.cu", "fft.cuh", "prefilter.cuh", "mm_internal.h"]),
+                   2: ("k_xinv", ["fft_passes.cu", "fft.cuh", "prefilter.cuh", "mm_internal.h"]),
+                   3: ("k_gather", ["gather.cu", "dfloat.cuh", "mm_internal.h"]),
                    4: ("k_stage", ["llg.cu", "mm_internal.h"])}
 
 
@@ -255,7 +265,8 @@ def run_gpu(args):
         import multiprocessing as mp
         pool = mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1)))
 
-    fp, m0, m1 = workloads.film_pair_stick_slip(seed=args.seed + 101 * rank)
+    wl_name, wl_make = WORKLOADS[args.workload]
+    fp, m0, m1 = wl_make(args.seed + 101 * rank)
     mm = gpu_pair(fp, m0, m1, adaptive=True, rtol=1e-5)
     cells = fp.cells()
     stream = torch.cuda.current_stream()
@@ -320,12 +331,13 @@ def run_gpu(args):
     avg_s = tot_ms / max(nl, 1) / 1e3
     peak, src = measured_peaks()
     achieved = ab[dom] / avg_s / 1e9
-    traffic, traffic_src = profiled_traffic(dom)
+    traffic, traffic_src = profiled_traffic(dom) if args.workload == "stick_slip" else (None, None)
     roof = {"bound": "hbm", "kernel": TIMING_CLASSES[dom], "achieved": round(achieved, 1),
             "peak": peak, "peak_source": src, "unit": "GB/s", "frac": round(achieved / peak, 4),
             "algorithmic_bytes_per_launch": int(ab[dom]), "avg_launch_ms": round(avg_s * 1e3, 5),
             "traffic": traffic, "traffic_source": traffic_src}
     ktab = {TIMING_CLASSES[c]: {"ms": round(kt[c][0], 3), "launches": kt[c][1]} for c in kt if kt[c][1]}
+    fft_cmp = cufft_compare(mm, fp, kt) if args.workload == "stick_slip" else None
     if pool is not None:
         try:
             cpu_base = cpu_oracle_sample(fp, m0, m1, pool)
@@ -337,7 +349,8 @@ def run_gpu(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "cells": cells, "fft": [mm.plan_info(0)["fft"]],
+            "config": {"workload": wl_name, "cells": cells,
+                       "fft": [list(mm.plan_info(0)["fft"]) + [mm.plan_info(0)["Qz"]]],
                        "adaptive_rtol": 1e-5, "accepted": acc1 - acc0, "rejected": rej1 - rej0,
                        "dt_final_s": dt, "parallelism": "replicas" if world > 1 else "single",
                        "l2": "no flush: per-step working set (~0.4 GB of spectra, kernels and RK "
@@ -347,6 +360,7 @@ def run_gpu(args):
             "gpu_launches": int(launches),
             "roofline": roof,
             "kernel_times": ktab,
+            "cufft_compare": fft_cmp,
             "clocks": clk,
             "cpu_baseline": cpu_base,
         }
@@ -355,6 +369,43 @@ def run_gpu(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def cufft_compare(mm, fp, kt, reps=20):
+    """cuFFT (through torch.fft) on the same grid, as a timed comparison only.
+
+    R2C of the source planes of both magnets and C2R of their output planes on
+    the zero-padded Qx x Qy grid: the bare transforms, with neither the
+    spectral products nor the prefilters that our three FFT passes also do.
+    """
+    import torch
+    info = [mm.plan_info(0), mm.plan_info(1)]
+    Qx, Qy = info[0]["fft"]
+    if info[0]["Qz"] or info[1]["Qz"]:
+        return None
+    nx, ny, nz = fp.n_base
+    n_in = 2 * 3 * nz
+    n_out = 2 * 3 * nz + info[0]["coef"][2] + info[1]["coef"][2]
+    x = torch.zeros((n_in, Qy, Qx), device="cuda")
+    x[:, :ny, :nx] = torch.randn((n_in, ny, nx), device="cuda")
+    Xo = torch.randn((n_out, Qy, Qx // 2 + 1), device="cuda", dtype=torch.complex64)
+    for _ in range(3):
+        torch.fft.rfft2(x)
+        torch.fft.irfft2(Xo, s=(Qy, Qx))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        torch.fft.rfft2(x)
+        torch.fft.irfft2(Xo, s=(Qy, Qx))
+    e1.record()
+    torch.cuda.synchronize()
+    ours = sum(kt[c][0] / max(kt[c][1], 1) for c in (0, 1, 2))
+    return {"cufft_ms_per_evaluation": round(e0.elapsed_time(e1) / reps, 4),
+            "ours_ms_per_evaluation": round(ours, 4),
+            "what": "cuFFT R2C of %d planes + C2R of %d planes on %dx%d (bare transforms) vs "
+                    "our x-forward, y and x-inverse passes (transforms + spectral products + "
+                    "prefilters)" % (n_in, n_out, Qx, Qy)}
 
 
 def run_reference(args):
