@@ -95,8 +95,10 @@ struct Magnet {
   float2* X1 = nullptr;
   float2* YH = nullptr;
   float* Nq = nullptr;
-  // thick sources (z by FFT): grid depth, spectra and the y / z pass buffers
-  bool thick = false;
+  // thick sources (y-forward, z and y-inverse passes): z by a direct sum over
+  // planes (zfft false, nz <= kMaxNzDirect; spectra Nq and Tq as for thin
+  // films) or by FFT (grid depth, spectra N3 / S3)
+  bool thick = false, zfft = false;
   int Qz = 0, Wz = 0, kzq = 0;
   float* N3 = nullptr;     // [6][kxh][kyq][kzq]
   float* S3 = nullptr;     // [3][kxh][kyq][kzq]
@@ -516,13 +518,16 @@ mm_status ensure_plan(mm_ctx* ctx) {
     Dir& D = S.dir;
     dir_geometry(ctx, s, false, &D);
     D.prefilter = 1;
-    // z by FFT when the source is thick or the box around the target is tall
+    // separate y / z passes when the source is thick or the box around the
+    // target is tall; z by FFT only for sources thicker than kMaxNzDirect
     const bool thick = S.nz > kMaxNz || ctx->mag[1 - s].nz > kMaxNz;
+    const bool zfft = thick && S.nz > kMaxNzDirect;
     const int wx = window_needed(S, D, 0), wy = window_needed(S, D, 1), wz = window_needed(S, D, 2);
     const bool regrid = S.Qx == 0 || 2 * wx + 2 > S.Qx || 2 * wy + 2 > S.Qy || thick != S.thick ||
-                        (thick && 2 * wz + 2 > S.Qz);
+                        zfft != S.zfft || (zfft && 2 * wz + 2 > S.Qz);
     if (regrid) {
       S.thick = thick;
+      S.zfft = zfft;
       S.Wx = wx + kWindowSlack;
       S.Wy = wy + kWindowSlack;
       S.Qx = smooth_even_at_least(2 * S.Wx + 2);
@@ -532,7 +537,7 @@ mm_status ensure_plan(mm_ctx* ctx) {
       S.Wy = (S.Qy - 2) / 2;
       S.kxh = S.Qx / 2 + 1;
       S.kyq = S.Qy / 2 + 1;
-      if (thick) {
+      if (zfft) {
         S.Wz = wz + kWindowSlack;
         S.Qz = smooth_even_at_least(2 * S.Wz + 2);
         S.Wz = (S.Qz - 2) / 2;
@@ -549,7 +554,7 @@ mm_status ensure_plan(mm_ctx* ctx) {
       } else {
         if ((size_t)(S.Qy + 1) * sizeof(float2) + 4096 > 220 * 1024)
           return fail(ctx, MM_ENOTSUP, "y extent too large for one shared-memory line");
-        if ((size_t)4 * zpass_tile(S.Qz) * (S.Qz + 1) * sizeof(float2) + 8192 > 220 * 1024)
+        if (zfft && (size_t)4 * zpass_tile(S.Qz) * (S.Qz + 1) * sizeof(float2) + 8192 > 220 * 1024)
           return fail(ctx, MM_ENOTSUP, "z extent too large for the z pass");
       }
       S.Nq_Ms = 0;  // force a spectra rebuild
@@ -563,11 +568,13 @@ mm_status ensure_plan(mm_ctx* ctx) {
     if (!S.X1) {
       CKS(alloc(ctx, (void**)&S.X1, sizeof(float2) * 3 * S.nz * S.kxh * (size_t)S.ny));
       CKS(alloc(ctx, (void**)&S.YH, sizeof(float2) * 3 * S.nz * S.kxh * (size_t)S.ny));
-      if (!S.thick) {
+      if (!S.zfft) {
         CKS(alloc(ctx, (void**)&S.Nq, sizeof(float) * 6 * S.nz * qsize));
       } else {
         CKS(alloc(ctx, (void**)&S.N3, sizeof(float) * 6 * qsize * S.kzq));
         CKS(alloc(ctx, (void**)&S.S3, sizeof(float) * 3 * qsize * S.kzq));
+      }
+      if (S.thick) {
         CKS(alloc(ctx, (void**)&S.Y3, sizeof(float2) * (size_t)S.kxh * S.Qy * 3 * S.nz));
         CKS(alloc(ctx, (void**)&S.Z3H, sizeof(float2) * (size_t)3 * S.nz * S.kxh * S.Qy));
       }
@@ -578,7 +585,7 @@ mm_status ensure_plan(mm_ctx* ctx) {
       CKS(get_fft(ctx, S.Qy, &fy));
       const size_t plane = (size_t)S.Qx * S.Qy;
       CKS(ensure_buf(ctx, &ctx->gen_work, &ctx->gen_work_bytes, sizeof(double2) * 2 * 6 * plane));
-      if (!S.thick) {
+      if (!S.zfft) {
         CKS(ensure_buf(ctx, &ctx->gen_q, &ctx->gen_q_bytes,
                        std::max(ctx->gen_q_bytes, sizeof(double) * 6 * qsize)));
         KernelPlan K{S.Qx, S.Qy, S.Wx, S.Wy, S.nz};
@@ -590,7 +597,7 @@ mm_status ensure_plan(mm_ctx* ctx) {
       CK(cudaStreamSynchronize(ctx->st));
       S.Nq_Ms = S.Ms;
     }
-    if (!S.thick) CKS(build_T(ctx, s, &D));
+    if (!S.zfft) CKS(build_T(ctx, s, &D));
     CKS(alloc_dir_outputs(ctx, s, &D));
     D.valid = true;
   }
@@ -706,51 +713,70 @@ mm_status run_source_passes(mm_ctx* ctx, const float* in[2], const int* which, i
   {
     Launch<YFwdJob> Lf{};
     Launch<ZJob> Lz{};
+    Launch<ZMixJob> Lm{};
     Launch<YInvJob> Li{};
-    int nf = 0, tf = 0, tz = 0, ni = 0, ti = 0;
+    int nf = 0, tf = 0, nzj = 0, tz = 0, nm = 0, tm = 0, ni = 0, ti = 0;
     for (int i = 0; i < n; ++i) {
       Magnet& S = ctx->mag[which[i]];
       if (!S.thick) continue;
       Dir* D = dirs[i];
-      FftTables fy, fz;
+      const bool do_H = (what[i] & 1) != 0, do_C = (what[i] & 2) != 0;
+      FftTables fy;
       CKS(get_fft(ctx, S.Qy, &fy));
-      CKS(get_fft(ctx, S.Qz, &fz));
       // planes per y-pass CTA: about 48 KB of lines, at most 16
       const int group = std::max(1, std::min(16, (int)((48 * 1024) / ((S.Qy + 1) * sizeof(float2)))));
       const int P3 = 3 * S.nz;
+      const int natural = S.zfft ? 0 : 1;
       YFwdJob& F = Lf.job[nf];
       F.in = S.X1; F.out = S.Y3; F.planes = P3; F.ny = S.ny; F.kxh = S.kxh; F.group = group; F.fy = fy;
+      F.natural = natural;
       Lf.tile_start[nf] = tf;
       tf += S.kxh * ((P3 + group - 1) / group);
-      ZJob& Z = Lz.job[nf];
-      Z.in = S.Y3; Z.nz = S.nz; Z.kxh = S.kxh; Z.fy = fy; Z.fz = fz; Z.kyq = S.kyq; Z.kzq = S.kzq;
-      Z.N3 = S.N3; Z.S3 = S.S3;
-      Z.do_H = (what[i] & 1) ? 1 : 0;
-      Z.do_C = (what[i] & 2) ? 1 : 0;
-      Z.outH = S.Z3H;
-      if (Z.do_C) {
-        Z.outC = D->Z3C;
-        Z.box_lo = D->box_lo[2]; Z.box_len = D->box_len[2]; Z.start = D->start[2]; Z.r = D->r[2];
-        Z.fir = D->prefilter;
-      }
-      Z.ztile = zpass_tile(S.Qz);
-      Lz.tile_start[nf] = tz;
-      tz += S.kxh * zpass_tiles(S.Qy, Z.ztile);
       ++nf;
-      if (Z.do_H) {
+      if (S.zfft) {
+        FftTables fz;
+        CKS(get_fft(ctx, S.Qz, &fz));
+        ZJob& Z = Lz.job[nzj];
+        Z.in = S.Y3; Z.nz = S.nz; Z.kxh = S.kxh; Z.fy = fy; Z.fz = fz; Z.kyq = S.kyq; Z.kzq = S.kzq;
+        Z.N3 = S.N3; Z.S3 = S.S3;
+        Z.do_H = do_H ? 1 : 0;
+        Z.do_C = do_C ? 1 : 0;
+        Z.outH = S.Z3H;
+        if (do_C) {
+          Z.outC = D->Z3C;
+          Z.box_lo = D->box_lo[2]; Z.box_len = D->box_len[2]; Z.start = D->start[2]; Z.r = D->r[2];
+          Z.fir = D->prefilter;
+        }
+        Z.ztile = zpass_tile(S.Qz);
+        Lz.tile_start[nzj] = tz;
+        tz += S.kxh * zpass_tiles(S.Qy, Z.ztile);
+        ++nzj;
+      } else {
+        ZMixJob& M = Lm.job[nm];
+        M.in = S.Y3; M.nz = S.nz; M.kxh = S.kxh; M.Qy = S.Qy; M.kyq = S.kyq;
+        M.Nq = S.Nq; M.Tq = do_C ? D->Tq : nullptr;
+        M.nH = do_H ? P3 : 0;
+        M.n_out = do_C ? D->r[2] : 0;
+        M.outH = S.Z3H;
+        M.outC = do_C ? D->Z3C : nullptr;
+        Lm.tile_start[nm] = tm;
+        tm += S.kxh * zmix_tiles(S.kyq, M.nH + M.n_out);
+        ++nm;
+      }
+      if (do_H) {
         YInvJob& J = Li.job[ni];
         J = YInvJob{};
-        J.in = S.Z3H; J.planes = P3; J.kxh = S.kxh; J.group = group; J.fy = fy; J.is_C = 0;
-        J.ny = S.ny; J.outH = S.YH;
+        J.in = S.Z3H; J.natural = natural; J.planes = P3; J.kxh = S.kxh; J.group = group; J.fy = fy;
+        J.is_C = 0; J.ny = S.ny; J.outH = S.YH;
         Li.tile_start[ni] = ti;
         ti += S.kxh * ((P3 + group - 1) / group);
         ++ni;
       }
-      if (Z.do_C) {
+      if (do_C) {
         YInvJob& J = Li.job[ni];
         J = YInvJob{};
-        J.in = D->Z3C; J.planes = D->r[2]; J.kxh = S.kxh; J.group = group; J.fy = fy; J.is_C = 1;
-        J.outC = D->YC;
+        J.in = D->Z3C; J.natural = natural; J.planes = D->r[2]; J.kxh = S.kxh; J.group = group; J.fy = fy;
+        J.is_C = 1; J.outC = D->YC;
         J.box_lo = D->box_lo[1]; J.box_len = D->box_len[1]; J.start = D->start[1]; J.r = D->r[1];
         J.fir = D->prefilter;
         Li.tile_start[ni] = ti;
@@ -760,15 +786,20 @@ mm_status run_source_passes(mm_ctx* ctx, const float* in[2], const int* which, i
     }
     if (nf) {
       Lf.njobs = nf; Lf.tile_start[nf] = tf;
-      Lz.njobs = nf; Lz.tile_start[nf] = tz;
+      Lz.njobs = nzj; Lz.tile_start[nzj] = tz;
+      Lm.njobs = nm; Lm.tile_start[nm] = tm;
       Li.njobs = ni; Li.tile_start[ni] = ti;
       {
         Timer t(ctx, 7);
         CK(launch_yfwd3(Lf, st));
       }
-      {
+      if (nzj) {
         Timer t(ctx, 8);
         CK(launch_zpass3(Lz, st));
+      }
+      if (nm) {
+        Timer t(ctx, 8);
+        CK(launch_zmix3(Lm, st));
       }
       Timer t(ctx, 9);
       CK(launch_yinv3(Li, st));
@@ -1337,13 +1368,10 @@ mm_status mm_compute_potential(mm_ctx* ctx, int src, int prefiltered, float* out
   const size_t need = (size_t)D.box_len[0] * D.box_len[1] * D.box_len[2];
   if (capacity < need) return fail(ctx, MM_EINVAL, "mm_compute_potential: output too small");
   if (!S.mset) return fail(ctx, MM_EINVAL, "magnetisation not set");
-  if (!S.thick) {
-    if ((size_t)std::max(3 * S.nz, D.r[2]) * S.Qy * sizeof(float2) > 220 * 1024)
-      return fail(ctx, MM_ENOTSUP, "box too tall for the fused y pass");
-    CKS(build_T(ctx, src, &D));
-  } else {
-    CKS(ensure_buf(ctx, &D.Z3C, &D.Z3C_bytes, sizeof(float2) * (size_t)D.r[2] * S.kxh * S.Qy));
-  }
+  if (!S.thick && (size_t)std::max(3 * S.nz, D.r[2]) * S.Qy * sizeof(float2) > 220 * 1024)
+    return fail(ctx, MM_ENOTSUP, "box too tall for the fused y pass");
+  if (!S.zfft) CKS(build_T(ctx, src, &D));
+  if (S.thick) CKS(ensure_buf(ctx, &D.Z3C, &D.Z3C_bytes, sizeof(float2) * (size_t)D.r[2] * S.kxh * S.Qy));
   CKS(ensure_buf(ctx, &D.YC, &D.YC_bytes, sizeof(float2) * (size_t)D.r[2] * S.kxh * D.r[1]));
   const float* in[2] = {ctx->mag[0].m, ctx->mag[1].m};
   const int which[1] = {src};
@@ -1560,7 +1588,7 @@ mm_status mm_get_plan_info(mm_ctx* ctx, int src, int fft_dims[3], int box_dims[3
   if (!ctx || bad_mag(src)) return MM_EINVAL;
   if (!ctx->planned) CKS(ensure_plan(ctx));
   const Magnet& S = ctx->mag[src];
-  if (fft_dims) { fft_dims[0] = S.Qx; fft_dims[1] = S.Qy; fft_dims[2] = S.thick ? S.Qz : 0; }
+  if (fft_dims) { fft_dims[0] = S.Qx; fft_dims[1] = S.Qy; fft_dims[2] = S.zfft ? S.Qz : 0; }
   for (int a = 0; a < 3; ++a) {
     if (box_dims) box_dims[a] = S.dir.box_len[a];
     if (box_lo) box_lo[a] = S.dir.box_lo[a];

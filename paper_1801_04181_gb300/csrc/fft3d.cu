@@ -6,6 +6,8 @@
 //   z pass (k_zpass3): per (kx, y position) the z FFT of the three components,
 //       H = -N.M and phi = S.M against the 3D kernel spectra, the inverse z
 //       FFT, and the z prefilter of phi on the box  -> Z[plane][kx][ypos]
+//   or, for sources of up to kMaxNzDirect layers, the direct z sum (k_zmix3)
+//       with thin-film spectra (z prefilter folded in), y in natural order
 //   y inverse (k_yinv3): inverse y FFT, demag rows and y prefilter
 //                                                    -> Y[plane][kx][row]
 //   x pass (k_xinv, shared)                          -> real rows
@@ -50,6 +52,14 @@ __global__ void __launch_bounds__(256, 2) k_yfwd3(const Launch<YFwdJob> Lc) {
   }
   __syncthreads();
   fft_smem<kFwdDif, float2>(sm, ldl, np, J.fy.plan, J.fy.tw_f, 0, blockDim.x);
+  if (J.natural) {
+    // frequency ky read from its DIF position: whole contiguous output rows
+    for (int l = 0; l < np; ++l) {
+      float2* row = J.out + ((size_t)(p0 + l) * J.kxh + kx) * Q;
+      for (int k = threadIdx.x; k < Q; k += blockDim.x) row[k] = sm[l * ldl + __ldg(J.fy.pos + k)];
+    }
+    return;
+  }
   float2* dst = J.out + (size_t)kx * Q * J.planes + p0;
   for (int i = threadIdx.x; i < Q * np; i += blockDim.x) {
     const int p = i / np, l = i - p * np;
@@ -187,13 +197,19 @@ __global__ void __launch_bounds__(256, 3) k_yinv3(const Launch<YInvJob> Lc) {
     const float2* col = J.in + ((size_t)(p0 + l) * J.kxh + kx) * Q;
     for (int p = threadIdx.x; p < Q; p += blockDim.x) sm[l * ldl + p] = col[p];
   }
-  if (J.is_C) build_pref_table(tab, J.r + 2 * kPrefWarm + kYChunk, J.box_lo, J.box_len, J.start, Q, nullptr);
+  // natural-order input: DIF stages of the inverse leave the rows in DIF
+  // order, read back through the position table; DIF-order input: DIT stages
+  // leave natural order
+  const FftPlanDev* P = J.natural ? &J.fy.plan : nullptr;
+  if (J.is_C) build_pref_table(tab, J.r + 2 * kPrefWarm + kYChunk, J.box_lo, J.box_len, J.start, Q, P);
   __syncthreads();
-  fft_smem<kInvDit, float2>(sm, ldl, np, J.fy.plan, J.fy.tw_f, 0, blockDim.x);
+  if (J.natural) fft_smem<kInvDif, float2>(sm, ldl, np, J.fy.plan, J.fy.tw_f, 0, blockDim.x);
+  else fft_smem<kInvDit, float2>(sm, ldl, np, J.fy.plan, J.fy.tw_f, 0, blockDim.x);
   if (!J.is_C) {
     for (int l = 0; l < np; ++l) {
       float2* dst = J.outH + ((size_t)(p0 + l) * J.kxh + kx) * J.ny;
-      for (int y = threadIdx.x; y < J.ny; y += blockDim.x) dst[y] = sm[l * ldl + y];
+      for (int y = threadIdx.x; y < J.ny; y += blockDim.x)
+        dst[y] = sm[l * ldl + (J.natural ? __ldg(J.fy.pos + y) : y)];
     }
     return;
   }
@@ -217,12 +233,103 @@ __global__ void __launch_bounds__(256, 3) k_yinv3(const Launch<YInvJob> Lc) {
   }
 }
 
-// ------------------------------------------------------------------ host side
+// dynamic shared memory of a launch, with the carveout set to shared memory
 static cudaError_t prep(const void* f, size_t smem) {
   cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
   return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
+// ------------------------------------------------------------------ direct z sum
+// Thread -> (kx, output plane, frequency pair ky, Qy - ky): the thin-film plane
+// mixing of Sec. III.A with the planes streamed from memory instead of held
+// in shared memory.  Consecutive threads take consecutive ky, so every load
+// and store is a coalesced run; the CTAs of one kx run together, so the
+// input planes they all read come from L2.  (Staging a chunk's inputs in
+// shared memory and looping over the outputs in the thread, or unrolling the
+// layer loop, measured 1.3-2.7x slower.)
+constexpr int kZMixThreads = 256;
+
+__device__ __forceinline__ float2 zm_kmul(float v, bool imag, float2 m) {
+  return imag ? make_float2(-v * m.y, v * m.x) : make_float2(v * m.x, v * m.y);
+}
+
+__global__ void __launch_bounds__(kZMixThreads) k_zmix3(const Launch<ZMixJob> Lc) {
+  const int j = find_job(Lc.tile_start, Lc.njobs, blockIdx.x);
+  const ZMixJob& J = Lc.job[j];
+  const int tile = blockIdx.x - Lc.tile_start[j];
+  const int nch = (J.kyq + kZMixThreads - 1) / kZMixThreads;
+  const int planes = J.nH + J.n_out;
+  const int kx = tile / (planes * nch);
+  const int rem = tile - kx * planes * nch;
+  const int o = rem / nch;
+  const int k = (rem - o * nch) * kZMixThreads + threadIdx.x;
+  if (k >= J.kyq) return;
+  const int Qy = J.Qy, nz = J.nz;
+  const bool two = k != 0 && 2 * k != Qy;
+  const size_t pstride = (size_t)J.kxh * Qy;     // one input / output plane
+  const size_t kstride = (size_t)J.kxh * J.kyq;  // one stored kernel plane
+  const size_t koff = (size_t)kx * J.kyq + k;
+  const float2* in0 = J.in + (size_t)kx * Qy + k;
+  const float2* in1 = J.in + (size_t)kx * Qy + (two ? Qy - k : k);
+  float2 acc0 = make_float2(0.f, 0.f), acc1 = acc0;
+  if (o < J.nH) {
+    // H_a(iz) = sum_jz sum_b Ns_ab(iz - jz) m_b(jz): xz, yz odd in dz and
+    // imaginary, xy and yz odd in y
+    const int a = o / nz, iz = o - a * nz;
+    for (int jz = 0; jz < nz; ++jz) {
+      const int adz = iz >= jz ? iz - jz : jz - iz;
+      const float sz = iz >= jz ? 1.f : -1.f;
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        int comp;
+        bool imag = false;
+        float sgn = 1.f, sy = 1.f;
+        if (a == b) comp = a;
+        else if (a + b == 1) { comp = 3; sy = -1.f; }
+        else if (a + b == 2) { comp = 4; sgn = sz; imag = true; }
+        else { comp = 5; sgn = sz; sy = -1.f; imag = true; }
+        const float v = sgn * __ldg(J.Nq + (size_t)(comp * nz + adz) * kstride + koff);
+        const float2 m0 = in0[(size_t)(b * nz + jz) * pstride];
+        const float2 m1 = in1[(size_t)(b * nz + jz) * pstride];
+        const float2 p0 = zm_kmul(v, imag, m0), p1 = zm_kmul(sy * v, imag, m1);
+        acc0.x += p0.x; acc0.y += p0.y;
+        acc1.x += p1.x; acc1.y += p1.y;
+      }
+    }
+    float2* dst = J.outH + (size_t)o * pstride + (size_t)kx * Qy;
+    dst[k] = acc0;
+    if (two) dst[Qy - k] = acc1;
+  } else {
+    // c(o) = sum_jz sum_c T_c(o, jz) m_c(jz); T_x, T_y imaginary, T_y odd in y
+    const int oc = o - J.nH;
+    for (int jz = 0; jz < nz; ++jz) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float v = __ldg(J.Tq + (size_t)((oc * nz + jz) * 3 + c) * kstride + koff);
+        const float2 m0 = in0[(size_t)(c * nz + jz) * pstride];
+        const float2 m1 = in1[(size_t)(c * nz + jz) * pstride];
+        const bool imag = c < 2;
+        const float2 p0 = zm_kmul(v, imag, m0), p1 = zm_kmul(c == 1 ? -v : v, imag, m1);
+        acc0.x += p0.x; acc0.y += p0.y;
+        acc1.x += p1.x; acc1.y += p1.y;
+      }
+    }
+    float2* dst = J.outC + (size_t)oc * pstride + (size_t)kx * Qy;
+    dst[k] = acc0;
+    if (two) dst[Qy - k] = acc1;
+  }
+}
+
+int zmix_tiles(int kyq, int planes) { return planes * ((kyq + kZMixThreads - 1) / kZMixThreads); }
+
+cudaError_t launch_zmix3(const Launch<ZMixJob>& L, cudaStream_t st) {
+  const int grid = L.tile_start[L.njobs];
+  if (grid == 0) return cudaSuccess;
+  k_zmix3<<<grid, kZMixThreads, 0, st>>>(L);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ host side
 // about 80 KB of lines per CTA (two CTAs per SM), at least 8 y positions:
 // short z grids get many positions, which spreads the per-CTA set-up
 int zpass_tile(int Qz) { return std::max(8, (80 * 1024) / (4 * (Qz + 1) * (int)sizeof(float2))); }

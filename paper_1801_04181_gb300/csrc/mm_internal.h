@@ -77,9 +77,11 @@ struct XInvJob {
 // y FFT of X1 columns; out[kx][pos][plane], positions in the plan's DIF order
 struct YFwdJob {
   const float2* in;       // [planes][kxh][ny]
-  float2* out;            // [kxh][Qy][planes]
+  float2* out;            // natural = 0: [kxh][Qy][planes], DIF positions
+                          // natural = 1: [planes][kxh][Qy], frequencies in natural order
   int planes, ny, kxh;
   int group;              // planes per CTA
+  int natural;
   FftTables fy;
 };
 
@@ -100,7 +102,8 @@ struct ZJob {
 
 // inverse y FFT (DIF-order positions in, natural out) and the y outputs
 struct YInvJob {
-  const float2* in;       // [planes][kxh][Qy]
+  const float2* in;       // [planes][kxh][Qy], DIF positions (natural = 0) or frequencies (1)
+  int natural;
   int planes, kxh;
   int group;
   FftTables fy;
@@ -110,6 +113,19 @@ struct YInvJob {
   float2* outC;           // [planes][kxh][r]
   int box_lo, box_len, start, r, fir;  // y box
 };
+
+// direct z sum for moderately thick sources (nz <= kMaxNzDirect): thin-film
+// style plane mixing between the y-forward and y-inverse passes, ky natural
+struct ZMixJob {
+  const float2* in;       // [3 nz][kxh][Qy]
+  int nz, kxh, Qy, kyq;
+  const float* Nq;        // [6][nz][kxh][kyq]
+  const float* Tq;        // [n_out][nz][3][kxh][kyq]
+  int nH, n_out;          // output planes: 3 nz demag (if nH), then n_out coefficient planes
+  float2* outH;           // [3 nz][kxh][Qy]
+  float2* outC;           // [n_out][kxh][Qy]
+};
+constexpr int kMaxNzDirect = 8;
 
 // ---------------------------------------------------------------- gather
 struct GatherJob {
@@ -224,6 +240,8 @@ cudaError_t launch_xinv(const Launch<XInvJob>& L, int Qmax, cudaStream_t st);
 cudaError_t launch_yfwd3(const Launch<YFwdJob>& L, cudaStream_t st);
 cudaError_t launch_zpass3(const Launch<ZJob>& L, cudaStream_t st);
 cudaError_t launch_yinv3(const Launch<YInvJob>& L, cudaStream_t st);
+cudaError_t launch_zmix3(const Launch<ZMixJob>& L, cudaStream_t st);
+int zmix_tiles(int kyq, int planes);
 int zpass_tile(int Qz);                 // y positions per z-pass CTA for a z grid
 int zpass_tiles(int Qy, int ztile);
 int gather_tiles(int nx, int ny, int nz);  // 32 x 8 columns x up to kMaxNz layers
