@@ -50,8 +50,9 @@ def parse():
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--seed", type=int, default=0)
-    p.add_argument("--workload", default="stick_slip", choices=sorted(WORKLOADS),
-                   help="stick_slip (the headline workload) or a thick-source workload")
+    p.add_argument("--workload", default="stick_slip", choices=sorted(WORKLOADS) + ["plain64_sweep"],
+                   help="stick_slip (the headline workload), a thick-source workload, or the "
+                        "plain 64x64x1 film pair swept over 16 sub-cell offsets (stray field only)")
     return p.parse_args()
 
 
@@ -440,10 +441,57 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_sweep(args):
+    """Plain film pair 64x64x1 (4 nm, gap 1, random unit m), the slider displaced
+    along x by 16 evenly spaced offsets in [0, 1) cell: both stray-field
+    directions with their forces per offset.  Metric: stray-field
+    cell-evaluations/s = 2 N offsets / time (no LLG in this workload)."""
+    import torch
+    import workloads
+    from tests.pair_setup import gpu_pair
+
+    fp, m0, m1 = workloads.film_pair_plain((64, 64, 1), 1, args.seed)
+    mm = gpu_pair(fp, m0, m1, mech=False)
+    offs = [k / 16.0 for k in range(16)]
+
+    def sweep():
+        for u in offs:
+            mm.set_displacement((u * fp.cell[0], 0.0, 0.0))
+            mm.compute_stray_field(0)
+            mm.compute_stray_field(1)
+
+    for _ in range(max(args.warmup, 3)):
+        sweep()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = mm.launch_count()
+    e0.record()
+    for _ in range(args.steps):
+        sweep()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    cells = fp.cells()
+    line = {"metric": "stray-field cell-evaluations/s (plain 64x64x1 pair, 16 offsets)",
+            "value": cells * len(offs) * args.steps / (ms / 1e3), "unit": "cell-evaluations/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": max(args.warmup, 3),
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "plain film pair 64x64x1 (4 nm), gap 1, 16 x-offsets in [0, 1)",
+                       "cells": cells, "fft": [mm.plan_info(0)["fft"]],
+                       "step": "one sweep: 16 offsets x both stray-field directions",
+                       "l2": "L2-resident: a launch- and latency-bound workload"},
+            "gpu_launches": int(mm.launch_count() - launches0)}
+    print(json.dumps(line))
+    mm.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "plain64_sweep":
+        run_sweep(args)
     else:
         run_gpu(args)
 
