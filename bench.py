@@ -169,7 +169,7 @@ def algorithmic_bytes(mm, fp):
 KERNEL_OF_CLASS = {0: ("k_xfwd", ["fft_passes.cu", "fft.cuh", "prefilter.cuh", "mm_internal.h"]),
                    1: ("k_ypass", ["fft_passes.cu", "fft.cuh", "prefilter.cuh", "mm_internal.h"]),
                    2: ("k_xinv", ["fft_passes.cu", "fft.cuh", "prefilter.cuh", "mm_internal.h"]),
-                   3: ("k_gather", ["gather.cu", "dfloat.cuh", "mm_internal.h"]),
+                   3: ("k_gather", ["gather.cu", "dfloat.cuh", "spline_w.cuh", "mm_internal.h"]),
                    4: ("k_stage", ["llg.cu", "mm_internal.h"])}
 
 

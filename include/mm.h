@@ -150,6 +150,25 @@ mm_status mm_compute_fields(mm_ctx* ctx);
  * evaluation.  FP64.  Synchronises. */
 mm_status mm_get_force(mm_ctx* ctx, int on_mag, double F_out[3], double* E_int_out);
 
+/*
+ * Gradients of the interaction energy E of magnet 1 - src in the stray field
+ * of `src` (the E that mm_get_force(1 - src) returns; Sec. II.A with
+ * Eq. (EQForce): E = mu0 V Ms_t sum_i m_t(i) . grad phi_src(x_i)) at the
+ * current m and displacement, computed by the transposed path:
+ *   dE_du:          3 doubles, dE/du (J/m) of the slider displacement u
+ *                   (exact for the spline interpolant: -F along the slider's
+ *                   motion when the target is the slider, +F otherwise);
+ *   dE_dm_src_dev:  3 N_src floats (J), dE/dm of the source's unit
+ *                   magnetisation, SoA like m: the transposed gradient
+ *                   evaluation, B-spline prefilter and potential sum;
+ *   dE_dm_tgt_dev:  3 N_tgt floats (J), dE/dm of the target's unit
+ *                   magnetisation (mu0 V Ms_t grad phi at its cells).
+ * Any output may be NULL.  Device pointers, caller-owned.  Also refreshes the
+ * target's stray field and force.  Synchronises.
+ */
+mm_status mm_backward_energy(mm_ctx* ctx, int src, double dE_du[3], float* dE_dm_src_dev,
+                             float* dE_dm_tgt_dev);
+
 /* dm/dt (1/s) of the LLG equation (Sec. II eq. 1, Landau-Lifshitz form) at the
  * current state, and the effective field (A/m); either pointer may be NULL. */
 mm_status mm_compute_torque(mm_ctx* ctx, int mag, float* dmdt_dev, float* Heff_dev);

@@ -148,6 +148,16 @@ class MovingMagnets:
         self._c(self.lib.mm_get_force(self.ctx, on_mag, F, C.byref(E)))
         return [F[0], F[1], F[2]], E.value
 
+    def backward_energy(self, src, want_src=True, want_tgt=True):
+        """Gradients of the energy of magnet 1 - src in the field of src:
+        (dE/du (J/m, 3 floats), dE/dm_src (J, like m_src), dE/dm_tgt (J, like m_tgt))."""
+        du = _native._d3()
+        gs = torch.empty(self.shapes[src], dtype=torch.float32, device="cuda") if want_src else None
+        gt = torch.empty(self.shapes[1 - src], dtype=torch.float32, device="cuda") if want_tgt else None
+        self._c(self.lib.mm_backward_energy(self.ctx, src, du, _ptr(gs) if gs is not None else None,
+                                            _ptr(gt) if gt is not None else None))
+        return [du[0], du[1], du[2]], gs, gt
+
     def compute_torque(self, mag):
         dm = torch.empty(self.shapes[mag], dtype=torch.float32, device="cuda")
         H = torch.empty(self.shapes[mag], dtype=torch.float32, device="cuda")
@@ -240,3 +250,27 @@ def eval_kernel_fp64(kind, offsets_m, cell):
     if st != 0:
         raise MMError(st, "mm_eval_kernel_fp64")
     return out
+
+
+class InteractionEnergy(torch.autograd.Function):
+    """E(m_src, m_tgt, u): the interaction energy of magnet 1 - src in the stray
+    field of src (J), differentiable in both unit magnetisations and in the
+    slider displacement u (metres, a float64 tensor of 3).  The forward sets
+    the context's state and evaluates; the backward returns the gradients that
+    mm_backward_energy computed with it (the transposed path, in CUDA)."""
+
+    @staticmethod
+    def forward(ctx, mm, src, m_src, m_tgt, u):
+        mm.set_magnetization(src, m_src.detach())
+        mm.set_magnetization(1 - src, m_tgt.detach())
+        mm.set_displacement(tuple(float(v) for v in u.detach().cpu()))
+        du, gs, gt = mm.backward_energy(src)
+        _, E = mm.get_force(1 - src)
+        ctx.save_for_backward(gs, gt, torch.tensor(du, dtype=torch.float64))
+        return torch.tensor(E, dtype=torch.float64)
+
+    @staticmethod
+    def backward(ctx, gE):
+        gs, gt, du = ctx.saved_tensors
+        g = float(gE)
+        return None, None, g * gs, g * gt, g * du.to(gE.device)

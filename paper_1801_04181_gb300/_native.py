@@ -51,6 +51,7 @@ SIGNATURES = [
     ("mm_compute_demag", C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     ("mm_compute_fields", C.c_int, [C.c_void_p]),
     ("mm_get_force", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    ("mm_backward_energy", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.c_void_p, C.c_void_p]),
     ("mm_compute_torque", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     ("mm_step", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     ("mm_get_step_stats", C.c_int, [C.c_void_p, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),

@@ -104,6 +104,18 @@ struct Magnet {
   float* S3 = nullptr;     // [3][kxh][kyq][kzq]
   float2* Y3 = nullptr;    // [kxh][Qy][3 nz]
   float2* Z3H = nullptr;   // [3 nz][kxh][Qy]
+  // energy gradients (mm_backward_energy) as a source: work arrays and the S
+  // spectra per z offset of the box
+  float* adj_box = nullptr;
+  float* adj_grid = nullptr;
+  float2* adj_X = nullptr;
+  float2* adj_Y = nullptr;
+  float2* adj_Z = nullptr;
+  float2* adj_YH = nullptr;
+  float* adj_Sq = nullptr;
+  size_t adj_bytes[7] = {};
+  int adj_key[4] = {0, 0, 0, 0};  // dz_lo, planes, Qx, Qy of adj_Sq
+  double adj_Ms = 0;
   Dir dir;   // hot path: coefficients around the other magnet
   Dir aux;   // mm_compute_potential output
 };
@@ -1158,6 +1170,8 @@ void mm_destroy(mm_ctx* ctx) {
     cudaFree(M.Hself); cudaFree(M.Hstray); cudaFree(M.scratch3); cudaFree(M.err_partial);
     cudaFree(M.X1); cudaFree(M.YH); cudaFree(M.Nq);
     cudaFree(M.N3); cudaFree(M.S3); cudaFree(M.Y3); cudaFree(M.Z3H);
+    cudaFree(M.adj_box); cudaFree(M.adj_grid); cudaFree(M.adj_X); cudaFree(M.adj_Y); cudaFree(M.adj_Z);
+    cudaFree(M.adj_YH); cudaFree(M.adj_Sq);
     free_dir(M.dir);
     free_dir(M.aux);
   }
@@ -1333,6 +1347,135 @@ mm_status mm_compute_stray_field(mm_ctx* ctx, int src, float* H_dev) {
   const MechParams P = mech_params(ctx, 1, 0, 0.0, src == 0, src == 1);
   CKS(run_gathers(ctx, in, which, 1, H));
   CKS(run_mech(ctx, P));
+  return MM_OK;
+}
+
+mm_status mm_backward_energy(mm_ctx* ctx, int src, double dE_du[3], float* dE_dm_src_dev,
+                             float* dE_dm_tgt_dev) {
+  if (!ctx || bad_mag(src)) return ctx ? fail(ctx, MM_EINVAL, "mm_backward_energy") : MM_EINVAL;
+  // forward: potential box, stray field at the target, force and energy
+  CKS(mm_compute_stray_field(ctx, src, nullptr));
+  const int t = 1 - src;
+  Magnet& S = ctx->mag[src];
+  const Magnet& T = ctx->mag[t];
+  const Dir& D = S.dir;
+  cudaStream_t st = ctx->st;
+  const double escale = kMu0 * T.d[0] * T.d[1] * T.d[2] * T.Ms;
+  // dE/dm_t = mu0 V Ms_t grad phi = -mu0 V Ms_t H
+  if (dE_dm_tgt_dev) CK(launch_scale(T.Hstray, dE_dm_tgt_dev, 3 * T.N, (float)(-escale), st));
+  if (dE_dm_src_dev) {
+    const int* bd = D.box_len;
+    const int bz = bd[2];
+    const int nzg = 3 * ((bz + 2) / 3);  // grid planes for the x pass (whole groups of three)
+    const int P3 = 3 * S.nz;
+    const size_t nbox = (size_t)bd[0] * bd[1] * bd[2];
+    CKS(ensure_buf(ctx, &S.adj_box, &S.adj_bytes[0], sizeof(float) * nbox));
+    CKS(ensure_buf(ctx, &S.adj_grid, &S.adj_bytes[1], sizeof(float) * (size_t)nzg * S.Qy * S.Qx));
+    CKS(ensure_buf(ctx, &S.adj_X, &S.adj_bytes[2], sizeof(float2) * (size_t)nzg * S.kxh * S.Qy));
+    CKS(ensure_buf(ctx, &S.adj_Y, &S.adj_bytes[3], sizeof(float2) * (size_t)bz * S.kxh * S.Qy));
+    CKS(ensure_buf(ctx, &S.adj_Z, &S.adj_bytes[4], sizeof(float2) * (size_t)P3 * S.kxh * S.Qy));
+    CKS(ensure_buf(ctx, &S.adj_YH, &S.adj_bytes[5], sizeof(float2) * (size_t)P3 * S.kxh * S.ny));
+    // S spectra of every z offset between a source layer and a box plane
+    const int dz_lo = D.box_lo[2] - (S.nz - 1), np = bz + S.nz - 1;
+    const size_t qsize = (size_t)S.kxh * S.kyq;
+    if (!S.adj_Sq || S.adj_key[0] != dz_lo || S.adj_key[1] != np || S.adj_key[2] != S.Qx ||
+        S.adj_key[3] != S.Qy || S.adj_Ms != S.Ms) {
+      CKS(ensure_buf(ctx, &S.adj_Sq, &S.adj_bytes[6], sizeof(float) * (size_t)np * 3 * qsize));
+      FftTables fx, fy;
+      CKS(get_fft(ctx, S.Qx, &fx));
+      CKS(get_fft(ctx, S.Qy, &fy));
+      CKS(ensure_buf(ctx, &ctx->gen_work, &ctx->gen_work_bytes, sizeof(double2) * 2 * 6 * (size_t)S.Qx * S.Qy));
+      CKS(ensure_buf(ctx, &ctx->gen_q, &ctx->gen_q_bytes, std::max(ctx->gen_q_bytes, sizeof(double) * 6 * qsize)));
+      const KernelPlan K{S.Qx, S.Qy, S.Wx, S.Wy, S.nz};
+      CK(build_S_planes(K, fx, fy, S.d[0], S.d[1], S.d[2], S.Ms / ((double)S.Qx * S.Qy), dz_lo, np, S.adj_Sq,
+                        ctx->gen_work, ctx->gen_q, st));
+      CK(cudaStreamSynchronize(st));
+      S.adj_key[0] = dz_lo; S.adj_key[1] = np; S.adj_key[2] = S.Qx; S.adj_key[3] = S.Qy;
+      S.adj_Ms = S.Ms;
+    }
+    CKS(join_mech(ctx));  // the scatter reads the displacement
+    // 1. transposed evaluation into the box
+    CK(cudaMemsetAsync(S.adj_box, 0, sizeof(float) * nbox, st));
+    AdjScatterJob A{};
+    A.m = T.m;
+    A.nx = T.nx; A.ny = T.ny; A.nz = T.nz;
+    A.u = ctx->mech->u;
+    A.sigma = src == 0 ? 1.0 : -1.0;
+    for (int a = 0; a < 3; ++a) {
+      A.U0[a] = D.U0[a];
+      A.guard[a] = D.guard[a];
+      A.inv_d[a] = (float)(1.0 / T.d[a]);
+      A.bdim[a] = bd[a];
+      A.start[a] = D.start[a];
+      A.r[a] = D.r[a];
+    }
+    A.escale = (float)escale;
+    A.box = S.adj_box;
+    A.err = ctx->err_flag;
+    CK(launch_adj_scatter(A, st));
+    // 2. transposed prefilter
+    CK(launch_pref_T(S.adj_box, bd, st));
+    // 3. transposed potential sum: onto the circular grid, x and y forward,
+    //    conjugate S spectra per source layer, y and x inverse
+    CK(cudaMemsetAsync(S.adj_grid, 0, sizeof(float) * (size_t)nzg * S.Qy * S.Qx, st));
+    CK(launch_place(S.adj_box, bd, D.box_lo, S.adj_grid, S.Qx, S.Qy, st));
+    FftTables fx, fy;
+    CKS(get_fft(ctx, S.Qx, &fx));
+    CKS(get_fft(ctx, S.Qy, &fy));
+    {
+      Launch<XFwdJob> L{};
+      L.njobs = 1;
+      XFwdJob& X = L.job[0];
+      X.m = S.adj_grid; X.out = S.adj_X; X.nx = S.Qx; X.ny = S.Qy; X.nz = nzg / 3; X.kxh = S.kxh; X.fx = fx;
+      L.tile_start[1] = (nzg * S.Qy + kRowsPerCta - 1) / kRowsPerCta;
+      CK(launch_xfwd(L, S.Qx, st));
+    }
+    const int group = std::max(1, std::min(16, (int)((48 * 1024) / ((S.Qy + 1) * sizeof(float2)))));
+    {
+      Launch<YFwdJob> L{};
+      L.njobs = 1;
+      YFwdJob& F = L.job[0];
+      F.in = S.adj_X; F.out = S.adj_Y; F.planes = bz; F.ny = S.Qy; F.kxh = S.kxh; F.group = group;
+      F.natural = 1; F.fy = fy;
+      L.tile_start[1] = S.kxh * ((bz + group - 1) / group);
+      CK(launch_yfwd3(L, st));
+    }
+    {
+      ZAdjJob Z{};
+      Z.in = S.adj_Y; Z.bz = bz; Z.nz = S.nz; Z.kxh = S.kxh; Z.Qy = S.Qy; Z.kyq = S.kyq;
+      Z.Sq = S.adj_Sq; Z.out = S.adj_Z;
+      CK(launch_zadj(Z, st));
+    }
+    {
+      Launch<YInvJob> L{};
+      L.njobs = 1;
+      YInvJob& J = L.job[0];
+      J.in = S.adj_Z; J.natural = 1; J.planes = P3; J.kxh = S.kxh; J.group = group; J.fy = fy;
+      J.is_C = 0; J.ny = S.ny; J.outH = S.adj_YH;
+      L.tile_start[1] = S.kxh * ((P3 + group - 1) / group);
+      CK(launch_yinv3(L, st));
+    }
+    {
+      Launch<XInvJob> L{};
+      L.njobs = 1;
+      XInvJob& J = L.job[0];
+      J.in = S.adj_YH; J.out = dE_dm_src_dev;
+      J.planes = P3; J.rows_per_plane = S.ny; J.kxh = S.kxh; J.fx = fx;
+      J.box_lo = 0; J.box_len = S.nx; J.start = 0; J.out_len = S.nx; J.fir = 0;
+      L.tile_start[1] = (P3 * S.ny + kRowsPerCta - 1) / kRowsPerCta;
+      CK(launch_xinv(L, S.Qx, st));
+    }
+    ctx->launches += 11;
+  }
+  // dE/du = -sigma F_t (sigma = +1 when the target is the slider)
+  CKS(join_mech(ctx));
+  CK(cudaMemcpyAsync(&ctx->host_mech, ctx->mech, sizeof(MechState), cudaMemcpyDeviceToHost, ctx->st));
+  CKS(check_device_error(ctx));
+  if (dE_du) {
+    const double* F = t == 1 ? ctx->host_mech.F_slider : ctx->host_mech.F_base;
+    const double sigma = t == 1 ? 1.0 : -1.0;
+    for (int a = 0; a < 3; ++a) dE_du[a] = -sigma * F[a];
+  }
   return MM_OK;
 }
 

@@ -366,6 +366,22 @@ cudaError_t build_T_spectra(const KernelPlan& K, const FftTables& fx, const FftT
   return cudaGetLastError();
 }
 
+cudaError_t build_S_planes(const KernelPlan& K, const FftTables& fx, const FftTables& fy, double a, double b,
+                           double c, double scale, int dz_lo, int nplanes, float* Sq, double2* work,
+                           double* qtmp, cudaStream_t st) {
+  static const int imag3[3] = {1, 1, 0};
+  const size_t qsize = (size_t)(K.Qx / 2 + 1) * (K.Qy / 2 + 1);
+  for (int p = 0; p < nplanes; ++p) {
+    cudaError_t e = plane_spectra(0, 3, K.Qx, K.Qy, K.Wx, K.Wy, dz_lo + p, a, b, c, fx, fy, work, qtmp, imag3, st);
+    if (e != cudaSuccess) return e;
+    const size_t n = 3 * qsize;
+    k_scale_to_float<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(qtmp, Sq + (size_t)p * n, n, scale);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 // ------------------------------------------------------------------ 3D spectra
 // q2 [Qz][qsize] (real) -> z lines [qsize][Qz] (complex; the 2D value was the
 // real or the imaginary part of the 2D spectrum)

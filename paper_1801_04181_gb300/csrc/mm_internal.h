@@ -127,6 +127,34 @@ struct ZMixJob {
 };
 constexpr int kMaxNzDirect = 8;
 
+// ---------------------------------------------------------------- adjoint (energy gradients)
+// transposed gradient evaluation: coefficient-region node n collects
+// escale * m_t,a(i) / d_a * (derivative weights of axis a) from the targets i
+// whose 64 taps cover it; written into the box at offset `start`
+struct AdjScatterJob {
+  const float* m;         // target unit magnetisation [3][N]
+  int nx, ny, nz;         // target grid
+  const double* u;        // slider displacement, lattice cells (device)
+  double sigma;
+  int U0[3], guard[3];
+  float inv_d[3];
+  float escale;           // mu0 V Ms_t
+  float* box;             // [bz][by][bx]
+  int bdim[3];            // box extents
+  int start[3];           // coefficient region inside the box
+  int r[3];               // coefficient region extents
+  int* err;
+};
+
+// transposed potential sum in the spectral domain (direct z): for source
+// plane (c, jz), sum over box planes zb of conj(S_c(zb - jz)) phibar(zb)
+struct ZAdjJob {
+  const float2* in;       // [bz][kxh][Qy], ky natural
+  int bz, nz, kxh, Qy, kyq;
+  const float* Sq;        // [bz + nz - 1][3][kxh][kyq]: quarter spectra per z offset, scaled
+  float2* out;            // [3 nz][kxh][Qy]
+};
+
 // ---------------------------------------------------------------- gather
 struct GatherJob {
   const float* C;         // coefficients [rz][ry][rx]
@@ -241,6 +269,12 @@ cudaError_t launch_yfwd3(const Launch<YFwdJob>& L, cudaStream_t st);
 cudaError_t launch_zpass3(const Launch<ZJob>& L, cudaStream_t st);
 cudaError_t launch_yinv3(const Launch<YInvJob>& L, cudaStream_t st);
 cudaError_t launch_zmix3(const Launch<ZMixJob>& L, cudaStream_t st);
+cudaError_t launch_adj_scatter(const AdjScatterJob& J, cudaStream_t st);
+cudaError_t launch_pref_T(float* box, const int bdim[3], cudaStream_t st);
+cudaError_t launch_place(const float* box, const int bdim[3], const int box_lo[3], float* grid, int Qx, int Qy,
+                         cudaStream_t st);
+cudaError_t launch_zadj(const ZAdjJob& J, cudaStream_t st);
+cudaError_t launch_scale(const float* in, float* out, size_t n, float s, cudaStream_t st);
 int zmix_tiles(int kyq, int planes);
 int zpass_tile(int Qz);                 // y positions per z-pass CTA for a z grid
 int zpass_tiles(int Qy, int ztile);
@@ -262,6 +296,12 @@ cudaError_t build_N_spectra(const KernelPlan& K, const FftTables& fx, const FftT
 cudaError_t build_spectra_3d(int kind, const KernelPlan3& K, const FftTables& fx, const FftTables& fy,
                              const FftTables& fz, double a, double b, double c, double scale, float* out,
                              double2* work, double* q2, double* qtmp, double2* zl, cudaStream_t st);
+// FP32 quarter spectra of S, one plane of 3 components per z offset dz_lo + p,
+// p < nplanes: Sq [p][3][kxh][kyq], scaled.  work as for build_N_spectra,
+// qtmp 3 kxh kyq doubles.
+cudaError_t build_S_planes(const KernelPlan& K, const FftTables& fx, const FftTables& fy, double a, double b,
+                           double c, double scale, int dz_lo, int nplanes, float* Sq, double2* work,
+                           double* qtmp, cudaStream_t st);
 cudaError_t build_T_spectra(const KernelPlan& K, const FftTables& fx, const FftTables& fy, double a,
                             double b, double c, double scale, int box_lo_z, int bz, int n_out,
                             const double* W_dev, float* Tq, double2* work, double* Sq,
