@@ -50,7 +50,8 @@ def parse():
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--seed", type=int, default=0)
-    p.add_argument("--workload", default="stick_slip", choices=sorted(WORKLOADS) + ["plain64_sweep"],
+    p.add_argument("--workload", default="stick_slip",
+                   choices=sorted(WORKLOADS) + ["plain64_sweep", "cubes64_gradients"],
                    help="stick_slip (the headline workload), a thick-source workload, or the "
                         "plain 64x64x1 film pair swept over 16 sub-cell offsets (stray field only)")
     return p.parse_args()
@@ -486,12 +487,48 @@ def run_sweep(args):
     mm.close()
 
 
+def run_gradients(args):
+    """Two 64^3 vortex cubes (2 nm, gap 3 along x, slider at 1.7 cells): one
+    step is mm_backward_energy of the slider's energy in the base's field --
+    the forward stray field and force plus the transposed path giving
+    dE/dm of both cubes and dE/du.  Metric: cells of both cubes / time."""
+    import torch
+    import workloads
+    from tests.pair_setup import gpu_pair
+
+    fp, m0, m1 = workloads.cube_pair((64, 64, 64), 3, args.seed)
+    fp.u0 = (1.7, 0.0, 0.0)
+    mm = gpu_pair(fp, m0, m1, mech=False)
+    for _ in range(max(args.warmup, 3)):
+        mm.backward_energy(0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        mm.backward_energy(0)
+    torch.cuda.synchronize()
+    s = time.perf_counter() - t0
+    cells = fp.cells()
+    line = {"metric": "energy-gradient cell-evaluations/s (forward + adjoint, 64^3 cube pair)",
+            "value": cells * args.steps / s, "unit": "cell-evaluations/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": 1e3 * s / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "vortex cube pair 64x64x64 (2 nm), gap 3 along x, u = 1.7 cells",
+                       "cells": cells, "fft": [list(mm.plan_info(0)["fft"]) + [mm.plan_info(0)["Qz"]]],
+                       "step": "mm_backward_energy(src=0): stray field, force, dE/dm (both), dE/du; "
+                               "host-timed, one synchronisation per step"}}
+    print(json.dumps(line))
+    mm.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "plain64_sweep":
         run_sweep(args)
+    elif args.workload == "cubes64_gradients":
+        run_gradients(args)
     else:
         run_gpu(args)
 

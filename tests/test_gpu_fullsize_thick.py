@@ -78,3 +78,21 @@ def test_full_size_cubes_index_shift_bitwise():
     mm.close()
     assert np.array_equal(H_a, H_b)
     assert F_a == F_b
+
+
+def test_full_size_cubes_64_energy_gradients():
+    """The adjoint at the differentiation workload's size: dE/dm of both cubes
+    and dE/du against the oracle's FP64 gradients."""
+    from oracle.adjoint import energy_gradients
+
+    fp, m0, m1 = workloads.cube_pair((64, 64, 64), 3, 2)
+    fp.u0 = (1.7, 0.0, 0.0)
+    mm = gpu_pair(fp, m0, m1, mech=False)
+    du, gs, gt = mm.backward_energy(0)
+    mm.close()
+    Ms = fp.mat_base.Ms
+    ref = energy_gradients(Ms * m0, Ms * m1, fp.cell, fp.offsets[0], fp.offsets[1], fp.u0, True)
+    assert rel_l2(gs.double().cpu().numpy(), Ms * ref["dE_dMs"]) < TOL
+    assert rel_l2(gt.double().cpu().numpy(), Ms * ref["dE_dMt"]) < TOL
+    assert np.max(np.abs(np.array(du) - ref["dE_du"])) < 1e-4 * np.max(np.abs(ref["dE_du"]))
+
