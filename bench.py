@@ -51,7 +51,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--workload", default="stick_slip",
-                   choices=sorted(WORKLOADS) + ["plain64_sweep", "cubes64_gradients"],
+                   choices=sorted(WORKLOADS) + ["plain64_sweep", "cubes64_gradients", "batch256"],
                    help="stick_slip (the headline workload), a thick-source workload, or the "
                         "plain 64x64x1 film pair swept over 16 sub-cell offsets (stray field only)")
     return p.parse_args()
@@ -528,6 +528,167 @@ def run_gradients(args):
     mm.close()
 
 
+BATCH_LANES = 16
+
+
+def run_batch(args):
+    """256 independent spring-pulled PMA film pairs of uneven sizes (nx in
+    64..512, ny in 64..256, nz in 1..4, slider displaced by U[0, 50) cells,
+    pulled at U[0.1, 10] m/s), spread over 16 lane streams by longest
+    processing time first; one bench step = one mm_step_batch call in which
+    every pair takes one accepted adaptive DP45 step.  Metric: cells of all
+    pairs x steps / time.  Under torchrun the pairs are spread over the ranks
+    the same way (strong scaling: the batch is fixed)."""
+    import torch
+    import workloads
+    from paper_1801_04181_gb300 import assign_lanes, step_batch
+    from tests.pair_setup import gpu_pair
+
+    # 16 lanes + each context's side stream: more hardware queues than the
+    # default 8, or unrelated streams serialise behind one another (this
+    # process only; read when CUDA initialises)
+    os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+    rank, world, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    pool = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import multiprocessing as mp
+        pool = mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1)))
+    specs = workloads.batch_pairs(256, seed=args.seed)
+    # cost model for the spread: grid area x (source layers + box layers)
+    cost = [fp.n_base[0] * fp.n_base[1] * (fp.n_base[2] + 4) for fp in specs]
+    mine = [i for i, r in enumerate(assign_lanes(cost, world)) if r == rank]
+    lanes = assign_lanes([cost[i] for i in mine], BATCH_LANES)
+    streams = [torch.cuda.Stream() for _ in range(BATCH_LANES)]
+    t_setup = time.perf_counter()
+    batch = []
+    for i, l in zip(mine, lanes):
+        m0, m1 = workloads.batch_patterns(specs[i])
+        batch.append(gpu_pair(specs[i], m0, m1, adaptive=True, rtol=1e-5, stream=streams[l]))
+    cells = sum(specs[i].cells() for i in mine)
+    dts = [1e-13] * len(batch)
+    for _ in range(max(args.warmup, 3)):
+        _, dts = step_batch(batch, 1, dts)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t_setup
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for mm in batch:
+        mm.set_timing(False)
+    cur = torch.cuda.current_stream()
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = sum(mm.launch_count() for mm in batch)
+    st0 = [mm.step_stats() for mm in batch]
+    barrier()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(cur)
+    for s in streams:
+        s.wait_event(ev0)
+    for _ in range(args.steps):
+        _, dts = step_batch(batch, 1, dts)
+    for s in streams:
+        cur.wait_stream(s)
+    ev1.record(cur)
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    launches = sum(mm.launch_count() for mm in batch) - launches0
+    st1 = [mm.step_stats() for mm in batch]
+    acc = sum(b[0] - a[0] for a, b in zip(st0, st1))
+    rej = sum(b[1] - a[1] for a, b in zip(st0, st1))
+    # modelled bytes per batched step: each pair's per-launch bytes x its launches per step
+    k_t = max(1, min(args.steps, 10))
+    for mm in batch:
+        mm.reset_timing()
+        mm.set_timing(True)
+    for _ in range(k_t):
+        _, dts = step_batch(batch, 1, dts)
+    torch.cuda.synchronize()
+    bytes_step = 0.0
+    for i, mm in zip(mine, batch):
+        ab = algorithmic_bytes(mm, specs[i])
+        for c, b in ab.items():
+            bytes_step += b * mm.timing(c)[1] / k_t
+        mm.set_timing(False)
+    ms = max_over_ranks(ms, world, "cuda")
+    total_cells = sum(fp.cells() for fp in specs)  # every rank's pairs together
+    value = total_cells * args.steps / (ms / 1e3)
+    # end to end through the public API: upload m of every pair from pinned
+    # host memory, step the batch, download m and read the slider force
+    pin = [[torch.empty(mm.shapes[g], dtype=torch.float32).pin_memory() for g in (0, 1)] for mm in batch]
+    for mm, p in zip(batch, pin):
+        for g in (0, 1):
+            mm.download_magnetization(g, p[g])
+    k_e2e = max(1, min(args.steps, 5))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        for mm, p in zip(batch, pin):
+            for g in (0, 1):
+                mm.upload_magnetization(g, p[g])
+        _, dts = step_batch(batch, 1, dts)
+        for mm, p in zip(batch, pin):
+            for g in (0, 1):
+                mm.download_magnetization(g, p[g])
+            mm.get_force(1)
+    barrier()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, "cuda")
+    e2e = total_cells * k_e2e / e2e_s
+    h2d = sum(int(np.prod(mm.shapes[g])) * 4 for mm in batch for g in (0, 1))
+    peak, src = measured_peaks()
+    achieved = bytes_step / (ms / args.steps / 1e3) / 1e9
+    roof = {"bound": "hbm", "kernel": "whole batched step (all kernel classes of all pairs, concurrent)",
+            "achieved": round(achieved, 1), "peak": peak, "peak_source": src, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "algorithmic_bytes_per_step": int(bytes_step),
+            "traffic": None,
+            "traffic_source": "not captured: a batched step is thousands of concurrent launches"}
+    cpu_base = None
+    if pool is not None:
+        try:
+            mid = int(np.argsort([fp.cells() for fp in specs])[len(specs) // 2])
+            m0, m1 = workloads.batch_patterns(specs[mid])
+            cpu_base = cpu_oracle_sample(specs[mid], m0, m1, pool)
+            cpu_base["sample"] += "; the median-size pair of the batch"
+        finally:
+            pool.close()
+            pool.join()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batch of 256 PMA film pairs, sizes U{64..512}xU{64..256}xU{1..4} "
+                                   "(4 nm), slider at U[0, 50) cells, pulled at U[0.1, 10] m/s, "
+                                   "adaptive DP45 per pair",
+                       "pairs": len(batch), "cells": cells, "lanes": BATCH_LANES,
+                       "accepted": acc, "rejected": rej, "setup_s": round(t_setup, 1),
+                       "parallelism": "pairs over ranks" if world > 1 else "single",
+                       "l2": "no flush: the batch's working set (tens of GB) exceeds the 129 MB L2"},
+            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": h2d + 32 * len(batch), "steps": k_e2e},
+            "gpu_launches": int(launches),
+            "roofline": roof,
+            "clocks": clk,
+            "cpu_baseline": cpu_base,
+        }
+        print(json.dumps(line))
+    for mm in batch:
+        mm.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -536,6 +697,8 @@ def main():
         run_sweep(args)
     elif args.workload == "cubes64_gradients":
         run_gradients(args)
+    elif args.workload == "batch256":
+        run_batch(args)
     else:
         run_gpu(args)
 

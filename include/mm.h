@@ -181,6 +181,37 @@ mm_status mm_compute_torque(mm_ctx* ctx, int mag, float* dmdt_dev, float* Heff_d
  */
 mm_status mm_step(mm_ctx* ctx, int nsteps, double* t_out, double* dt_inout);
 
+/*
+ * Many independent pairs (one context each) advanced together: every context
+ * takes `nsteps` accepted Dormand-Prince steps exactly as mm_step would take
+ * them on its own (the same launches in the same order on its own stream, so
+ * each pair's result is bit-identical to mm_step's), with its own adaptive dt.
+ * Every pair's first attempt is queued before the first wait, and a pair's next
+ * attempt is queued as soon as its previous one is concluded, so while the host
+ * waits on one pair the streams of the others keep the GPU busy; contexts
+ * created on different streams run concurrently.  The paper steps one pair;
+ * batching many pairs is this library's addition.
+ *   ctxs: npairs distinct contexts; dt_inout: npairs step sizes (s) to try,
+ *   returning the next ones; t_out: npairs simulated times after the steps
+ *   (may be NULL); failed_pair: index of the pair whose error is returned
+ *   (-1 on success; may be NULL), its text in mm_last_error of that context.
+ * On an error the other pairs may hold an unconcluded attempt, which the next
+ * mm_step / mm_step_batch discards like a rejected one.  MM_EINVAL for a NULL
+ * or repeated context or a non-positive dt.
+ */
+mm_status mm_step_batch(mm_ctx* const* ctxs, int npairs, int nsteps, double* t_out, double* dt_inout,
+                        int* failed_pair);
+
+/*
+ * Host-only helper for batches: spread npairs pairs of the given costs (any
+ * non-negative unit, e.g. modelled bytes per field evaluation) over nlanes
+ * streams, longest processing time first (pairs by decreasing cost, ties by
+ * index, each to the least loaded lane, ties by lane index).  lane_out: npairs
+ * lane indices in [0, nlanes).  MM_EINVAL for nlanes < 1 or a negative or
+ * non-finite cost.  Needs no GPU.
+ */
+mm_status mm_assign_lanes(const double* cost, int npairs, int nlanes, int* lane_out);
+
 /* Accepted / rejected step counters since creation. */
 mm_status mm_get_step_stats(mm_ctx* ctx, long long* accepted, long long* rejected);
 

@@ -12,7 +12,7 @@ import torch
 from . import _native
 from ._native import MMError, mm_options
 
-__all__ = ["MovingMagnets", "MMError", "eval_kernel_fp64", "load_library"]
+__all__ = ["MovingMagnets", "MMError", "assign_lanes", "eval_kernel_fp64", "load_library", "step_batch"]
 
 
 def load_library():
@@ -71,6 +71,19 @@ class MovingMagnets:
     def _c(self, status):
         _check(self.lib, self.ctx, status)
 
+    def _in(self):
+        """Order the context stream after the caller's stream (tensors it made)."""
+        cur = torch.cuda.current_stream()
+        if cur != self.stream:
+            self.stream.wait_stream(cur)
+
+    def _out(self, *ts):
+        """Order the caller's stream after the context stream (tensors written there)."""
+        cur = torch.cuda.current_stream()
+        if cur != self.stream:
+            cur.wait_stream(self.stream)
+        return ts[0] if len(ts) == 1 else ts
+
     # ---------------------------------------------------------------- set-up
     def set_grid(self, mag, n, cell, offset=(0, 0, 0)):
         nx, ny, nz = n
@@ -90,12 +103,14 @@ class MovingMagnets:
 
     def set_magnetization(self, mag, m):
         _need_cuda_f32(m, self.shapes[mag])
+        self._in()
         self._c(self.lib.mm_set_magnetization(self.ctx, mag, _ptr(m)))
 
     def get_magnetization(self, mag):
         out = torch.empty(self.shapes[mag], dtype=torch.float32, device="cuda")
+        self._in()
         self._c(self.lib.mm_get_magnetization(self.ctx, mag, _ptr(out)))
-        return out
+        return self._out(out)
 
     def upload_magnetization(self, mag, m_host):
         if m_host.is_cuda or m_host.dtype != torch.float32 or not m_host.is_contiguous():
@@ -125,19 +140,22 @@ class MovingMagnets:
         lo = _native._ll3()
         self._c(self.lib.mm_compute_potential(self.ctx, src, int(prefiltered), None, 0, dims, lo))
         out = torch.empty((dims[2], dims[1], dims[0]), dtype=torch.float32, device="cuda")
+        self._in()
         self._c(self.lib.mm_compute_potential(self.ctx, src, int(prefiltered), _ptr(out), out.numel(),
                                               dims, lo))
-        return out, (lo[0], lo[1], lo[2])
+        return self._out(out), (lo[0], lo[1], lo[2])
 
     def compute_stray_field(self, src):
         H = torch.empty(self.shapes[1 - src], dtype=torch.float32, device="cuda")
+        self._in()
         self._c(self.lib.mm_compute_stray_field(self.ctx, src, _ptr(H)))
-        return H
+        return self._out(H)
 
     def compute_demag(self, mag):
         H = torch.empty(self.shapes[mag], dtype=torch.float32, device="cuda")
+        self._in()
         self._c(self.lib.mm_compute_demag(self.ctx, mag, _ptr(H)))
-        return H
+        return self._out(H)
 
     def compute_fields(self):
         self._c(self.lib.mm_compute_fields(self.ctx))
@@ -154,15 +172,18 @@ class MovingMagnets:
         du = _native._d3()
         gs = torch.empty(self.shapes[src], dtype=torch.float32, device="cuda") if want_src else None
         gt = torch.empty(self.shapes[1 - src], dtype=torch.float32, device="cuda") if want_tgt else None
+        self._in()
         self._c(self.lib.mm_backward_energy(self.ctx, src, du, _ptr(gs) if gs is not None else None,
                                             _ptr(gt) if gt is not None else None))
+        self._out(gs)
         return [du[0], du[1], du[2]], gs, gt
 
     def compute_torque(self, mag):
         dm = torch.empty(self.shapes[mag], dtype=torch.float32, device="cuda")
         H = torch.empty(self.shapes[mag], dtype=torch.float32, device="cuda")
+        self._in()
         self._c(self.lib.mm_compute_torque(self.ctx, mag, _ptr(dm), _ptr(H)))
-        return dm, H
+        return self._out(dm, H)
 
     def step(self, nsteps, dt):
         t = C.c_double()
@@ -209,6 +230,38 @@ class MovingMagnets:
 
     def launch_count(self):
         return self.lib.mm_launch_count(self.ctx)
+
+
+def step_batch(pairs, nsteps, dts):
+    """mm_step_batch: advance every MovingMagnets in `pairs` by nsteps accepted
+    steps, each with its own adaptive dt (dts: one step size per pair).
+    Returns (times, next step sizes) as lists."""
+    n = len(pairs)
+    if len(dts) != n:
+        raise ValueError("one dt per pair")
+    lib = _native.load()
+    ctxs = (C.c_void_p * n)(*[p.ctx.value for p in pairs])
+    t = (C.c_double * n)()
+    d = (C.c_double * n)(*[float(x) for x in dts])
+    bad = C.c_int(-1)
+    s = lib.mm_step_batch(ctxs, n, int(nsteps), t, d, C.byref(bad))
+    if s != 0:
+        i = bad.value
+        msg = lib.mm_last_error(pairs[i].ctx).decode() if 0 <= i < n else ""
+        raise MMError(s, "pair %d: %s" % (i, msg))
+    return list(t), list(d)
+
+
+def assign_lanes(costs, nlanes):
+    """mm_assign_lanes: longest-processing-time spread of pairs over nlanes streams."""
+    lib = _native.load()
+    n = len(costs)
+    c = (C.c_double * n)(*[float(x) for x in costs])
+    out = (C.c_int * n)()
+    s = lib.mm_assign_lanes(c, n, int(nlanes), out)
+    if s != 0:
+        raise MMError(s, "mm_assign_lanes")
+    return list(out)
 
 
 def spline_field_noalloc(coef, coef_lo, pos0_nodes, m_target, cell, Ms, H_out=None, FE_out=None,

@@ -19,7 +19,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <map>
+#include <set>
 #include <string>
 #include <vector>
 
@@ -146,6 +148,14 @@ struct mm_ctx {
   double u_base[3] = {0, 0, 0};       // metres
   MechState host_mech{};
   MechState* mech = nullptr;          // device
+  // pinned landing place of the readback that ends a step attempt; ev_done
+  // marks its arrival, so a caller can queue other work behind it
+  struct Readback {
+    MechState mech;
+    int err, pad;
+  };
+  Readback* rb = nullptr;
+  cudaEvent_t ev_done = nullptr;
   int* err_flag = nullptr;            // device
   int* tickets = nullptr;             // device: last-block counters of the gather and stage launches
   bool k1_valid = false;
@@ -1037,8 +1047,9 @@ mm_status check_device_error(mm_ctx* ctx) {
   return MM_OK;
 }
 
-// One step attempt of size dt; returns the error norm in *err.
-mm_status attempt_step(mm_ctx* ctx, double dt, double* err) {
+// Queues one step attempt of size dt and the readback of its slider state
+// and range flag; attempt_finish waits for them.
+mm_status attempt_enqueue(mm_ctx* ctx, double dt) {
   Magnet* M = ctx->mag;
   if (!ctx->k1_valid) {
     CKS(run_mech(ctx, mech_params(ctx, 4, 0, dt, false, false)));
@@ -1081,9 +1092,78 @@ mm_status attempt_step(mm_ctx* ctx, double dt, double* err) {
   // 5th-order solution) always ends in ys[1]
   (void)cur;
   CKS(join_mech(ctx));
-  CK(cudaMemcpyAsync(&ctx->host_mech, ctx->mech, sizeof(MechState), cudaMemcpyDeviceToHost, ctx->st));
-  CKS(check_device_error(ctx));
+  CK(cudaMemcpyAsync(&ctx->rb->mech, ctx->mech, sizeof(MechState), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaMemcpyAsync(&ctx->rb->err, ctx->err_flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaEventRecord(ctx->ev_done, ctx->st));
+  return MM_OK;
+}
+
+// Waits for the attempt queued by attempt_enqueue; its error norm in *err.
+mm_status attempt_finish(mm_ctx* ctx, double* err) {
+  CK(cudaEventSynchronize(ctx->ev_done));
+  ctx->host_mech = ctx->rb->mech;
+  if (ctx->rb->err) {
+    ctx->rb->err = 0;
+    CK(cudaMemsetAsync(ctx->err_flag, 0, sizeof(int), ctx->st));
+    return fail(ctx, MM_ERANGE, "slider displacement left the planned potential box during a step");
+  }
   *err = ctx->host_mech.err;
+  return MM_OK;
+}
+
+// Step-size control after an attempt with error norm err: on acceptance the
+// new m, the slider state and the first-same-as-last k1 are committed (and
+// the plan follows a whole-cell move); dt becomes the next attempt's size.
+mm_status conclude_attempt(mm_ctx* ctx, double* dt_io, double err, bool* accepted) {
+  double dt = *dt_io;
+  const bool accept = !ctx->opt.adaptive || err <= ctx->opt.rtol || dt <= ctx->opt.dt_min;
+  double fac = 5.0;
+  if (err > 0.0) fac = std::min(5.0, std::max(0.2, 0.9 * pow(ctx->opt.rtol / err, 0.2)));
+  if (accept) {
+    Launch<CombineJob> L{};
+    L.njobs = 2;
+    int tiles = 0;
+    for (int g = 0; g < 2; ++g) {
+      CombineJob& J = L.job[g];
+      // after an attempt the 5th-order solution is in ys[1] (stages 2..7 alternate 0,1,0,1,0,1)
+      J.y = ctx->mag[g].ys[1];
+      J.out = ctx->mag[g].m;
+      J.n = ctx->mag[g].N;
+      L.tile_start[g] = tiles;
+      tiles += (int)((ctx->mag[g].N + 255) / 256);
+    }
+    L.tile_start[2] = tiles;
+    {
+      Timer t(ctx, 6);
+      CK(launch_normalise(L, ctx->st));
+    }
+    for (int g = 0; g < 2; ++g) std::swap(ctx->mag[g].k[0], ctx->mag[g].k[6]);
+    CKS(run_mech(ctx, mech_params(ctx, 3, 7, dt, false, false)));
+    ctx->host_mech.x = ctx->host_mech.xs;
+    ctx->host_mech.v = ctx->host_mech.vs;
+    ctx->host_mech.t = ctx->host_mech.t + dt;
+    ctx->host_mech.kx[0] = ctx->host_mech.kx[6];
+    ctx->host_mech.kv[0] = ctx->host_mech.kv[6];
+    ctx->k1_valid = true;
+    ctx->accepted++;
+    // a whole-cell move beyond the guard needs new boxes (and a fresh k1)
+    bool moved = false;
+    for (int s = 0; s < 2 && !moved; ++s)
+      for (int a = 0; a < 3; ++a) {
+        const double sigma = s == 0 ? 1.0 : -1.0;
+        if ((int)floor(sigma * u_cells(ctx, a, ctx->host_mech.x)) != ctx->mag[s].dir.U0[a]) moved = true;
+      }
+    if (moved) {
+      CKS(ensure_plan(ctx));
+      CKS(upload_mech(ctx));
+      ctx->k1_valid = false;
+    }
+  } else {
+    ctx->rejected++;
+  }
+  if (ctx->opt.adaptive) dt = std::min(std::max(dt * fac, ctx->opt.dt_min), ctx->opt.dt_max);
+  *dt_io = dt;
+  *accepted = accept;
   return MM_OK;
 }
 
@@ -1136,6 +1216,9 @@ mm_status mm_create(mm_ctx** out, const mm_options* opt) {
   cudaError_t e = cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_done, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->rb, sizeof(mm_ctx::Readback));
+  if (e == cudaSuccess) memset(ctx->rb, 0, sizeof(mm_ctx::Readback));
   if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->mech, sizeof(MechState));
   if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->err_flag, sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->tickets, 2 * sizeof(int));
@@ -1183,6 +1266,8 @@ void mm_destroy(mm_ctx* ctx) {
   for (auto& p : ctx->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+  if (ctx->ev_done) cudaEventDestroy(ctx->ev_done);
+  if (ctx->rb) cudaFreeHost(ctx->rb);
   if (ctx->side) cudaStreamDestroy(ctx->side);
   for (auto e : ctx->free_events) cudaEventDestroy(e);
   delete ctx;
@@ -1571,57 +1656,94 @@ mm_status mm_step(mm_ctx* ctx, int nsteps, double* t_out, double* dt_inout) {
     if (++guard_iter > 100 * (nsteps + 1) + 1000)
       return fail(ctx, MM_EINVAL, "mm_step: step size control did not converge");
     double err = 0.0;
-    CKS(attempt_step(ctx, dt, &err));
-    // after attempt_step the 5th-order solution is in ys[1] (stages 2..7 alternate 0,1,0,1,0,1)
-    const bool accept = !ctx->opt.adaptive || err <= ctx->opt.rtol || dt <= ctx->opt.dt_min;
-    double fac = 5.0;
-    if (err > 0.0) fac = std::min(5.0, std::max(0.2, 0.9 * pow(ctx->opt.rtol / err, 0.2)));
-    if (accept) {
-      Launch<CombineJob> L{};
-      L.njobs = 2;
-      int tiles = 0;
-      for (int g = 0; g < 2; ++g) {
-        CombineJob& J = L.job[g];
-        J.y = ctx->mag[g].ys[1];
-        J.out = ctx->mag[g].m;
-        J.n = ctx->mag[g].N;
-        L.tile_start[g] = tiles;
-        tiles += (int)((ctx->mag[g].N + 255) / 256);
-      }
-      L.tile_start[2] = tiles;
-      {
-        Timer t(ctx, 6);
-        CK(launch_normalise(L, ctx->st));
-      }
-      for (int g = 0; g < 2; ++g) std::swap(ctx->mag[g].k[0], ctx->mag[g].k[6]);
-      CKS(run_mech(ctx, mech_params(ctx, 3, 7, dt, false, false)));
-      ctx->host_mech.x = ctx->host_mech.xs;
-      ctx->host_mech.v = ctx->host_mech.vs;
-      ctx->host_mech.t = ctx->host_mech.t + dt;
-      ctx->host_mech.kx[0] = ctx->host_mech.kx[6];
-      ctx->host_mech.kv[0] = ctx->host_mech.kv[6];
-      ctx->k1_valid = true;
-      ctx->accepted++;
-      ++done;
-      // a whole-cell move beyond the guard needs new boxes (and a fresh k1)
-      bool moved = false;
-      for (int s = 0; s < 2 && !moved; ++s)
-        for (int a = 0; a < 3; ++a) {
-          const double sigma = s == 0 ? 1.0 : -1.0;
-          if ((int)floor(sigma * u_cells(ctx, a, ctx->host_mech.x)) != ctx->mag[s].dir.U0[a]) moved = true;
-        }
-      if (moved) {
-        CKS(ensure_plan(ctx));
-        CKS(upload_mech(ctx));
-        ctx->k1_valid = false;
-      }
-    } else {
-      ctx->rejected++;
-    }
-    if (ctx->opt.adaptive) dt = std::min(std::max(dt * fac, ctx->opt.dt_min), ctx->opt.dt_max);
+    bool accepted = false;
+    CKS(attempt_enqueue(ctx, dt));
+    CKS(attempt_finish(ctx, &err));
+    CKS(conclude_attempt(ctx, &dt, err, &accepted));
+    if (accepted) ++done;
   }
   *dt_inout = dt;
   if (t_out) *t_out = ctx->host_mech.t;
+  return MM_OK;
+}
+
+mm_status mm_step_batch(mm_ctx* const* ctxs, int npairs, int nsteps, double* t_out, double* dt_inout,
+                        int* failed_pair) {
+  if (failed_pair) *failed_pair = -1;
+  if (npairs < 0 || nsteps < 0 || (npairs > 0 && (!ctxs || !dt_inout))) return MM_EINVAL;
+  {
+    std::set<const mm_ctx*> seen;
+    for (int i = 0; i < npairs; ++i)
+      if (!ctxs[i] || !seen.insert(ctxs[i]).second) {
+        if (failed_pair) *failed_pair = i;
+        return MM_EINVAL;
+      }
+  }
+  int bad = -1;
+  auto at = [&](int i, mm_status s) {
+    if (s != MM_OK && bad < 0) bad = i;
+    return s;
+  };
+#define CKB(i, expr)                     \
+  do {                                   \
+    mm_status s_ = at((i), (expr));      \
+    if (s_ != MM_OK) {                   \
+      if (failed_pair) *failed_pair = bad; \
+      return s_;                         \
+    }                                    \
+  } while (0)
+  for (int i = 0; i < npairs; ++i)
+    if (!(dt_inout[i] > 0)) CKB(i, fail(ctxs[i], MM_EINVAL, "mm_step_batch: dt must be positive"));
+  for (int i = 0; i < npairs; ++i) CKB(i, prepare(ctxs[i]));
+  std::vector<int> done(npairs, 0), iters(npairs, 0);
+  std::vector<char> active(npairs, nsteps > 0 ? 1 : 0);
+  int left = nsteps > 0 ? npairs : 0;
+  // every pair's first attempt is queued before the first wait; afterwards a
+  // pair's next attempt is queued as soon as its previous one is concluded,
+  // so the streams of the other pairs keep the GPU busy meanwhile
+  for (int i = 0; i < npairs && nsteps > 0; ++i) CKB(i, attempt_enqueue(ctxs[i], dt_inout[i]));
+  while (left > 0) {
+    for (int i = 0; i < npairs; ++i) {
+      if (!active[i]) continue;
+      mm_ctx* c = ctxs[i];
+      if (++iters[i] > 100 * (nsteps + 1) + 1000)
+        CKB(i, fail(c, MM_EINVAL, "mm_step_batch: step size control did not converge"));
+      double err = 0.0;
+      bool accepted = false;
+      CKB(i, attempt_finish(c, &err));
+      CKB(i, conclude_attempt(c, &dt_inout[i], err, &accepted));
+      if (accepted) ++done[i];
+      if (done[i] < nsteps) {
+        CKB(i, attempt_enqueue(c, dt_inout[i]));
+      } else {
+        active[i] = 0;
+        --left;
+      }
+    }
+  }
+#undef CKB
+  if (t_out)
+    for (int i = 0; i < npairs; ++i) t_out[i] = ctxs[i]->host_mech.t;
+  return MM_OK;
+}
+
+mm_status mm_assign_lanes(const double* cost, int npairs, int nlanes, int* lane_out) {
+  if (npairs < 0 || nlanes < 1 || (npairs > 0 && (!cost || !lane_out))) return MM_EINVAL;
+  for (int i = 0; i < npairs; ++i)
+    if (!(cost[i] >= 0) || !std::isfinite(cost[i])) return MM_EINVAL;
+  // longest processing time first: pairs by decreasing cost (ties by index),
+  // each to the lane with the least cost so far (ties by lane index)
+  std::vector<int> order(npairs);
+  for (int i = 0; i < npairs; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  std::vector<double> load(nlanes, 0.0);
+  for (int i : order) {
+    int best = 0;
+    for (int l = 1; l < nlanes; ++l)
+      if (load[l] < load[best]) best = l;
+    lane_out[i] = best;
+    load[best] += cost[i];
+  }
   return MM_OK;
 }
 

@@ -11,17 +11,21 @@ def rel_l2(a, b):
     return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
 
 
-def gpu_pair(fp, m0, m1, margin=4, adaptive=False, rtol=1e-5, mech=True):
-    """MovingMagnets context for a workloads.FilmPair with the given unit m arrays."""
+def gpu_pair(fp, m0, m1, margin=4, adaptive=False, rtol=1e-5, mech=True, stream=None):
+    """MovingMagnets context for a workloads.FilmPair with the given unit m arrays,
+    on `stream` (a torch.cuda.Stream; default: the current stream)."""
     import torch
     from paper_1801_04181_gb300 import MovingMagnets
 
-    mm = MovingMagnets(margin=margin, adaptive=adaptive, rtol=rtol)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    mm = MovingMagnets(margin=margin, adaptive=adaptive, rtol=rtol, stream=st)
     for g, (n, mat, m) in enumerate(((fp.n_base, fp.mat_base, m0), (fp.n_slider, fp.mat_slider, m1))):
         mm.set_grid(g, n, fp.cell, fp.offsets[g])
         mm.set_material(g, mat.Ms, mat.Aex, mat.Ku, mat.ku_axis, mat.alpha)
-        mm.set_magnetization(g, torch.as_tensor(np.ascontiguousarray(m), dtype=torch.float32,
-                                                device="cuda"))
+        # the tensor is made on the context's stream, which the library's copy follows
+        with torch.cuda.stream(st):
+            mt = torch.as_tensor(np.ascontiguousarray(m), dtype=torch.float32, device="cuda")
+        mm.set_magnetization(g, mt)
     mm.set_external_field(fp.H_ext)
     if mech:
         me = fp.mech

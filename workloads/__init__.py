@@ -136,3 +136,33 @@ def cube_pair(n=(64, 64, 64), gap=3, seed=0):
     fp = FilmPair("cube_pair_%dx%dx%d_gap%d" % (n + (gap,)), n, n, (2e-9, 2e-9, 2e-9), gap, mat, mat,
                   stack_axis=0)
     return fp, vortex(n, seed), vortex(n, seed + 1)
+
+
+def batch_pairs(npairs=256, seed=0, nx=(64, 512), ny=(64, 256), nz=(1, 4), u_max=50.0,
+                v_drive=(0.1, 10.0)):
+    """Independent spring-pulled PMA film pairs of uneven sizes (the stick-slip
+    pair's materials, mechanics and gap): per pair the two films share a size
+    drawn uniformly from the integer ranges nx x ny x nz, the slider is displaced
+    along x by u ~ U[0, u_max) cells and pulled at v_drive ~ U[v0, v1] m/s.
+    Returns FilmPair descriptions only; pair i's domain patterns come from
+    `batch_patterns(fp)` (pma_domains with the seeds stored on the pair), so
+    a large batch need not hold all patterns on the host at once."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(npairs):
+        n = (int(rng.integers(nx[0], nx[1] + 1)), int(rng.integers(ny[0], ny[1] + 1)),
+             int(rng.integers(nz[0], nz[1] + 1)))
+        u = float(rng.uniform(0.0, u_max))
+        vd = float(rng.uniform(v_drive[0], v_drive[1]))
+        mat = Material(Ms=1.1e6, Aex=1.5e-11, Ku=1.0e6, ku_axis=(0.0, 0.0, 1.0), alpha=0.5)
+        mech = Mechanics(mass=2.5e-18, k=1e-3, v_drive=vd, gamma_v=4e7, dir=(1.0, 0.0, 0.0))
+        fp = FilmPair("batch_pair_%d_%dx%dx%d" % ((i,) + n), n, n, (4e-9, 4e-9, 4e-9), 5, mat, mat, mech,
+                      u0=(u, 0.0, 0.0))
+        fp.pattern_seeds = (1000003 * seed + 2 * i, 1000003 * seed + 2 * i + 1)
+        out.append(fp)
+    return out
+
+
+def batch_patterns(fp):
+    """The seeded ~20-cell up/down domain patterns of both films of a batch pair."""
+    return pma_domains(fp.n_base, fp.pattern_seeds[0]), pma_domains(fp.n_slider, fp.pattern_seeds[1])
