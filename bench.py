@@ -42,6 +42,9 @@ TIMING_CLASSES = ["fft_x_forward", "fft_y_pass_mix_prefilter", "fft_x_inverse_pr
                   "fft_y_forward_thick", "fft_z_pass_thick", "fft_y_inverse_thick"]
 
 
+BATCH_LANES = 16
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -50,6 +53,7 @@ def parse():
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--seed", type=int, default=0)
+    p.add_argument("--lanes", type=int, default=BATCH_LANES, help="streams of the batch256 workload")
     p.add_argument("--workload", default="stick_slip",
                    choices=sorted(WORKLOADS) + ["plain64_sweep", "cubes64_gradients", "batch256"],
                    help="stick_slip (the headline workload), a thick-source workload, or the "
@@ -528,13 +532,10 @@ def run_gradients(args):
     mm.close()
 
 
-BATCH_LANES = 16
-
-
 def run_batch(args):
     """256 independent spring-pulled PMA film pairs of uneven sizes (nx in
     64..512, ny in 64..256, nz in 1..4, slider displaced by U[0, 50) cells,
-    pulled at U[0.1, 10] m/s), spread over 16 lane streams by longest
+    pulled at U[0.1, 10] m/s), spread over --lanes streams (16) by longest
     processing time first; one bench step = one mm_step_batch call in which
     every pair takes one accepted adaptive DP45 step.  Metric: cells of all
     pairs x steps / time.  Under torchrun the pairs are spread over the ranks
@@ -544,10 +545,6 @@ def run_batch(args):
     from paper_1801_04181_gb300 import assign_lanes, step_batch
     from tests.pair_setup import gpu_pair
 
-    # 16 lanes + each context's side stream: more hardware queues than the
-    # default 8, or unrelated streams serialise behind one another (this
-    # process only; read when CUDA initialises)
-    os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
     rank, world, local = dist_info()
     if world > 1:
         import torch.distributed as dist
@@ -561,8 +558,8 @@ def run_batch(args):
     # cost model for the spread: grid area x (source layers + box layers)
     cost = [fp.n_base[0] * fp.n_base[1] * (fp.n_base[2] + 4) for fp in specs]
     mine = [i for i, r in enumerate(assign_lanes(cost, world)) if r == rank]
-    lanes = assign_lanes([cost[i] for i in mine], BATCH_LANES)
-    streams = [torch.cuda.Stream() for _ in range(BATCH_LANES)]
+    lanes = assign_lanes([cost[i] for i in mine], args.lanes)
+    streams = [torch.cuda.Stream() for _ in range(args.lanes)]
     t_setup = time.perf_counter()
     batch = []
     for i, l in zip(mine, lanes):
@@ -670,7 +667,7 @@ def run_batch(args):
             "config": {"workload": "batch of 256 PMA film pairs, sizes U{64..512}xU{64..256}xU{1..4} "
                                    "(4 nm), slider at U[0, 50) cells, pulled at U[0.1, 10] m/s, "
                                    "adaptive DP45 per pair",
-                       "pairs": len(batch), "cells": cells, "lanes": BATCH_LANES,
+                       "pairs": len(batch), "cells": cells, "lanes": args.lanes,
                        "accepted": acc, "rejected": rej, "setup_s": round(t_setup, 1),
                        "parallelism": "pairs over ranks" if world > 1 else "single",
                        "l2": "no flush: the batch's working set (tens of GB) exceeds the 129 MB L2"},
