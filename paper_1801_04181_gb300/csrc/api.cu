@@ -244,9 +244,73 @@ void radix_search(int L, int max_r, std::vector<int>& cur, std::vector<int>& bes
   }
 }
 
+// Every ordering of every radix sequence with `stages` stages that multiplies to L.
+void radix_orders(int L, int stages, std::vector<int>& cur, std::vector<std::vector<int>>& out) {
+  static const int kRadices[] = {16, 15, 12, 10, 9, 8, 6, 5, 4, 3, 2};
+  if ((int)cur.size() == stages) {
+    if (L == 1) out.push_back(cur);
+    return;
+  }
+  for (int r : kRadices) {
+    if (L % r) continue;
+    cur.push_back(r);
+    radix_orders(L / r, stages, cur, out);
+    cur.pop_back();
+  }
+}
+
+// Shared-memory wavefronts of all stage loads of a plan (stores mirror them):
+// the butterflies of fft_smem on 4 lines of stride L + 4, a warp's 32
+// consecutive butterflies issuing one 8-byte access each, served per half
+// warp with one wavefront per distinct 4-byte word in the busiest bank.
+long long plan_wavefronts(int L, const std::vector<int>& radix) {
+  const int nlines = 4, ldl = L + 4;
+  long long total = 0;
+  int Lb = L;
+  std::vector<int> words;
+  for (int R : radix) {
+    const int M = Lb / R, per_line = L / R, nb = nlines * per_line;
+    for (int k = 0; k < R; ++k)
+      for (int w0 = 0; w0 < nb; w0 += 32)
+        for (int h = w0; h < std::min(w0 + 32, nb); h += 16) {
+          int count[32] = {0};
+          words.clear();
+          for (int b = h; b < std::min(h + 16, nb); ++b) {
+            const int line = b / per_line, rem = b - line * per_line, blk = rem / M, n1 = rem - blk * M;
+            const int a = line * ldl + blk * Lb + n1 + k * M;
+            words.push_back(2 * a);
+            words.push_back(2 * a + 1);
+          }
+          std::sort(words.begin(), words.end());
+          words.erase(std::unique(words.begin(), words.end()), words.end());
+          int worst = 0;
+          for (int w : words) worst = std::max(worst, ++count[w & 31]);
+          total += worst;
+        }
+    Lb /= R;
+  }
+  return total;
+}
+
+// The fewest stages; among those orderings, the fewest modelled shared-memory
+// wavefronts (a stage whose blocks start in the same banks, e.g. an even
+// radix last, costs up to several times the conflict-free count), ties going
+// to the largest-radix-first order.
 std::vector<int> plan_radices(int L) {
   std::vector<int> cur, best;
   radix_search(L, 16, cur, best);
+  if (best.empty()) return best;
+  std::vector<std::vector<int>> orders;
+  cur.clear();
+  radix_orders(L, (int)best.size(), cur, orders);
+  long long best_w = plan_wavefronts(L, best);
+  for (const auto& o : orders) {
+    const long long w = plan_wavefronts(L, o);
+    if (w < best_w) {
+      best_w = w;
+      best = o;
+    }
+  }
   return best;
 }
 
