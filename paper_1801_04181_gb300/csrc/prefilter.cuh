@@ -19,7 +19,7 @@ constexpr float kPrefGain = 1.6076951545867362f; // -6 z1
 // prefilter outputs per thread; odd, so neighbouring threads' table reads
 // fall in different shared-memory banks
 constexpr int kYChunk = 9;   // y pass (complex)
-constexpr int kXChunk = 17;  // x pass (real)
+constexpr int kXChunk = 9;   // x pass (real)
 constexpr int kZChunk = 9;   // z pass of thick sources (complex)
 // Shared-memory index of the samples the prefilter reads: entry j holds the
 // position, in a line of `Q` transformed by `P` (natural order when P is
