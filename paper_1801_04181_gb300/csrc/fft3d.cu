@@ -200,8 +200,9 @@ __global__ void __launch_bounds__(256, 3) k_yinv3(const Launch<YInvJob> Lc) {
   // natural-order input: DIF stages of the inverse leave the rows in DIF
   // order, read back through the position table; DIF-order input: DIT stages
   // leave natural order
-  const FftPlanDev* P = J.natural ? &J.fy.plan : nullptr;
-  if (J.is_C) build_pref_table(tab, J.r + 2 * kPrefWarm + kYChunk, J.box_lo, J.box_len, J.start, Q, P);
+  if (J.is_C)
+    build_pref_table(tab, J.r + 2 * kPrefWarm + kYChunk, J.box_lo, J.box_len, J.start, Q,
+                     J.natural ? J.fy.pos : nullptr);
   __syncthreads();
   if (J.natural) fft_smem<kInvDif, float2>(sm, ldl, np, J.fy.plan, J.fy.tw_f, 0, blockDim.x);
   else fft_smem<kInvDit, float2>(sm, ldl, np, J.fy.plan, J.fy.tw_f, 0, blockDim.x);

@@ -374,7 +374,7 @@ __global__ void __launch_bounds__(256, 3) k_xinv(const Launch<XInvJob> Lc) {
       xinv_put(sm, l * ldl, Q, kx, a, b);
     }
   }
-  build_pref_table(tab, J.out_len + 2 * kPrefWarm + kXChunk, J.box_lo, J.box_len, J.start, Q, &J.fx.plan);
+  build_pref_table(tab, J.out_len + 2 * kPrefWarm + kXChunk, J.box_lo, J.box_len, J.start, Q, J.fx.pos);
   __syncthreads();
   // natural-order input, digit-reversed output: the table above maps through it
   fft_smem<kInvDif, float2>(sm, ldl, nlines, J.fx.plan, J.fx.tw_f, 0, blockDim.x);

@@ -22,13 +22,14 @@ constexpr int kYChunk = 9;   // y pass (complex)
 constexpr int kXChunk = 9;   // x pass (real)
 constexpr int kZChunk = 9;   // z pass of thick sources (complex)
 // Shared-memory index of the samples the prefilter reads: entry j holds the
-// position, in a line of `Q` transformed by `P` (natural order when P is
-// null), of box-local node mirror(start - kPrefWarm + j).
+// position, in a line of `Q` left in the digit-reversed order of a transform
+// (`pos`: its frequency -> position table; natural order when null), of
+// box-local node mirror(start - kPrefWarm + j).
 __device__ __forceinline__ void build_pref_table(int* tab, int n, int box_lo, int box_len, int start, int Q,
-                                                 const FftPlanDev* P) {
+                                                 const int* __restrict__ pos) {
   for (int j = threadIdx.x; j < n; j += blockDim.x) {
     const int g = wrap_once(box_lo + mirror_index(start - kPrefWarm + j, box_len), Q);
-    tab[j] = P ? fft_pos(g, *P) : g;
+    tab[j] = pos ? __ldg(pos + g) : g;
   }
 }
 
