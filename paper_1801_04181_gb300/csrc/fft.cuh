@@ -203,9 +203,12 @@ __device__ __forceinline__ void stage_twiddles(const C* __restrict__ col, int M,
   for (int k = 1; k < R; ++k) w[k] = col[(k - 1) * M];
 }
 
-template <int R, bool INV, typename C>
+// PRUNE (first forward stage only, Lb = L): inputs at or beyond `nvalid` are
+// zero padding, taken as zero without being read (or ever written).
+template <int R, bool INV, typename C, bool PRUNE = false>
 __device__ __forceinline__ void fft_stage(C* buf, int ldl, int nlines, int L, int Lb, unsigned mpl,
-                                          unsigned mM, const C* __restrict__ stw, int tid, int nthr) {
+                                          unsigned mM, const C* __restrict__ stw, int tid, int nthr,
+                                          int nvalid = 0) {
   const int M = Lb / R;
   const int per_line = L / R;
   const int nb = nlines * per_line;
@@ -217,7 +220,7 @@ __device__ __forceinline__ void fft_stage(C* buf, int ldl, int nlines, int L, in
     C* base = buf + (line * ldl + blk * Lb + n1);  // shared memory: 32-bit offsets
     C v[R];
 #pragma unroll
-    for (int k = 0; k < R; ++k) v[k] = base[k * M];
+    for (int k = 0; k < R; ++k) v[k] = (!PRUNE || n1 + k * M < nvalid) ? base[k * M] : cmake<C>(0, 0);
     if (!INV) {
       Dft<R, C>::run(v, -1);
       if (n1) {
@@ -278,9 +281,11 @@ enum FftMode { kFwdDif = 0, kInvDit = 1, kInvDif = 2 };
 //   kInvDit: inverse, digit-reversed in, natural out
 //   kInvDif: inverse, natural in, digit-reversed out
 // stw: the stage twiddle tables of the plan (stage s at P.stw_off[s]).
+// nvalid (kFwdDif): 0 < nvalid < L means entries [nvalid, L) of every line
+// are zero padding that the caller need not write.
 template <int MODE, typename C>
 __device__ __forceinline__ void fft_smem(C* buf, int ldl, int nlines, const FftPlanDev& P,
-                                         const C* __restrict__ stw, int tid0, int nthr) {
+                                         const C* __restrict__ stw, int tid0, int nthr, int nvalid = 0) {
   const int L = P.L;
   const int tid = (int)threadIdx.x - tid0;
   const bool mine = tid >= 0 && tid < nthr;
@@ -289,10 +294,13 @@ __device__ __forceinline__ void fft_smem(C* buf, int ldl, int nlines, const FftP
     const int Lb = P.blocklen[st];
     const unsigned mpl = P.magic_per_line[st], mM = P.magic_M[st];
     const C* tws = stw + P.stw_off[st];
+    const bool prune = MODE == kFwdDif && si == 0 && nvalid > 0 && nvalid < L;
     if (mine) {
 #define MM_STAGE(R)                                                                                  \
   case R:                                                                                            \
     if (MODE == kInvDit) fft_stage<R, true, C>(buf, ldl, nlines, L, Lb, mpl, mM, tws, tid, nthr); \
+    else if (MODE == kFwdDif && prune)                                                               \
+      fft_stage<R, false, C, true>(buf, ldl, nlines, L, Lb, mpl, mM, tws, tid, nthr, nvalid);   \
     else if (MODE == kFwdDif)                                                                        \
       fft_stage<R, false, C>(buf, ldl, nlines, L, Lb, mpl, mM, tws, tid, nthr);                 \
     else fft_stage_dif_inv<R, C>(buf, ldl, nlines, L, Lb, mpl, mM, tws, tid, nthr);             \

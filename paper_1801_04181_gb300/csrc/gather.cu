@@ -99,7 +99,7 @@ __device__ __forceinline__ void gather_column(const GatherJob& J, const float* A
   }
 }
 
-__global__ void __launch_bounds__(TX * TY, 3) k_gather(const Launch<GatherJob> Lc) {
+__global__ void __launch_bounds__(TX * TY, 4) k_gather(const Launch<GatherJob> Lc) {
   extern __shared__ float gsm[];
   __shared__ float w_s[3][12];
   __shared__ int shift_s[3];
