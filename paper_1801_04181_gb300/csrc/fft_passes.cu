@@ -86,6 +86,23 @@ __global__ void __launch_bounds__(256, 3) k_xfwd(const Launch<XFwdJob> Lc) {
   const int ny = J.ny;
   const int pa0 = r0 / ny;
   const bool pairs = (ny & 1) == 0 && (nrows & 1) == 0;  // both rows of a line in one plane, 16-B aligned
+  if (pairs && nlines == kLines) {
+    // full tile: blockDim is a multiple of kLines, so every thread keeps one
+    // line and its output row pair for all its kx
+    const int l = threadIdx.x % kLines;
+    int pa = pa0, ya = r0 + 2 * l - pa0 * ny;
+    while (ya >= ny) { ++pa; ya -= ny; }
+    float2* dst0 = J.out + (size_t)pa * J.kxh * ny + ya;
+    const float2* line = sm + l * ldl;
+    for (int kx = threadIdx.x / kLines; kx < J.kxh; kx += blockDim.x / kLines) {
+      const ushort2 pp = ptab[kx];
+      const float2 Zk = line[pp.x];
+      const float2 Zm = line[pp.y];
+      *reinterpret_cast<float4*>(dst0 + (size_t)kx * ny) =
+          make_float4(0.5f * (Zk.x + Zm.x), 0.5f * (Zk.y - Zm.y), 0.5f * (Zk.y + Zm.y), -0.5f * (Zk.x - Zm.x));
+    }
+    return;
+  }
   const int n = J.kxh * nlines;
   for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
     const int kx = nlines == kLines ? idx / kLines : idx / nlines;
@@ -342,7 +359,27 @@ __global__ void __launch_bounds__(256, 3) k_xinv(const Launch<XInvJob> Lc) {
   };
   const bool paired = (rpp & 1) == 0 && (nrows & 1) == 0;  // row pairs adjacent, 16-byte aligned
   const int n = J.kxh * nlines;
-  if (paired) {
+  if (paired && nlines == kLines) {
+    // full tile: blockDim is a multiple of kLines, so every thread keeps one
+    // line (its input row pair) for all its kx; kBatchX reads in flight
+    constexpr int kBatchX = 4;
+    const int l = threadIdx.x % kLines;
+    const float2* src = rowptr(2 * l);
+    const int step = blockDim.x / kLines;
+    for (int kx0 = threadIdx.x / kLines; kx0 < J.kxh; kx0 += kBatchX * step) {
+      float4 v[kBatchX];
+#pragma unroll
+      for (int u = 0; u < kBatchX; ++u) {
+        const int kx = kx0 + u * step;
+        if (kx < J.kxh) v[u] = *reinterpret_cast<const float4*>(src + (size_t)kx * rpp);
+      }
+#pragma unroll
+      for (int u = 0; u < kBatchX; ++u) {
+        const int kx = kx0 + u * step;
+        if (kx < J.kxh) xinv_put(sm, l * ldl, Q, kx, make_float2(v[u].x, v[u].y), make_float2(v[u].z, v[u].w));
+      }
+    }
+  } else if (paired) {
     // thread -> (kx, line), line fastest: a warp reads 8 runs of 64 bytes;
     // kBatchX such reads in flight per thread
     constexpr int kBatchX = 4;
