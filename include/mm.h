@@ -75,7 +75,8 @@ const char* mm_status_string(mm_status s);
  * Sources with nz <= 4 take z by a direct sum over planes (thin films);
  * thicker sources, or sources whose box around a thick target is tall, take z
  * by FFT (Sec. III.A on a three-dimensional grid).  Grids whose FFT lines do
- * not fit one shared-memory pass return MM_ENOTSUP when planned.
+ * not fit one shared-memory pass return MM_ENOTSUP when planned, and so do
+ * magnets of more than 2^30 cells (here).
  */
 mm_status mm_set_grid(mm_ctx* ctx, int mag, int nx, int ny, int nz, double dx, double dy, double dz,
                       const long long offset_cells[3]);

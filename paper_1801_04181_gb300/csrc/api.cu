@@ -1346,6 +1346,7 @@ mm_status mm_set_grid(mm_ctx* ctx, int mag, int nx, int ny, int nz, double dx, d
   if (!ctx) return MM_EINVAL;
   if (bad_mag(mag) || nx < 1 || ny < 1 || nz < 1 || !(dx > 0) || !(dy > 0) || !(dz > 0) || !offset_cells)
     return fail(ctx, MM_EINVAL, "mm_set_grid: bad argument");
+  if ((long long)nx * ny * nz > (1ll << 30)) return fail(ctx, MM_ENOTSUP, "mm_set_grid: more than 2^30 cells");
   const Magnet& O = ctx->mag[1 - mag];
   if (O.grid && (O.d[0] != dx || O.d[1] != dy || O.d[2] != dz))
     return fail(ctx, MM_EINVAL, "mm_set_grid: both magnets must share the cell size");

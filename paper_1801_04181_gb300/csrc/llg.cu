@@ -33,9 +33,13 @@ __global__ void __launch_bounds__(256) k_stage(const Launch<StageJob> Lc, const 
   const size_t idx = (size_t)tile * blockDim.x + threadIdx.x;
   float emax = 0.f;
   if (idx < N) {
-    const int x = (int)(idx % nx);
-    const int y = (int)((idx / nx) % ny);
-    const int z = (int)(idx / ((size_t)nx * ny));
+    // 32-bit index arithmetic: a magnet holds at most 2^30 cells
+    const unsigned nxy = (unsigned)nx * (unsigned)ny;
+    const unsigned i32 = (unsigned)idx;
+    const int z = (int)(i32 / nxy);
+    const unsigned rem = i32 - (unsigned)z * nxy;
+    const int y = (int)(rem / (unsigned)nx);
+    const int x = (int)(rem - (unsigned)y * (unsigned)nx);
     const float* m = J.ys;
     const float m0 = m[idx], m1 = m[N + idx], m2 = m[2 * N + idx];
     float h0 = J.Hself[idx] + J.Hstray[idx] + J.hext[0];
