@@ -27,6 +27,7 @@ constexpr int kLinePad = 4;              // float2 between lines of an x-pass CT
 cudaError_t init_fft_constants_passes() { return upload_roots(); }
 
 // ------------------------------------------------------------------ x forward
+template <unsigned RSET>
 __global__ void __launch_bounds__(256, 3) k_xfwd(const Launch<XFwdJob> Lc) {
   extern __shared__ float2 sm[];
   const int j = find_job(Lc.tile_start, Lc.njobs, blockIdx.x);
@@ -79,7 +80,7 @@ __global__ void __launch_bounds__(256, 3) k_xfwd(const Launch<XFwdJob> Lc) {
     ptab[kx] = make_ushort2((unsigned short)__ldg(J.fx.pos + kx),
                             (unsigned short)__ldg(J.fx.pos + (kx == 0 ? 0 : Q - kx)));
   __syncthreads();
-  fft_smem<kFwdDif, float2>(sm, ldl, nlines, J.fx.plan, J.fx.tw_f, 0, blockDim.x, nx);
+  fft_smem<kFwdDif, float2, RSET>(sm, ldl, nlines, J.fx.plan, J.fx.tw_f, 0, blockDim.x, nx);
 
   // Z = A + iB:  A_k = (Z_k + conj Z_{Q-k}) / 2,  B_k = (Z_k - conj Z_{Q-k}) / (2i)
   // thread -> (kx, line) with the line fastest: a warp writes 8 runs of 64 bytes
@@ -237,7 +238,7 @@ __device__ __forceinline__ void ypass_mix(const YJob& J, float2* sm, int kx, int
 // warps) covers the 271 frequency pairs of a 540-point line in one round of
 // the spectral products.
 constexpr int kYThreads = 288;
-template <int NZ>
+template <int NZ, unsigned RSET>
 __global__ void __launch_bounds__(kYThreads, NZ <= 2 ? 3 : 2) k_ypass(const Launch<YJob> Lc) {
   constexpr int Pin = 3 * NZ;
   extern __shared__ float2 sm[];
@@ -294,10 +295,10 @@ __global__ void __launch_bounds__(kYThreads, NZ <= 2 ? 3 : 2) k_ypass(const Laun
     for (int p = 0; p < Pin; ++p) sm[p * Q + y] = make_float2(0.f, 0.f);
   if (J.do_C) build_pref_table(tab, J.r + 2 * kPrefWarm + kYChunk, J.box_lo, J.box_len, J.start, Q, nullptr);
   __syncthreads();
-  fft_smem<kFwdDif, float2>(sm, Q, Pin, J.fy.plan, J.fy.tw_f, 0, blockDim.x);
+  fft_smem<kFwdDif, float2, RSET>(sm, Q, Pin, J.fy.plan, J.fy.tw_f, 0, blockDim.x);
   ypass_mix<NZ>(J, sm, kx, Q, nH);
   __syncthreads();
-  fft_smem<kInvDit, float2>(sm, Q, Pout, J.fy.plan, J.fy.tw_f, 0, blockDim.x);
+  fft_smem<kInvDit, float2, RSET>(sm, Q, Pout, J.fy.plan, J.fy.tw_f, 0, blockDim.x);
 
   if (J.do_H) {
     float2* out0 = J.outH + (size_t)kx * ny;
@@ -336,6 +337,7 @@ __device__ __forceinline__ void xinv_put(float2* sm, int off, int Q, int kx, flo
   if (kx > 0 && 2 * kx != Q) sm[off + Q - kx] = make_float2(A.x + B.y, B.x - A.y);
 }
 
+template <unsigned RSET>
 __global__ void __launch_bounds__(256, 3) k_xinv(const Launch<XInvJob> Lc) {
   extern __shared__ float2 sm[];
   const int j = find_job(Lc.tile_start, Lc.njobs, blockIdx.x);
@@ -414,7 +416,7 @@ __global__ void __launch_bounds__(256, 3) k_xinv(const Launch<XInvJob> Lc) {
   build_pref_table(tab, J.out_len + 2 * kPrefWarm + kXChunk, J.box_lo, J.box_len, J.start, Q, J.fx.pos);
   __syncthreads();
   // natural-order input, digit-reversed output: the table above maps through it
-  fft_smem<kInvDif, float2>(sm, ldl, nlines, J.fx.plan, J.fx.tw_f, 0, blockDim.x);
+  fft_smem<kInvDif, float2, RSET>(sm, ldl, nlines, J.fx.plan, J.fx.tw_f, 0, blockDim.x);
 
   const int r = J.out_len;
   float* out0 = J.out + (size_t)r0 * r;
@@ -454,23 +456,29 @@ static void max_carveout(const void* f) {
 cudaError_t launch_xfwd(const Launch<XFwdJob>& L, int Qmax, cudaStream_t st) {
   const size_t smem =
       (size_t)kLines * (Qmax + kLinePad) * sizeof(float2) + sizeof(ushort2) * (size_t)(Qmax / 2 + 1);
-  max_carveout((const void*)k_xfwd);
-  cudaError_t e = cudaFuncSetAttribute(k_xfwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  unsigned rs = 0;
+  for (int i = 0; i < L.njobs; ++i) rs |= plan_radix_set(L.job[i].fx.plan);
+  auto k = (rs & ~kRadixSetA) == 0u ? k_xfwd<kRadixSetA> : k_xfwd<kAllRadices>;
+  max_carveout((const void*)k);
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int grid = L.tile_start[L.njobs];
   if (grid == 0) return cudaSuccess;
-  k_xfwd<<<grid, 256, smem, st>>>(L);
+  k<<<grid, 256, smem, st>>>(L);
   return cudaGetLastError();
 }
 
 template <int NZ>
 static cudaError_t launch_ypass_nz(const Launch<YJob>& L, size_t smem, cudaStream_t st) {
-  max_carveout((const void*)k_ypass<NZ>);
-  cudaError_t e = cudaFuncSetAttribute(k_ypass<NZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  unsigned rs = 0;
+  for (int i = 0; i < L.njobs; ++i) rs |= plan_radix_set(L.job[i].fy.plan);
+  auto k = (rs & ~kRadixSetA) == 0u ? k_ypass<NZ, kRadixSetA> : k_ypass<NZ, kAllRadices>;
+  max_carveout((const void*)k);
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int grid = L.tile_start[L.njobs];
   if (grid == 0) return cudaSuccess;
-  k_ypass<NZ><<<grid, kYThreads, smem, st>>>(L);
+  k<<<grid, kYThreads, smem, st>>>(L);
   return cudaGetLastError();
 }
 
@@ -501,12 +509,15 @@ cudaError_t launch_xinv(const Launch<XInvJob>& L, int Qmax, cudaStream_t st) {
   int out_max = 0;
   for (int i = 0; i < L.njobs; ++i) out_max = max(out_max, L.job[i].out_len);
   const size_t smem = xinv_smem(Qmax, out_max);
-  max_carveout((const void*)k_xinv);
-  cudaError_t e = cudaFuncSetAttribute(k_xinv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  unsigned rs = 0;
+  for (int i = 0; i < L.njobs; ++i) rs |= plan_radix_set(L.job[i].fx.plan);
+  auto k = (rs & ~kRadixSetA) == 0u ? k_xinv<kRadixSetA> : k_xinv<kAllRadices>;
+  max_carveout((const void*)k);
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int grid = L.tile_start[L.njobs];
   if (grid == 0) return cudaSuccess;
-  k_xinv<<<grid, 256, smem, st>>>(L);
+  k<<<grid, 256, smem, st>>>(L);
   return cudaGetLastError();
 }
 
