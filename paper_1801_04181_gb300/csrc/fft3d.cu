@@ -34,6 +34,7 @@ namespace mm {
 cudaError_t init_fft_constants_3d() { return upload_roots(); }
 
 // ------------------------------------------------------------------ y forward
+template <unsigned RSET>
 __global__ void __launch_bounds__(256, 2) k_yfwd3(const Launch<YFwdJob> Lc) {
   extern __shared__ float2 sm[];
   const int j = find_job(Lc.tile_start, Lc.njobs, blockIdx.x);
@@ -51,7 +52,7 @@ __global__ void __launch_bounds__(256, 2) k_yfwd3(const Launch<YFwdJob> Lc) {
       sm[l * ldl + y] = y < J.ny ? col[y] : make_float2(0.f, 0.f);
   }
   __syncthreads();
-  fft_smem<kFwdDif, float2>(sm, ldl, np, J.fy.plan, J.fy.tw_f, 0, blockDim.x);
+  fft_smem<kFwdDif, float2, RSET>(sm, ldl, np, J.fy.plan, J.fy.tw_f, 0, blockDim.x);
   if (J.natural) {
     // frequency ky read from its DIF position: whole contiguous output rows
     for (int l = 0; l < np; ++l) {
@@ -70,6 +71,7 @@ __global__ void __launch_bounds__(256, 2) k_yfwd3(const Launch<YFwdJob> Lc) {
 // ------------------------------------------------------------------ z pass
 __device__ __forceinline__ float2 c_i_times(float2 m) { return make_float2(-m.y, m.x); }
 
+template <unsigned RSET>
 __global__ void __launch_bounds__(256, 2) k_zpass3(const Launch<ZJob> Lc) {
   extern __shared__ float2 sm[];
   const int j = find_job(Lc.tile_start, Lc.njobs, blockIdx.x);
@@ -100,7 +102,7 @@ __global__ void __launch_bounds__(256, 2) k_zpass3(const Launch<ZJob> Lc) {
   }
   if (J.do_C) build_pref_table(tab, J.r + 2 * kPrefWarm + kZChunk, J.box_lo, J.box_len, J.start, Qz, nullptr);
   __syncthreads();
-  fft_smem<kFwdDif, float2>(sm, ldz, 3 * nt, J.fz.plan, J.fz.tw_f, 0, blockDim.x);
+  fft_smem<kFwdDif, float2, RSET>(sm, ldz, 3 * nt, J.fz.plan, J.fz.tw_f, 0, blockDim.x);
 
   // spectral products at the pair (kz, Qz - kz) of every y position of the tile
   const int half = Qz >> 1;
@@ -149,8 +151,8 @@ __global__ void __launch_bounds__(256, 2) k_zpass3(const Launch<ZJob> Lc) {
     }
   }
   __syncthreads();
-  if (J.do_H) fft_smem<kInvDit, float2>(sm, ldz, 3 * nt, J.fz.plan, J.fz.tw_f, 0, blockDim.x);
-  if (J.do_C) fft_smem<kInvDit, float2>(phi, ldz, nt, J.fz.plan, J.fz.tw_f, 0, blockDim.x);
+  if (J.do_H) fft_smem<kInvDit, float2, RSET>(sm, ldz, 3 * nt, J.fz.plan, J.fz.tw_f, 0, blockDim.x);
+  if (J.do_C) fft_smem<kInvDit, float2, RSET>(phi, ldz, nt, J.fz.plan, J.fz.tw_f, 0, blockDim.x);
 
   if (J.do_H) {
     for (int i = threadIdx.x; i < P3 * nt; i += blockDim.x) {
@@ -181,6 +183,7 @@ __global__ void __launch_bounds__(256, 2) k_zpass3(const Launch<ZJob> Lc) {
 }
 
 // ------------------------------------------------------------------ y inverse
+template <unsigned RSET>
 __global__ void __launch_bounds__(256, 3) k_yinv3(const Launch<YInvJob> Lc) {
   extern __shared__ float2 sm[];
   const int j = find_job(Lc.tile_start, Lc.njobs, blockIdx.x);
@@ -204,8 +207,8 @@ __global__ void __launch_bounds__(256, 3) k_yinv3(const Launch<YInvJob> Lc) {
     build_pref_table(tab, J.r + 2 * kPrefWarm + kYChunk, J.box_lo, J.box_len, J.start, Q,
                      J.natural ? J.fy.pos : nullptr);
   __syncthreads();
-  if (J.natural) fft_smem<kInvDif, float2>(sm, ldl, np, J.fy.plan, J.fy.tw_f, 0, blockDim.x);
-  else fft_smem<kInvDit, float2>(sm, ldl, np, J.fy.plan, J.fy.tw_f, 0, blockDim.x);
+  if (J.natural) fft_smem<kInvDif, float2, RSET>(sm, ldl, np, J.fy.plan, J.fy.tw_f, 0, blockDim.x);
+  else fft_smem<kInvDit, float2, RSET>(sm, ldl, np, J.fy.plan, J.fy.tw_f, 0, blockDim.x);
   if (!J.is_C) {
     for (int l = 0; l < np; ++l) {
       float2* dst = J.outH + ((size_t)(p0 + l) * J.kxh + kx) * J.ny;
@@ -340,11 +343,14 @@ cudaError_t launch_yfwd3(const Launch<YFwdJob>& L, cudaStream_t st) {
   size_t smem = 0;
   for (int i = 0; i < L.njobs; ++i)
     smem = std::max(smem, sizeof(float2) * (size_t)L.job[i].group * (L.job[i].fy.plan.L + 1));
-  cudaError_t e = prep((const void*)k_yfwd3, smem);
+  unsigned rs = 0;
+  for (int i = 0; i < L.njobs; ++i) rs |= plan_radix_set(L.job[i].fy.plan);
+  auto k = (rs & ~kRadixSetA) == 0u ? k_yfwd3<kRadixSetA> : k_yfwd3<kAllRadices>;
+  cudaError_t e = prep((const void*)k, smem);
   if (e != cudaSuccess) return e;
   const int grid = L.tile_start[L.njobs];
   if (grid == 0) return cudaSuccess;
-  k_yfwd3<<<grid, 256, smem, st>>>(L);
+  k<<<grid, 256, smem, st>>>(L);
   return cudaGetLastError();
 }
 
@@ -356,11 +362,14 @@ cudaError_t launch_zpass3(const Launch<ZJob>& L, cudaStream_t st) {
     const size_t tab = sizeof(int) * (size_t)(J.do_C ? J.r + 2 * kPrefWarm + kZChunk : 0);
     smem = std::max(smem, lines + tab);
   }
-  cudaError_t e = prep((const void*)k_zpass3, smem);
+  unsigned rs = 0;
+  for (int i = 0; i < L.njobs; ++i) rs |= plan_radix_set(L.job[i].fz.plan);
+  auto k = (rs & ~kRadixSetA) == 0u ? k_zpass3<kRadixSetA> : k_zpass3<kAllRadices>;
+  cudaError_t e = prep((const void*)k, smem);
   if (e != cudaSuccess) return e;
   const int grid = L.tile_start[L.njobs];
   if (grid == 0) return cudaSuccess;
-  k_zpass3<<<grid, 256, smem, st>>>(L);
+  k<<<grid, 256, smem, st>>>(L);
   return cudaGetLastError();
 }
 
@@ -372,11 +381,14 @@ cudaError_t launch_yinv3(const Launch<YInvJob>& L, cudaStream_t st) {
     const size_t tab = sizeof(int) * (size_t)(J.is_C ? J.r + 2 * kPrefWarm + kYChunk : 0);
     smem = std::max(smem, lines + tab);
   }
-  cudaError_t e = prep((const void*)k_yinv3, smem);
+  unsigned rs = 0;
+  for (int i = 0; i < L.njobs; ++i) rs |= plan_radix_set(L.job[i].fy.plan);
+  auto k = (rs & ~kRadixSetA) == 0u ? k_yinv3<kRadixSetA> : k_yinv3<kAllRadices>;
+  cudaError_t e = prep((const void*)k, smem);
   if (e != cudaSuccess) return e;
   const int grid = L.tile_start[L.njobs];
   if (grid == 0) return cudaSuccess;
-  k_yinv3<<<grid, 256, smem, st>>>(L);
+  k<<<grid, 256, smem, st>>>(L);
   return cudaGetLastError();
 }
 
