@@ -1141,7 +1141,8 @@ mm_status attempt_enqueue(mm_ctx* ctx, double dt) {
       Timer t(ctx, 6);
       CK(launch_combine(L, ctx->st));
     }
-    CKS(run_mech(ctx, mech_params(ctx, 2, 1, dt, false, false)));
+    // the slider's stage-2 input is first read by the gathers: beside the FFT passes
+    CKS(fork_mech(ctx, mech_params(ctx, 2, 1, dt, false, false)));
   }
   int cur = 0;
   for (int i = 2; i <= 7; ++i) {
@@ -1202,7 +1203,8 @@ mm_status conclude_attempt(mm_ctx* ctx, double* dt_io, double err, bool* accepte
       CK(launch_normalise(L, ctx->st));
     }
     for (int g = 0; g < 2; ++g) std::swap(ctx->mag[g].k[0], ctx->mag[g].k[6]);
-    CKS(run_mech(ctx, mech_params(ctx, 3, 7, dt, false, false)));
+    // the accepted slider state, beside the normalisation
+    CKS(fork_mech(ctx, mech_params(ctx, 3, 7, dt, false, false)));
     ctx->host_mech.x = ctx->host_mech.xs;
     ctx->host_mech.v = ctx->host_mech.vs;
     ctx->host_mech.t = ctx->host_mech.t + dt;
