@@ -13,6 +13,8 @@ field of the other magnet (Sec. II.A).
 Slider (Sec. III, IV.B): m_s x'' = k (v_d t + x_0 - x) - gamma_v m_s x' + F_m . e,
 with F_m the Eq. (EQForce) force of the base on the slider; x is integrated
 with the magnetisation by the Dormand-Prince 5(4) pair (Sec. III).
+Power bookkeeping (Sec. III, after Eq. (EQForce)): the input -F_m . v_s and the
+Gilbert dissipation of each magnet (dissipation_power, power_balance).
 """
 
 import numpy as np
@@ -188,3 +190,32 @@ def run_adaptive(system, y0, dt, nsteps, rtol, t0=0.0, dt_min=0.0, dt_max=np.inf
             rejected += 1
         dt = min(max(dt * fac, dt_min), dt_max)
     return t, y, dt, accepted, rejected
+
+
+def dissipation_power(m, H, Ms, alpha, cell):
+    """Gilbert dissipation of one magnet (Sec. III, after Eq. (EQForce)), W:
+
+        P_diss = gamma0 alpha mu0 V / ((1 + alpha^2) Ms) sum_i |M_i x H_eff,i|^2
+
+    with M = Ms m and gamma0 = mu0 * 1.7595e11 the prefactor of the LLG
+    equation of Sec. II eq. (1) (its H is in A/m, so its gamma is gamma0).
+    m (3, ...) unit vectors, H (3, ...) the effective field in A/m."""
+    gamma0 = MU0 * GAMMA_LL
+    V = float(np.prod(np.asarray(cell, dtype=np.float64)))
+    M = Ms * np.asarray(m, dtype=np.float64)
+    MxH = np.cross(M, np.asarray(H, dtype=np.float64), axis=0)
+    return gamma0 * alpha * MU0 * V / ((1.0 + alpha * alpha) * Ms) * float(np.sum(MxH * MxH))
+
+
+def power_balance(system, m0, m1, x, v):
+    """Power bookkeeping of the moving slider (Sec. III, after Eq. (EQForce)):
+    P_in = -F_m^s . v_s, pumped into the magnets by the slider moving at
+    v_s = v e against the force F_m^s of the base on it; P_diss of each magnet
+    at its effective field; P_visc = gamma_v m v^2, the viscous damping of the
+    drive.  In the steady state P_in balances the two dissipations."""
+    H, on1, _ = system.fields(m0, m1, x)
+    P_diss = [dissipation_power(m, H[g], system.mat[g]["Ms"], system.mat[g]["alpha"], system.cell)
+              for g, m in enumerate((m0, m1))]
+    P_in = -float(np.dot(on1["F"], v * system.e))
+    me = system.mech
+    return dict(P_in=P_in, P_diss=P_diss, P_visc=me["gamma_v"] * me["mass"] * v * v, F=on1["F"], H=H)

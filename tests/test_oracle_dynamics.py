@@ -117,3 +117,54 @@ def test_slider_critically_damped_spring():
     # x'' + 2w x' + w^2 x = w^2 v t:  x = v t - 2v/w + (2v/w + v t) e^{-wt} ... (x(0)=x'(0)=0)
     x_ref = v * t - 2 * v / w + (2 * v / w + v * t) * np.exp(-w * t)
     assert abs(yy[2] - x_ref) < 1e-6 * abs(x_ref)
+
+
+def test_dissipation_power_is_the_llg_energy_rate():
+    """For the Landau-Lifshitz right-hand side, mu0 Ms V sum H . dm/dt (the rate
+    at which the field's energy -mu0 Ms V m . H changes for a frozen H, with
+    the sign of a loss) equals P_diss: a pin of the formula against the
+    independently pinned LLG right-hand side."""
+    rng = np.random.default_rng(11)
+    m = rng.standard_normal((3, 2, 3, 4))
+    m /= np.sqrt((m * m).sum(axis=0))
+    H = 1e5 * rng.standard_normal((3, 2, 3, 4))
+    Ms, alpha, cell = 1.1e6, 0.37, (4e-9, 3e-9, 2e-9)
+    V = np.prod(cell)
+    rate = MU0 * Ms * V * float(np.sum(H * D.llg_rhs(m, H, alpha)))
+    P = D.dissipation_power(m, H, Ms, alpha, cell)
+    assert P > 0
+    assert abs(P - rate) <= 1e-12 * abs(rate)
+
+
+def test_dissipation_power_single_spin_closed_form():
+    """One spin at angle theta to a uniform field H: |M x H|^2 = Ms^2 H^2 sin^2(theta)."""
+    from oracle import GAMMA_LL
+    th, Hz, Ms, alpha, cell = 0.7, 2e5, 8e5, 0.1, (2e-9, 2e-9, 2e-9)
+    m = np.array([np.sin(th), 0.0, np.cos(th)])[:, None, None, None]
+    H = np.array([0.0, 0.0, Hz])[:, None, None, None]
+    ref = MU0 * GAMMA_LL * alpha * MU0 * np.prod(cell) * Ms * Hz ** 2 * np.sin(th) ** 2 / (1 + alpha ** 2)
+    assert abs(D.dissipation_power(m, H, Ms, alpha, cell) - ref) <= 1e-13 * ref
+    # parallel to the field: nothing to relax
+    m_par = np.array([0.0, 0.0, 1.0])[:, None, None, None]
+    assert D.dissipation_power(m_par, H, Ms, alpha, cell) == 0.0
+
+
+def test_power_input_is_minus_force_dot_velocity():
+    """P_in = -F . v_s with the force of the base on the slider (the
+    System's own Eq. (EQForce) evaluation) and v_s along the drive direction."""
+    from oracle.dynamics import System
+    cell = (4e-9, 4e-9, 4e-9)
+    mat = dict(Ms=8e5, Aex=1.3e-11, Ku=0.0, ku_axis=(0, 0, 1), alpha=0.5)
+    mech = dict(mass=2.5e-18, k=1e-3, v_drive=1.0, gamma_v=4e7, dir=(1, 1, 0))
+    sys = System([(6, 5, 1), (5, 4, 1)], cell, [(0, 0, 0), (1, 0, 2)], [mat, mat], mech, u0=(0.3, 0.1, 0))
+    rng = np.random.default_rng(3)
+    m0 = rng.standard_normal((3, 1, 5, 6)); m0 /= np.sqrt((m0 * m0).sum(axis=0))
+    m1 = rng.standard_normal((3, 1, 4, 5)); m1 /= np.sqrt((m1 * m1).sum(axis=0))
+    v = 2.5
+    P = D.power_balance(sys, m0, m1, 1e-10, v)
+    e = np.array([1.0, 1.0, 0.0]) / np.sqrt(2.0)
+    assert abs(P["P_in"] + float(np.dot(P["F"], v * e))) <= 1e-15 * np.linalg.norm(P["F"]) * v
+    assert abs(P["P_visc"] - 4e7 * 2.5e-18 * v * v) <= 1e-15 * P["P_visc"]
+    assert all(p > 0 for p in P["P_diss"])
+    # reversing the velocity reverses the input power
+    assert abs(D.power_balance(sys, m0, m1, 1e-10, -v)["P_in"] + P["P_in"]) <= 1e-12 * abs(P["P_in"])
