@@ -337,6 +337,16 @@ def run_gpu(args):
     e2e = whole_job_rate(cells, k_e2e, e2e_s, world)
     h2d = sum(int(np.prod(mm.shapes[g])) * 4 for g in (0, 1))
 
+    # power bookkeeping at the final state (one field evaluation, the torque
+    # with H_eff and the |m x H_eff|^2 sums), host-timed around the call
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    pw = mm.power()
+    power = {"P_in_W": pw["P_in"], "P_diss_W": pw["P_diss"], "P_visc_W": pw["P_visc"],
+             "ms": round((time.perf_counter() - t0) * 1e3, 3),
+             "what": "mm_get_power at the final state: P_in = -F.v_s, Gilbert dissipation per magnet, "
+                     "viscous drive loss"}
+
     # roofline of the dominant kernel class
     ab = algorithmic_bytes(mm, fp)
     dom = max(ab.keys(), key=lambda c: kt[c][0])
@@ -374,6 +384,7 @@ def run_gpu(args):
             "roofline": roof,
             "kernel_times": ktab,
             "cufft_compare": fft_cmp,
+            "power": power,
             "clocks": clk,
             "cpu_baseline": cpu_base,
         }

@@ -213,6 +213,22 @@ mm_status mm_step_batch(mm_ctx* const* ctxs, int npairs, int nsteps, double* t_o
  */
 mm_status mm_assign_lanes(const double* cost, int npairs, int nlanes, int* lane_out);
 
+/*
+ * Power bookkeeping at the current state (Sec. III, after Eq. (EQForce)), W:
+ *   P_in      = -F_m^s . v_s, the power the moving slider pumps into the
+ *               magnets (F_m^s the force of the base on the slider, v_s = v e
+ *               its velocity along the drive direction; 0 for a fixed slider);
+ *   P_diss[g] = gamma0 alpha mu0 V / ((1 + alpha^2) Ms) sum_i |M_i x H_eff,i|^2,
+ *               the Gilbert relaxation of magnet g (gamma0 = mu0 1.7595e11, the
+ *               LLG prefactor of Sec. II eq. 1, whose H is in A/m);
+ *   P_visc    = gamma_v mass v^2, the viscous damping of the drive.
+ * In the steady state P_in balances P_diss[0] + P_diss[1] + the drive's share,
+ * and <P_diss / v> estimates the friction force.  Evaluates the fields at the
+ * current m and displacement (like mm_compute_torque, so the next mm_step
+ * recomputes its first stage).  Any output pointer may be NULL.  Synchronises.
+ */
+mm_status mm_get_power(mm_ctx* ctx, double* P_in, double P_diss[2], double* P_visc);
+
 /* Accepted / rejected step counters since creation. */
 mm_status mm_get_step_stats(mm_ctx* ctx, long long* accepted, long long* rejected);
 

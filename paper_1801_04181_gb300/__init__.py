@@ -191,6 +191,13 @@ class MovingMagnets:
         self._c(self.lib.mm_step(self.ctx, int(nsteps), C.byref(t), C.byref(d)))
         return t.value, d.value
 
+    def power(self):
+        """mm_get_power: dict with P_in, P_diss (one per magnet) and P_visc in W."""
+        pin, pv = C.c_double(), C.c_double()
+        pd = (C.c_double * 2)()
+        self._c(self.lib.mm_get_power(self.ctx, C.byref(pin), pd, C.byref(pv)))
+        return dict(P_in=pin.value, P_diss=[pd[0], pd[1]], P_visc=pv.value)
+
     def step_stats(self):
         a, r = C.c_longlong(), C.c_longlong()
         self._c(self.lib.mm_get_step_stats(self.ctx, C.byref(a), C.byref(r)))

@@ -89,6 +89,11 @@ struct Magnet {
   float* Hself = nullptr;
   float* Hstray = nullptr;
   float* scratch3 = nullptr;  // 3N scratch for rhs-only evaluations
+  // power bookkeeping (allocated on first use): H_eff, block sums, the sum
+  float* pow_H = nullptr;
+  size_t pow_H_bytes = 0;
+  double* pow_part = nullptr;
+  size_t pow_part_bytes = 0;
   float* err_partial = nullptr;
   int nerr = 0;
   // as a source
@@ -1317,6 +1322,7 @@ void mm_destroy(mm_ctx* ctx) {
     for (auto p : M.ys) cudaFree(p);
     for (auto p : M.k) cudaFree(p);
     cudaFree(M.Hself); cudaFree(M.Hstray); cudaFree(M.scratch3); cudaFree(M.err_partial);
+    cudaFree(M.pow_H); cudaFree(M.pow_part);
     cudaFree(M.X1); cudaFree(M.YH); cudaFree(M.Nq);
     cudaFree(M.N3); cudaFree(M.S3); cudaFree(M.Y3); cudaFree(M.Z3H);
     cudaFree(M.adj_box); cudaFree(M.adj_grid); cudaFree(M.adj_X); cudaFree(M.adj_Y); cudaFree(M.adj_Z);
@@ -1709,6 +1715,50 @@ mm_status mm_compute_torque(mm_ctx* ctx, int mag, float* dmdt_dev, float* Heff_d
     CK(launch_stage(L, MechParams{}, nullptr, ctx->st));
   }
   ctx->k1_valid = false;
+  return MM_OK;
+}
+
+mm_status mm_get_power(mm_ctx* ctx, double* P_in, double P_diss[2], double* P_visc) {
+  if (!ctx) return MM_EINVAL;
+  CKS(mm_compute_fields(ctx));
+  for (int g = 0; g < 2; ++g) {
+    Magnet& M = ctx->mag[g];
+    CKS(ensure_buf(ctx, &M.pow_H, &M.pow_H_bytes, sizeof(float) * 3 * M.N));
+    CKS(ensure_buf(ctx, &M.pow_part, &M.pow_part_bytes, sizeof(double) * (power_blocks(M.N) + 1)));
+    float* kp[7];
+    for (int i = 0; i < 7; ++i) kp[i] = M.k[i];
+    kp[0] = M.scratch3;  // the torque itself is not kept
+    Launch<StageJob> L{};
+    L.njobs = 1;
+    L.job[0] = stage_job(ctx, g, M.m, nullptr, 1, 1, 0.0, kp, M.pow_H);
+    L.tile_start[0] = 0;
+    L.tile_start[1] = M.nerr;
+    {
+      Timer t(ctx, 4);
+      CK(launch_stage(L, MechParams{}, nullptr, ctx->st));
+    }
+    // the sum lands after the block sums
+    CK(launch_mxh2(M.m, M.pow_H, M.N, M.pow_part, M.pow_part + power_blocks(M.N), ctx->st));
+  }
+  ctx->k1_valid = false;
+  double S[2] = {0.0, 0.0};
+  for (int g = 0; g < 2; ++g)
+    CK(cudaMemcpyAsync(&S[g], ctx->mag[g].pow_part + power_blocks(ctx->mag[g].N), sizeof(double),
+                       cudaMemcpyDeviceToHost, ctx->st));
+  CKS(join_mech(ctx));
+  CK(cudaMemcpyAsync(&ctx->host_mech, ctx->mech, sizeof(MechState), cudaMemcpyDeviceToHost, ctx->st));
+  CKS(check_device_error(ctx));
+  const MechState& H = ctx->host_mech;
+  const double v = ctx->move ? H.v : 0.0;
+  const double Fe = H.F_slider[0] * ctx->e[0] + H.F_slider[1] * ctx->e[1] + H.F_slider[2] * ctx->e[2];
+  if (P_in) *P_in = -Fe * v;
+  for (int g = 0; g < 2; ++g) {
+    const Magnet& M = ctx->mag[g];
+    const double V = M.d[0] * M.d[1] * M.d[2];
+    const double a = M.alpha;
+    if (P_diss) P_diss[g] = kMu0 * kGammaLL * a * kMu0 * V * M.Ms / (1.0 + a * a) * S[g];
+  }
+  if (P_visc) *P_visc = ctx->move ? ctx->gamma_v * ctx->mass * v * v : 0.0;
   return MM_OK;
 }
 

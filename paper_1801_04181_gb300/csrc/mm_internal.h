@@ -275,6 +275,11 @@ cudaError_t launch_place(const float* box, const int bdim[3], const int box_lo[3
                          cudaStream_t st);
 cudaError_t launch_zadj(const ZAdjJob& J, cudaStream_t st);
 cudaError_t launch_scale(const float* in, float* out, size_t n, float s, cudaStream_t st);
+
+// power bookkeeping (power.cu): *out = sum_i |m_i x H_i|^2 over N cells;
+// partial holds power_blocks(N) doubles
+int power_blocks(size_t N);
+cudaError_t launch_mxh2(const float* m, const float* H, size_t N, double* partial, double* out, cudaStream_t st);
 int zmix_tiles(int kyq, int planes);
 int zpass_tile(int Qz);                 // y positions per z-pass CTA for a z grid
 int zpass_tiles(int Qy, int ztile);

@@ -243,3 +243,29 @@ def test_bad_arguments_are_rejected():
     with pytest.raises(MMError):
         mm.compute_fields()                             # nothing else set
     mm.close()
+
+
+def test_power_bookkeeping_matches_oracle():
+    """P_in = -F . v_s, the Gilbert dissipation of each magnet and the drive's
+    viscous loss at a state with the slider moving (Sec. III, after Eq. (EQForce))."""
+    from oracle.dynamics import power_balance
+    from tests.pair_setup import oracle_system
+
+    fp, m0, m1 = workloads.film_pair_stick_slip(n=(44, 22, 2), gap=5, seed=6)
+    fp.u0 = (0.35, 0.0, 0.0)
+    fp.H_ext = (2e4, 0.0, -1e4)
+    mm = gpu_pair(fp, m0, m1)
+    x, v = 3e-10, 4.0
+    mm.set_slider_state(x, v, 0.0)
+    P = mm.power()
+    ref = power_balance(oracle_system(fp), m0, m1, x, v)
+    for g in (0, 1):
+        assert abs(P["P_diss"][g] - ref["P_diss"][g]) <= TOL * ref["P_diss"][g]
+    box = stray_interaction(fp.mat_base.Ms * m0, fp.mat_slider.Ms * m1, fp.cell, fp.offsets[0], fp.offsets[1],
+                            oracle_system(fp).displacement(x), True, return_box=True)
+    scale = force_scale(box["hess_n"], fp.mat_slider.Ms * m1, fp.cell)
+    assert abs(P["P_in"] - ref["P_in"]) <= TOL * scale * v
+    assert abs(P["P_visc"] - ref["P_visc"]) <= 1e-12 * ref["P_visc"]
+    # the call leaves the state alone: stepping still works and repeats it
+    mm.step(1, 5e-14)
+    mm.close()
