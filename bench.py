@@ -55,7 +55,7 @@ def parse():
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--lanes", type=int, default=BATCH_LANES, help="streams of the batch256 workload")
     p.add_argument("--workload", default="stick_slip",
-                   choices=sorted(WORKLOADS) + ["plain64_sweep", "cubes64_gradients", "batch256"],
+                   choices=sorted(WORKLOADS) + ["plain64_sweep", "cubes64_gradients", "batch256", "divcurl_sweep"],
                    help="stick_slip (the headline workload), a thick-source workload, or the "
                         "plain 64x64x1 film pair swept over 16 sub-cell offsets (stray field only)")
     return p.parse_args()
@@ -509,6 +509,51 @@ def run_sweep(args):
     mm.close()
 
 
+def run_divcurl(args):
+    """Sec. IV.A: a frozen random base film 64x64x4 (4 nm), the slider film
+    above it (gap 1) moved along x by 16 partial offsets in [0, 1) cell; per
+    offset the base's stray field inside the slider (potential, prefilter,
+    gather) and its divergence and curl means D(x), C(x) by central
+    differences.  Reported: D(x)/D(0) - 1 and C(x)/C(0) - 1, the paper's
+    measure of what the interpolation does to div and curl; timed: offsets
+    per second (field + diagnostics, one synchronisation per offset)."""
+    import torch
+    import workloads
+    from tests.pair_setup import gpu_pair
+
+    fp, m0, m1 = workloads.film_pair_plain((64, 64, 4), 1, args.seed)
+    mm = gpu_pair(fp, m0, m1, mech=False)
+    offs = [k / 16.0 for k in range(16)]
+
+    def sweep():
+        out = []
+        for u in offs:
+            mm.set_displacement((u * fp.cell[0], 0.0, 0.0))
+            H = mm.compute_stray_field(0)
+            out.append(mm.div_curl(H, fp.cell))
+        return out
+
+    for _ in range(max(args.warmup, 3)):
+        sweep()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        dc = sweep()
+    torch.cuda.synchronize()
+    s = time.perf_counter() - t0
+    D0, C0 = dc[0]
+    line = {"metric": "div/curl diagnostic offsets/s (frozen random base 64x64x4, 16 partial moves)",
+            "value": len(offs) * args.steps / s, "unit": "offsets/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": 1e3 * s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "random-unit film pair 64x64x4 (4 nm), gap 1, slider moved by x in [0, 1)",
+                       "step": "one sweep: 16 offsets x (stray field of the base in the slider + D, C)"},
+            "div_curl": {"x": offs, "D0": D0, "C0": C0,
+                         "D_rel": [d / D0 - 1.0 for d, _ in dc], "C_rel": [c / C0 - 1.0 for _, c in dc]}}
+    print(json.dumps(line))
+    mm.close()
+
+
 def run_gradients(args):
     """Two 64^3 vortex cubes (2 nm, gap 3 along x, slider at 1.7 cells): one
     step is mm_backward_energy of the slider's energy in the base's field --
@@ -707,6 +752,8 @@ def main():
         run_gradients(args)
     elif args.workload == "batch256":
         run_batch(args)
+    elif args.workload == "divcurl_sweep":
+        run_divcurl(args)
     else:
         run_gpu(args)
 

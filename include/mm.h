@@ -229,6 +229,19 @@ mm_status mm_assign_lanes(const double* cost, int npairs, int nlanes, int* lane_
  */
 mm_status mm_get_power(mm_ctx* ctx, double* P_in, double P_diss[2], double* P_visc);
 
+/*
+ * Divergence and curl diagnostics of a field (Sec. IV.A): for H_dev (3 N
+ * floats, [3][nz][ny][nx], A/m, device) on cells dx x dy x dz,
+ *   D = (1/N') sum |div H|,  C = (1/N') sum ||curl H||   (A/m^2)
+ * with two-point central differences (H(i+1) - H(i-1)) / (2 d) over the N'
+ * cells that have both neighbours along every axis of at least three cells;
+ * an axis of fewer than three cells contributes no derivative.  FP32
+ * differences, FP64 sums in a fixed order.  Runs on the context's stream with
+ * its scratch; synchronises.
+ */
+mm_status mm_field_div_curl(mm_ctx* ctx, const float* H_dev, int nx, int ny, int nz, double dx, double dy,
+                            double dz, double* D, double* C);
+
 /* Accepted / rejected step counters since creation. */
 mm_status mm_get_step_stats(mm_ctx* ctx, long long* accepted, long long* rejected);
 

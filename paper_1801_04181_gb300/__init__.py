@@ -198,6 +198,17 @@ class MovingMagnets:
         self._c(self.lib.mm_get_power(self.ctx, C.byref(pin), pd, C.byref(pv)))
         return dict(P_in=pin.value, P_diss=[pd[0], pd[1]], P_visc=pv.value)
 
+    def div_curl(self, H, cell):
+        """mm_field_div_curl: (D, C), the mean |div H| and ||curl H|| (A/m^2) of a
+        (3, nz, ny, nx) float32 CUDA field on cells `cell` (m)."""
+        _need_cuda_f32(H)
+        _, nz, ny, nx = H.shape
+        D, Cc = C.c_double(), C.c_double()
+        self._in()
+        self._c(self.lib.mm_field_div_curl(self.ctx, _ptr(H), nx, ny, nz, *[float(c) for c in cell],
+                                           C.byref(D), C.byref(Cc)))
+        return D.value, Cc.value
+
     def step_stats(self):
         a, r = C.c_longlong(), C.c_longlong()
         self._c(self.lib.mm_get_step_stats(self.ctx, C.byref(a), C.byref(r)))

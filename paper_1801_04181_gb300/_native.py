@@ -58,6 +58,8 @@ SIGNATURES = [
                                 C.POINTER(C.c_double), C.POINTER(C.c_int)]),
     ("mm_assign_lanes", C.c_int, [C.POINTER(C.c_double), C.c_int, C.c_int, C.POINTER(C.c_int)]),
     ("mm_get_power", C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    ("mm_field_div_curl", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
+                                    C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     ("mm_get_step_stats", C.c_int, [C.c_void_p, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
     ("mm_get_state", C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_size_t)]),
     ("mm_set_state", C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),

@@ -173,6 +173,9 @@ struct mm_ctx {
   size_t gen_q_bytes = 0;
   double* W_dev = nullptr;
   size_t W_bytes = 0;
+  // div / curl diagnostics: block sums, then the two totals
+  double* dc_buf = nullptr;
+  size_t dc_bytes = 0;
   // timing
   bool timing = false;
   std::vector<TimedLaunch> pending;
@@ -1333,7 +1336,7 @@ void mm_destroy(mm_ctx* ctx) {
   for (auto& kv : ctx->ffts) {
     cudaFree(kv.second.tw_f); cudaFree(kv.second.tw_d); cudaFree(kv.second.pos); cudaFree(kv.second.freq);
   }
-  cudaFree(ctx->gen_work); cudaFree(ctx->gen_q); cudaFree(ctx->W_dev);
+  cudaFree(ctx->gen_work); cudaFree(ctx->gen_q); cudaFree(ctx->W_dev); cudaFree(ctx->dc_buf);
   cudaFree(ctx->mech); cudaFree(ctx->err_flag); cudaFree(ctx->tickets);
   for (auto& p : ctx->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
@@ -1759,6 +1762,26 @@ mm_status mm_get_power(mm_ctx* ctx, double* P_in, double P_diss[2], double* P_vi
     if (P_diss) P_diss[g] = kMu0 * kGammaLL * a * kMu0 * V * M.Ms / (1.0 + a * a) * S[g];
   }
   if (P_visc) *P_visc = ctx->move ? ctx->gamma_v * ctx->mass * v * v : 0.0;
+  return MM_OK;
+}
+
+mm_status mm_field_div_curl(mm_ctx* ctx, const float* H_dev, int nx, int ny, int nz, double dx, double dy,
+                            double dz, double* D, double* C) {
+  if (!ctx) return MM_EINVAL;
+  if (!H_dev || nx < 1 || ny < 1 || nz < 1 || !(dx > 0) || !(dy > 0) || !(dz > 0) ||
+      (long long)nx * ny * nz > (1ll << 30))
+    return fail(ctx, MM_EINVAL, "mm_field_div_curl: bad argument");
+  const size_t cells = divcurl_cells(nx, ny, nz);
+  const int nb = divcurl_blocks(nx, ny, nz);
+  CKS(ensure_buf(ctx, &ctx->dc_buf, &ctx->dc_bytes, sizeof(double) * (2 * (size_t)nb + 2)));
+  double out[2] = {0.0, 0.0};
+  if (nb > 0) {
+    CK(launch_divcurl(H_dev, nx, ny, nz, dx, dy, dz, ctx->dc_buf, ctx->dc_buf + 2 * nb, ctx->st));
+    CK(cudaMemcpyAsync(out, ctx->dc_buf + 2 * nb, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+  }
+  if (D) *D = cells ? out[0] / (double)cells : 0.0;
+  if (C) *C = cells ? out[1] / (double)cells : 0.0;
   return MM_OK;
 }
 

@@ -280,6 +280,12 @@ cudaError_t launch_scale(const float* in, float* out, size_t n, float s, cudaStr
 // partial holds power_blocks(N) doubles
 int power_blocks(size_t N);
 cudaError_t launch_mxh2(const float* m, const float* H, size_t N, double* partial, double* out, cudaStream_t st);
+// div / curl means (power.cu): out[0] = sum |div H|, out[1] = sum ||curl H|| over
+// divcurl_cells interior cells; partial holds 2 divcurl_blocks doubles
+size_t divcurl_cells(int nx, int ny, int nz);
+int divcurl_blocks(int nx, int ny, int nz);
+cudaError_t launch_divcurl(const float* H, int nx, int ny, int nz, double dx, double dy, double dz,
+                           double* partial, double* out, cudaStream_t st);
 int zmix_tiles(int kyq, int planes);
 int zpass_tile(int Qz);                 // y positions per z-pass CTA for a z grid
 int zpass_tiles(int Qy, int ztile);

@@ -269,3 +269,39 @@ def test_power_bookkeeping_matches_oracle():
     # the call leaves the state alone: stepping still works and repeats it
     mm.step(1, 5e-14)
     mm.close()
+
+
+def _dc_bound(H_ref, cell, rel):
+    """Bound on |D - D_ref| (and |C - C_ref|) from a field error of `rel` times the
+    rms field: each central difference moves by at most twice the field error
+    over 2 d_a, and a divergence or curl component sums two or three of them."""
+    rms = float(np.sqrt(np.mean(np.sum(np.asarray(H_ref, float) ** 2, axis=0))))
+    return rel * 3.0 * rms * sum(1.0 / d for d in cell)
+
+
+def test_div_curl_of_interpolated_stray_field_matches_oracle():
+    """Sec. IV.A: a frozen random base film (four layers, so z derivatives
+    exist), its stray field sampled inside the slider at partial moves x; the
+    CUDA diagnostic on the CUDA field against the oracle's diagnostic on the
+    same FP32 field and on the oracle's own FP64 field."""
+    from oracle.diagnostics import div_curl_means
+
+    fp, m0, m1 = workloads.film_pair_plain((26, 21, 4), 1, 5)
+    fp.n_slider = (23, 19, 4)
+    M0, M1 = fp.mat_base.Ms * m0, fp.mat_slider.Ms * workloads.random_unit(fp.n_slider, 6)
+    for u in (0.0, 0.3125, 0.75):
+        fp.u0 = (u, 0.0, 0.0)
+        mm = gpu_pair(fp, m0, M1 / fp.mat_slider.Ms, mech=False)
+        H = mm.compute_stray_field(0)
+        D, C = mm.div_curl(H, fp.cell)
+        Hn = H.double().cpu().numpy()
+        Dg, Cg = div_curl_means(Hn, fp.cell)
+        b32 = _dc_bound(Hn, fp.cell, 1e-6)
+        assert abs(D - Dg) <= b32 and abs(C - Cg) <= b32
+        ref = stray_interaction(M0, M1, fp.cell, fp.offsets[0], fp.offsets[1], fp.u0, True)
+        Dr, Cr = div_curl_means(ref["H"], fp.cell)
+        assert rel_l2(Hn, ref["H"]) < TOL
+        b = _dc_bound(ref["H"], fp.cell, TOL)
+        assert abs(D - Dr) <= b and abs(C - Cr) <= b
+        assert D > 0 and C > 0
+        mm.close()
