@@ -275,17 +275,10 @@ __device__ __forceinline__ void fft_stage_dif_inv(C* buf, int ldl, int nlines, i
 // Stage orders of fft_smem.
 enum FftMode { kFwdDif = 0, kInvDit = 1, kInvDif = 2 };
 
-// Radix sets: bit i stands for radix kRadixList[i].  A kernel instantiated for
-// a set carries the stage code of those radices only; compact code for the
+// Radix sets (radix_bit, kRadixSetA in mm_internal.h): a kernel instantiated
+// for a set carries the stage code of those radices only; compact code for the
 // radices a plan actually uses measured several per cent faster than the
 // kernel with every radix compiled in.
-__host__ __device__ constexpr unsigned radix_bit(int R) {
-  return R == 2 ? 1u : R == 3 ? 2u : R == 4 ? 4u : R == 5 ? 8u : R == 6 ? 16u : R == 8 ? 32u
-       : R == 9 ? 64u : R == 10 ? 128u : R == 12 ? 256u : R == 15 ? 512u : R == 16 ? 1024u : 0u;
-}
-constexpr unsigned kAllRadices = 2047u;
-// {4, 9, 15, 16}: every length 4^a 9^b 15^c 16^d, among them 540 = 4 15 9 and 2160 = 9 16 15
-constexpr unsigned kRadixSetA = 4u | 64u | 512u | 1024u;
 inline unsigned plan_radix_set(const FftPlanDev& P) {
   unsigned s = 0;
   for (int i = 0; i < P.nstages; ++i) s |= radix_bit(P.radix[i]);

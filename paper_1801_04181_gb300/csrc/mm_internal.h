@@ -12,6 +12,16 @@ constexpr int kMaxNz = 4;          // thin-film path: z handled by direct plane 
 constexpr int kMaxOut = kMaxNz + 5; // coefficient planes: nz + 3 + 2 guard
 constexpr int kRowsPerCta = 8;     // real rows per CTA in the x passes (4 complex lines)
 
+// FFT radix sets: one bit per radix the shared-memory FFT implements
+__host__ __device__ constexpr unsigned radix_bit(int R) {
+  return R == 2 ? 1u : R == 3 ? 2u : R == 4 ? 4u : R == 5 ? 8u : R == 6 ? 16u : R == 8 ? 32u
+       : R == 9 ? 64u : R == 10 ? 128u : R == 12 ? 256u : R == 15 ? 512u : R == 16 ? 1024u : 0u;
+}
+constexpr unsigned kAllRadices = 2047u;
+// the set the FFT pass kernels are also built for: {4, 9, 15, 16} (every length
+// 4^a 9^b 15^c 16^d, among them 540 = 4 9 15 and 2160 = 16 9 15)
+constexpr unsigned kRadixSetA = 4u | 64u | 512u | 1024u;
+
 struct FftPlanDev {
   int L;
   int nstages;
