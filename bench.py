@@ -588,6 +588,21 @@ def run_gradients(args):
     mm.close()
 
 
+def batch_cost(fp):
+    """Cost model for spreading pairs: grid area x (source layers + box layers)."""
+    return fp.n_base[0] * fp.n_base[1] * (fp.n_base[2] + 4)
+
+
+def batch_shard(specs, world, rank, lanes):
+    """This rank's pairs (longest processing time first over the ranks) and
+    their lane streams (the same rule over the rank's lanes)."""
+    from paper_1801_04181_gb300 import assign_lanes
+
+    cost = [batch_cost(fp) for fp in specs]
+    mine = [i for i, r in enumerate(assign_lanes(cost, world)) if r == rank]
+    return mine, assign_lanes([cost[i] for i in mine], lanes)
+
+
 def run_batch(args):
     """256 independent spring-pulled PMA film pairs of uneven sizes (nx in
     64..512, ny in 64..256, nz in 1..4, slider displaced by U[0, 50) cells,
@@ -598,7 +613,7 @@ def run_batch(args):
     the same way (strong scaling: the batch is fixed)."""
     import torch
     import workloads
-    from paper_1801_04181_gb300 import assign_lanes, step_batch
+    from paper_1801_04181_gb300 import step_batch
     from tests.pair_setup import gpu_pair
 
     rank, world, local = dist_info()
@@ -611,10 +626,7 @@ def run_batch(args):
         import multiprocessing as mp
         pool = mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1)))
     specs = workloads.batch_pairs(256, seed=args.seed)
-    # cost model for the spread: grid area x (source layers + box layers)
-    cost = [fp.n_base[0] * fp.n_base[1] * (fp.n_base[2] + 4) for fp in specs]
-    mine = [i for i, r in enumerate(assign_lanes(cost, world)) if r == rank]
-    lanes = assign_lanes([cost[i] for i in mine], args.lanes)
+    mine, lanes = batch_shard(specs, world, rank, args.lanes)
     streams = [torch.cuda.Stream() for _ in range(args.lanes)]
     t_setup = time.perf_counter()
     batch = []

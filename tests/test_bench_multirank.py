@@ -55,3 +55,48 @@ def test_single_rank_needs_no_process_group():
 
     assert bench.max_over_ranks(3.5, 1, "cpu") == 3.5
     assert bench.whole_job_rate(10, 4, 2.0, 1) == 20.0
+
+
+def _batch_worker(rank, world, port, out):
+    import torch.distributed as dist
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    import workloads
+
+    specs = workloads.batch_pairs(256, seed=0)
+    mine, lanes = bench.batch_shard(specs, world, rank, 16)
+    got = [None] * world
+    dist.all_gather_object(got, (mine, lanes))
+    out[rank] = got
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_rank_batch_shard_covers_every_pair_once():
+    """Under torchrun the 256-pair batch is spread over the ranks (no data-path
+    collective): every pair on exactly one rank, the ranks' loads within one
+    pair's cost of each other, every lane index in range."""
+    from paper_1801_04181_gb300.build import build
+
+    build()
+    world = 2
+    port = _free_port()
+    with tmp.Manager() as mgr:
+        out = mgr.dict()
+        tmp.spawn(_batch_worker, args=(world, port, out), nprocs=world, join=True)
+        res = dict(out)
+    assert res[0] == res[1]
+    shards = res[0]
+    import bench
+    import workloads
+
+    specs = workloads.batch_pairs(256, seed=0)
+    allp = sorted(i for mine, _ in shards for i in mine)
+    assert allp == list(range(256))
+    loads = [sum(bench.batch_cost(specs[i]) for i in mine) for mine, _ in shards]
+    assert abs(loads[0] - loads[1]) <= max(bench.batch_cost(fp) for fp in specs)
+    for mine, lanes in shards:
+        assert len(lanes) == len(mine) and all(0 <= l < 16 for l in lanes)
