@@ -244,92 +244,118 @@ static cudaError_t prep(const void* f, size_t smem) {
 }
 
 // ------------------------------------------------------------------ direct z sum
-// Thread -> (kx, output plane, frequency pair ky, Qy - ky): the thin-film plane
-// mixing of Sec. III.A with the planes streamed from memory instead of held
-// in shared memory.  Consecutive threads take consecutive ky, so every load
-// and store is a coalesced run; the CTAs of one kx run together, so the
-// input planes they all read come from L2.  (Staging a chunk's inputs in
-// shared memory and looping over the outputs in the thread, or unrolling the
-// layer loop, measured 1.3-2.7x slower.)
+// The thin-film plane mixing of Sec. III.A for sources of up to kMaxNzDirect
+// layers.  CTA -> (kx, a chunk of kZMixChunk frequency pairs ky, Qy - ky): the
+// input planes of the chunk are staged in shared memory once, then each warp
+// takes one output plane at a time with one frequency pair per lane, so the
+// kernel-spectrum loads and the output stores are coalesced runs and the
+// inputs are read from shared memory instead of again from L2 for every
+// output plane.  (Staging inputs and looping over all outputs inside one
+// thread measured 1.3-2.7x slower than streaming; this layout keeps a warp
+// per output plane.)
 constexpr int kZMixThreads = 256;
+constexpr int kZMixChunk = 32;  // frequency pairs per CTA, one per lane
 
 __device__ __forceinline__ float2 zm_kmul(float v, bool imag, float2 m) {
   return imag ? make_float2(-v * m.y, v * m.x) : make_float2(v * m.x, v * m.y);
 }
 
 __global__ void __launch_bounds__(kZMixThreads) k_zmix3(const Launch<ZMixJob> Lc) {
+  extern __shared__ float2 zs[];  // [2][3 nz][kZMixChunk]: inputs at ky, then at Qy - ky
   const int j = find_job(Lc.tile_start, Lc.njobs, blockIdx.x);
   const ZMixJob& J = Lc.job[j];
   const int tile = blockIdx.x - Lc.tile_start[j];
-  const int nch = (J.kyq + kZMixThreads - 1) / kZMixThreads;
-  const int planes = J.nH + J.n_out;
-  const int kx = tile / (planes * nch);
-  const int rem = tile - kx * planes * nch;
-  const int o = rem / nch;
-  const int k = (rem - o * nch) * kZMixThreads + threadIdx.x;
-  if (k >= J.kyq) return;
-  const int Qy = J.Qy, nz = J.nz;
+  const int nch = (J.kyq + kZMixChunk - 1) / kZMixChunk;
+  const int kx = tile / nch;
+  const int k0 = (tile - kx * nch) * kZMixChunk;
+  const int nk = min(kZMixChunk, J.kyq - k0);
+  const int Qy = J.Qy, nz = J.nz, P3 = 3 * nz;
+  const size_t pstride = (size_t)J.kxh * Qy;  // one input / output plane
+  const float2* inb = J.in + (size_t)kx * Qy;
+  for (int i = threadIdx.x; i < P3 * kZMixChunk; i += blockDim.x) {
+    const int p = i / kZMixChunk, l = i - p * kZMixChunk;
+    if (l < nk) {
+      const int k = k0 + l;
+      const bool two = k != 0 && 2 * k != Qy;
+      const float2* row = inb + (size_t)p * pstride;
+      zs[i] = row[k];
+      zs[P3 * kZMixChunk + i] = row[two ? Qy - k : k];
+    }
+  }
+  __syncthreads();
+  const int l = threadIdx.x % kZMixChunk;
+  if (l >= nk) return;
+  const int k = k0 + l;
   const bool two = k != 0 && 2 * k != Qy;
-  const size_t pstride = (size_t)J.kxh * Qy;     // one input / output plane
   const size_t kstride = (size_t)J.kxh * J.kyq;  // one stored kernel plane
   const size_t koff = (size_t)kx * J.kyq + k;
-  const float2* in0 = J.in + (size_t)kx * Qy + k;
-  const float2* in1 = J.in + (size_t)kx * Qy + (two ? Qy - k : k);
-  float2 acc0 = make_float2(0.f, 0.f), acc1 = acc0;
-  if (o < J.nH) {
-    // H_a(iz) = sum_jz sum_b Ns_ab(iz - jz) m_b(jz): xz, yz odd in dz and
-    // imaginary, xy and yz odd in y
-    const int a = o / nz, iz = o - a * nz;
-    for (int jz = 0; jz < nz; ++jz) {
-      const int adz = iz >= jz ? iz - jz : jz - iz;
-      const float sz = iz >= jz ? 1.f : -1.f;
+  const float2* s0 = zs + l;
+  const float2* s1 = zs + P3 * kZMixChunk + l;
+  const int planes = J.nH + J.n_out;
+  for (int o = threadIdx.x / kZMixChunk; o < planes; o += kZMixThreads / kZMixChunk) {
+    float2 acc0 = make_float2(0.f, 0.f), acc1 = acc0;
+    if (o < J.nH) {
+      // H_a(iz) = sum_jz sum_b Ns_ab(iz - jz) m_b(jz): xz, yz odd in dz and
+      // imaginary, xy and yz odd in y
+      const int a = o / nz, iz = o - a * nz;
+      for (int jz = 0; jz < nz; ++jz) {
+        const int adz = iz >= jz ? iz - jz : jz - iz;
+        const float sz = iz >= jz ? 1.f : -1.f;
 #pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        int comp;
-        bool imag = false;
-        float sgn = 1.f, sy = 1.f;
-        if (a == b) comp = a;
-        else if (a + b == 1) { comp = 3; sy = -1.f; }
-        else if (a + b == 2) { comp = 4; sgn = sz; imag = true; }
-        else { comp = 5; sgn = sz; sy = -1.f; imag = true; }
-        const float v = sgn * __ldg(J.Nq + (size_t)(comp * nz + adz) * kstride + koff);
-        const float2 m0 = in0[(size_t)(b * nz + jz) * pstride];
-        const float2 m1 = in1[(size_t)(b * nz + jz) * pstride];
-        const float2 p0 = zm_kmul(v, imag, m0), p1 = zm_kmul(sy * v, imag, m1);
-        acc0.x += p0.x; acc0.y += p0.y;
-        acc1.x += p1.x; acc1.y += p1.y;
+        for (int b = 0; b < 3; ++b) {
+          int comp;
+          bool imag = false;
+          float sgn = 1.f, sy = 1.f;
+          if (a == b) comp = a;
+          else if (a + b == 1) { comp = 3; sy = -1.f; }
+          else if (a + b == 2) { comp = 4; sgn = sz; imag = true; }
+          else { comp = 5; sgn = sz; sy = -1.f; imag = true; }
+          const float v = sgn * __ldg(J.Nq + (size_t)(comp * nz + adz) * kstride + koff);
+          const float2 m0 = s0[(b * nz + jz) * kZMixChunk];
+          const float2 m1 = s1[(b * nz + jz) * kZMixChunk];
+          const float2 p0 = zm_kmul(v, imag, m0), p1 = zm_kmul(sy * v, imag, m1);
+          acc0.x += p0.x; acc0.y += p0.y;
+          acc1.x += p1.x; acc1.y += p1.y;
+        }
       }
-    }
-    float2* dst = J.outH + (size_t)o * pstride + (size_t)kx * Qy;
-    dst[k] = acc0;
-    if (two) dst[Qy - k] = acc1;
-  } else {
-    // c(o) = sum_jz sum_c T_c(o, jz) m_c(jz); T_x, T_y imaginary, T_y odd in y
-    const int oc = o - J.nH;
-    for (int jz = 0; jz < nz; ++jz) {
+      float2* dst = J.outH + (size_t)o * pstride + (size_t)kx * Qy;
+      dst[k] = acc0;
+      if (two) dst[Qy - k] = acc1;
+    } else {
+      // c(o) = sum_jz sum_c T_c(o, jz) m_c(jz); T_x, T_y imaginary, T_y odd in y
+      const int oc = o - J.nH;
+      for (int jz = 0; jz < nz; ++jz) {
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const float v = __ldg(J.Tq + (size_t)((oc * nz + jz) * 3 + c) * kstride + koff);
-        const float2 m0 = in0[(size_t)(c * nz + jz) * pstride];
-        const float2 m1 = in1[(size_t)(c * nz + jz) * pstride];
-        const bool imag = c < 2;
-        const float2 p0 = zm_kmul(v, imag, m0), p1 = zm_kmul(c == 1 ? -v : v, imag, m1);
-        acc0.x += p0.x; acc0.y += p0.y;
-        acc1.x += p1.x; acc1.y += p1.y;
+        for (int c = 0; c < 3; ++c) {
+          const float v = __ldg(J.Tq + (size_t)((oc * nz + jz) * 3 + c) * kstride + koff);
+          const float2 m0 = s0[(c * nz + jz) * kZMixChunk];
+          const float2 m1 = s1[(c * nz + jz) * kZMixChunk];
+          const bool imag = c < 2;
+          const float2 p0 = zm_kmul(v, imag, m0), p1 = zm_kmul(c == 1 ? -v : v, imag, m1);
+          acc0.x += p0.x; acc0.y += p0.y;
+          acc1.x += p1.x; acc1.y += p1.y;
+        }
       }
+      float2* dst = J.outC + (size_t)oc * pstride + (size_t)kx * Qy;
+      dst[k] = acc0;
+      if (two) dst[Qy - k] = acc1;
     }
-    float2* dst = J.outC + (size_t)oc * pstride + (size_t)kx * Qy;
-    dst[k] = acc0;
-    if (two) dst[Qy - k] = acc1;
   }
 }
 
-int zmix_tiles(int kyq, int planes) { return planes * ((kyq + kZMixThreads - 1) / kZMixThreads); }
+// CTAs per kx (the output planes are covered inside each CTA)
+int zmix_tiles(int kyq, int planes) {
+  (void)planes;
+  return (kyq + kZMixChunk - 1) / kZMixChunk;
+}
 
 cudaError_t launch_zmix3(const Launch<ZMixJob>& L, cudaStream_t st) {
   const int grid = L.tile_start[L.njobs];
   if (grid == 0) return cudaSuccess;
-  k_zmix3<<<grid, kZMixThreads, 0, st>>>(L);
+  int nzmax = 1;
+  for (int i = 0; i < L.njobs; ++i) nzmax = max(nzmax, L.job[i].nz);
+  const size_t smem = sizeof(float2) * 2 * 3 * (size_t)nzmax * kZMixChunk;
+  k_zmix3<<<grid, kZMixThreads, smem, st>>>(L);
   return cudaGetLastError();
 }
 
