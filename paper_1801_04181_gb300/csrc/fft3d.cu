@@ -35,7 +35,7 @@ cudaError_t init_fft_constants_3d() { return upload_roots(); }
 
 // ------------------------------------------------------------------ y forward
 template <unsigned RSET>
-__global__ void __launch_bounds__(256, 2) k_yfwd3(const Launch<YFwdJob> Lc) {
+__global__ void __launch_bounds__(256, 3) k_yfwd3(const Launch<YFwdJob> Lc) {
   extern __shared__ float2 sm[];
   const int j = find_job(Lc.tile_start, Lc.njobs, blockIdx.x);
   const YFwdJob& J = Lc.job[j];
