@@ -56,3 +56,17 @@ def test_null_context_is_rejected_without_gpu(lib):
     assert L.mm_create(None, None) == _native.MM_EINVAL
     assert L.mm_set_displacement(None, None) == _native.MM_EINVAL
     assert L.mm_launch_count(None) == 0
+
+
+def test_new_entry_points_reject_null_context_without_gpu(lib):
+    """The batch, power and diagnostics calls validate their arguments before any CUDA work."""
+    from paper_1801_04181_gb300 import _native
+
+    L = _native.load()
+    d = (ctypes.c_double * 2)()
+    x = ctypes.c_double()
+    assert L.mm_get_power(None, ctypes.byref(x), d, ctypes.byref(x)) == _native.MM_EINVAL
+    assert L.mm_field_div_curl(None, None, 4, 4, 4, 1e-9, 1e-9, 1e-9, ctypes.byref(x),
+                               ctypes.byref(x)) == _native.MM_EINVAL
+    assert L.mm_step_batch(None, 1, 1, None, None, None) == _native.MM_EINVAL
+    assert L.mm_assign_lanes(None, 0, 1, None) == 0
