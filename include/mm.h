@@ -44,7 +44,7 @@ typedef enum {
   MM_ERANGE = -4,   /* displacement left the planned potential box */
   MM_ETIMEOUT = -5, /* reserved */
   MM_ESTATE = -6,   /* state buffer of the wrong size or version */
-  MM_ENOTSUP = -7,  /* geometry outside what this build supports */
+  MM_ENOTSUP = -7,  /* geometry or option the library does not support */
   MM_ETOOBIG = -8   /* larger than the fixed scratch of mm_spline_field_noalloc */
 } mm_status;
 
