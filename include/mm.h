@@ -214,6 +214,17 @@ mm_status mm_step_batch(mm_ctx* const* ctxs, int npairs, int nsteps, double* t_o
 mm_status mm_assign_lanes(const double* cost, int npairs, int nlanes, int* lane_out);
 
 /*
+ * Host-only query of the shared-memory FFT planner: the radix of each stage
+ * (first stage first; at most 8) that transforms of length L use.  Fewest
+ * stages of radices up to 16; among their orderings, the near-fewest modelled
+ * shared-memory bank conflicts, then the radix set {4, 9, 15, 16} the pass
+ * kernels are also compiled for, then the largest last and first radix.
+ * MM_EINVAL unless L = 2^a 3^b 5^c >= 1; MM_ENOTSUP for plans with too many
+ * stages.  Needs no GPU.
+ */
+mm_status mm_fft_plan(int L, int radices[8], int* nstages);
+
+/*
  * Power bookkeeping at the current state (Sec. III, after Eq. (EQForce)), W:
  *   P_in      = -F_m^s . v_s, the power the moving slider pumps into the
  *               magnets (F_m^s the force of the base on the slider, v_s = v e

@@ -12,7 +12,7 @@ import torch
 from . import _native
 from ._native import MMError, mm_options
 
-__all__ = ["MovingMagnets", "MMError", "assign_lanes", "eval_kernel_fp64", "load_library", "step_batch"]
+__all__ = ["MovingMagnets", "MMError", "assign_lanes", "eval_kernel_fp64", "fft_plan", "load_library", "step_batch"]
 
 
 def load_library():
@@ -268,6 +268,17 @@ def step_batch(pairs, nsteps, dts):
         msg = lib.mm_last_error(pairs[i].ctx).decode() if 0 <= i < n else ""
         raise MMError(s, "pair %d: %s" % (i, msg))
     return list(t), list(d)
+
+
+def fft_plan(L):
+    """mm_fft_plan: the radices (first stage first) the FFT passes use for length L."""
+    lib = _native.load()
+    r = (C.c_int * 8)()
+    n = C.c_int()
+    s = lib.mm_fft_plan(int(L), r, C.byref(n))
+    if s != 0:
+        raise MMError(s, "mm_fft_plan")
+    return [r[i] for i in range(n.value)]
 
 
 def assign_lanes(costs, nlanes):

@@ -1889,6 +1889,19 @@ mm_status mm_step_batch(mm_ctx* const* ctxs, int npairs, int nsteps, double* t_o
   return MM_OK;
 }
 
+mm_status mm_fft_plan(int L, int radices[8], int* nstages) {
+  if (L < 1 || !radices || !nstages) return MM_EINVAL;
+  int r = L;
+  for (int p : {2, 3, 5})
+    while (r % p == 0) r /= p;
+  if (r != 1) return MM_EINVAL;
+  const std::vector<int> plan = plan_radices(L);
+  if ((int)plan.size() > kMaxStages || plan.size() > 8) return MM_ENOTSUP;
+  *nstages = (int)plan.size();
+  for (size_t i = 0; i < plan.size(); ++i) radices[i] = plan[i];
+  return MM_OK;
+}
+
 mm_status mm_assign_lanes(const double* cost, int npairs, int nlanes, int* lane_out) {
   if (npairs < 0 || nlanes < 1 || (npairs > 0 && (!cost || !lane_out))) return MM_EINVAL;
   for (int i = 0; i < npairs; ++i)

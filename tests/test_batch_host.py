@@ -76,3 +76,4 @@ def test_step_batch_rejects_bad_arguments_without_gpu():
     ctxs = (C.c_void_p * 2)(None, None)
     assert L.mm_step_batch(ctxs, 2, 3, None, dt, C.byref(bad)) == _native.MM_EINVAL and bad.value == 0
     assert L.mm_step_batch(ctxs, -1, 3, None, dt, None) == _native.MM_EINVAL
+
