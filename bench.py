@@ -551,6 +551,11 @@ def run_divcurl(args):
     mm.set_displacement((fp.cell[0], 0.0, 0.0))
     H1 = mm.compute_stray_field(0)
     lin = [mm.div_curl(((1.0 - u) * H0 + u * H1).contiguous(), fp.cell) for u in offs]
+    # the four-point difference variant of the gradient, judged against its own x = 0
+    fd4 = []
+    for u in offs:
+        mm.set_displacement((u * fp.cell[0], 0.0, 0.0))
+        fd4.append(mm.div_curl(mm.compute_stray_field_fd4(0), fp.cell))
     line = {"metric": "div/curl diagnostic offsets/s (frozen random base 64x64x4, 16 partial moves)",
             "value": len(offs) * args.steps / s, "unit": "offsets/s", "n_gpus": 1, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": 1e3 * s / args.steps, "higher_is_better": True,
@@ -560,7 +565,10 @@ def run_divcurl(args):
             "div_curl": {"x": offs, "D0": D0, "C0": C0,
                          "D_rel": [d / D0 - 1.0 for d, _ in dc], "C_rel": [c / C0 - 1.0 for _, c in dc],
                          "linear_D_rel": [d / D0 - 1.0 for d, _ in lin],
-                         "linear_C_rel": [c / C0 - 1.0 for _, c in lin]}}
+                         "linear_C_rel": [c / C0 - 1.0 for _, c in lin],
+                         "fd4_D0": fd4[0][0], "fd4_C0": fd4[0][1],
+                         "fd4_D_rel": [d / fd4[0][0] - 1.0 for d, _ in fd4],
+                         "fd4_C_rel": [c / fd4[0][1] - 1.0 for _, c in fd4]}}
     print(json.dumps(line))
     mm.close()
 

@@ -241,6 +241,17 @@ mm_status mm_fft_plan(int L, int radices[8], int* nstages);
 mm_status mm_get_power(mm_ctx* ctx, double* P_in, double P_diss[2], double* P_visc);
 
 /*
+ * Comparison variant (Sec. III.A mentions a four-point central difference for
+ * the gradient): the stray field of `src` at the other magnet's displaced cell
+ * centres as H_a = -(-phi(+2) + 8 phi(+1) - 8 phi(-1) + phi(-2)) / (12 d_a),
+ * phi the same B-spline interpolant of the potential evaluated at the centres
+ * one and two cells away along each axis, instead of its analytic gradient.
+ * H_dev: 3 N_target floats (A/m).  Needs a margin of at least 2 (MM_ENOTSUP
+ * otherwise).  No force or energy.
+ */
+mm_status mm_compute_stray_field_fd4(mm_ctx* ctx, int src, float* H_dev);
+
+/*
  * Divergence and curl diagnostics of a field (Sec. IV.A): for H_dev (3 N
  * floats, [3][nz][ny][nx], A/m, device) on cells dx x dy x dz,
  *   D = (1/N') sum |div H|,  C = (1/N') sum ||curl H||   (A/m^2)

@@ -151,6 +151,13 @@ class MovingMagnets:
         self._c(self.lib.mm_compute_stray_field(self.ctx, src, _ptr(H)))
         return self._out(H)
 
+    def compute_stray_field_fd4(self, src):
+        """mm_compute_stray_field_fd4: the four-point difference variant of the stray field."""
+        H = torch.empty(self.shapes[1 - src], dtype=torch.float32, device="cuda")
+        self._in()
+        self._c(self.lib.mm_compute_stray_field_fd4(self.ctx, src, _ptr(H)))
+        return self._out(H)
+
     def compute_demag(self, mag):
         H = torch.empty(self.shapes[mag], dtype=torch.float32, device="cuda")
         self._in()

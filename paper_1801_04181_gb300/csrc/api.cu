@@ -176,6 +176,11 @@ struct mm_ctx {
   // div / curl diagnostics: block sums, then the two totals
   double* dc_buf = nullptr;
   size_t dc_bytes = 0;
+  // four-point difference variant: box coefficients, extended values
+  float* fd4_C = nullptr;
+  size_t fd4_C_bytes = 0;
+  float* fd4_V = nullptr;
+  size_t fd4_V_bytes = 0;
   // timing
   bool timing = false;
   std::vector<TimedLaunch> pending;
@@ -1359,6 +1364,7 @@ void mm_destroy(mm_ctx* ctx) {
     cudaFree(kv.second.tw_f); cudaFree(kv.second.tw_d); cudaFree(kv.second.pos); cudaFree(kv.second.freq);
   }
   cudaFree(ctx->gen_work); cudaFree(ctx->gen_q); cudaFree(ctx->W_dev); cudaFree(ctx->dc_buf);
+  cudaFree(ctx->fd4_C); cudaFree(ctx->fd4_V);
   cudaFree(ctx->mech); cudaFree(ctx->err_flag); cudaFree(ctx->tickets);
   for (auto& p : ctx->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
@@ -1784,6 +1790,29 @@ mm_status mm_get_power(mm_ctx* ctx, double* P_in, double P_diss[2], double* P_vi
     if (P_diss) P_diss[g] = kMu0 * kGammaLL * a * kMu0 * V * M.Ms / (1.0 + a * a) * S[g];
   }
   if (P_visc) *P_visc = ctx->move ? ctx->gamma_v * ctx->mass * v * v : 0.0;
+  return MM_OK;
+}
+
+mm_status mm_compute_stray_field_fd4(mm_ctx* ctx, int src, float* H_dev) {
+  if (!ctx || bad_mag(src) || !H_dev) return ctx ? fail(ctx, MM_EINVAL, "mm_compute_stray_field_fd4") : MM_EINVAL;
+  if (ctx->opt.margin < 2) return fail(ctx, MM_ENOTSUP, "mm_compute_stray_field_fd4: needs a margin of 2 or more");
+  int dims[3];
+  long long lo[3];
+  CKS(mm_compute_potential(ctx, src, 1, nullptr, 0, dims, lo));
+  const size_t nb = (size_t)dims[0] * dims[1] * dims[2];
+  CKS(ensure_buf(ctx, &ctx->fd4_C, &ctx->fd4_C_bytes, sizeof(float) * nb));
+  CKS(mm_compute_potential(ctx, src, 1, ctx->fd4_C, nb, dims, lo));
+  const Magnet& T = ctx->mag[1 - src];
+  const int nt[3] = {T.nx, T.ny, T.nz};
+  CKS(ensure_buf(ctx, &ctx->fd4_V, &ctx->fd4_V_bytes,
+                 sizeof(float) * (size_t)(nt[0] + 4) * (nt[1] + 4) * (nt[2] + 4)));
+  const double sigma = src == 0 ? 1.0 : -1.0;  // +1: the target is the slider
+  double frac[3];
+  for (int a = 0; a < 3; ++a) {
+    const double su = sigma * u_cells(ctx, a, ctx->host_mech.x);
+    frac[a] = su - floor(su);
+  }
+  CK(launch_fd4_field(ctx->fd4_C, dims, nt, ctx->opt.margin, frac, T.d, ctx->fd4_V, H_dev, ctx->st));
   return MM_OK;
 }
 

@@ -290,6 +290,11 @@ cudaError_t launch_scale(const float* in, float* out, size_t n, float s, cudaStr
 // partial holds power_blocks(N) doubles
 int power_blocks(size_t N);
 cudaError_t launch_mxh2(const float* m, const float* H, size_t N, double* partial, double* out, cudaStream_t st);
+// four-point difference gradient of the interpolant (variants.cu): V holds
+// (nx + 4)(ny + 4)(nz + 4) floats, H 3 nx ny nz; needs margin >= 2
+cudaError_t launch_fd4_field(const float* C, const int bdim[3], const int nt[3], int margin, const double frac[3],
+                             const double cell[3], float* V, float* H, cudaStream_t st);
+
 // div / curl means (power.cu): out[0] = sum |div H|, out[1] = sum ||curl H|| over
 // divcurl_cells interior cells; partial holds 2 divcurl_blocks doubles
 size_t divcurl_cells(int nx, int ny, int nz);

@@ -305,3 +305,34 @@ def test_div_curl_of_interpolated_stray_field_matches_oracle():
         assert abs(D - Dr) <= b and abs(C - Cr) <= b
         assert D > 0 and C > 0
         mm.close()
+
+
+@pytest.mark.parametrize("n0,n1,gap,u", [
+    ((30, 22, 2), (27, 19, 3), 2, (0.41, 0.17, 0.0)),
+    ((25, 24, 1), (25, 24, 1), 1, (1.75, -0.3, 0.0)),
+])
+def test_fd4_variant_matches_oracle(n0, n1, gap, u):
+    """The four-point difference variant of the stray field against the oracle's.
+    Differencing FP32 values of phi costs up to (1 + 8 + 8 + 1)/12 of their
+    rounding per cell over d: the bar is the larger of the field bar and three
+    FP32 roundings of the rms interpolant value propagated that way."""
+    from oracle.variants import stray_field_fd4
+
+    fp, m0, m1, offs = _pair(n0, n1, gap, 12, u)
+    mm = _gpu(fp, m0, m1, offs)
+    for src in (0, 1):
+        t = 1 - src
+        H = mm.compute_stray_field_fd4(src).double().cpu().numpy()
+        Ms = fp.mat_base.Ms if src == 0 else fp.mat_slider.Ms
+        m_s = m0 if src == 0 else m1
+        n_t = fp.n_slider if t == 1 else fp.n_base
+        ref, val = stray_field_fd4(Ms * m_s, fp.cell, offs[src], offs[t], n_t, u, t == 1)
+        err = np.linalg.norm((H - ref).ravel())
+        rms_v = float(np.sqrt(np.mean(val ** 2)))
+        bound = 3 * 2.0 ** -23 * rms_v * 1.5 * np.sqrt(sum(1.0 / d ** 2 for d in fp.cell)) * np.sqrt(H[0].size)
+        assert err <= max(TOL * np.linalg.norm(ref.ravel()), bound)
+        # a sanity check only: the variant and the analytic gradient of the same
+        # interpolant differ by the difference's truncation error
+        Ha = mm.compute_stray_field(src).double().cpu().numpy()
+        assert 0.0 < rel_l2(H, Ha) < 1.0
+    mm.close()

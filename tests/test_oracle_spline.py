@@ -86,3 +86,43 @@ def test_weights_partition_of_unity():
     np.testing.assert_allclose(w[2].sum(axis=0), 0.0, atol=1e-14)
     # first moment: sum_k w_k (k - 1) = t  (nodes floor-1 .. floor+2)
     np.testing.assert_allclose((w[0] * (np.arange(4) - 1)[:, None]).sum(axis=0), t, atol=1e-15)
+
+
+def test_fd4_gradient_of_interpolated_cubic_is_exact():
+    """The four-point difference is exact for cubics, and the B-spline of a cubic
+    reproduces it in the interior: the variant's H equals -grad of the cubic at
+    every displaced centre (pins the stencil, its signs and the centre offsets)."""
+    from oracle.variants import fd4_gradient
+
+    cell = (4e-9, 3e-9, 2e-9)
+    rng = np.random.default_rng(4)
+    a = rng.standard_normal(10)
+
+    def phi(x, y, z):  # node coordinates
+        return (a[0] * x ** 3 + a[1] * y ** 3 + a[2] * z ** 3 + a[3] * x * y * z + a[4] * x * x * y
+                + a[5] * y * y * z + a[6] * x + a[7] * y * z + a[8] * z * z + a[9])
+
+    def grad(x, y, z):
+        return np.stack([3 * a[0] * x ** 2 + a[3] * y * z + 2 * a[4] * x * y + a[6],
+                         3 * a[1] * y ** 2 + a[3] * x * z + a[4] * x * x + 2 * a[5] * y * z + a[7] * z,
+                         3 * a[2] * z ** 2 + a[3] * x * y + a[5] * y * y + a[7] * y + 2 * a[8] * z])
+
+    from oracle.spline import evaluate
+    # exact cubic values at the extended centres, then FD4 in node units (cell 1)
+    n = (5, 4, 3)
+    f = (0.37, 0.61, 0.13)
+    zz, yy, xx = np.meshgrid(np.arange(n[2] + 4) - 2 + f[2], np.arange(n[1] + 4) - 2 + f[1],
+                             np.arange(n[0] + 4) - 2 + f[0], indexing="ij")
+    H = fd4_gradient(phi(xx, yy, zz), (1.0, 1.0, 1.0))
+    g = grad(xx[2:-2, 2:-2, 2:-2], yy[2:-2, 2:-2, 2:-2], zz[2:-2, 2:-2, 2:-2])
+    np.testing.assert_allclose(H, -g, rtol=1e-11, atol=1e-11 * np.abs(g).max())
+    # through the interpolant: samples of the cubic on a box whose ends are far away
+    B = 40
+    bz, by, bx = np.meshgrid(np.arange(B), np.arange(B), np.arange(B), indexing="ij")
+    coef = S.prefilter_3d(phi(bx, by, bz))
+    pos = np.stack([xx + 17, yy + 17, zz + 17], axis=-1)
+    val, _, _ = evaluate(coef, pos)
+    H2 = fd4_gradient(val, cell)
+    g2 = grad(xx[2:-2, 2:-2, 2:-2] + 17, yy[2:-2, 2:-2, 2:-2] + 17, zz[2:-2, 2:-2, 2:-2] + 17)
+    for c in range(3):
+        np.testing.assert_allclose(H2[c], -g2[c] / cell[c], rtol=1e-6, atol=1e-6 * np.abs(g2[c]).max() / cell[c])
