@@ -282,14 +282,14 @@ mm_status mm_eval_kernel_fp64(int kind, int n, const double* offsets_dev, double
                               double dz, double* out_dev);
 
 /* FFT grid and potential box of the path from `src` (for reporting).
- * fft_dims: Qx, Qy and Qz (0 for a thin source, whose z is summed directly). */
+ * fft_dims: Qx, Qy and Qz (0 when z is summed directly: sources of up to 8 layers). */
 mm_status mm_get_plan_info(mm_ctx* ctx, int src, int fft_dims[3], int box_dims[3],
                            long long box_lo[3], int coef_dims[3]);
 
 /* Per-kernel timing with CUDA events on the context stream (off by default).
  * Classes: 0 x-forward FFT, 1 y pass, 2 x-inverse FFT, 3 gather, 4 LLG stage,
- * 5 slider/reduction, 6 combine/normalise; thick sources: 7 y forward,
- * 8 z pass, 9 y inverse. */
+ * 5 slider/reduction, 6 combine/normalise; sources of more than 4 layers:
+ * 7 y forward, 8 z pass (z FFT or direct z sum), 9 y inverse. */
 mm_status mm_set_timing(mm_ctx* ctx, int on);
 mm_status mm_get_timing(mm_ctx* ctx, int kernel_class, double* total_ms, long long* launches);
 mm_status mm_reset_timing(mm_ctx* ctx);
