@@ -300,30 +300,41 @@ def assign_lanes(costs, nlanes):
     return list(out)
 
 
-def spline_field_noalloc(coef, coef_lo, pos0_nodes, m_target, cell, Ms, H_out=None, FE_out=None,
-                         stream=None):
+def spline_field_noalloc(coef, coef_lo, pos0_nodes, m_target, cell, Ms, H_out, FE_out, stream=None):
     """mm_spline_field_noalloc: stray field / force / energy from a coefficient box, no allocation.
 
     coef: (bz, by, bx) float32 CUDA tensor of B-spline coefficients whose node
     [0, 0, 0] is source lattice node coef_lo; pos0_nodes: source-lattice
     position of target cell (0, 0, 0); m_target: (3, nz, ny, nx) float32 CUDA.
-    H_out (3, nz, ny, nx) float32 and FE_out (4,) float64 are caller-provided
-    CUDA tensors (FE_out = [Fx, Fy, Fz, E]); nothing is allocated here.
+    H_out (3, nz, ny, nx) float32 (or None) and FE_out (4,) float64 are
+    caller-provided CUDA tensors (FE_out = [Fx, Fy, Fz, E]); nothing is
+    allocated here.  Every tensor must sit on one device; the call runs with
+    that device current.
     """
     lib = _native.load()
     _need_cuda_f32(coef)
     _need_cuda_f32(m_target)
+    if coef.dim() != 3:
+        raise ValueError("coef must be a (bz, by, bx) tensor")
+    if m_target.dim() != 4 or m_target.shape[0] != 3:
+        raise ValueError("m_target must be a (3, nz, ny, nx) tensor")
     if H_out is not None:
         _need_cuda_f32(H_out, tuple(m_target.shape))
-    if not (FE_out.is_cuda and FE_out.dtype == torch.float64 and FE_out.numel() == 4):
-        raise ValueError("FE_out must be a (4,) float64 CUDA tensor")
+    if FE_out is None or not (FE_out.is_cuda and FE_out.dtype == torch.float64 and FE_out.numel() == 4
+                              and FE_out.is_contiguous()):
+        raise ValueError("FE_out must be a contiguous (4,) float64 CUDA tensor")
+    dev = coef.device
+    for t in (m_target, H_out, FE_out):
+        if t is not None and t.device != dev:
+            raise ValueError("coef, m_target, H_out and FE_out must be on one device")
     bz, by, bx = coef.shape
     _, nz, ny, nx = m_target.shape
-    st = stream if stream is not None else torch.cuda.current_stream()
-    s = lib.mm_spline_field_noalloc(_ptr(coef), _native._i3(bx, by, bz), _native._ll3(*coef_lo),
-                                    _native._d3(*pos0_nodes), _ptr(m_target), nx, ny, nz,
-                                    *[float(c) for c in cell], float(Ms), _ptr(H_out), _ptr(FE_out),
-                                    C.c_void_p(st.cuda_stream))
+    with torch.cuda.device(dev):
+        st = stream if stream is not None else torch.cuda.current_stream(dev)
+        s = lib.mm_spline_field_noalloc(_ptr(coef), _native._i3(bx, by, bz), _native._ll3(*coef_lo),
+                                        _native._d3(*pos0_nodes), _ptr(m_target), nx, ny, nz,
+                                        *[float(c) for c in cell], float(Ms), _ptr(H_out), _ptr(FE_out),
+                                        C.c_void_p(st.cuda_stream))
     if s != 0:
         raise MMError(s, "mm_spline_field_noalloc")
     return H_out, FE_out

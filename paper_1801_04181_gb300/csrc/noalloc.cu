@@ -107,10 +107,16 @@ extern "C" mm_status mm_spline_field_noalloc(const float* coef_dev, const int co
   if (!coef_dev || !coef_dims || !coef_lo || !pos0_nodes || !m_dev || !FE_dev) return MM_EINVAL;
   if (nx < 1 || ny < 1 || nz < 1 || nz > kMaxNz || !(dx > 0) || !(dy > 0) || !(dz > 0) || !(Ms > 0))
     return MM_EINVAL;
+  // positions beyond 2^30 nodes would overflow the int lattice indices of the gather
   for (int a = 0; a < 3; ++a)
-    if (coef_dims[a] < 4 || !isfinite(pos0_nodes[a])) return MM_EINVAL;
+    if (coef_dims[a] < 4 || !isfinite(pos0_nodes[a]) || fabs(pos0_nodes[a]) >= 1073741824.0 ||
+        coef_lo[a] <= -(1ll << 40) || coef_lo[a] >= (1ll << 40))
+      return MM_EINVAL;
+  // tile count in 64 bits: a huge nx * ny must not wrap below the limit
+  const long long ntiles_ll = ((long long)nx + 31) / 32 * (((long long)ny + 7) / 8) *
+                              (((long long)nz + kMaxNz - 1) / kMaxNz);
+  if (ntiles_ll > kNoAllocMaxTiles) return MM_ETOOBIG;
   const int ntiles = gather_tiles(nx, ny, nz);
-  if (ntiles > kNoAllocMaxTiles) return MM_ETOOBIG;
   // support of every target centre must lie inside the coefficient box
   const int n[3] = {nx, ny, nz};
   GatherJob J{};

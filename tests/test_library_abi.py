@@ -70,3 +70,33 @@ def test_new_entry_points_reject_null_context_without_gpu(lib):
                                ctypes.byref(x)) == _native.MM_EINVAL
     assert L.mm_step_batch(None, 1, 1, None, None, None) == _native.MM_EINVAL
     assert L.mm_assign_lanes(None, 0, 1, None) == 0
+
+
+def test_noalloc_argument_checks_without_gpu(lib):
+    """mm_spline_field_noalloc checks its arguments on the host before any CUDA
+    call: the pointers below are never dereferenced."""
+    from paper_1801_04181_gb300 import _native
+
+    L = _native.load()
+    dummy = ctypes.c_void_p(0x1000)  # non-null, never touched
+    dims = _native._i3(20, 20, 8)
+    lo = _native._ll3(0, 0, 0)
+
+    def call(pos, nx=8, ny=8, nz=2, d=(1e-9, 1e-9, 1e-9), Ms=1e6, dims=dims, lo=lo, FE=dummy):
+        return L.mm_spline_field_noalloc(dummy, dims, lo, _native._d3(*pos), dummy, nx, ny, nz, *d, Ms,
+                                         None, FE, None)
+
+    assert call((2.0, 2.0, 2.0), FE=None) == _native.MM_EINVAL          # no force/energy output
+    assert call((2.0, 2.0, 2.0), nz=0) == _native.MM_EINVAL             # empty target
+    assert call((2.0, 2.0, 2.0), nz=5) == _native.MM_EINVAL             # more layers than a chunk
+    assert call((2.0, 2.0, 2.0), Ms=0.0) == _native.MM_EINVAL
+    assert call((2.0, 2.0, 2.0), d=(1e-9, -1e-9, 1e-9)) == _native.MM_EINVAL
+    assert call((float("nan"), 2.0, 2.0)) == _native.MM_EINVAL
+    assert call((2.0 ** 31, 2.0, 2.0)) == _native.MM_EINVAL             # beyond the int lattice
+    assert call((2.0, 2.0, 2.0), dims=_native._i3(3, 20, 8)) == _native.MM_EINVAL
+    assert call((2.0, 2.0, 2.0), lo=_native._ll3(-(1 << 62), 0, 0)) == _native.MM_EINVAL
+    assert call((15.0, 2.0, 2.0)) == _native.MM_ERANGE                  # support leaves the box
+    # 65536 tiles of 32 x 8 columns is the limit of the fixed scratch
+    assert call((1.5, 1.5, 1.5), nx=4097, ny=4096, nz=1) == _native.MM_ETOOBIG
+    # a tile count that wraps a 32-bit product must still be refused
+    assert call((1.5, 1.5, 1.5), nx=2 ** 31 - 1, ny=2 ** 31 - 1, nz=4) == _native.MM_ETOOBIG

@@ -56,7 +56,11 @@ def test_noalloc_matches_allocating_entry_point_twice():
     mm.close()
 
 
-def test_noalloc_rejects_out_of_box_and_oversized_targets():
+def test_noalloc_rejects_out_of_box_targets_and_bad_shapes():
+    """A target whose spline support leaves the box is refused with MM_ERANGE;
+    the Python side refuses arrays of the wrong shape before the C call (the
+    kernel reads m at 0, N and 2N, so a (2, ...) array would be read past its
+    end).  Oversized targets are covered by the CPU test of the C ABI."""
     import torch
     from paper_1801_04181_gb300 import MMError, spline_field_noalloc
 
@@ -66,8 +70,9 @@ def test_noalloc_rejects_out_of_box_and_oversized_targets():
     with pytest.raises(MMError) as e:
         spline_field_noalloc(coef, (0, 0, 0), (15.0, 2.0, 2.0), m_t, (1e-9,) * 3, 1e6, None, FE)
     assert e.value.status == -4  # MM_ERANGE: support leaves the box
-    big = torch.zeros((3, 1, 4096, 4097), dtype=torch.float32, device="cuda")
-    with pytest.raises(MMError) as e:
-        spline_field_noalloc(torch.zeros((4, 4100, 4100), dtype=torch.float32, device="cuda"),
-                             (0, 0, 0), (1.5, 1.5, 1.5), big, (1e-9,) * 3, 1e6, None, FE)
-    assert e.value.status == -8  # MM_ETOOBIG: more tiles than the fixed scratch holds
+    with pytest.raises(ValueError):
+        spline_field_noalloc(coef, (0, 0, 0), (2.0, 2.0, 2.0), m_t[:2], (1e-9,) * 3, 1e6, None, FE)
+    with pytest.raises(ValueError):
+        spline_field_noalloc(coef[0], (0, 0, 0), (2.0, 2.0, 2.0), m_t, (1e-9,) * 3, 1e6, None, FE)
+    with pytest.raises(ValueError):
+        spline_field_noalloc(coef, (0, 0, 0), (2.0, 2.0, 2.0), m_t, (1e-9,) * 3, 1e6, None, None)
