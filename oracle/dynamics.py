@@ -140,18 +140,32 @@ def _axpy_state(y, ks, coefs, dt):
     return out
 
 
-def dp45_step(system, t, y, dt, k1=None):
-    """One Dormand-Prince 5(4) step of size dt (no rejection).
-
-    Returns (y5, err, k7): y5 the 5th-order solution (not renormalised), err the
-    max-norm over both magnets' m of dt * sum (b5 - b4) k, k7 = f(t + dt, y5)
-    for first-same-as-last reuse.
-    """
+def dp45_stages(system, t, y, dt, k1=None):
+    """The seven stage derivatives k_1..k_7 of one Dormand-Prince step of size
+    dt from (t, y) and the 5th-order solution y5 (the stage-7 input, since
+    a_7j = b5_j); k1 may be passed in (first-same-as-last)."""
     ks = [system.rhs(t, y) if k1 is None else k1]
     for i in range(1, 7):
         yi = _axpy_state(y, ks, DP_A[i], dt)
         ks.append(system.rhs(t + DP_C[i] * dt, yi))
-    y5 = yi  # stage 7 input equals the 5th-order solution (a_7j = b5_j)
+    return ks, yi
+
+
+def dp45_embedded(system, t, y, dt, k1=None):
+    """The 5th- and embedded 4th-order solutions of one step: (y5, y4, ks)."""
+    ks, y5 = dp45_stages(system, t, y, dt, k1)
+    return y5, _axpy_state(y, ks, DP_B4, dt), ks
+
+
+def dp45_step(system, t, y, dt, k1=None):
+    """One Dormand-Prince 5(4) step of size dt (no rejection).
+
+    Returns (y5, err, k7): y5 the 5th-order solution (not renormalised), err the
+    max-norm over both magnets' m of dt * sum (b5 - b4) k (= y5 - y4, the
+    local error estimate of the embedded 4th-order solution), k7 = f(t + dt, y5)
+    for first-same-as-last reuse.
+    """
+    ks, y5 = dp45_stages(system, t, y, dt, k1)
     err = 0.0
     for idx in (0, 1):
         e = sum((DP_B5[j] - DP_B4[j]) * ks[j][idx] for j in range(7))
@@ -174,14 +188,20 @@ def run_fixed(system, y0, dt, nsteps, t0=0.0):
     return t, y
 
 
-def run_adaptive(system, y0, dt, nsteps, rtol, t0=0.0, dt_min=0.0, dt_max=np.inf):
-    """nsteps accepted adaptive DP45 steps; controller dt *= clamp(0.9 (rtol/err)^(1/5), 0.2, 5)."""
+def run_adaptive(system, y0, dt, nsteps, rtol, t0=0.0, dt_min=0.0, dt_max=np.inf, trace=None):
+    """nsteps accepted adaptive DP45 steps; controller dt *= clamp(0.9 (rtol/err)^(1/5), 0.2, 5).
+
+    An attempt is accepted when err <= rtol (or dt <= dt_min).  trace: a list
+    that receives one dict per attempt (t, dt, err, accepted) in order."""
     t, y, k1 = t0, list(y0), None
     accepted = rejected = 0
     while accepted < nsteps:
         y5, err, k7 = dp45_step(system, t, y, dt, k1)
         fac = 5.0 if err == 0.0 else min(5.0, max(0.2, 0.9 * (rtol / err) ** 0.2))
-        if err <= rtol or dt <= dt_min:
+        ok = err <= rtol or dt <= dt_min
+        if trace is not None:
+            trace.append(dict(t=t, dt=dt, err=err, accepted=ok))
+        if ok:
             y = [normalise(y5[0]), normalise(y5[1]), y5[2], y5[3]]
             t += dt
             k1 = k7

@@ -4,6 +4,13 @@
   tan(theta/2) = tan(theta0/2) exp(-alpha gamma0 H t/(1+alpha^2)), azimuth rate
   gamma0 H/(1+alpha^2);
 * the DP45 pair is 5th order on a linear ODE (global error ~ dt^5);
+* the tableau satisfies the Runge-Kutta order conditions (b5: order 5, b4:
+  order 4 and not 5); the embedded solution converges at rate 4; the error
+  estimate scales as dt^5 and equals the 4th-order local error against an
+  independent integrator (scipy DOP853);
+* the adaptive controller on a single spin: rejection of an oversized first
+  step with the 0.2 clamp, err held near 0.9^5 rtol, the 5x growth clamp and
+  dt_max when nothing moves, tolerance proportionality of the global error;
 * exchange field of a spin wave: eigenvalue (2A/mu0 Ms)(2 cos(k d) - 2)/d^2;
 * anisotropy field along the axis, 2 Ku/(mu0 Ms) (m.k);
 * slider without magnetic force: critically damped spring, closed form.
@@ -168,3 +175,175 @@ def test_power_input_is_minus_force_dot_velocity():
     assert all(p > 0 for p in P["P_diss"])
     # reversing the velocity reverses the input power
     assert abs(D.power_balance(sys, m0, m1, 1e-10, -v)["P_in"] + P["P_in"]) <= 1e-12 * abs(P["P_in"])
+
+
+# ---------------------------------------------------------------- adaptive stepping
+# Order conditions of explicit Runge-Kutta methods (Butcher rooted trees): a
+# weight vector b is of order p when sum_i b_i Phi_i(tree) = 1/gamma(tree) for
+# every tree of up to p nodes.  With c = A 1, the elementary weights are
+# products of c and A as written in each entry.
+def _order_conditions(A, b, c):
+    A = np.array([list(r) + [0.0] * (7 - len(r)) for r in A])
+    b = np.asarray(b)
+    c = np.asarray(c)
+    Ac, Ac2, Ac3 = A @ c, A @ c ** 2, A @ c ** 3
+    AAc = A @ Ac
+    return {
+        # order 1..4 (8 trees)
+        "b": (b.sum(), 1.0), "bc": (b @ c, 1 / 2), "bc2": (b @ c ** 2, 1 / 3), "bAc": (b @ Ac, 1 / 6),
+        "bc3": (b @ c ** 3, 1 / 4), "bcAc": (b @ (c * Ac), 1 / 8), "bAc2": (b @ Ac2, 1 / 12),
+        "bAAc": (b @ AAc, 1 / 24),
+        # order 5 (9 trees)
+        "bc4": (b @ c ** 4, 1 / 5), "bc2Ac": (b @ (c ** 2 * Ac), 1 / 10), "bcAc2": (b @ (c * Ac2), 1 / 15),
+        "bcAAc": (b @ (c * AAc), 1 / 30), "b(Ac)2": (b @ Ac ** 2, 1 / 20), "bAc3": (b @ Ac3, 1 / 20),
+        "bAcAc": (b @ (A @ (c * Ac)), 1 / 40), "bAAc2": (b @ (A @ Ac2), 1 / 60),
+        "bAAAc": (b @ (A @ AAc), 1 / 120),
+    }
+
+
+def test_dp45_tableau_satisfies_the_order_conditions():
+    """b5 is of order 5, the embedded b4 of order 4 but not 5 (so y5 - y4 is a
+    nonzero estimate of the 4th-order local error), and c_i = sum_j a_ij."""
+    A, c = D.DP_A, np.asarray(D.DP_C)
+    for i, row in enumerate(A):
+        assert abs(sum(row) - c[i]) < 1e-14
+    cond5 = _order_conditions(A, D.DP_B5, c)
+    for name, (got, want) in cond5.items():
+        assert abs(got - want) < 1e-14, name
+    cond4 = _order_conditions(A, D.DP_B4, c)
+    names4 = ["b", "bc", "bc2", "bAc", "bc3", "bcAc", "bAc2", "bAAc"]
+    for name in names4:
+        got, want = cond4[name]
+        assert abs(got - want) < 1e-14, name
+    assert max(abs(g - w) for n, (g, w) in cond4.items() if n not in names4) > 1e-4
+
+
+def test_dp45_embedded_solution_is_fourth_order():
+    """Propagating the embedded solution y4 alone converges at rate 4 on
+    y' = lambda y (global error against exp(lambda t))."""
+    lam = -1.0 + 2.0j
+    errs = []
+    for n in (10, 20, 40, 80):
+        dt = 1.0 / n
+        y = [np.ones(1, complex), np.ones(1, complex), 0.0, 0.0]
+        t = 0.0
+        for _ in range(n):
+            _, y, _ = D.dp45_embedded(Linear(lam), t, y, dt)
+            t += dt
+        errs.append(abs(y[0][0] - np.exp(lam)))
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all((rates > 3.7) & (rates < 4.5)), rates
+
+
+class SmoothNonlinear:
+    """A smooth non-autonomous system in the two 'magnet' slots:
+    a' = -a b + sin(t),  b' = a^2 - b/2  (elementwise on arrays of 2)."""
+
+    def rhs(self, t, y):
+        a, b = y[0], y[1]
+        return [-a * b + np.sin(t), a * a - 0.5 * b, 0.0, 0.0]
+
+
+def _reference_step(t0, y0, dt):
+    from scipy.integrate import solve_ivp
+
+    def f(t, z):
+        a, b = z[:2], z[2:]
+        return np.concatenate([-a * b + np.sin(t), a * a - 0.5 * b])
+
+    sol = solve_ivp(f, (t0, t0 + dt), np.concatenate([y0[0], y0[1]]), method="DOP853", rtol=1e-13,
+                    atol=1e-15)
+    z = sol.y[:, -1]
+    return z[:2], z[2:]
+
+
+def test_dp45_error_estimate_is_the_fourth_order_local_error():
+    """err = max |y5 - y4| scales as dt^5 on a smooth nonlinear problem and
+    equals, to leading order, the true local error of y4 against an
+    independent high-accuracy integrator (scipy's DOP853)."""
+    sysm = SmoothNonlinear()
+    y0 = [np.array([0.7, -0.4]), np.array([0.2, 1.1]), 0.0, 0.0]
+    t0 = 0.3
+    errs = []
+    for dt in (0.2, 0.1, 0.05, 0.025):
+        _, err, _ = D.dp45_step(sysm, t0, y0, dt)
+        errs.append(err)
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all((rates > 4.6) & (rates < 5.4)), rates
+    dt = 0.025
+    y5, y4, _ = D.dp45_embedded(sysm, t0, y0, dt)
+    a_ref, b_ref = _reference_step(t0, y0, dt)
+    true4 = max(np.max(np.abs(y4[0] - a_ref)), np.max(np.abs(y4[1] - b_ref)))
+    true5 = max(np.max(np.abs(y5[0] - a_ref)), np.max(np.abs(y5[1] - b_ref)))
+    assert true5 < 0.05 * true4
+    assert abs(errs[-1] - true4) < 0.05 * true4
+
+
+def _spin_y0(th0=0.8, ph0=0.3):
+    m0 = np.array([np.sin(th0) * np.cos(ph0), np.sin(th0) * np.sin(ph0), np.cos(th0)])
+    # the second slot holds a frozen unit vector (SingleSpin gives it no motion)
+    return [m0[:, None, None, None].copy(), m0[:, None, None, None].copy(), 0.0, 0.0]
+
+
+def test_run_adaptive_controller_sequence_on_a_single_spin():
+    """Damped precession with a first step far too large: the attempt is
+    rejected and dt shrinks by the clamped controller factor; every attempt
+    after that is accepted with err near 0.9^5 rtol; the accepted trajectory
+    matches the closed form within the summed per-step tolerance."""
+    H0, alpha, rtol = 1e5, 0.1, 1e-8
+    gamma0 = MU0 * GAMMA_LL
+    sysm = SingleSpin((0, 0, H0), alpha)
+    trace = []
+    t, y, dt_next, acc, rej = D.run_adaptive(sysm, _spin_y0(), 5e-11, 40, rtol, trace=trace)
+    assert acc == 40 and rej == len(trace) - 40 and rej >= 1
+    assert not trace[0]["accepted"] and trace[0]["err"] > 1e3 * rtol
+    # hand-applied controller: factor 0.9 (rtol/err)^(1/5), clamped to [0.2, 5]
+    for a, b in zip(trace[:-1], trace[1:]):
+        fac = min(5.0, max(0.2, 0.9 * (rtol / a["err"]) ** 0.2))
+        assert b["dt"] == a["dt"] * fac
+        assert b["t"] == (a["t"] + a["dt"] if a["accepted"] else a["t"])
+        assert a["accepted"] == (a["err"] <= rtol)
+    # the first attempt is so far off that its factor is the 0.2 clamp
+    assert trace[1]["dt"] == 0.2 * trace[0]["dt"]
+    # once converged the controller holds err at 0.9^5 rtol ~ 0.59 rtol
+    tail = [a["err"] / rtol for a in trace[-20:]]
+    assert all(a["accepted"] for a in trace[-20:])
+    assert 0.4 < np.median(tail) < 0.8, tail
+    m = y[0][:, 0, 0, 0]
+    th_ref = 2 * np.arctan(np.tan(0.4) * np.exp(-alpha * gamma0 * H0 * t / (1 + alpha ** 2)))
+    assert abs(np.arccos(m[2]) - th_ref) < 40 * rtol
+
+
+def test_run_adaptive_zero_error_grows_dt_by_five_to_dt_max():
+    """With no field nothing moves, err = 0, every attempt is accepted and dt
+    grows by the upper clamp 5 per step until dt_max holds it."""
+    sysm = SingleSpin((0, 0, 0.0), 0.1)
+    trace = []
+    D.run_adaptive(sysm, _spin_y0(), 1e-15, 6, 1e-6, dt_max=1e-12, trace=trace)
+    np.testing.assert_allclose([a["dt"] for a in trace], [1e-15, 5e-15, 2.5e-14, 1.25e-13, 6.25e-13, 1e-12],
+                               rtol=1e-14)
+    assert all(a["accepted"] and a["err"] == 0.0 for a in trace)
+
+
+def test_run_adaptive_tolerance_proportionality():
+    """Tightening rtol by 1e3 tightens the global error of the accepted
+    trajectory (against the closed form) by at least 1e2."""
+    H0, alpha = 1e5, 0.1
+    gamma0 = MU0 * GAMMA_LL
+    sysm = SingleSpin((0, 0, H0), alpha)
+    errs = []
+    T = 2e-10
+    for rtol in (1e-5, 1e-8):
+        t, y, dt = 0.0, _spin_y0(), 1e-13
+        # stop exactly at T: accepted steps until the last one, then one fixed step to T
+        k = 0
+        while True:
+            t1, y1, dt1, _, _ = D.run_adaptive(sysm, y, dt, 1, rtol, t0=t)
+            if t1 >= T:
+                break
+            t, y, dt = t1, y1, dt1
+            k += 1
+        t, y = D.run_fixed(sysm, y, T - t, 1, t0=t)
+        th_ref = 2 * np.arctan(np.tan(0.4) * np.exp(-alpha * gamma0 * H0 * t / (1 + alpha ** 2)))
+        errs.append(abs(np.arccos(y[0][2, 0, 0, 0]) - th_ref))
+    assert errs[1] < 1e-2 * errs[0], errs
