@@ -213,51 +213,115 @@ def measured_peaks():
 
 
 # ------------------------------------------------------------------ CPU oracle sample
-def cpu_oracle_sample(fp, m0, m1, pool=None):
-    """Time the oracle on a bounded sample of one RK45 step and scale to cell-updates/s.
+# A bounded sample of one Dormand-Prince step of the oracle: one stray-field
+# direction (potential on the box by linear convolution, banded prefilter,
+# 64-term evaluation, force) plus one self-demag field, i.e. half of one field
+# evaluation; a step makes six evaluations, so the sample is 1/12 of a step.
+# The kernel windows are set-up, computed beforehand by the process pool and
+# handed to the workers through shared memory.
+SAMPLE_SHARE = 12
 
-    Sample: one stray-field direction (potential on the box by linear
-    convolution, banded prefilter, 64-term evaluation, force) plus one
-    self-demag field, i.e. half of one field evaluation; a DP45 step makes six.
-    The kernel windows are set-up, computed beforehand by a process pool.
-    """
+
+def _oracle_sample(fp, m0, m1, S, N):
     from oracle import fields as OF
     from oracle.interaction import stray_interaction
-    import multiprocessing as mp
 
-    own = pool is None
-    if own:
-        pool = mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1)))
-    from tests.pair_setup import oracle_kernel_windows
-
-    n_s = fp.n_base
     box_lo, box_dims = OF.box_for_target(fp.n_slider, fp.offsets[1], fp.offsets[0], fp.u0, True)
-    S, N = oracle_kernel_windows(n_s, fp.cell, box_lo, box_dims, pool)
-    if own:
-        pool.close()
-        pool.join()
-    key = ("S", (3,) + tuple(reversed(n_s)), tuple(fp.cell), tuple(box_lo), tuple(box_dims))
-    cache = {key: S}
-    M0 = fp.mat_base.Ms * m0
-    M1 = fp.mat_slider.Ms * m1
+    key = ("S", (3,) + tuple(reversed(fp.n_base)), tuple(fp.cell), tuple(box_lo), tuple(box_dims))
     t0 = time.perf_counter()
-    stray_interaction(M0, M1, fp.cell, fp.offsets[0], fp.offsets[1], fp.u0, True, kernel_cache=cache)
-    OF.demag_conv(M0, fp.cell, kernel=N)
-    t = time.perf_counter() - t0
+    stray_interaction(fp.mat_base.Ms * m0, fp.mat_slider.Ms * m1, fp.cell, fp.offsets[0], fp.offsets[1],
+                      fp.u0, True, kernel_cache={key: S})
+    OF.demag_conv(fp.mat_base.Ms * m0, fp.cell, kernel=N)
+    return time.perf_counter() - t0
+
+
+def _oracle_sample_task(job):
+    """One oracle sample in a pool worker, its windows attached from shared memory."""
+    from multiprocessing import shared_memory
+
+    fp, m0, m1, (s_name, s_shape), (n_name, n_shape) = job
+    blocks = [shared_memory.SharedMemory(name=s_name), shared_memory.SharedMemory(name=n_name)]
+    try:
+        S = np.ndarray(s_shape, dtype=np.float64, buffer=blocks[0].buf)
+        N = np.ndarray(n_shape, dtype=np.float64, buffer=blocks[1].buf)
+        t = _oracle_sample(fp, m0, m1, S, N)
+        del S, N
+        return t
+    finally:
+        for b in blocks:
+            b.close()
+
+
+class OracleSampler:
+    """Times the oracle on the bounded sample: in this process (one thread) and
+    as one concurrent sample per worker of a spawn pool (all host cores)."""
+
+    def __init__(self, fp, m0, m1, pool, workers):
+        from multiprocessing import shared_memory
+
+        from oracle import fields as OF
+        from oracle.fields import kernel_windows_pooled
+
+        self.fp, self.m0, self.m1, self.pool, self.workers = fp, m0, m1, pool, workers
+        box_lo, box_dims = OF.box_for_target(fp.n_slider, fp.offsets[1], fp.offsets[0], fp.u0, True)
+        S, N = kernel_windows_pooled(fp.n_base, fp.cell, box_lo, box_dims, pool)
+        self.blocks, self.views = [], []
+        for a in (S, N):
+            b = shared_memory.SharedMemory(create=True, size=a.nbytes)
+            v = np.ndarray(a.shape, dtype=np.float64, buffer=b.buf)
+            v[...] = a
+            self.blocks.append(b)
+            self.views.append(v)
+        self.job = (fp, m0, m1, (self.blocks[0].name, S.shape), (self.blocks[1].name, N.shape))
+
+    def single(self):
+        """Seconds of one sample on one thread."""
+        return _oracle_sample(self.fp, self.m0, self.m1, *self.views)
+
+    def concurrent(self):
+        """Wall seconds of `workers` samples run at once, one per worker."""
+        t0 = time.perf_counter()
+        self.pool.map(_oracle_sample_task, [self.job] * self.workers, chunksize=1)
+        return time.perf_counter() - t0
+
+    def close(self):
+        self.views = []
+        for b in self.blocks:
+            b.close()
+            b.unlink()
+        self.blocks = []
+
+    def describe(self):
+        return "one stray-field direction + one self-demag of the %dx%dx%d pair (1/%d of a DP45 step: " \
+               "6 field evaluations x 2 halves); kernel windows precomputed as set-up" % \
+               (tuple(self.fp.n_base) + (SAMPLE_SHARE,))
+
+
+def oracle_pool_size():
+    return max(1, min(64, os.cpu_count() or 1))
+
+
+def cpu_oracle_sample(fp, m0, m1, pool, workers):
+    """cpu_baseline entry: the oracle on all `workers` host cores (concurrent
+    samples, one per core) and on one thread, scaled to cell-updates/s."""
+    smp = OracleSampler(fp, m0, m1, pool, workers)
+    try:
+        t1 = smp.single()
+        tw = smp.concurrent()
+    finally:
+        smp.close()
     cells = fp.cells()
-    step_time = t * 2 * 6  # two halves per evaluation, six evaluations per DP45 step
-    return {"value": cells / step_time, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "one stray-field direction + one self-demag of the %dx%dx%d pair "
-                      "(1/12 of a DP45 step: 6 field evaluations x 2 halves), %.1f s on 1 "
-                      "thread; kernel windows precomputed as set-up" % (tuple(fp.n_base) + (t,)),
-            "sample_seconds": t}
+    return {"value": workers * cells / (SAMPLE_SHARE * tw), "unit": UNIT, "cores": workers, "kind": "oracle",
+            "sample": smp.describe() + "; %d concurrent samples (one per core) in %.1f s" % (workers, tw),
+            "sample_seconds": tw,
+            "single_thread": {"value": cells / (SAMPLE_SHARE * t1), "cores": 1, "sample_seconds": t1}}
 
 
 # ------------------------------------------------------------------ GPU arm
 def run_gpu(args):
     import torch
     import workloads
-    from tests.pair_setup import gpu_pair
+    from paper_1801_04181_gb300 import pair_context as gpu_pair
 
     rank, world, local = dist_info()
     if world > 1:
@@ -269,7 +333,7 @@ def run_gpu(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         # start the oracle's process pool before the first GPU call
         import multiprocessing as mp
-        pool = mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1)))
+        pool = mp.get_context("spawn").Pool(oracle_pool_size())
 
     wl_name, wl_make = WORKLOADS[args.workload]
     fp, m0, m1 = wl_make(args.seed + 101 * rank)
@@ -363,7 +427,7 @@ def run_gpu(args):
     fft_cmp = cufft_compare(mm, fp, kt) if args.workload == "stick_slip" else None
     if pool is not None:
         try:
-            cpu_base = cpu_oracle_sample(fp, m0, m1, pool)
+            cpu_base = cpu_oracle_sample(fp, m0, m1, pool, oracle_pool_size())
         finally:
             pool.close()
             pool.join()
@@ -433,33 +497,49 @@ def cufft_compare(mm, fp, kt, reps=20):
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle as it stands, on the host cores.
+
+    One reference step = one round of concurrent bounded samples, one per
+    core (each 1/12 of a DP45 step of the stick-slip pair); the steps are
+    capped so the run ends within a few minutes, and the line reports the
+    steps actually timed with their measured time per step."""
     rank, world, _ = dist_info()
     if rank != 0:
         return
+    import multiprocessing as mp
+
     import workloads
 
     fp, m0, m1 = workloads.film_pair_stick_slip(seed=args.seed)
-    samples = []
     nw = min(args.warmup, 1)
-    ns = max(1, min(args.steps, 2))
-    import multiprocessing as mp
-    pool = mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1)))
+    ns = max(1, min(args.steps, 3))
+    workers = oracle_pool_size()
+    pool = mp.get_context("spawn").Pool(workers)
     try:
-        for i in range(nw + ns):
-            r = cpu_oracle_sample(fp, m0, m1, pool)
-            if i >= nw:
-                samples.append(r)
+        smp = OracleSampler(fp, m0, m1, pool, workers)
+        try:
+            for _ in range(nw):
+                smp.concurrent()
+            t0 = time.perf_counter()
+            for _ in range(ns):
+                smp.concurrent()
+            wall = time.perf_counter() - t0
+            desc = smp.describe()
+        finally:
+            smp.close()
     finally:
         pool.close()
         pool.join()
-    v = float(np.median([s["value"] for s in samples]))
-    step_s = fp.cells() / v
+    step_s = wall / ns
+    v = workers * fp.cells() / SAMPLE_SHARE / step_s
+    sample = desc + "; one step = %d concurrent samples (one per core)" % workers
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
             "steps": ns, "warmup": nw, "ms_per_step": step_s * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "cells": fp.cells()},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": samples[0]["sample"]},
+            "config": {"workload": WORKLOAD, "cells": fp.cells(),
+                       "step": "%d/%d of a DP45 step of the pair (one bounded sample per core)"
+                               % (workers, SAMPLE_SHARE)},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": workers, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -471,7 +551,7 @@ def run_sweep(args):
     cell-evaluations/s = 2 N offsets / time (no LLG in this workload)."""
     import torch
     import workloads
-    from tests.pair_setup import gpu_pair
+    from paper_1801_04181_gb300 import pair_context as gpu_pair
 
     fp, m0, m1 = workloads.film_pair_plain((64, 64, 1), 1, args.seed)
     mm = gpu_pair(fp, m0, m1, mech=False)
@@ -519,7 +599,7 @@ def run_divcurl(args):
     per second (field + diagnostics, one synchronisation per offset)."""
     import torch
     import workloads
-    from tests.pair_setup import gpu_pair
+    from paper_1801_04181_gb300 import pair_context as gpu_pair
 
     fp, m0, m1 = workloads.film_pair_plain((64, 64, 4), 1, args.seed)
     mm = gpu_pair(fp, m0, m1, mech=False)
@@ -580,7 +660,7 @@ def run_gradients(args):
     dE/dm of both cubes and dE/du.  Metric: cells of both cubes / time."""
     import torch
     import workloads
-    from tests.pair_setup import gpu_pair
+    from paper_1801_04181_gb300 import pair_context as gpu_pair
 
     fp, m0, m1 = workloads.cube_pair((64, 64, 64), 3, args.seed)
     fp.u0 = (1.7, 0.0, 0.0)
@@ -633,7 +713,7 @@ def run_batch(args):
     import torch
     import workloads
     from paper_1801_04181_gb300 import step_batch
-    from tests.pair_setup import gpu_pair
+    from paper_1801_04181_gb300 import pair_context as gpu_pair
 
     rank, world, local = dist_info()
     if world > 1:
@@ -643,7 +723,7 @@ def run_batch(args):
     pool = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import multiprocessing as mp
-        pool = mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1)))
+        pool = mp.get_context("spawn").Pool(oracle_pool_size())
     specs = workloads.batch_pairs(256, seed=args.seed)
     mine, lanes = batch_shard(specs, world, rank, args.lanes)
     streams = [torch.cuda.Stream() for _ in range(args.lanes)]
@@ -741,7 +821,7 @@ def run_batch(args):
         try:
             mid = int(np.argsort([fp.cells() for fp in specs])[len(specs) // 2])
             m0, m1 = workloads.batch_patterns(specs[mid])
-            cpu_base = cpu_oracle_sample(specs[mid], m0, m1, pool)
+            cpu_base = cpu_oracle_sample(specs[mid], m0, m1, pool, oracle_pool_size())
             cpu_base["sample"] += "; the median-size pair of the batch"
         finally:
             pool.close()

@@ -267,6 +267,22 @@ mm_status mm_field_div_curl(mm_ctx* ctx, const float* H_dev, int nx, int ny, int
 /* Accepted / rejected step counters since creation. */
 mm_status mm_get_step_stats(mm_ctx* ctx, long long* accepted, long long* rejected);
 
+/*
+ * Record of the most recent step attempts of mm_step / mm_step_batch (the
+ * context keeps the last 4096), oldest first: for each attempt its start time
+ * t (s), its size dt (s), its error norm err (the max over both magnets' cells
+ * and components of |dt sum_j (b5_j - b4_j) k_j|, the Dormand-Prince local
+ * error estimate of Sec. III's modified RK45, computed in fixed-dt mode
+ * too) and whether it was accepted
+ * (err <= rtol, or dt <= dt_min, or fixed-dt mode).  Writes the last
+ * min(capacity, kept) attempts to the arrays that are not NULL (host
+ * pointers, capacity entries each) and their number to *n_out.  Host only.
+ * mm_clear_attempt_log forgets the record.
+ */
+mm_status mm_get_attempt_log(mm_ctx* ctx, int capacity, double* t_out, double* dt_out, double* err_out,
+                             int* accepted_out, int* n_out);
+mm_status mm_clear_attempt_log(mm_ctx* ctx);
+
 /* Checkpoint: m of both magnets, slider state, displacement and time.
  * mm_get_state with buf = NULL returns the size in *bytes. */
 mm_status mm_get_state(mm_ctx* ctx, void* buf, size_t* bytes);

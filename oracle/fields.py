@@ -133,3 +133,34 @@ def demag_conv(M, cell, kernel=None):
         for b in range(3):
             H[a] -= fftconvolve(N[..., comp[(a, b)]], M[b], mode="valid")
     return H
+
+
+def _S_chunk(args):
+    X, Y, Z, cell = args
+    return S_kernel(X, Y, Z, *cell)
+
+
+def _N_chunk(args):
+    X, Y, Z, cell = args
+    return N_kernel(X, Y, Z, *cell)
+
+
+def _window_pooled(fun, lo, length, cell, pool):
+    dx, dy, dz = cell
+    jobs = []
+    for iz in range(length[2]):
+        Y, X = np.meshgrid(np.arange(length[1]) + lo[1], np.arange(length[0]) + lo[0], indexing="ij")
+        Z = np.full_like(X, iz + lo[2])
+        jobs.append((X * dx, Y * dy, Z * dz, cell))
+    return np.stack(pool.map(fun, jobs))
+
+
+def kernel_windows_pooled(n_s, cell, box_lo, box_dims, pool):
+    """The S window of a box and the N window of a source grid, one z plane per
+    pool task: the same values as potential_kernel_window / demag_kernel_window,
+    computed in parallel (pass a multiprocessing pool made with 'spawn')."""
+    d_lo = [box_lo[a] - (n_s[a] - 1) for a in range(3)]
+    d_len = [box_dims[a] + n_s[a] - 1 for a in range(3)]
+    S = _window_pooled(_S_chunk, d_lo, d_len, cell, pool)
+    N = _window_pooled(_N_chunk, [-(n - 1) for n in n_s], [2 * n - 1 for n in n_s], cell, pool)
+    return S, N

@@ -12,7 +12,8 @@ import torch
 from . import _native
 from ._native import MMError, mm_options
 
-__all__ = ["MovingMagnets", "MMError", "assign_lanes", "eval_kernel_fp64", "fft_plan", "load_library", "step_batch"]
+__all__ = ["MovingMagnets", "MMError", "assign_lanes", "eval_kernel_fp64", "fft_plan", "load_library", "pair_context",
+           "step_batch"]
 
 
 def load_library():
@@ -221,6 +222,20 @@ class MovingMagnets:
         self._c(self.lib.mm_get_step_stats(self.ctx, C.byref(a), C.byref(r)))
         return a.value, r.value
 
+    def attempt_log(self, capacity=4096):
+        """mm_get_attempt_log: the most recent step attempts, oldest first, as a
+        list of dicts (t, dt, err, accepted)."""
+        t = (C.c_double * capacity)()
+        dt = (C.c_double * capacity)()
+        err = (C.c_double * capacity)()
+        acc = (C.c_int * capacity)()
+        n = C.c_int()
+        self._c(self.lib.mm_get_attempt_log(self.ctx, int(capacity), t, dt, err, acc, C.byref(n)))
+        return [dict(t=t[i], dt=dt[i], err=err[i], accepted=bool(acc[i])) for i in range(n.value)]
+
+    def clear_attempt_log(self):
+        self._c(self.lib.mm_clear_attempt_log(self.ctx))
+
     def get_state(self):
         n = C.c_size_t()
         self._c(self.lib.mm_get_state(self.ctx, None, C.byref(n)))
@@ -374,3 +389,6 @@ class InteractionEnergy(torch.autograd.Function):
         gs, gt, du = ctx.saved_tensors
         g = float(gE)
         return None, None, g * gs, g * gt, g * du.to(gE.device)
+
+
+from .pairs import pair_context  # noqa: E402  (needs MovingMagnets above)

@@ -63,6 +63,9 @@ SIGNATURES = [
     ("mm_field_div_curl", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
                                     C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     ("mm_get_step_stats", C.c_int, [C.c_void_p, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
+    ("mm_get_attempt_log", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                     C.POINTER(C.c_double), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    ("mm_clear_attempt_log", C.c_int, [C.c_void_p]),
     ("mm_get_state", C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_size_t)]),
     ("mm_set_state", C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     ("mm_eval_kernel_fp64", C.c_int, [C.c_int, C.c_int, C.c_void_p, C.c_double, C.c_double, C.c_double,

@@ -20,6 +20,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <deque>
 #include <map>
 #include <set>
 #include <string>
@@ -36,6 +37,7 @@ constexpr double kMu0 = 4e-7 * 3.14159265358979323846;
 constexpr double kGammaLL = 1.7595e11;  // rad / (s T)
 constexpr int kWindowSlack = 8;         // cells of displacement before the FFT grid is re-planned
 constexpr int kTimingClasses = 10;
+constexpr int kAttemptLog = 4096;  // step attempts the context remembers
 
 // Dormand-Prince 5(4)
 const double DP_C[7] = {0.0, 1.0 / 5, 3.0 / 10, 4.0 / 5, 8.0 / 9, 1.0, 1.0};
@@ -165,6 +167,12 @@ struct mm_ctx {
   int* tickets = nullptr;             // device: last-block counters of the gather and stage launches
   bool k1_valid = false;
   long long accepted = 0, rejected = 0;
+  // the most recent step attempts (oldest first), kAttemptLog at most
+  struct Attempt {
+    double t, dt, err;
+    int accepted;
+  };
+  std::deque<Attempt> attempts;
   bool planned = false;
   // setup scratch (FP64 spectra generation)
   double2* gen_work = nullptr;
@@ -1217,6 +1225,8 @@ mm_status attempt_finish(mm_ctx* ctx, double* err) {
 mm_status conclude_attempt(mm_ctx* ctx, double* dt_io, double err, bool* accepted) {
   double dt = *dt_io;
   const bool accept = !ctx->opt.adaptive || err <= ctx->opt.rtol || dt <= ctx->opt.dt_min;
+  if (ctx->attempts.size() >= (size_t)kAttemptLog) ctx->attempts.pop_front();
+  ctx->attempts.push_back({ctx->host_mech.t, dt, err, accept ? 1 : 0});
   double fac = 5.0;
   if (err > 0.0) fac = std::min(5.0, std::max(0.2, 0.9 * pow(ctx->opt.rtol / err, 0.2)));
   if (accept) {
@@ -1948,6 +1958,28 @@ mm_status mm_assign_lanes(const double* cost, int npairs, int nlanes, int* lane_
     lane_out[i] = best;
     load[best] += cost[i];
   }
+  return MM_OK;
+}
+
+mm_status mm_get_attempt_log(mm_ctx* ctx, int capacity, double* t_out, double* dt_out, double* err_out,
+                             int* accepted_out, int* n_out) {
+  if (!ctx || !n_out || capacity < 0) return ctx ? fail(ctx, MM_EINVAL, "mm_get_attempt_log") : MM_EINVAL;
+  const int have = (int)ctx->attempts.size();
+  const int n = std::min(capacity, have);
+  for (int i = 0; i < n; ++i) {
+    const auto& a = ctx->attempts[(size_t)(have - n + i)];
+    if (t_out) t_out[i] = a.t;
+    if (dt_out) dt_out[i] = a.dt;
+    if (err_out) err_out[i] = a.err;
+    if (accepted_out) accepted_out[i] = a.accepted;
+  }
+  *n_out = n;
+  return MM_OK;
+}
+
+mm_status mm_clear_attempt_log(mm_ctx* ctx) {
+  if (!ctx) return MM_EINVAL;
+  ctx->attempts.clear();
   return MM_OK;
 }
 

@@ -14,24 +14,9 @@ def rel_l2(a, b):
 def gpu_pair(fp, m0, m1, margin=4, adaptive=False, rtol=1e-5, mech=True, stream=None):
     """MovingMagnets context for a workloads.FilmPair with the given unit m arrays,
     on `stream` (a torch.cuda.Stream; default: the current stream)."""
-    import torch
-    from paper_1801_04181_gb300 import MovingMagnets
+    from paper_1801_04181_gb300 import pair_context
 
-    st = stream if stream is not None else torch.cuda.current_stream()
-    mm = MovingMagnets(margin=margin, adaptive=adaptive, rtol=rtol, stream=st)
-    for g, (n, mat, m) in enumerate(((fp.n_base, fp.mat_base, m0), (fp.n_slider, fp.mat_slider, m1))):
-        mm.set_grid(g, n, fp.cell, fp.offsets[g])
-        mm.set_material(g, mat.Ms, mat.Aex, mat.Ku, mat.ku_axis, mat.alpha)
-        # the tensor is made on the context's stream, which the library's copy follows
-        with torch.cuda.stream(st):
-            mt = torch.as_tensor(np.ascontiguousarray(m), dtype=torch.float32, device="cuda")
-        mm.set_magnetization(g, mt)
-    mm.set_external_field(fp.H_ext)
-    if mech:
-        me = fp.mech
-        mm.set_mechanics(me.mass, me.k, me.v_drive, me.gamma_v, me.dir, me.x0_spring)
-    mm.set_displacement(tuple(u * c for u, c in zip(fp.u0, fp.cell)))
-    return mm
+    return pair_context(fp, m0, m1, margin=margin, adaptive=adaptive, rtol=rtol, mech=mech, stream=stream)
 
 
 def oracle_system(fp):
@@ -42,39 +27,11 @@ def oracle_system(fp):
                   H_ext=fp.H_ext)
 
 
-def _S_chunk(args):
-    from oracle.kernels import S_kernel
-    X, Y, Z, cell = args
-    return S_kernel(X, Y, Z, *cell)
-
-
-def _N_chunk(args):
-    from oracle.kernels import N_kernel
-    X, Y, Z, cell = args
-    return N_kernel(X, Y, Z, *cell)
-
-
-def _window(fun, lo, length, cell, pool):
-    dx, dy, dz = cell
-    jobs = []
-    for iz in range(length[2]):
-        Y, X = np.meshgrid(np.arange(length[1]) + lo[1], np.arange(length[0]) + lo[0], indexing="ij")
-        Z = np.full_like(X, iz + lo[2])
-        jobs.append((X * dx, Y * dy, Z * dz, cell))
-    return np.stack(pool.map(fun, jobs))
-
-
 def oracle_kernel_windows(n_s, cell, box_lo, box_dims, pool):
-    """The oracle's S window of a box and N window of a source grid, one z plane per pool task.
+    """The oracle's S window of a box and N window of a source grid, in parallel."""
+    from oracle.fields import kernel_windows_pooled
 
-    Same values as oracle.fields.potential_kernel_window / demag_kernel_window,
-    computed in parallel; pass a multiprocessing pool made with 'spawn'.
-    """
-    d_lo = [box_lo[a] - (n_s[a] - 1) for a in range(3)]
-    d_len = [box_dims[a] + n_s[a] - 1 for a in range(3)]
-    S = _window(_S_chunk, d_lo, d_len, cell, pool)
-    N = _window(_N_chunk, [-(n - 1) for n in n_s], [2 * n - 1 for n in n_s], cell, pool)
-    return S, N
+    return kernel_windows_pooled(n_s, cell, box_lo, box_dims, pool)
 
 
 def force_scale(hess_n, M_t, cell):

@@ -229,6 +229,75 @@ def test_adaptive_steps_accept_and_stay_normalised():
     mm.close()
 
 
+def test_adaptive_attempts_match_oracle():
+    """Adaptive Dormand-Prince steps of shrunk stick-slip films, attempt by
+    attempt, with a first step far too large (so the controller rejects and
+    shrinks it):
+      * replay: the oracle steps from the same state with the GPU's dt of each
+        attempt; the error norms agree within TOL times the size of the terms
+        that cancel in them (dt sum_j |b5_j - b4_j| max |k_j|, the reading of
+        the force tolerance applied to the error estimate) and the accept /
+        reject decisions are identical wherever err is not within that
+        tolerance of rtol;
+      * run_adaptive from the same start: the same decisions, and step sizes
+        within 1e-3 relative (dt is 0.9 (rtol/err)^(1/5) times the last one,
+        so a relative error e of err moves the next dt by e/5 and nothing
+        accumulates);
+      * the accepted state (m of both films, x, v) against run_adaptive's."""
+    from oracle import dynamics as D
+    from tests.pair_setup import oracle_system
+
+    fp, m0, m1 = workloads.film_pair_stick_slip(n=(40, 24, 2), gap=5, seed=21)
+    fp.u0 = (0.3, 0.0, 0.0)
+    fp.mech.x0_spring = 2e-9
+    fp.mech.v_drive = 50.0
+    # about four times the step the controller settles to (~1e-12 s): err ~ 4^5
+    # rtol, so the attempt is rejected while the stage values stay bounded (a
+    # step of 1e-11 s blows the stage magnetisation up, and with it the force
+    # on the slider, which then leaves the planned box: MM_ERANGE)
+    rtol, dt0, nacc = 1e-5, 4e-12, 6
+    mm = gpu_pair(fp, m0, m1, adaptive=True, rtol=rtol)
+    mm.clear_attempt_log()
+    t_gpu, dt_gpu = mm.step(nacc, dt0)
+    log = mm.attempt_log()
+    assert sum(a["accepted"] for a in log) == nacc
+    assert not log[0]["accepted"], "the first attempt should be rejected"
+    x_gpu, v_gpu, _ = mm.get_slider_state()
+    got = [mm.get_magnetization(g).double().cpu().numpy() for g in (0, 1)]
+    mm.close()
+
+    sysm = oracle_system(fp)
+    sum_db = sum(abs(b5 - b4) for b5, b4 in zip(D.DP_B5, D.DP_B4))
+    # replay at the GPU's step sizes
+    t, y, k1 = 0.0, [m0, m1, 0.0, 0.0], None
+    for a in log:
+        assert abs(a["t"] - t) <= 1e-12 * max(t, 1e-30)
+        y5, y4, ks = D.dp45_embedded(sysm, t, y, a["dt"], k1)
+        err = max(float(np.max(np.abs(y5[i] - y4[i]))) for i in (0, 1))
+        kmax = max(float(np.max(np.abs(k[i]))) for k in ks for i in (0, 1))
+        tol = TOL * a["dt"] * sum_db * kmax
+        assert abs(a["err"] - err) <= tol, (a, err, tol)
+        if abs(err - rtol) > tol:
+            assert a["accepted"] == (err <= rtol), (a, err)
+        if a["accepted"]:
+            y = [D.normalise(y5[0]), D.normalise(y5[1]), y5[2], y5[3]]
+            t += a["dt"]
+            k1 = ks[6]
+    # the oracle's own adaptive run from the same start
+    trace = []
+    t_ref, y_ref, dt_ref, acc, rej = D.run_adaptive(sysm, [m0, m1, 0.0, 0.0], dt0, nacc, rtol, trace=trace)
+    assert len(trace) == len(log)
+    for a, b in zip(log, trace):
+        assert a["accepted"] == b["accepted"]
+        assert abs(a["dt"] - b["dt"]) <= 1e-3 * b["dt"]
+    assert abs(dt_gpu - dt_ref) <= 1e-3 * dt_ref
+    assert abs(t_gpu - t_ref) <= 1e-3 * t_ref
+    for g in (0, 1):
+        assert rel_l2(got[g], y_ref[g]) < 1e-4
+    assert abs(x_gpu - y_ref[2]) <= 1e-3 * abs(y_ref[2])
+    assert abs(v_gpu - y_ref[3]) <= 1e-3 * abs(y_ref[3])
+
+
 def test_bad_arguments_are_rejected():
     from paper_1801_04181_gb300 import MMError, MovingMagnets
 
