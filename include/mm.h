@@ -50,6 +50,8 @@ typedef enum {
 
 enum { MM_FP32 = 0 };
 
+enum { MM_PERIODIC_X = 1, MM_PERIODIC_Y = 2 };
+
 typedef struct {
   int precision;     /* MM_FP32 */
   int margin;        /* potential box margin in cells beyond the spline support (Sec. III.A: 4) */
@@ -57,9 +59,26 @@ typedef struct {
   double rtol;       /* adaptive: accepted max-norm error of m per step */
   double dt_min, dt_max;
   void* stream;      /* cudaStream_t */
+  /*
+   * Periodic in-plane boundaries (Sec. III: the extension supports periodic
+   * boundary conditions; Sec. IV.B runs the friction films periodic in the
+   * film plane): MM_PERIODIC_X | MM_PERIODIC_Y, 0 = open.  Along a periodic
+   * axis both magnets must span one period (equal nx, resp. ny; even, and of
+   * the form 2^a 3^b 5^c); the kernels are summed over (2 pbc_images + 1)
+   * periodic images per periodic axis (the Nyquist offset of the period
+   * averaged over its two truncations), the convolutions are circular over
+   * the period, the potential covers the whole period with a periodic cubic
+   * B-spline (Sec. III.A: its margin values are the other side's), the
+   * interpolation and the exchange field wrap around.  z stays open.  Not with
+   * sources of more than 8 layers, the energy gradients or the comparison
+   * variants (MM_ENOTSUP).
+   */
+  int periodic;
+  int pbc_images;    /* images on each side of the period, 0 .. 64 */
 } mm_options;
 
-/* Defaults: FP32, margin 4, adaptive, rtol 1e-5, dt in [1e-16, 1e-11] s, default stream. */
+/* Defaults: FP32, margin 4, adaptive, rtol 1e-5, dt in [1e-16, 1e-11] s, default stream,
+ * open boundaries (periodic 0, pbc_images 2). */
 void mm_default_options(mm_options* opt);
 
 /* Context.  Does not allocate device memory until a grid is planned. */
@@ -72,9 +91,10 @@ const char* mm_status_string(mm_status s);
  * Grid of magnet `mag` (0 base, 1 slider): nx x ny x nz cuboid cells of size
  * dx x dy x dz metres (Sec. II: uniform M per cell at its centre) with lattice
  * offset `offset_cells` (x, y, z).  Both magnets must use the same cell size.
- * Sources with nz <= 4 take z by a direct sum over planes (thin films);
- * thicker sources, or sources whose box around a thick target is tall, take z
- * by FFT (Sec. III.A on a three-dimensional grid).  Grids whose FFT lines do
+ * Every source of up to 8 layers takes z by a direct sum over planes: inside
+ * the fused y pass when both magnets have at most 4 layers (thin films), else
+ * in a pass of its own between a y-forward and a y-inverse pass.  Sources of
+ * more than 8 layers take z by FFT (Sec. III.A on a three-dimensional grid).  Grids whose FFT lines do
  * not fit one shared-memory pass return MM_ENOTSUP when planned, and so do
  * magnets of more than 2^30 cells (here).
  */
@@ -250,6 +270,19 @@ mm_status mm_get_power(mm_ctx* ctx, double* P_in, double P_diss[2], double* P_vi
  * otherwise).  No force or energy.
  */
 mm_status mm_compute_stray_field_fd4(mm_ctx* ctx, int src, float* H_dev);
+
+/*
+ * Comparison variant (Sec. II.A: the demagnetising field "can be interpolated
+ * in two ways"; this is the direct one, which Sec. IV.A compares with the
+ * potential method): the stray field of `src` at the other magnet's displaced
+ * cell centres by cubic B-spline interpolation of each component of the field
+ * of the tensor method, H_a(n) = -sum_j sum_b N_ab(n - j) M_b(j) (N the
+ * cell-averaged demagnetising tensor of the self-demag field), computed on the
+ * nodes of the same box as the potential and prefiltered with mirror ends,
+ * 64 taps per component.  H_dev: 3 N_target floats (A/m).  No force or
+ * energy.  Sources of more than 8 layers (z by FFT): MM_ENOTSUP.
+ */
+mm_status mm_compute_stray_field_componentwise(mm_ctx* ctx, int src, float* H_dev);
 
 /*
  * Divergence and curl diagnostics of a field (Sec. IV.A): for H_dev (3 N

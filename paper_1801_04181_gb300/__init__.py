@@ -40,10 +40,15 @@ def _need_cuda_f32(t, shape=None):
 class MovingMagnets:
     """Two magnets (0 base, 1 slider) and the slider's motion; one libmm context."""
 
-    def __init__(self, margin=4, adaptive=True, rtol=1e-5, dt_min=1e-16, dt_max=1e-11, stream=None):
+    def __init__(self, margin=4, adaptive=True, rtol=1e-5, dt_min=1e-16, dt_max=1e-11, stream=None,
+                 periodic=0, pbc_images=2):
+        """periodic: 0 (open), or MM_PERIODIC_X | MM_PERIODIC_Y (1, 2, 3) with
+        pbc_images periodic images on each side."""
         self.lib = _native.load()
         opt = mm_options()
         self.lib.mm_default_options(C.byref(opt))
+        opt.periodic = int(periodic)
+        opt.pbc_images = int(pbc_images)
         opt.margin = margin
         opt.adaptive = 1 if adaptive else 0
         opt.rtol = rtol
@@ -157,6 +162,14 @@ class MovingMagnets:
         H = torch.empty(self.shapes[1 - src], dtype=torch.float32, device="cuda")
         self._in()
         self._c(self.lib.mm_compute_stray_field_fd4(self.ctx, src, _ptr(H)))
+        return self._out(H)
+
+    def compute_stray_field_componentwise(self, src):
+        """mm_compute_stray_field_componentwise: the stray field by direct
+        componentwise interpolation of the tensor field (comparison variant)."""
+        H = torch.empty(self.shapes[1 - src], dtype=torch.float32, device="cuda")
+        self._in()
+        self._c(self.lib.mm_compute_stray_field_componentwise(self.ctx, src, _ptr(H)))
         return self._out(H)
 
     def compute_demag(self, mag):

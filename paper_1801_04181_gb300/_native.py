@@ -13,10 +13,13 @@ MM_OK, MM_EINVAL, MM_ENOMEM, MM_ECUDA, MM_ERANGE, MM_ETIMEOUT, MM_ESTATE, MM_ENO
 MM_ETOOBIG = -8
 
 
+MM_PERIODIC_X, MM_PERIODIC_Y = 1, 2
+
+
 class mm_options(C.Structure):
     _fields_ = [("precision", C.c_int), ("margin", C.c_int), ("adaptive", C.c_int),
                 ("rtol", C.c_double), ("dt_min", C.c_double), ("dt_max", C.c_double),
-                ("stream", C.c_void_p)]
+                ("stream", C.c_void_p), ("periodic", C.c_int), ("pbc_images", C.c_int)]
 
 
 _d3 = C.c_double * 3
@@ -60,6 +63,7 @@ SIGNATURES = [
     ("mm_assign_lanes", C.c_int, [C.POINTER(C.c_double), C.c_int, C.c_int, C.POINTER(C.c_int)]),
     ("mm_get_power", C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     ("mm_compute_stray_field_fd4", C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    ("mm_compute_stray_field_componentwise", C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     ("mm_field_div_curl", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
                                     C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     ("mm_get_step_stats", C.c_int, [C.c_void_p, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),

@@ -69,6 +69,7 @@ struct Dir {
   int box_lo[3] = {0, 0, 0}, box_len[3] = {0, 0, 0};
   int start[3] = {0, 0, 0}, r[3] = {0, 0, 0}, guard[3] = {0, 0, 0};
   int Tq_box_lo_z = 0, Tq_bz = 0, Tq_start_z = 0, Tq_nout = 0, Tq_prefilter = -1, Tq_Q[2] = {0, 0};
+  int Tq_kind = 0;             // 0: S (potential); 1: rows of -N (componentwise field variant)
   float* Tq = nullptr;
   float2* YC = nullptr;
   float* C = nullptr;
@@ -127,6 +128,9 @@ struct Magnet {
   double adj_Ms = 0;
   Dir dir;   // hot path: coefficients around the other magnet
   Dir aux;   // mm_compute_potential output
+  Dir cw;    // componentwise field variant: three coefficient boxes
+  float2* cw_Y = nullptr;  // its y-forward spectra [3 nz][kxh][Qy]
+  size_t cw_Y_bytes = 0;
 };
 
 struct TimedLaunch {
@@ -358,7 +362,8 @@ std::vector<int> plan_radices(int L) {
 }
 
 mm_status get_fft(mm_ctx* ctx, int L, FftTables* out) {
-  auto it = ctx->ffts.find(L);
+  const int key = L;
+  auto it = ctx->ffts.find(key);
   if (it != ctx->ffts.end()) {
     *out = it->second.t;
     return MM_OK;
@@ -432,7 +437,7 @@ mm_status get_fft(mm_ctx* ctx, int L, FftTables* out) {
   R.t.tw_d = R.tw_d;
   R.t.pos = R.pos;
   R.t.freq = R.freq;
-  ctx->ffts[L] = R;
+  ctx->ffts[key] = R;
   *out = R.t;
   return MM_OK;
 }
@@ -502,6 +507,19 @@ int host_mirror(int j, int b) {
   return j < b ? j : P - j;
 }
 
+// x (a = 0) or y (a = 1) periodic (mm_options.periodic); z never
+bool periodic_axis(const mm_ctx* ctx, int a) {
+  return a < 2 && (ctx->opt.periodic & (1 << a)) != 0;
+}
+
+KernelPlan kernel_plan(const mm_ctx* ctx, const Magnet& S) {
+  KernelPlan K{S.Qx, S.Qy, S.Wx, S.Wy, S.nz};
+  K.px = periodic_axis(ctx, 0) ? 1 : 0;
+  K.py = periodic_axis(ctx, 1) ? 1 : 0;
+  K.R = ctx->opt.pbc_images;
+  return K;
+}
+
 void dir_geometry(const mm_ctx* ctx, int s, bool full_box, Dir* D) {
   const int t = 1 - s;
   const Magnet& S = ctx->mag[s];
@@ -513,6 +531,17 @@ void dir_geometry(const mm_ctx* ctx, int s, bool full_box, Dir* D) {
     const double su = sigma * u_cells(ctx, a, ctx->host_mech.x);
     const int U = (int)floor(su);
     D->U0[a] = U;
+    if (periodic_axis(ctx, a)) {
+      // the potential lives on every node of the period (Sec. III.A: the
+      // margin beyond the domain is the other side's values)
+      const int P = a == 0 ? S.nx : S.ny;
+      D->box_lo[a] = 0;
+      D->box_len[a] = P;
+      D->guard[a] = 0;
+      D->start[a] = 0;
+      D->r[a] = P;
+      continue;
+    }
     const long long Dd = T.off[a] - S.off[a];
     D->box_lo[a] = (int)(Dd + U - 1 - m);
     D->box_len[a] = nt[a] + 3 + 2 * m;
@@ -537,19 +566,22 @@ int window_needed(const Magnet& S, const Dir& D, int a) {
   return w;
 }
 
-mm_status build_T(mm_ctx* ctx, int s, Dir* D) {
+// kind 0: the W-folded S spectra of the potential (Tq [n_out][nz][3]);
+// kind 1: the W-folded rows of -N of the componentwise field variant
+// (Tq [3][n_out][nz][3]).
+mm_status build_T(mm_ctx* ctx, int s, Dir* D, int kind = 0) {
   Magnet& S = ctx->mag[s];
   const int n_out = D->r[2];
   const int bz = D->box_len[2];
   if (D->Tq && D->Tq_box_lo_z == D->box_lo[2] && D->Tq_bz == bz && D->Tq_start_z == D->start[2] &&
       D->Tq_nout == n_out && D->Tq_prefilter == D->prefilter && D->Tq_Q[0] == S.Qx &&
-      D->Tq_Q[1] == S.Qy)
+      D->Tq_Q[1] == S.Qy && D->Tq_kind == kind)
     return MM_OK;
   FftTables fx, fy;
   CKS(get_fft(ctx, S.Qx, &fx));
   CKS(get_fft(ctx, S.Qy, &fy));
   const size_t qsize = (size_t)S.kxh * S.kyq;
-  CKS(ensure_buf(ctx, &D->Tq, &D->Tq_bytes, sizeof(float) * (size_t)n_out * S.nz * 3 * qsize));
+  CKS(ensure_buf(ctx, &D->Tq, &D->Tq_bytes, sizeof(float) * (size_t)(kind ? 3 : 1) * n_out * S.nz * 3 * qsize));
   // z mixing matrix: rows = output planes, columns = box planes
   std::vector<double> W((size_t)n_out * bz, 0.0);
   double h[kFirHalf + 1];
@@ -567,11 +599,15 @@ mm_status build_T(mm_ctx* ctx, int s, Dir* D) {
   const size_t plane = (size_t)S.Qx * S.Qy;
   CKS(ensure_buf(ctx, &ctx->gen_work, &ctx->gen_work_bytes, sizeof(double2) * 2 * 6 * plane));
   const int nplanes = bz + S.nz - 1;
-  CKS(ensure_buf(ctx, &ctx->gen_q, &ctx->gen_q_bytes, sizeof(double) * (size_t)nplanes * 3 * qsize));
-  KernelPlan K{S.Qx, S.Qy, S.Wx, S.Wy, S.nz};
+  CKS(ensure_buf(ctx, &ctx->gen_q, &ctx->gen_q_bytes, sizeof(double) * (size_t)nplanes * (kind ? 6 : 3) * qsize));
+  const KernelPlan K = kernel_plan(ctx, S);
   const double scale = S.Ms / ((double)S.Qx * S.Qy);
-  CK(build_T_spectra(K, fx, fy, S.d[0], S.d[1], S.d[2], scale, D->box_lo[2], bz, n_out, ctx->W_dev, D->Tq,
-                     ctx->gen_work, ctx->gen_q, ctx->st));
+  if (kind == 0)
+    CK(build_T_spectra(K, fx, fy, S.d[0], S.d[1], S.d[2], scale, D->box_lo[2], bz, n_out, ctx->W_dev, D->Tq,
+                       ctx->gen_work, ctx->gen_q, ctx->st));
+  else  // H = -N M
+    CK(build_TN_spectra(K, fx, fy, S.d[0], S.d[1], S.d[2], -scale, D->box_lo[2], bz, n_out, ctx->W_dev, D->Tq,
+                        ctx->gen_work, ctx->gen_q, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));  // W_dev / scratch reuse
   D->Tq_box_lo_z = D->box_lo[2];
   D->Tq_bz = bz;
@@ -580,6 +616,7 @@ mm_status build_T(mm_ctx* ctx, int s, Dir* D) {
   D->Tq_prefilter = D->prefilter;
   D->Tq_Q[0] = S.Qx;
   D->Tq_Q[1] = S.Qy;
+  D->Tq_kind = kind;
   return MM_OK;
 }
 
@@ -642,6 +679,15 @@ mm_status ensure_plan(mm_ctx* ctx) {
     if (!ctx->mag[g].grid) return fail(ctx, MM_EINVAL, "grid of magnet " + std::to_string(g) + " not set");
     if (!ctx->mag[g].mat) return fail(ctx, MM_EINVAL, "material of magnet " + std::to_string(g) + " not set");
   }
+  for (int a = 0; a < 2; ++a) {
+    if (!periodic_axis(ctx, a)) continue;
+    const int n0 = a == 0 ? ctx->mag[0].nx : ctx->mag[0].ny;
+    const int n1 = a == 0 ? ctx->mag[1].nx : ctx->mag[1].ny;
+    if (n0 != n1)
+      return fail(ctx, MM_EINVAL, "periodic boundaries: both magnets must span the period (equal nx / ny)");
+    if (n0 % 2 || smooth_even_at_least(n0) != n0)
+      return fail(ctx, MM_ENOTSUP, "periodic boundaries: the period must be even and 2^a 3^b 5^c cells");
+  }
   for (int s = 0; s < 2; ++s) {
     Magnet& S = ctx->mag[s];
     Dir& D = S.dir;
@@ -651,17 +697,23 @@ mm_status ensure_plan(mm_ctx* ctx) {
     // target is tall; z by FFT only for sources thicker than kMaxNzDirect
     const bool thick = S.nz > kMaxNz || ctx->mag[1 - s].nz > kMaxNz;
     const bool zfft = thick && S.nz > kMaxNzDirect;
+    if (zfft && ctx->opt.periodic)
+      return fail(ctx, MM_ENOTSUP, "periodic boundaries: sources of more than 8 layers");
+    const bool px = periodic_axis(ctx, 0), py = periodic_axis(ctx, 1);
     const int wx = window_needed(S, D, 0), wy = window_needed(S, D, 1), wz = window_needed(S, D, 2);
-    const bool regrid = S.Qx == 0 || 2 * wx + 2 > S.Qx || 2 * wy + 2 > S.Qy || thick != S.thick ||
+    // a periodic axis: the circular grid is the period itself
+    const bool regrid = S.Qx == 0 || (px ? S.Qx != S.nx : 2 * wx + 2 > S.Qx) ||
+                        (py ? S.Qy != S.ny : 2 * wy + 2 > S.Qy) || thick != S.thick ||
                         zfft != S.zfft || (zfft && 2 * wz + 2 > S.Qz);
     if (regrid) {
       S.thick = thick;
       S.zfft = zfft;
       S.Wx = wx + kWindowSlack;
       S.Wy = wy + kWindowSlack;
-      S.Qx = smooth_even_at_least(2 * S.Wx + 2);
-      S.Qy = smooth_even_at_least(2 * S.Wy + 2);
+      S.Qx = px ? S.nx : smooth_even_at_least(2 * S.Wx + 2);
+      S.Qy = py ? S.ny : smooth_even_at_least(2 * S.Wy + 2);
       // keep the window inside the grid: the largest W with 2W + 2 <= Q
+      // (periodic axes ignore it: every offset of the period counts)
       S.Wx = (S.Qx - 2) / 2;
       S.Wy = (S.Qy - 2) / 2;
       S.kxh = S.Qx / 2 + 1;
@@ -717,7 +769,7 @@ mm_status ensure_plan(mm_ctx* ctx) {
       if (!S.zfft) {
         CKS(ensure_buf(ctx, &ctx->gen_q, &ctx->gen_q_bytes,
                        std::max(ctx->gen_q_bytes, sizeof(double) * 6 * qsize)));
-        KernelPlan K{S.Qx, S.Qy, S.Wx, S.Wy, S.nz};
+        const KernelPlan K = kernel_plan(ctx, S);
         CK(build_N_spectra(K, fx, fy, S.d[0], S.d[1], S.d[2], -S.Ms / ((double)S.Qx * S.Qy), S.Nq,
                            ctx->gen_work, ctx->gen_q, ctx->st));
       } else {
@@ -741,6 +793,7 @@ mm_status replan_if_needed(mm_ctx* ctx) {
     const Dir& D = ctx->mag[s].dir;
     const double sigma = s == 0 ? 1.0 : -1.0;
     for (int a = 0; a < 3; ++a) {
+      if (periodic_axis(ctx, a)) continue;  // the box is the whole period
       const int U = (int)floor(sigma * u_cells(ctx, a, ctx->host_mech.x));
       if (U != D.U0[a]) return ensure_plan(ctx);
     }
@@ -823,6 +876,7 @@ mm_status run_source_passes(mm_ctx* ctx, const float* in[2], const int* which, i
         J.start = D->start[1];
         J.r = D->r[1];
         J.fir = D->prefilter;
+        J.periodic = periodic_axis(ctx, 1) ? 1 : 0;
       }
       const int Pout = (J.do_H ? 3 * S.nz : 0) + (J.do_C ? J.n_out : 0);
       const int P = std::max(3 * S.nz, Pout);
@@ -908,6 +962,7 @@ mm_status run_source_passes(mm_ctx* ctx, const float* in[2], const int* which, i
         J.is_C = 1; J.outC = D->YC;
         J.box_lo = D->box_lo[1]; J.box_len = D->box_len[1]; J.start = D->start[1]; J.r = D->r[1];
         J.fir = D->prefilter;
+        J.periodic = periodic_axis(ctx, 1) ? 1 : 0;
         Li.tile_start[ni] = ti;
         ti += S.kxh * ((J.planes + group - 1) / group);
         ++ni;
@@ -961,6 +1016,7 @@ mm_status run_source_passes(mm_ctx* ctx, const float* in[2], const int* which, i
         J.fx = fx;
         J.box_lo = D->box_lo[0]; J.box_len = D->box_len[0]; J.start = D->start[0];
         J.out_len = D->r[0]; J.fir = D->prefilter;
+        J.periodic = periodic_axis(ctx, 0) ? 1 : 0;
         L.tile_start[nj] = tiles;
         tiles += (J.planes * J.rows_per_plane + kRowsPerCta - 1) / kRowsPerCta;
         ++nj;
@@ -994,6 +1050,13 @@ GatherJob gather_job(mm_ctx* ctx, int s, const float* m_t, float* H) {
   J.H = H;
   J.partial = D.partial;
   J.err = ctx->err_flag;
+  for (int a = 0; a < 2; ++a)
+    if (periodic_axis(ctx, a)) {
+      const int P = a == 0 ? S.nx : S.ny;
+      J.wrapP[a] = P;
+      // first tap of target cell 0: source node (T.off - S.off) + floor(sigma u) - 1
+      J.tap0[a] = (int)(((T.off[a] - S.off[a] - 1) % P + P) % P);
+    }
   return J;
 }
 
@@ -1107,6 +1170,8 @@ StageJob stage_job(mm_ctx* ctx, int g, const float* ys, float* ys_next, int stag
   J.Hstray = M.Hstray;
   J.Heff = Heff;
   J.nx = M.nx; J.ny = M.ny; J.nz = M.nz;
+  J.wrap[0] = periodic_axis(ctx, 0) ? 1 : 0;
+  J.wrap[1] = periodic_axis(ctx, 1) ? 1 : 0;
   for (int a = 0; a < 3; ++a) {
     J.ex[a] = (float)(2.0 * M.Aex / (kMu0 * M.Ms * M.d[a] * M.d[a]));
     J.hext[a] = (float)ctx->Hext[a];
@@ -1261,6 +1326,7 @@ mm_status conclude_attempt(mm_ctx* ctx, double* dt_io, double err, bool* accepte
     bool moved = false;
     for (int s = 0; s < 2 && !moved; ++s)
       for (int a = 0; a < 3; ++a) {
+        if (periodic_axis(ctx, a)) continue;
         const double sigma = s == 0 ? 1.0 : -1.0;
         if ((int)floor(sigma * u_cells(ctx, a, ctx->host_mech.x)) != ctx->mag[s].dir.U0[a]) moved = true;
       }
@@ -1292,6 +1358,8 @@ void mm_default_options(mm_options* o) {
   o->dt_min = 1e-16;
   o->dt_max = 1e-11;
   o->stream = nullptr;
+  o->periodic = 0;
+  o->pbc_images = 2;
 }
 
 const char* mm_status_string(mm_status s) {
@@ -1319,7 +1387,8 @@ mm_status mm_create(mm_ctx** out, const mm_options* opt) {
     delete ctx;
     return MM_ENOTSUP;
   }
-  if (ctx->opt.margin < 0 || ctx->opt.margin > 64) {
+  if (ctx->opt.margin < 0 || ctx->opt.margin > 64 || ctx->opt.periodic < 0 || ctx->opt.periodic > 3 ||
+      ctx->opt.pbc_images < 0 || ctx->opt.pbc_images > 64) {
     delete ctx;
     return MM_EINVAL;
   }
@@ -1369,6 +1438,8 @@ void mm_destroy(mm_ctx* ctx) {
     cudaFree(M.adj_YH); cudaFree(M.adj_Sq);
     free_dir(M.dir);
     free_dir(M.aux);
+    free_dir(M.cw);
+    cudaFree(M.cw_Y);
   }
   for (auto& kv : ctx->ffts) {
     cudaFree(kv.second.tw_f); cudaFree(kv.second.tw_d); cudaFree(kv.second.pos); cudaFree(kv.second.freq);
@@ -1551,6 +1622,7 @@ mm_status mm_compute_stray_field(mm_ctx* ctx, int src, float* H_dev) {
 
 mm_status mm_backward_energy(mm_ctx* ctx, int src, double dE_du[3], float* dE_dm_src_dev,
                              float* dE_dm_tgt_dev) {
+  if (ctx && ctx->opt.periodic) return fail(ctx, MM_ENOTSUP, "mm_backward_energy: periodic boundaries");
   if (!ctx || bad_mag(src)) return ctx ? fail(ctx, MM_EINVAL, "mm_backward_energy") : MM_EINVAL;
   // forward: potential box, stray field at the target, force and energy
   CKS(mm_compute_stray_field(ctx, src, nullptr));
@@ -1804,6 +1876,7 @@ mm_status mm_get_power(mm_ctx* ctx, double* P_in, double P_diss[2], double* P_vi
 }
 
 mm_status mm_compute_stray_field_fd4(mm_ctx* ctx, int src, float* H_dev) {
+  if (ctx && ctx->opt.periodic) return fail(ctx, MM_ENOTSUP, "mm_compute_stray_field_fd4: periodic boundaries");
   if (!ctx || bad_mag(src) || !H_dev) return ctx ? fail(ctx, MM_EINVAL, "mm_compute_stray_field_fd4") : MM_EINVAL;
   if (ctx->opt.margin < 2) return fail(ctx, MM_ENOTSUP, "mm_compute_stray_field_fd4: needs a margin of 2 or more");
   int dims[3];
@@ -1823,6 +1896,98 @@ mm_status mm_compute_stray_field_fd4(mm_ctx* ctx, int src, float* H_dev) {
     frac[a] = su - floor(su);
   }
   CK(launch_fd4_field(ctx->fd4_C, dims, nt, ctx->opt.margin, frac, T.d, ctx->fd4_V, H_dev, ctx->st));
+  return MM_OK;
+}
+
+mm_status mm_compute_stray_field_componentwise(mm_ctx* ctx, int src, float* H_dev) {
+  if (ctx && ctx->opt.periodic)
+    return fail(ctx, MM_ENOTSUP, "mm_compute_stray_field_componentwise: periodic boundaries");
+  if (!ctx || bad_mag(src) || !H_dev)
+    return ctx ? fail(ctx, MM_EINVAL, "mm_compute_stray_field_componentwise") : MM_EINVAL;
+  if (!ctx->mag[0].grid || !ctx->mag[1].grid) return fail(ctx, MM_EINVAL, "grids not set");
+  if (!ctx->mag[0].mat || !ctx->mag[1].mat) return fail(ctx, MM_EINVAL, "materials not set");
+  CKS(replan_if_needed(ctx));
+  Magnet& S = ctx->mag[src];
+  const Magnet& T = ctx->mag[1 - src];
+  if (!S.mset) return fail(ctx, MM_EINVAL, "magnetisation not set");
+  if (S.zfft)
+    return fail(ctx, MM_ENOTSUP, "mm_compute_stray_field_componentwise: sources of more than 8 layers");
+  cudaStream_t st = ctx->st;
+  Dir& D = S.cw;
+  dir_geometry(ctx, src, true, &D);
+  D.prefilter = 1;
+  const int nb = D.r[2];  // every box plane
+  const int P3 = 3 * S.nz, PC = 3 * nb;
+  CKS(build_T(ctx, src, &D, 1));
+  CKS(ensure_buf(ctx, &S.cw_Y, &S.cw_Y_bytes, sizeof(float2) * (size_t)P3 * S.kxh * S.Qy));
+  CKS(ensure_buf(ctx, &D.Z3C, &D.Z3C_bytes, sizeof(float2) * (size_t)PC * S.kxh * S.Qy));
+  CKS(ensure_buf(ctx, &D.YC, &D.YC_bytes, sizeof(float2) * (size_t)PC * S.kxh * D.r[1]));
+  CKS(ensure_buf(ctx, &D.C, &D.C_bytes, sizeof(float) * (size_t)PC * D.r[1] * D.r[0]));
+  FftTables fy;
+  CKS(get_fft(ctx, S.Qy, &fy));
+  CKS(join_mech(ctx));
+  const float* in[2] = {ctx->mag[0].m, ctx->mag[1].m};
+  const int which[1] = {src};
+  int Qmax = 0;
+  {
+    Launch<XFwdJob> L = xfwd_launch(ctx, in, which, 1, &Qmax);
+    Timer t(ctx, 0);
+    CK(launch_xfwd(L, Qmax, st));
+  }
+  const int group = std::max(1, std::min(16, (int)((48 * 1024) / ((S.Qy + 1) * sizeof(float2)))));
+  {
+    Launch<YFwdJob> L{};
+    L.njobs = 1;
+    YFwdJob& F = L.job[0];
+    F.in = S.X1; F.out = S.cw_Y; F.planes = P3; F.ny = S.ny; F.kxh = S.kxh; F.group = group; F.fy = fy;
+    F.natural = 1;
+    L.tile_start[1] = S.kxh * ((P3 + group - 1) / group);
+    Timer t(ctx, 7);
+    CK(launch_yfwd3(L, st));
+  }
+  {
+    Launch<ZMixJob> L{};
+    L.njobs = 1;
+    ZMixJob& M = L.job[0];
+    M.in = S.cw_Y; M.nz = S.nz; M.kxh = S.kxh; M.Qy = S.Qy; M.kyq = S.kyq;
+    M.Nq = S.Nq; M.Tq = D.Tq; M.nH = 0; M.n_out = PC; M.outH = nullptr; M.outC = D.Z3C;
+    M.field_nbox = nb;
+    L.tile_start[1] = S.kxh * zmix_tiles(S.kyq, PC);
+    Timer t(ctx, 8);
+    CK(launch_zmix3(L, st));
+  }
+  {
+    Launch<YInvJob> L{};
+    L.njobs = 1;
+    YInvJob& J = L.job[0];
+    J.in = D.Z3C; J.natural = 1; J.planes = PC; J.kxh = S.kxh; J.group = group; J.fy = fy;
+    J.is_C = 1; J.outC = D.YC;
+    J.box_lo = D.box_lo[1]; J.box_len = D.box_len[1]; J.start = D.start[1]; J.r = D.r[1]; J.fir = 1;
+    L.tile_start[1] = S.kxh * ((PC + group - 1) / group);
+    Timer t(ctx, 9);
+    CK(launch_yinv3(L, st));
+  }
+  {
+    Launch<XInvJob> L{};
+    L.njobs = 1;
+    XInvJob& J = L.job[0];
+    J.in = D.YC; J.out = D.C; J.planes = PC; J.rows_per_plane = D.r[1]; J.kxh = S.kxh;
+    CKS(get_fft(ctx, S.Qx, &J.fx));
+    J.box_lo = D.box_lo[0]; J.box_len = D.box_len[0]; J.start = D.start[0]; J.out_len = D.r[0]; J.fir = 1;
+    L.tile_start[1] = (PC * D.r[1] + kRowsPerCta - 1) / kRowsPerCta;
+    Timer t(ctx, 2);
+    CK(launch_xinv(L, S.Qx, st));
+  }
+  const double sigma = src == 0 ? 1.0 : -1.0;  // +1: the target is the slider
+  double frac[3];
+  for (int a = 0; a < 3; ++a) {
+    const double su = sigma * u_cells(ctx, a, ctx->host_mech.x);
+    frac[a] = su - floor(su);
+  }
+  const int bdim[3] = {D.r[0], D.r[1], nb};
+  const int nt[3] = {T.nx, T.ny, T.nz};
+  CK(launch_field_values(D.C, bdim, nt, ctx->opt.margin, frac, H_dev, st));
+  D.valid = false;
   return MM_OK;
 }
 

@@ -68,7 +68,7 @@ static inline cudaError_t upload_roots() {
   return e;
 }
 
-template <typename C> __device__ __forceinline__ C root(int j);  // exp(+2 pi i j / 240)
+template <typename C> __device__ __forceinline__ C root(int j);  // exp(+2 pi i j / kRootN)
 template <> __device__ __forceinline__ float2 root<float2>(int j) {
   return make_float2(c_root_f[0][j], c_root_f[1][j]);
 }
@@ -194,6 +194,7 @@ template <typename C> struct Dft<10, C> : DftPfa<2, 5, C> {};
 template <typename C> struct Dft<12, C> : DftPfa<4, 3, C> {};
 template <typename C> struct Dft<15, C> : DftPfa<3, 5, C> {};
 template <typename C> struct Dft<16, C> : DftComp<4, 4, C> {};
+
 
 // Stage twiddles w[k] = W_Lb^{n1 k}, k = 1..R-1: entry (k - 1) M + n1 of the
 // stage table, so the lanes of a warp (consecutive n1) read consecutive words.

@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(256, 3) k_yinv3(const Launch<YInvJob> Lc) {
   // leave natural order
   if (J.is_C)
     build_pref_table(tab, J.r + 2 * kPrefWarm + kYChunk, J.box_lo, J.box_len, J.start, Q,
-                     J.natural ? J.fy.pos : nullptr);
+                     J.natural ? J.fy.pos : nullptr, J.periodic != 0);
   __syncthreads();
   if (J.natural) fft_smem<kInvDif, float2, RSET>(sm, ldl, np, J.fy.plan, J.fy.tw_f, 0, blockDim.x);
   else fft_smem<kInvDit, float2, RSET>(sm, ldl, np, J.fy.plan, J.fy.tw_f, 0, blockDim.x);
@@ -322,16 +322,20 @@ __global__ void __launch_bounds__(kZMixThreads) k_zmix3(const Launch<ZMixJob> Lc
       dst[k] = acc0;
       if (two) dst[Qy - k] = acc1;
     } else {
-      // c(o) = sum_jz sum_c T_c(o, jz) m_c(jz); T_x, T_y imaginary, T_y odd in y
+      // c(o) = sum_jz sum_c T_c(o, jz) m_c(jz); T_x, T_y imaginary, T_y odd in y.
+      // Field variant: H_a(o) = sum_jz sum_c TN_ac(o, jz) m_c(jz), TN_ac from
+      // N_ac, imaginary when odd in x (xz, zx) or y (yz, zy), odd in y for xy, yx, yz, zy.
       const int oc = o - J.nH;
+      const int a = J.field_nbox > 0 ? oc / J.field_nbox : 2;  // row z of N has the parities of S
       for (int jz = 0; jz < nz; ++jz) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           const float v = __ldg(J.Tq + (size_t)((oc * nz + jz) * 3 + c) * kstride + koff);
           const float2 m0 = s0[(c * nz + jz) * kZMixChunk];
           const float2 m1 = s1[(c * nz + jz) * kZMixChunk];
-          const bool imag = c < 2;
-          const float2 p0 = zm_kmul(v, imag, m0), p1 = zm_kmul(c == 1 ? -v : v, imag, m1);
+          const bool imag = (a == 2) != (c == 2);
+          const bool odd_y = (a == 1) != (c == 1);
+          const float2 p0 = zm_kmul(v, imag, m0), p1 = zm_kmul(odd_y ? -v : v, imag, m1);
           acc0.x += p0.x; acc0.y += p0.y;
           acc1.x += p1.x; acc1.y += p1.y;
         }

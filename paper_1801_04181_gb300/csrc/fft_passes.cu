@@ -293,7 +293,8 @@ __global__ void __launch_bounds__(kYThreads, NZ <= 2 ? 3 : 2) k_ypass(const Laun
   for (int y = ny + threadIdx.x; y < Q; y += blockDim.x)
 #pragma unroll
     for (int p = 0; p < Pin; ++p) sm[p * Q + y] = make_float2(0.f, 0.f);
-  if (J.do_C) build_pref_table(tab, J.r + 2 * kPrefWarm + kYChunk, J.box_lo, J.box_len, J.start, Q, nullptr);
+  if (J.do_C)
+    build_pref_table(tab, J.r + 2 * kPrefWarm + kYChunk, J.box_lo, J.box_len, J.start, Q, nullptr, J.periodic != 0);
   __syncthreads();
   fft_smem<kFwdDif, float2, RSET>(sm, Q, Pin, J.fy.plan, J.fy.tw_f, 0, blockDim.x);
   ypass_mix<NZ>(J, sm, kx, Q, nH);
@@ -312,14 +313,25 @@ __global__ void __launch_bounds__(kYThreads, NZ <= 2 ? 3 : 2) k_ypass(const Laun
     const size_t ostride = (size_t)J.kxh * r;
     if (J.fir) {
       const int nch = (r + kYChunk - 1) / kYChunk;
+      // A thread runs the recursion over a chunk of consecutive outputs, so
+      // its stores stride by the chunk across a warp.  When the demag planes
+      // (already written out) leave room, the chunks land in their shared
+      // memory first and leave the CTA as whole coalesced rows.
+      const bool stage = nH > 0 && J.n_out * r <= nH * Q;
+      if (stage) __syncthreads();  // every demag plane has been read out
       for (int idx = threadIdx.x; idx < J.n_out * nch; idx += blockDim.x) {
         const int o = idx / nch;
         const int k0 = (idx - o * nch) * kYChunk;
         const float2* col = sm + (nH + o) * Q;
-        float2* dst = out0 + o * ostride;
+        float2* dst = stage ? sm + o * r : out0 + o * ostride;
         prefilter_chunk<kYChunk, f2>(
             k0, r, [&](int jj) { return f2(col[tab[jj]]); },
             [&](int k, f2 v) { dst[k] = make_float2(v.x, v.y); });
+      }
+      if (stage) {
+        __syncthreads();
+        for (int o = 0; o < J.n_out; ++o)
+          for (int k = threadIdx.x; k < r; k += blockDim.x) out0[o * ostride + k] = sm[o * r + k];
       }
     } else {
       for (int k = threadIdx.x; k < r; k += blockDim.x) {
@@ -413,7 +425,8 @@ __global__ void __launch_bounds__(256, 3) k_xinv(const Launch<XInvJob> Lc) {
       xinv_put(sm, l * ldl, Q, kx, a, b);
     }
   }
-  build_pref_table(tab, J.out_len + 2 * kPrefWarm + kXChunk, J.box_lo, J.box_len, J.start, Q, J.fx.pos);
+  build_pref_table(tab, J.out_len + 2 * kPrefWarm + kXChunk, J.box_lo, J.box_len, J.start, Q, J.fx.pos,
+                   J.periodic != 0);
   __syncthreads();
   // natural-order input, digit-reversed output: the table above maps through it
   fft_smem<kInvDif, float2, RSET>(sm, ldl, nlines, J.fx.plan, J.fx.tw_f, 0, blockDim.x);

@@ -125,12 +125,19 @@ __global__ void __launch_bounds__(TX * TY, 4) k_gather(const Launch<GatherJob> L
     const double fl = floor(su);
     const int U = (int)fl;
     bspline_w((float)(su - fl), w_s[a]);
-    int sh = J.guard[a] + (U - J.U0[a]);
-    const int need = (a == 0 ? J.nx : a == 1 ? J.ny : J.nz) + 3;
-    const int have = a == 0 ? J.rx : a == 1 ? J.ry : J.rz;
-    if (sh < 0 || sh + need > have) {
-      atomicExch(J.err, 1);
-      sh = 0x7fffffff;
+    int sh;
+    if (a < 2 && J.wrapP[a] > 0) {
+      // periodic axis: the coefficients span the period, the taps wrap
+      const int P = J.wrapP[a];
+      sh = (J.tap0[a] + (U % P + P) % P) % P;
+    } else {
+      sh = J.guard[a] + (U - J.U0[a]);
+      const int need = (a == 0 ? J.nx : a == 1 ? J.ny : J.nz) + 3;
+      const int have = a == 0 ? J.rx : a == 1 ? J.ry : J.rz;
+      if (sh < 0 || sh + need > have) {
+        atomicExch(J.err, 1);
+        sh = 0x7fffffff;
+      }
     }
     shift_s[a] = sh;
   }
@@ -147,7 +154,12 @@ __global__ void __launch_bounds__(TX * TY, 4) k_gather(const Launch<GatherJob> L
   if (!bad) {
     const int sx = shift_s[0], sy = shift_s[1], sz = shift_s[2];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const float* colp = J.C + (min(x0 + lane, J.nx - 1) + sx);
+    // column of each of the four x taps (wrapped around a periodic x)
+    const int P0 = J.wrapP[0], P1 = J.wrapP[1];
+    const int xb = min(x0 + lane, J.nx - 1) + sx;
+    int xt[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) xt[k] = P0 > 0 ? (xb + k) % P0 : xb + k;
     const float w0 = w_s[0][0], w1 = w_s[0][1], w2 = w_s[0][2], w3 = w_s[0][3];
     const float d0 = w_s[0][4], d1 = w_s[0][5], d2 = w_s[0][6], d3 = w_s[0][7];
     const float e0 = w_s[0][8], e1 = w_s[0][9], e2 = w_s[0][10], e3 = w_s[0][11];
@@ -160,10 +172,11 @@ __global__ void __launch_bounds__(TX * TY, 4) k_gather(const Launch<GatherJob> L
         const int r = min(r0 + b * (TX * TY / 32), nrow - 1);
         const int zz = r / (TY + 3), yy = r - zz * (TY + 3);
         // rows past the target's last support row are clamped in the box
-        const int gy = min(y0 + yy, J.ny + 2) + sy;
-        const float* src = colp + ((size_t)(z0 + zz + sz) * J.ry + gy) * J.rx;
+        // (a periodic y wraps them around the period instead)
+        const int gy = P1 > 0 ? (y0 + yy + sy) % P1 : min(y0 + yy, J.ny + 2) + sy;
+        const float* src = J.C + ((size_t)(z0 + zz + sz) * J.ry + gy) * J.rx;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) c[b][k] = __ldg(src + k);
+        for (int k = 0; k < 4; ++k) c[b][k] = __ldg(src + xt[k]);
       }
 #pragma unroll
       for (int b = 0; b < kRowBatch; ++b) {

@@ -173,10 +173,32 @@ __device__ __forceinline__ bool is_far(double ix, double iy, double iz) {
   return fmax(fabs(ix), fmax(fabs(iy), fabs(iz))) > kFarCells + 1e-9;
 }
 
+// acc += w K(offset (ix, iy, iz) cells): S (3 values) or N (6 values)
+__device__ __forceinline__ void add_kernel(int kind, double ix, double iy, int iz, double a, double b,
+                                           double c, double w, double* acc) {
+  const double X = ix * a, Y = iy * b, Z = iz * c;
+  if (kind == 0) {
+    double S[3];
+    if (is_far(ix, iy, iz)) S_far(X, Y, Z, a, b, c, S);
+    else S_closed(X, Y, Z, a, b, c, S);
+    for (int q = 0; q < 3; ++q) acc[q] += w * S[q];
+  } else {
+    double N[6];
+    if (is_far(ix, iy, iz)) N_far(X, Y, Z, a, b, c, N);
+    else
+      for (int q = 0; q < 6; ++q) N[q] = N_closed(q, X, Y, Z, a, b, c);
+    for (int q = 0; q < 6; ++q) acc[q] += w * N[q];
+  }
+}
+
 // Real-space kernel of one z offset on the circular grid, as complex (re, 0).
-// kind 0: S (ncomp 3), kind 1: N (ncomp 6).  out[comp][y][x].
+// kind 0: S (ncomp 3), kind 1: N (ncomp 6).  out[comp][y][x].  An open axis
+// keeps the offsets |d| <= W; a periodic one (px, py) keeps every offset of the
+// period and sums the images d + i Q, |i| <= R; at the Nyquist offset Q/2 of an
+// even period it averages the image sums of +Q/2 and -Q/2, so the periodic
+// kernel stays exactly even or odd along that axis.
 __global__ void k_gen_plane(double2* out, int kind, int Qx, int Qy, int Wx, int Wy, int dz, double a,
-                            double b, double c) {
+                            double b, double c, int px, int py, int R) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y;
   if (x >= Qx) return;
@@ -184,25 +206,22 @@ __global__ void k_gen_plane(double2* out, int kind, int Qx, int Qy, int Wx, int 
   const int sy = 2 * y > Qy ? y - Qy : y;
   const size_t plane = (size_t)Qx * Qy;
   const size_t o = (size_t)y * Qx + x;
-  const bool inside = (sx >= -Wx && sx <= Wx && sy >= -Wy && sy <= Wy);
-  if (kind == 0) {
-    double S[3] = {0.0, 0.0, 0.0};
-    if (inside) {
-      const double X = sx * a, Y = sy * b, Z = dz * c;
-      if (is_far(sx, sy, dz)) S_far(X, Y, Z, a, b, c, S);
-      else S_closed(X, Y, Z, a, b, c, S);
-    }
-    for (int q = 0; q < 3; ++q) out[q * plane + o] = make_double2(S[q], 0.0);
-  } else {
-    double N[6] = {0, 0, 0, 0, 0, 0};
-    if (inside) {
-      const double X = sx * a, Y = sy * b, Z = dz * c;
-      if (is_far(sx, sy, dz)) N_far(X, Y, Z, a, b, c, N);
-      else
-        for (int q = 0; q < 6; ++q) N[q] = N_closed(q, X, Y, Z, a, b, c);
-    }
-    for (int q = 0; q < 6; ++q) out[q * plane + o] = make_double2(N[q], 0.0);
+  const bool inside = (px || (sx >= -Wx && sx <= Wx)) && (py || (sy >= -Wy && sy <= Wy));
+  const int ncomp = kind == 0 ? 3 : 6;
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  if (inside) {
+    const bool nyx = px && 2 * x == Qx, nyy = py && 2 * y == Qy;
+    const int Rx = px ? R : 0, Ry = py ? R : 0;
+    const double w = (nyx ? 0.5 : 1.0) * (nyy ? 0.5 : 1.0);
+    for (int fx = 0; fx <= (nyx ? 1 : 0); ++fx)
+      for (int fy = 0; fy <= (nyy ? 1 : 0); ++fy) {
+        const int bx = fx ? -sx : sx, by = fy ? -sy : sy;
+        for (int i = -Rx; i <= Rx; ++i)
+          for (int j = -Ry; j <= Ry; ++j)
+            add_kernel(kind, (double)bx + (double)i * Qx, (double)by + (double)j * Qy, dz, a, b, c, w, acc);
+      }
   }
+  for (int q = 0; q < ncomp; ++q) out[q * plane + o] = make_double2(acc[q], 0.0);
 }
 
 // Point evaluation of S (3) or N (6) at listed offsets (metres), for tests.
@@ -281,6 +300,27 @@ __global__ void k_mix_T(const double* Sq, const double* W, float* T, int n_out, 
   T[((size_t)oj * 3 + c) * qsize + i] = (float)(scale * acc);
 }
 
+// Componentwise field variant: TN[(a n_out + o) nz + jz][b] = scale * sum_zb
+// W[o][zb] N_ab((zb - jz) - dz_lo), from the six N components of every z
+// offset (Nq6 [plane][6][qsize], xx yy zz xy xz yz).
+__global__ void k_mix_TN(const double* Nq6, const double* W, float* T, int n_out, int nz, int bz,
+                         size_t qsize, double scale) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= qsize) return;
+  const int a = blockIdx.y / 3, b = blockIdx.y - 3 * (blockIdx.y / 3);
+  const int comp = a == b ? a : (a + b == 1 ? 3 : (a + b == 2 ? 4 : 5));
+  const int oj = blockIdx.z;  // o * nz + jz
+  const int o = oj / nz, jz = oj - o * nz;
+  double acc = 0.0;
+  for (int zb = 0; zb < bz; ++zb) {
+    const double w = W[o * bz + zb];
+    if (w == 0.0) continue;
+    const int plane = zb - jz + nz - 1;
+    acc += w * Nq6[((size_t)plane * 6 + comp) * qsize + i];
+  }
+  T[((((size_t)a * n_out + o) * nz + jz) * 3 + b) * qsize + i] = (float)(scale * acc);
+}
+
 __global__ void k_scale_to_float(const double* in, float* out, size_t n, double scale) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = (float)(scale * in[i]);
@@ -297,14 +337,15 @@ cudaError_t eval_points_fp64(int kind, int n, const double* off_dev, double a, d
 
 // Spectrum quarters of `ncomp` kernel components for one z offset.
 // work: 2 * ncomp * Qx * Qy double2; out_q: ncomp quarter planes (double).
-static cudaError_t plane_spectra(int kind, int ncomp, int Qx, int Qy, int Wx, int Wy, int dz, double a,
+static cudaError_t plane_spectra(int kind, int ncomp, const KernelPlan& K, int dz, double a,
                                  double b, double c, const FftTables& fx, const FftTables& fy,
                                  double2* work, double* out_q, const int* take_imag, cudaStream_t st) {
+  const int Qx = K.Qx, Qy = K.Qy;
   const size_t plane = (size_t)Qx * Qy;
   double2* A = work;
   double2* B = work + ncomp * plane;
   dim3 g((Qx + 127) / 128, Qy);
-  k_gen_plane<<<g, 128, 0, st>>>(A, kind, Qx, Qy, Wx, Wy, dz, a, b, c);
+  k_gen_plane<<<g, 128, 0, st>>>(A, kind, Qx, Qy, K.Wx, K.Wy, dz, a, b, c, K.px, K.py, K.R);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int kxh = Qx / 2 + 1, kyq = Qy / 2 + 1;
@@ -332,7 +373,7 @@ cudaError_t build_N_spectra(const KernelPlan& K, const FftTables& fx, const FftT
   const size_t qsize = (size_t)kxh * kyq;
   static const int imag6[6] = {0, 0, 0, 0, 1, 1};
   for (int dz = 0; dz < K.nz; ++dz) {
-    cudaError_t e = plane_spectra(1, 6, K.Qx, K.Qy, K.Wx, K.Wy, dz, a, b, c, fx, fy, work, qbuf, imag6, st);
+    cudaError_t e = plane_spectra(1, 6, K, dz, a, b, c, fx, fy, work, qbuf, imag6, st);
     if (e != cudaSuccess) return e;
     // Nq layout [6][nz][kxh][kyq]
     for (int q = 0; q < 6; ++q) {
@@ -356,7 +397,7 @@ cudaError_t build_T_spectra(const KernelPlan& K, const FftTables& fx, const FftT
   const int dz_lo = box_lo_z - (K.nz - 1);
   const int nplanes = bz + K.nz - 1;
   for (int p = 0; p < nplanes; ++p) {
-    cudaError_t e = plane_spectra(0, 3, K.Qx, K.Qy, K.Wx, K.Wy, dz_lo + p, a, b, c, fx, fy, work,
+    cudaError_t e = plane_spectra(0, 3, K, dz_lo + p, a, b, c, fx, fy, work,
                                   Sq + (size_t)p * 3 * qsize, imag3, st);
     if (e != cudaSuccess) return e;
   }
@@ -366,13 +407,30 @@ cudaError_t build_T_spectra(const KernelPlan& K, const FftTables& fx, const FftT
   return cudaGetLastError();
 }
 
+cudaError_t build_TN_spectra(const KernelPlan& K, const FftTables& fx, const FftTables& fy, double a,
+                             double b, double c, double scale, int box_lo_z, int bz, int n_out,
+                             const double* W_dev, float* TN, double2* work, double* Nq6, cudaStream_t st) {
+  const size_t qsize = (size_t)(K.Qx / 2 + 1) * (K.Qy / 2 + 1);
+  static const int imag6[6] = {0, 0, 0, 0, 1, 1};
+  const int dz_lo = box_lo_z - (K.nz - 1);
+  const int nplanes = bz + K.nz - 1;
+  for (int p = 0; p < nplanes; ++p) {
+    cudaError_t e = plane_spectra(1, 6, K, dz_lo + p, a, b, c, fx, fy, work,
+                                  Nq6 + (size_t)p * 6 * qsize, imag6, st);
+    if (e != cudaSuccess) return e;
+  }
+  dim3 g((unsigned)((qsize + 255) / 256), 9, n_out * K.nz);
+  k_mix_TN<<<g, 256, 0, st>>>(Nq6, W_dev, TN, n_out, K.nz, bz, qsize, scale);
+  return cudaGetLastError();
+}
+
 cudaError_t build_S_planes(const KernelPlan& K, const FftTables& fx, const FftTables& fy, double a, double b,
                            double c, double scale, int dz_lo, int nplanes, float* Sq, double2* work,
                            double* qtmp, cudaStream_t st) {
   static const int imag3[3] = {1, 1, 0};
   const size_t qsize = (size_t)(K.Qx / 2 + 1) * (K.Qy / 2 + 1);
   for (int p = 0; p < nplanes; ++p) {
-    cudaError_t e = plane_spectra(0, 3, K.Qx, K.Qy, K.Wx, K.Wy, dz_lo + p, a, b, c, fx, fy, work, qtmp, imag3, st);
+    cudaError_t e = plane_spectra(0, 3, K, dz_lo + p, a, b, c, fx, fy, work, qtmp, imag3, st);
     if (e != cudaSuccess) return e;
     const size_t n = 3 * qsize;
     k_scale_to_float<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(qtmp, Sq + (size_t)p * n, n, scale);
@@ -431,8 +489,10 @@ cudaError_t build_spectra_3d(int kind, const KernelPlan3& K, const FftTables& fx
   const size_t qsize = (size_t)kxh * kyq;
   cudaError_t e = cudaMemsetAsync(q2, 0, sizeof(double) * ncomp * (size_t)K.Qz * qsize, st);
   if (e != cudaSuccess) return e;
+  KernelPlan K2{};  // open boundaries: sources thicker than the direct z sum are not periodic
+  K2.Qx = K.Qx; K2.Qy = K.Qy; K2.Wx = K.Wx; K2.Wy = K.Wy;
   for (int dz = -K.Wz; dz <= K.Wz; ++dz) {
-    e = plane_spectra(kind, ncomp, K.Qx, K.Qy, K.Wx, K.Wy, dz, a, b, c, fx, fy, work, qtmp, imag2d, st);
+    e = plane_spectra(kind, ncomp, K2, dz, a, b, c, fx, fy, work, qtmp, imag2d, st);
     if (e != cudaSuccess) return e;
     const int zs = dz < 0 ? dz + K.Qz : dz;
     for (int q = 0; q < ncomp; ++q) {

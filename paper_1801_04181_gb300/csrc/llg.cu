@@ -45,7 +45,8 @@ __global__ void __launch_bounds__(256) k_stage(const Launch<StageJob> Lc, const 
     float h0 = J.Hself[idx] + J.Hstray[idx] + J.hext[0];
     float h1 = J.Hself[N + idx] + J.Hstray[N + idx] + J.hext[1];
     float h2 = J.Hself[2 * N + idx] + J.Hstray[2 * N + idx] + J.hext[2];
-    // exchange, free ends: only neighbours inside the magnet contribute
+    // exchange, free ends: only neighbours inside the magnet contribute;
+    // periodic x / y: the neighbours wrap around the period
     float e0 = 0.f, e1 = 0.f, e2 = 0.f;
 #define MM_NB(cond, off, coef)                                          \
     if (cond) {                                                         \
@@ -54,10 +55,11 @@ __global__ void __launch_bounds__(256) k_stage(const Launch<StageJob> Lc, const 
       e1 += (coef) * (m[N + q] - m1);                                   \
       e2 += (coef) * (m[2 * N + q] - m2);                               \
     }
-    MM_NB(x > 0, -1, J.ex[0])
-    MM_NB(x < nx - 1, 1, J.ex[0])
-    MM_NB(y > 0, -(ptrdiff_t)nx, J.ex[1])
-    MM_NB(y < ny - 1, (ptrdiff_t)nx, J.ex[1])
+    const bool wx = J.wrap[0] && nx > 1, wy = J.wrap[1] && ny > 1;
+    MM_NB(x > 0 || wx, x > 0 ? -1 : (ptrdiff_t)nx - 1, J.ex[0])
+    MM_NB(x < nx - 1 || wx, x < nx - 1 ? 1 : -((ptrdiff_t)nx - 1), J.ex[0])
+    MM_NB(y > 0 || wy, y > 0 ? -(ptrdiff_t)nx : (ptrdiff_t)nx * (ny - 1), J.ex[1])
+    MM_NB(y < ny - 1 || wy, y < ny - 1 ? (ptrdiff_t)nx : -(ptrdiff_t)nx * (ny - 1), J.ex[1])
     MM_NB(z > 0, -(ptrdiff_t)nx * ny, J.ex[2])
     MM_NB(z < nz - 1, (ptrdiff_t)nx * ny, J.ex[2])
 #undef MM_NB

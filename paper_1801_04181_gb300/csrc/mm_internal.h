@@ -71,6 +71,7 @@ struct YJob {
   const float* Tq;        // [n_out][nz][3][kxh][kyq]
   float2* outC;           // [n_out][kxh][r]
   int box_lo, box_len, start, r, fir;
+  int periodic;           // the y box is the whole period: the prefilter wraps
 };
 
 // ---------------------------------------------------------------- x inverse
@@ -81,6 +82,7 @@ struct XInvJob {
   FftTables fx;
   // output window along x: circular index (box_lo + j) mod Q for box-local j
   int box_lo, box_len, start, out_len, fir;
+  int periodic;           // the x box is the whole period: the prefilter wraps
 };
 
 // ---------------------------------------------------------------- 3D sources (nz > kMaxNz)
@@ -122,6 +124,7 @@ struct YInvJob {
   float2* outH;           // [planes][kxh][ny]
   float2* outC;           // [planes][kxh][r]
   int box_lo, box_len, start, r, fir;  // y box
+  int periodic;           // the y box is the whole period: the prefilter wraps
 };
 
 // direct z sum for moderately thick sources (nz <= kMaxNzDirect): thin-film
@@ -134,6 +137,10 @@ struct ZMixJob {
   int nH, n_out;          // output planes: 3 nz demag (if nH), then n_out coefficient planes
   float2* outH;           // [3 nz][kxh][Qy]
   float2* outC;           // [n_out][kxh][Qy]
+  // 0: potential planes (Tq of S); > 0: the componentwise field variant, whose
+  // n_out = 3 field_nbox planes are H_a of box plane o at a field_nbox + o,
+  // with Tq the W-folded rows of -N (build_TN_spectra)
+  int field_nbox;
 };
 constexpr int kMaxNzDirect = 8;
 
@@ -179,6 +186,10 @@ struct GatherJob {
   float* H;               // stray field out [3][N] (A/m), may be null
   float2* partial;        // [tiles][4] double-float (hi, lo): sum m.Hess (3), sum m.grad
   int* err;               // set to 1 when the displacement leaves the box
+  // periodic x (a = 0), y (a = 1): the coefficients span the period wrapP[a]
+  // from source node 0, and the first tap of target cell i is node
+  // tap0[a] + floor(sigma u_a) + i (mod the period); 0 = open axis
+  int wrapP[2], tap0[2];
 };
 
 // ---------------------------------------------------------------- LLG / RK
@@ -202,6 +213,7 @@ struct StageJob {
   float comb[7];          // dt a_{stage+1, j}
   float ecoef[7];         // dt (b5_j - b4_j)
   float* err_partial;     // per-CTA max |error| (stage 7)
+  int wrap[2];            // exchange neighbours wrap around x (0), y (1): periodic boundaries
 };
 
 struct CombineJob {
@@ -261,6 +273,8 @@ struct KernelPlan {
   int Qx, Qy;             // circular grid
   int Wx, Wy;             // kernel window |d| <= W (cells)
   int nz;                 // source layers
+  int px = 0, py = 0;     // periodic axis: Q is the period, every offset counts, images summed
+  int R = 0;              // periodic images on each side
 };
 
 struct KernelPlan3 {
@@ -292,6 +306,11 @@ int power_blocks(size_t N);
 cudaError_t launch_mxh2(const float* m, const float* H, size_t N, double* partial, double* out, cudaStream_t st);
 // four-point difference gradient of the interpolant (variants.cu): V holds
 // (nx + 4)(ny + 4)(nz + 4) floats, H 3 nx ny nz; needs margin >= 2
+// componentwise field variant (variants.cu): H_a at every target centre from
+// the coefficients C [3][bdim z][bdim y][bdim x] of the three components on
+// the full box (taps of centre i start at node i + margin)
+cudaError_t launch_field_values(const float* C, const int bdim[3], const int nt[3], int margin,
+                                const double frac[3], float* H, cudaStream_t st);
 cudaError_t launch_fd4_field(const float* C, const int bdim[3], const int nt[3], int margin, const double frac[3],
                              const double cell[3], float* V, float* H, cudaStream_t st);
 
@@ -325,6 +344,12 @@ cudaError_t build_spectra_3d(int kind, const KernelPlan3& K, const FftTables& fx
 // FP32 quarter spectra of S, one plane of 3 components per z offset dz_lo + p,
 // p < nplanes: Sq [p][3][kxh][kyq], scaled.  work as for build_N_spectra,
 // qtmp 3 kxh kyq doubles.
+// Componentwise field variant: TN [3][n_out][nz][3][kxh][kyq], the rows of N
+// folded with the z mixing matrix W, scaled.  Nq6 scratch (bz + nz - 1) 6 kxh kyq
+// doubles, work as for build_N_spectra.
+cudaError_t build_TN_spectra(const KernelPlan& K, const FftTables& fx, const FftTables& fy, double a,
+                             double b, double c, double scale, int box_lo_z, int bz, int n_out,
+                             const double* W_dev, float* TN, double2* work, double* Nq6, cudaStream_t st);
 cudaError_t build_S_planes(const KernelPlan& K, const FftTables& fx, const FftTables& fy, double a, double b,
                            double c, double scale, int dz_lo, int nplanes, float* Sq, double2* work,
                            double* qtmp, cudaStream_t st);

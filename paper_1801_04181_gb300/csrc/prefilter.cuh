@@ -24,11 +24,19 @@ constexpr int kZChunk = 9;   // z pass of thick sources (complex)
 // Shared-memory index of the samples the prefilter reads: entry j holds the
 // position, in a line of `Q` left in the digit-reversed order of a transform
 // (`pos`: its frequency -> position table; natural order when null), of
-// box-local node mirror(start - kPrefWarm + j).
+// box-local node mirror(start - kPrefWarm + j) -- or, when the box is a whole
+// period (periodic boundaries), of that node wrapped around the period.
 __device__ __forceinline__ void build_pref_table(int* tab, int n, int box_lo, int box_len, int start, int Q,
-                                                 const int* __restrict__ pos) {
+                                                 const int* __restrict__ pos, bool periodic = false) {
   for (int j = threadIdx.x; j < n; j += blockDim.x) {
-    const int g = wrap_once(box_lo + mirror_index(start - kPrefWarm + j, box_len), Q);
+    int local;
+    if (periodic) {
+      local = (start - kPrefWarm + j) % box_len;
+      if (local < 0) local += box_len;
+    } else {
+      local = mirror_index(start - kPrefWarm + j, box_len);
+    }
+    const int g = wrap_once(box_lo + local, Q);
     tab[j] = pos ? __ldg(pos + g) : g;
   }
 }

@@ -1,3 +1,5 @@
+// Comparison variants of the stray field.
+//
 // The four-point finite-difference gradient of the interpolated potential
 // (Sec. III.A mentions a four-point central difference for the gradient; the
 // main path differentiates the spline analytically).  With the B-spline
@@ -65,6 +67,53 @@ __global__ void __launch_bounds__(256) k_fd4(const float* __restrict__ V, int nx
   H[t] = sx * (-V[c + 2] + 8.f * V[c + 1] - 8.f * V[c - 1] + V[c - 2]);
   H[N + t] = sy * (-V[c + 2 * dy] + 8.f * V[c + dy] - 8.f * V[c - dy] + V[c - 2 * dy]);
   H[2 * N + t] = sz * (-V[c + 2 * dz] + 8.f * V[c + dz] - 8.f * V[c - dz] + V[c - 2 * dz]);
+}
+
+// Componentwise field variant (Sec. II.A, the direct method): H_a(i) = the
+// B-spline interpolant of component a at target centre i, 64 taps from the
+// coefficients of that component on the full box; the taps of centre i start
+// at box node i + m along every axis.
+__global__ void __launch_bounds__(256) k_field_values(const float* __restrict__ C, int bx, int by, int bz,
+                                                      int nx, int ny, int nz, int m, float fx, float fy,
+                                                      float fz, float* __restrict__ H) {
+  __shared__ float w[3][12];
+  if (threadIdx.x < 3) bspline_w(threadIdx.x == 0 ? fx : (threadIdx.x == 1 ? fy : fz), w[threadIdx.x]);
+  __syncthreads();
+  const size_t N = (size_t)nx * ny * nz;
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= N) return;
+  const int i = (int)(t % nx);
+  const int j = (int)((t / nx) % ny);
+  const int k = (int)(t / ((size_t)nx * ny));
+  const int x0 = i + m, y0 = j + m, z0 = k + m;
+  const size_t box = (size_t)bx * by * bz;
+  for (int a = 0; a < 3; ++a) {
+    float v = 0.f;
+    if (x0 + 3 < bx && y0 + 3 < by && z0 + 3 < bz) {  // always true on the full box (host-checked)
+#pragma unroll
+      for (int kz = 0; kz < 4; ++kz) {
+        float vy = 0.f;
+#pragma unroll
+        for (int ky = 0; ky < 4; ++ky) {
+          const float* row = C + a * box + ((size_t)(z0 + kz) * by + (y0 + ky)) * bx + x0;
+          const float vx = w[0][0] * row[0] + w[0][1] * row[1] + w[0][2] * row[2] + w[0][3] * row[3];
+          vy += w[1][ky] * vx;
+        }
+        v += w[2][kz] * vy;
+      }
+    }
+    H[a * N + t] = v;
+  }
+}
+
+cudaError_t launch_field_values(const float* C, const int bdim[3], const int nt[3], int margin,
+                                const double frac[3], float* H, cudaStream_t st) {
+  const size_t N = (size_t)nt[0] * nt[1] * nt[2];
+  if (N == 0) return cudaSuccess;
+  k_field_values<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(C, bdim[0], bdim[1], bdim[2], nt[0], nt[1], nt[2],
+                                                               margin, (float)frac[0], (float)frac[1],
+                                                               (float)frac[2], H);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_fd4_field(const float* C, const int bdim[3], const int nt[3], int margin, const double frac[3],
