@@ -36,6 +36,9 @@ WORKLOADS = {
                 lambda seed: __import__("workloads").cube_pair((64, 64, 64), 3, seed)),
     "films512x512x8": ("random-unit film pair 512x512x8 (4 nm), gap 1, adaptive DP45",
                        lambda seed: __import__("workloads").film_pair_plain((512, 512, 8), 1, seed)),
+    "friction_pbc": ("friction films of Sec. IV.B: CoCrPt 256x256x5 (4 nm), gap 5, periodic in-plane "
+                     "(2 images each side), 20-cell stripes, spring 0.005 N/m at 2 m/s, adaptive DP45",
+                     lambda seed: __import__("workloads").film_pair_friction(seed=seed)),
 }
 TIMING_CLASSES = ["fft_x_forward", "fft_y_pass_mix_prefilter", "fft_x_inverse_prefilter",
                   "spline_gather_force", "llg_stage", "slider_reduce", "combine_normalise",
@@ -54,6 +57,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--lanes", type=int, default=BATCH_LANES, help="streams of the batch256 workload")
+    p.add_argument("--no-autotune", action="store_true",
+                   help="batch256: keep the planner's model FFT plans instead of timing candidates per length")
     p.add_argument("--workload", default="stick_slip",
                    choices=sorted(WORKLOADS) + ["plain64_sweep", "cubes64_gradients", "batch256", "divcurl_sweep"],
                    help="stick_slip (the headline workload), a thick-source workload, or the "
@@ -330,7 +335,8 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     cpu_base = None
     pool = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    # the CPU sample times the open-boundary oracle: periodic workloads report none
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload != "friction_pbc":
         # start the oracle's process pool before the first GPU call
         import multiprocessing as mp
         pool = mp.get_context("spawn").Pool(oracle_pool_size())
@@ -742,6 +748,15 @@ def run_batch(args):
         m0, m1 = workloads.batch_patterns(specs[i])
         batch.append(gpu_pair(specs[i], m0, m1, adaptive=True, rtol=1e-5, stream=streams[l]))
     cells = sum(specs[i].cells() for i in mine)
+    # the project's autotuner: candidate radix orders per transform length,
+    # timed on the pairs themselves (a length is timed once, then shared)
+    tune = {"enabled": not args.no_autotune, "lengths_timed": 0, "seconds": 0.0}
+    if not args.no_autotune:
+        t_tune = time.perf_counter()
+        for mm in batch:
+            tune["lengths_timed"] += mm.autotune(candidates=4, reps=2)
+        torch.cuda.synchronize()
+        tune["seconds"] = round(time.perf_counter() - t_tune, 2)
     dts = [1e-13] * len(batch)
     for _ in range(max(args.warmup, 3)):
         _, dts = step_batch(batch, 1, dts)
@@ -844,7 +859,7 @@ def run_batch(args):
                                    "(4 nm), slider at U[0, 50) cells, pulled at U[0.1, 10] m/s, "
                                    "adaptive DP45 per pair",
                        "pairs": len(batch), "cells": cells, "lanes": args.lanes,
-                       "accepted": acc, "rejected": rej, "setup_s": round(t_setup, 1),
+                       "accepted": acc, "rejected": rej, "setup_s": round(t_setup, 1), "autotune": tune,
                        "parallelism": "pairs over ranks" if world > 1 else "single",
                        "l2": "no flush: the batch's working set (tens of GB) exceeds the 129 MB L2"},
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,

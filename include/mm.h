@@ -234,8 +234,9 @@ mm_status mm_step_batch(mm_ctx* const* ctxs, int npairs, int nsteps, double* t_o
 mm_status mm_assign_lanes(const double* cost, int npairs, int nlanes, int* lane_out);
 
 /*
- * Host-only query of the shared-memory FFT planner: the radix of each stage
- * (first stage first; at most 8) that transforms of length L use.  Fewest
+ * Host-only query of the shared-memory FFT planner's model choice: the radix
+ * of each stage (first stage first; at most 8) for transforms of length L
+ * (mm_get_tuned_plan gives the autotuned one, which takes precedence).  Fewest
  * stages of radices up to 16; among their orderings, the near-fewest modelled
  * shared-memory bank conflicts, then the radix set {4, 9, 15, 16} the pass
  * kernels are also compiled for, then the largest last and first radix.
@@ -243,6 +244,26 @@ mm_status mm_assign_lanes(const double* cost, int npairs, int nlanes, int* lane_
  * stages.  Needs no GPU.
  */
 mm_status mm_fft_plan(int L, int radices[8], int* nstages);
+
+/*
+ * Autotuner of the FFT plans (the batched form's schedule choice; the paper
+ * has no counterpart).  For every transform length this context's pass
+ * kernels use, times up to `candidates` radix orderings (the planner's model
+ * choice first, then the next orderings by modelled shared-memory
+ * wavefronts) on the context's own data, `reps` field evaluations each with
+ * CUDA events around the passes that use the length, and keeps the fastest
+ * for the whole process: contexts created later, and this one, build their
+ * tables of that length from it; a length tuned before is reused, not timed
+ * again.  Leaves m, the slider and the timing record as they were (the
+ * fields of the last evaluation stay in the buffers).  *n_tuned (may be NULL):
+ * lengths timed.  Synchronises.  MM_EINVAL for candidates outside 1..16 or
+ * reps < 1.
+ */
+mm_status mm_autotune(mm_ctx* ctx, int candidates, int reps, int* n_tuned);
+
+/* The radix order mm_autotune chose for length L (first stage first), host
+ * only; MM_ESTATE if L has not been tuned in this process. */
+mm_status mm_get_tuned_plan(int L, int radices[8], int* nstages);
 
 /*
  * Power bookkeeping at the current state (Sec. III, after Eq. (EQForce)), W:

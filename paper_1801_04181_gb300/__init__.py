@@ -13,7 +13,7 @@ from . import _native
 from ._native import MMError, mm_options
 
 __all__ = ["MovingMagnets", "MMError", "assign_lanes", "eval_kernel_fp64", "fft_plan", "load_library", "pair_context",
-           "step_batch"]
+           "step_batch", "tuned_plan"]
 
 
 def load_library():
@@ -249,6 +249,13 @@ class MovingMagnets:
     def clear_attempt_log(self):
         self._c(self.lib.mm_clear_attempt_log(self.ctx))
 
+    def autotune(self, candidates=4, reps=3):
+        """mm_autotune: time candidate FFT radix orders on this pair and keep the
+        fastest per length (process-wide).  Returns the number of lengths timed."""
+        n = C.c_int()
+        self._c(self.lib.mm_autotune(self.ctx, int(candidates), int(reps), C.byref(n)))
+        return n.value
+
     def get_state(self):
         n = C.c_size_t()
         self._c(self.lib.mm_get_state(self.ctx, None, C.byref(n)))
@@ -313,6 +320,17 @@ def fft_plan(L):
     s = lib.mm_fft_plan(int(L), r, C.byref(n))
     if s != 0:
         raise MMError(s, "mm_fft_plan")
+    return [r[i] for i in range(n.value)]
+
+
+def tuned_plan(L):
+    """mm_get_tuned_plan: the autotuned radix order of length L, or None."""
+    lib = _native.load()
+    r = (C.c_int * 8)()
+    n = C.c_int()
+    s = lib.mm_get_tuned_plan(int(L), r, C.byref(n))
+    if s != 0:
+        return None
     return [r[i] for i in range(n.value)]
 
 

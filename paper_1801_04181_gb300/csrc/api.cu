@@ -22,6 +22,7 @@
 #include <cmath>
 #include <deque>
 #include <map>
+#include <mutex>
 #include <set>
 #include <string>
 #include <vector>
@@ -361,6 +362,48 @@ std::vector<int> plan_radices(int L) {
   return best;
 }
 
+// ------------------------------------------------------------ autotuned plans
+// Process-wide radix order per transform length, chosen by mm_autotune from
+// timed runs of the pass kernels; the planner's model choice otherwise.
+std::mutex g_tune_mu;
+std::map<int, std::vector<int>> g_tuned;
+
+bool tuned_plan(int L, std::vector<int>* out) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  auto it = g_tuned.find(L);
+  if (it == g_tuned.end()) return false;
+  if (out) *out = it->second;
+  return true;
+}
+
+void set_tuned_plan(int L, const std::vector<int>& r) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tuned[L] = r;
+}
+
+// The candidates an autotuner times for length L: the model's choice first,
+// then the other orderings of the fewest-stage factorisations by modelled
+// shared-memory wavefronts, at most `k` in all.
+std::vector<std::vector<int>> plan_candidates(int L, int k) {
+  std::vector<std::vector<int>> out;
+  const std::vector<int> model = plan_radices(L);
+  if (model.empty()) return out;
+  out.push_back(model);
+  std::vector<int> cur;
+  std::vector<std::vector<int>> orders;
+  radix_orders(L, (int)model.size(), cur, orders);
+  std::vector<std::pair<long long, std::vector<int>>> w;
+  for (const auto& o : orders) w.push_back({plan_wavefronts(L, o), o});
+  std::sort(w.begin(), w.end());
+  for (const auto& e : w) {
+    if ((int)out.size() >= k) break;
+    if (std::find(out.begin(), out.end(), e.second) == out.end()) out.push_back(e.second);
+  }
+  return out;
+}
+
+// FFT resources of length L (plan, twiddle and position tables), cached per
+// context; the plan is the autotuned one when mm_autotune has chosen it.
 mm_status get_fft(mm_ctx* ctx, int L, FftTables* out) {
   const int key = L;
   auto it = ctx->ffts.find(key);
@@ -375,7 +418,8 @@ mm_status get_fft(mm_ctx* ctx, int L, FftTables* out) {
   while (r % 5 == 0) { r /= 5; ++p5; }
   if (r != 1) return fail(ctx, MM_EINVAL, "FFT length is not 2^a 3^b 5^c");
   (void)p2; (void)p3; (void)p5;
-  std::vector<int> radix = plan_radices(L);
+  std::vector<int> radix;
+  if (!tuned_plan(L, &radix)) radix = plan_radices(L);
   if (radix.empty() || (int)radix.size() > kMaxStages)
     return fail(ctx, MM_ENOTSUP, "FFT length has too many factors");
   FftPlanDev P{};
@@ -2123,6 +2167,100 @@ mm_status mm_assign_lanes(const double* cost, int npairs, int nlanes, int* lane_
     lane_out[i] = best;
     load[best] += cost[i];
   }
+  return MM_OK;
+}
+
+// Drops this context's tables of length L (after its work has drained), so
+// the next launch builds them from the current plan of L.
+static mm_status drop_fft(mm_ctx* ctx, int L) {
+  auto it = ctx->ffts.find(L);
+  if (it == ctx->ffts.end()) return MM_OK;
+  CK(cudaStreamSynchronize(ctx->st));
+  if (ctx->side) CK(cudaStreamSynchronize(ctx->side));
+  cudaFree(it->second.tw_f); cudaFree(it->second.tw_d); cudaFree(it->second.pos); cudaFree(it->second.freq);
+  ctx->ffts.erase(it);
+  return MM_OK;
+}
+
+mm_status mm_autotune(mm_ctx* ctx, int candidates, int reps, int* n_tuned) {
+  if (!ctx || candidates < 1 || candidates > 16 || reps < 1)
+    return ctx ? fail(ctx, MM_EINVAL, "mm_autotune") : MM_EINVAL;
+  if (n_tuned) *n_tuned = 0;
+  CKS(prepare(ctx));
+  // transform lengths of this context and the timing classes of the passes using them
+  std::map<int, std::set<int>> classes;
+  for (const Magnet& S : ctx->mag) {
+    classes[S.Qx].insert(0);
+    classes[S.Qx].insert(2);
+    if (!S.thick) {
+      classes[S.Qy].insert(1);
+    } else {
+      classes[S.Qy].insert(7);
+      classes[S.Qy].insert(9);
+    }
+    if (S.zfft) classes[S.Qz].insert(8);
+  }
+  // the tuning runs must not disturb the caller's timing record
+  const bool timing0 = ctx->timing;
+  drain_timing(ctx);
+  double t_ms0[kTimingClasses];
+  long long t_n0[kTimingClasses];
+  std::copy(ctx->t_ms, ctx->t_ms + kTimingClasses, t_ms0);
+  std::copy(ctx->t_n, ctx->t_n + kTimingClasses, t_n0);
+  ctx->timing = true;
+  const float* in[2] = {ctx->mag[0].m, ctx->mag[1].m};
+  auto run = [&]() -> mm_status {
+    CKS(evaluate_fields(ctx, in, mech_params(ctx, 1, 0, 0.0, true, true)));  // warm-up
+    drain_timing(ctx);
+    for (int i = 0; i < kTimingClasses; ++i) {
+      ctx->t_ms[i] = 0;
+      ctx->t_n[i] = 0;
+    }
+    for (int r = 0; r < reps; ++r) CKS(evaluate_fields(ctx, in, mech_params(ctx, 1, 0, 0.0, true, true)));
+    drain_timing(ctx);
+    return MM_OK;
+  };
+  mm_status st = MM_OK;
+  for (const auto& kv : classes) {
+    const int L = kv.first;
+    if (L <= 0) continue;
+    if (tuned_plan(L, nullptr)) {  // chosen by an earlier context: use it here too
+      if ((st = drop_fft(ctx, L)) != MM_OK) break;
+      continue;
+    }
+    const auto cands = plan_candidates(L, candidates);
+    if (cands.empty()) continue;
+    double best_ms = 0.0;
+    size_t best = 0;
+    for (size_t c = 0; c < cands.size() && cands.size() > 1; ++c) {
+      set_tuned_plan(L, cands[c]);
+      if ((st = drop_fft(ctx, L)) != MM_OK) break;
+      if ((st = run()) != MM_OK) break;
+      double ms = 0.0;
+      for (int cls : kv.second) ms += ctx->t_ms[cls];
+      if (c == 0 || ms < best_ms) {
+        best_ms = ms;
+        best = c;
+      }
+    }
+    if (st != MM_OK) break;
+    set_tuned_plan(L, cands[best]);
+    if ((st = drop_fft(ctx, L)) != MM_OK) break;
+    if (n_tuned) ++*n_tuned;
+  }
+  drain_timing(ctx);
+  std::copy(t_ms0, t_ms0 + kTimingClasses, ctx->t_ms);
+  std::copy(t_n0, t_n0 + kTimingClasses, ctx->t_n);
+  ctx->timing = timing0;
+  return st;
+}
+
+mm_status mm_get_tuned_plan(int L, int radices[8], int* nstages) {
+  if (!radices || !nstages) return MM_EINVAL;
+  std::vector<int> r;
+  if (!tuned_plan(L, &r)) return MM_ESTATE;
+  *nstages = (int)std::min<size_t>(8, r.size());
+  for (int i = 0; i < *nstages; ++i) radices[i] = r[i];
   return MM_OK;
 }
 

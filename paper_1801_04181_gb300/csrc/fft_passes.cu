@@ -313,25 +313,14 @@ __global__ void __launch_bounds__(kYThreads, NZ <= 2 ? 3 : 2) k_ypass(const Laun
     const size_t ostride = (size_t)J.kxh * r;
     if (J.fir) {
       const int nch = (r + kYChunk - 1) / kYChunk;
-      // A thread runs the recursion over a chunk of consecutive outputs, so
-      // its stores stride by the chunk across a warp.  When the demag planes
-      // (already written out) leave room, the chunks land in their shared
-      // memory first and leave the CTA as whole coalesced rows.
-      const bool stage = nH > 0 && J.n_out * r <= nH * Q;
-      if (stage) __syncthreads();  // every demag plane has been read out
       for (int idx = threadIdx.x; idx < J.n_out * nch; idx += blockDim.x) {
         const int o = idx / nch;
         const int k0 = (idx - o * nch) * kYChunk;
         const float2* col = sm + (nH + o) * Q;
-        float2* dst = stage ? sm + o * r : out0 + o * ostride;
+        float2* dst = out0 + o * ostride;
         prefilter_chunk<kYChunk, f2>(
             k0, r, [&](int jj) { return f2(col[tab[jj]]); },
             [&](int k, f2 v) { dst[k] = make_float2(v.x, v.y); });
-      }
-      if (stage) {
-        __syncthreads();
-        for (int o = 0; o < J.n_out; ++o)
-          for (int k = threadIdx.x; k < r; k += blockDim.x) out0[o * ostride + k] = sm[o * r + k];
       }
     } else {
       for (int k = threadIdx.x; k < r; k += blockDim.x) {

@@ -99,6 +99,9 @@ __device__ __forceinline__ void gather_column(const GatherJob& J, const float* A
   }
 }
 
+// WRAP: some job has a periodic x or y (the taps wrap around the period);
+// open boundaries run the instantiation without the wrapping arithmetic.
+template <bool WRAP>
 __global__ void __launch_bounds__(TX * TY, 4) k_gather(const Launch<GatherJob> Lc) {
   extern __shared__ float gsm[];
   __shared__ float w_s[3][12];
@@ -126,7 +129,7 @@ __global__ void __launch_bounds__(TX * TY, 4) k_gather(const Launch<GatherJob> L
     const int U = (int)fl;
     bspline_w((float)(su - fl), w_s[a]);
     int sh;
-    if (a < 2 && J.wrapP[a] > 0) {
+    if (WRAP && a < 2 && J.wrapP[a] > 0) {
       // periodic axis: the coefficients span the period, the taps wrap
       const int P = J.wrapP[a];
       sh = (J.tap0[a] + (U % P + P) % P) % P;
@@ -155,7 +158,7 @@ __global__ void __launch_bounds__(TX * TY, 4) k_gather(const Launch<GatherJob> L
     const int sx = shift_s[0], sy = shift_s[1], sz = shift_s[2];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // column of each of the four x taps (wrapped around a periodic x)
-    const int P0 = J.wrapP[0], P1 = J.wrapP[1];
+    const int P0 = WRAP ? J.wrapP[0] : 0, P1 = WRAP ? J.wrapP[1] : 0;
     const int xb = min(x0 + lane, J.nx - 1) + sx;
     int xt[4];
 #pragma unroll
@@ -235,13 +238,16 @@ size_t gather_smem(int nz) {
 
 cudaError_t launch_gather(const Launch<GatherJob>& L, int nz_max, cudaStream_t st) {
   const size_t smem = gather_smem(nz_max);
-  cudaFuncSetAttribute((const void*)k_gather, cudaFuncAttributePreferredSharedMemoryCarveout,
+  bool wrap = false;
+  for (int i = 0; i < L.njobs; ++i) wrap = wrap || L.job[i].wrapP[0] > 0 || L.job[i].wrapP[1] > 0;
+  auto k = wrap ? k_gather<true> : k_gather<false>;
+  cudaFuncSetAttribute((const void*)k, cudaFuncAttributePreferredSharedMemoryCarveout,
                        cudaSharedmemCarveoutMaxShared);
-  cudaError_t e = cudaFuncSetAttribute(k_gather, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int grid = L.tile_start[L.njobs];
   if (grid == 0) return cudaSuccess;
-  k_gather<<<grid, TX * TY, smem, st>>>(L);
+  k<<<grid, TX * TY, smem, st>>>(L);
   return cudaGetLastError();
 }
 

@@ -23,6 +23,9 @@ __device__ __forceinline__ float warp_max(float v) {
   return v;
 }
 
+// WRAP: some job has periodic x or y (exchange neighbours wrap around the
+// period); open boundaries run the instantiation without the wrap tests.
+template <bool WRAP>
 __global__ void __launch_bounds__(256) k_stage(const Launch<StageJob> Lc, const MechParams Perr, int* ticket) {
   __shared__ float red[8];
   const int j = find_job(Lc.tile_start, Lc.njobs, blockIdx.x);
@@ -55,7 +58,7 @@ __global__ void __launch_bounds__(256) k_stage(const Launch<StageJob> Lc, const 
       e1 += (coef) * (m[N + q] - m1);                                   \
       e2 += (coef) * (m[2 * N + q] - m2);                               \
     }
-    const bool wx = J.wrap[0] && nx > 1, wy = J.wrap[1] && ny > 1;
+    const bool wx = WRAP && J.wrap[0] && nx > 1, wy = WRAP && J.wrap[1] && ny > 1;
     MM_NB(x > 0 || wx, x > 0 ? -1 : (ptrdiff_t)nx - 1, J.ex[0])
     MM_NB(x < nx - 1 || wx, x < nx - 1 ? 1 : -((ptrdiff_t)nx - 1), J.ex[0])
     MM_NB(y > 0 || wy, y > 0 ? -(ptrdiff_t)nx : (ptrdiff_t)nx * (ny - 1), J.ex[1])
@@ -148,7 +151,10 @@ __global__ void __launch_bounds__(256) k_mech(const MechParams P) { mech_block(P
 cudaError_t launch_stage(const Launch<StageJob>& L, const MechParams& Perr, int* ticket, cudaStream_t st) {
   const int grid = L.tile_start[L.njobs];
   if (grid == 0) return cudaSuccess;
-  k_stage<<<grid, 256, 0, st>>>(L, Perr, ticket);
+  bool wrap = false;
+  for (int i = 0; i < L.njobs; ++i) wrap = wrap || L.job[i].wrap[0] || L.job[i].wrap[1];
+  if (wrap) k_stage<true><<<grid, 256, 0, st>>>(L, Perr, ticket);
+  else k_stage<false><<<grid, 256, 0, st>>>(L, Perr, ticket);
   return cudaGetLastError();
 }
 cudaError_t launch_combine(const Launch<CombineJob>& L, cudaStream_t st) {

@@ -100,3 +100,16 @@ def test_noalloc_argument_checks_without_gpu(lib):
     assert call((1.5, 1.5, 1.5), nx=4097, ny=4096, nz=1) == _native.MM_ETOOBIG
     # a tile count that wraps a 32-bit product must still be refused
     assert call((1.5, 1.5, 1.5), nx=2 ** 31 - 1, ny=2 ** 31 - 1, nz=4) == _native.MM_ETOOBIG
+
+
+def test_autotune_entry_points_without_gpu(lib):
+    """mm_autotune rejects a null context before any CUDA work; a length that
+    was never tuned has no tuned plan."""
+    from paper_1801_04181_gb300 import _native
+
+    L = _native.load()
+    n = ctypes.c_int(-1)
+    assert L.mm_autotune(None, 4, 3, ctypes.byref(n)) == _native.MM_EINVAL
+    r = (ctypes.c_int * 8)()
+    assert L.mm_get_tuned_plan(1234567, r, ctypes.byref(n)) == _native.MM_ESTATE
+    assert L.mm_get_tuned_plan(540, None, ctypes.byref(n)) == _native.MM_EINVAL

@@ -11,7 +11,9 @@ Patterns (reading of the workload descriptions):
     `size`-cell blocks (block boundaries shifted by a random phase), mz = +-1
     with a small seeded in-plane tilt, normalised;
   * vortex: m = normalise(-chi (y - yc), chi (x - xc), p exp(-rho^2 / rc^2))
-    with random chirality chi, polarity p and core offset.
+    with random chirality chi, polarity p and core offset;
+  * stripes: up/down stripes of a given width along x with a random phase
+    and a small seeded in-plane tilt.
 Arrays are float64, shape (3, nz, ny, nx), x fastest.
 """
 
@@ -127,6 +129,39 @@ def film_pair_stick_slip(n=(1024, 256, 2), gap=5, seed=0):
     fp = FilmPair("stick_slip_%dx%dx%d_gap%d" % (n + (gap,)), n, n, (4e-9, 4e-9, 4e-9), gap,
                   mat, mat, mech)
     return fp, pma_domains(n, seed), pma_domains(n, seed + 1)
+
+
+def stripes(shape_xyz, seed, width=20, tilt=0.05):
+    """Up/down stripe domains of `width` cells along x (stripes run along y),
+    phase drawn at random, mz = +-1 with a small seeded in-plane tilt, normalised."""
+    nx, ny, nz = shape_xyz
+    rng = np.random.default_rng(seed)
+    phase = int(rng.integers(0, 2 * width))
+    mz = np.where(((np.arange(nx) + phase) // width) % 2 == 0, 1.0, -1.0)
+    m = np.empty((3, nz, ny, nx))
+    m[2] = mz[None, None, :]
+    m[0:2] = tilt * rng.standard_normal((2, nz, ny, nx))
+    return m / np.sqrt(np.sum(m * m, axis=0, keepdims=True))
+
+
+def film_pair_friction(n=(256, 256, 5), gap=5, seed=0, pbc_images=2):
+    """The friction films of Sec. IV.B: 1024 x 1024 x 20 nm (256 x 256 x 5 cells
+    of 4 nm), 20 nm apart, periodic in the film plane, CoCrPt (Ku = 1.225e5 J/m^3
+    along z, Ms = 3.5e5 A/m, Aex = 5e-12 J/m, alpha = 0.05), ~80 nm (20-cell)
+    stripe domains, spring k = 0.005 N/m pulled at 2 m/s with the spring 80 nm
+    ahead of the slider.  Mass and viscous damping: critically damped, the
+    viscous force at v_d a tenth of a 0.7 nN magnetic force (the order of
+    Sec. IV.B's friction), so gamma_v m = 3.5e-11 kg/s, m = (gamma_v m)^2 / 4k.
+    Grain disorder is not modelled (uniform easy axis)."""
+    mat = Material(Ms=3.5e5, Aex=5e-12, Ku=1.225e5, ku_axis=(0.0, 0.0, 1.0), alpha=0.05)
+    gm = 3.5e-11
+    k = 0.005
+    mass = gm * gm / (4.0 * k)
+    mech = Mechanics(mass=mass, k=k, v_drive=2.0, gamma_v=gm / mass, dir=(1.0, 0.0, 0.0), x0_spring=80e-9)
+    fp = FilmPair("friction_%dx%dx%d_gap%d_pbc" % (n + (gap,)), n, n, (4e-9, 4e-9, 4e-9), gap, mat, mat, mech)
+    fp.periodic = 3
+    fp.pbc_images = pbc_images
+    return fp, stripes(n, seed), stripes(n, seed + 1)
 
 
 def cube_pair(n=(64, 64, 64), gap=3, seed=0):
