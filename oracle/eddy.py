@@ -1,0 +1,145 @@
+"""Eddy currents of a conducting magnet, FP64 (test infrastructure only).
+
+Sec. III.B (the method of Torres et al.): with the rate of change dB/dt of the
+flux density in the magnet's cells,
+
+  1. the solenoidal electric field by the cell-integrated kernel S of the
+     scalar potential (Sec. III.A),
+         E_sol(r_i) = -sum_j dB/dt(r_j) x S(r_i - r_j)
+     -- the sign of the section's first formula, -(1/4 pi) dB/dt x the
+     integral of (r - r')/|r - r'|^3, which is 4 pi S (Faraday's law; the
+     second printed form drops the minus);
+  2. the irrotational field E_irrot = -grad phi_E, phi_E solving Laplace's
+     equation in the magnet with d phi_E / dn = E_sol . n on its surface, so
+     that the current stays tangential to the surface;
+  3. J = sigma (E_sol + E_irrot), sigma uniform;
+  4. the field of the currents by the same kernel,
+         H_eddy(r_i) = sum_j J(r_j) x S(r_i - r_j)
+     (Biot-Savart: (1/4 pi) integral of J x (r - r')/|r - r'|^3).
+
+Discretisation of step 2 (the paper's is not given; this reading is the
+plain cell-centred one): for every cell and axis a of spacing d_a, the face
+flux towards a neighbour is (phi_nb - phi)/d_a and, on a surface face,
+d phi/dn = E_sol . n taken from the cell; the divergence of the fluxes is
+zero in every cell.  The source term is made exactly compatible by removing
+its mean, and phi_E has zero mean.  At a surface face the cell-centred
+gradient uses the ghost value that the boundary condition gives.
+"""
+
+import numpy as np
+from scipy.signal import fftconvolve
+from scipy.sparse import coo_matrix
+from scipy.sparse.linalg import cg
+
+from .kernels import S_kernel
+
+
+def self_S_window(n, cell):
+    """S over the offsets d = i - j of a magnet's own cells, (2nz-1, 2ny-1, 2nx-1, 3)."""
+    nx, ny, nz = n
+    dx, dy, dz = cell
+    Z, Y, X = np.meshgrid(np.arange(-(nz - 1), nz), np.arange(-(ny - 1), ny), np.arange(-(nx - 1), nx),
+                          indexing="ij")
+    return S_kernel(X * dx, Y * dy, Z * dz, dx, dy, dz)
+
+
+def cross_S(V, S):
+    """sum_j V(r_j) x S(r_i - r_j) over the own cells: (3, nz, ny, nx)."""
+    conv = [[fftconvolve(S[..., c], V[b], mode="valid") for c in range(3)] for b in range(3)]
+    out = np.empty_like(V)
+    out[0] = conv[1][2] - conv[2][1]
+    out[1] = conv[2][0] - conv[0][2]
+    out[2] = conv[0][1] - conv[1][0]
+    return out
+
+
+def neumann_system(n, cell, Esol):
+    """The cell-centred Neumann problem of step 2: (A, b) with A phi = b, the
+    source b compatible (zero mean)."""
+    nx, ny, nz = n
+    d = (cell[0], cell[1], cell[2])
+    N = nx * ny * nz
+    idx = np.arange(N).reshape(nz, ny, nx)
+    rows, cols, vals = [], [], []
+    b = np.zeros(N)
+    diag = np.zeros(N)
+    for a, ax in ((0, 2), (1, 1), (2, 0)):
+        w = 1.0 / (d[a] * d[a])
+        n_a = (nx, ny, nz)[a]
+        E = Esol[a]
+        for side in (+1, -1):
+            # cells whose neighbour on this side exists
+            sl_in = [slice(None)] * 3
+            sl_nb = [slice(None)] * 3
+            sl_bd = [slice(None)] * 3
+            if side > 0:
+                sl_in[ax] = slice(0, n_a - 1)
+                sl_nb[ax] = slice(1, n_a)
+                sl_bd[ax] = slice(n_a - 1, n_a)
+            else:
+                sl_in[ax] = slice(1, n_a)
+                sl_nb[ax] = slice(0, n_a - 1)
+                sl_bd[ax] = slice(0, 1)
+            i_in = idx[tuple(sl_in)].ravel()
+            i_nb = idx[tuple(sl_nb)].ravel()
+            rows.append(i_in)
+            cols.append(i_nb)
+            vals.append(np.full(i_in.size, w))
+            np.add.at(diag, i_in, -w)
+            # surface faces on this side: flux d phi / d x_a = E_sol,a of the cell
+            i_bd = idx[tuple(sl_bd)].ravel()
+            Eb = E[tuple(sl_bd)].ravel()
+            # divergence term (flux_plus - flux_minus) / d_a with the known flux moved to b
+            b[i_bd] -= side * Eb / d[a]
+    rows.append(np.arange(N))
+    cols.append(np.arange(N))
+    vals.append(diag)
+    A = coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(N, N)).tocsr()
+    return A, b - b.mean()
+
+
+def solve_phi(n, cell, Esol, tol=1e-13):
+    """phi_E with zero mean (conjugate gradients on the negative semi-definite system)."""
+    A, b = neumann_system(n, cell, Esol)
+    phi, info = cg(-A, -b, rtol=tol, atol=0.0, maxiter=20000)
+    if info != 0:
+        raise RuntimeError("phi_E did not converge")
+    phi -= phi.mean()
+    nx, ny, nz = n
+    return phi.reshape(nz, ny, nx)
+
+
+def grad_with_ghosts(phi, Esol, cell):
+    """Cell-centred gradient of phi; a missing neighbour is the ghost value of the
+    boundary condition (phi + d E_sol,a on the + side, phi - d E_sol,a on the - side)."""
+    g = np.empty((3,) + phi.shape)
+    for a, ax in ((0, 2), (1, 1), (2, 0)):
+        d = cell[a]
+        n_a = phi.shape[ax]
+        plus = np.roll(phi, -1, axis=ax)
+        minus = np.roll(phi, 1, axis=ax)
+        last = [slice(None)] * 3
+        first = [slice(None)] * 3
+        last[ax] = slice(n_a - 1, n_a)
+        first[ax] = slice(0, 1)
+        plus[tuple(last)] = phi[tuple(last)] + d * Esol[a][tuple(last)]
+        minus[tuple(first)] = phi[tuple(first)] - d * Esol[a][tuple(first)]
+        g[a] = (plus - minus) / (2 * d)
+    return g
+
+
+def eddy_field(dBdt, cell, sigma, S=None, return_all=False):
+    """Steps 1-4 for a magnet whose cells carry dB/dt (3, nz, ny, nx) in T/s:
+    H_eddy in A/m (and E_sol, phi_E, E_irrot, J with return_all)."""
+    _, nz, ny, nx = dBdt.shape
+    n = (nx, ny, nz)
+    if S is None:
+        S = self_S_window(n, cell)
+    Esol = -cross_S(dBdt, S)
+    phi = solve_phi(n, cell, Esol)
+    Eirr = -grad_with_ghosts(phi, Esol, cell)
+    J = sigma * (Esol + Eirr)
+    H = cross_S(J, S)
+    if return_all:
+        return dict(H=H, Esol=Esol, phi=phi, Eirr=Eirr, J=J)
+    return H

@@ -1,0 +1,131 @@
+"""Pins of the eddy-current oracle (oracle/eddy.py), CPU only.
+
+* step 1, E_sol = -sum dB/dt x S: far from one cell it is the point form
+  -V dB/dt x r / (4 pi r^3) with (d/r)^2 convergence; for a uniform dB/dt in
+  a cube it is -dB/dt x g, g = sum S the field of a uniform cube (div g = 1,
+  and by cubic symmetry (v . grad) g = v/3 at the centre), so its curl at the
+  centre is -dB/dt + dB/dt/3 = -(2/3) dB/dt (the dB/dt of the cells alone is
+  cut off at the surface) and its divergence vanishes;
+* step 2 reproduces a manufactured solution: phi* = x^2 - y^2 is harmonic
+  also for the discrete Laplacian, and with the surface fluxes it implies
+  the solver returns phi* - mean(phi*) exactly;
+* the current leaves no charge: the source the surface fluxes of E_sol make
+  has (nearly) zero sum, by the divergence theorem;
+* step 4, H = sum J x S: far from one cell it is the Biot-Savart point form
+  V J x r / (4 pi r^3);
+* Lenz's law: the field of the eddy currents a uniform dB/dt drives opposes
+  dB/dt at the centre of the magnet (this fixes the sign of step 1), and
+  it is linear in dB/dt.
+"""
+
+import numpy as np
+
+from oracle import eddy as E
+
+CELL = (2e-9, 2e-9, 2e-9)
+
+
+def _point_form(vec, r, V):
+    rn = np.linalg.norm(r)
+    return V * np.cross(vec, r) / (4 * np.pi * rn ** 3)
+
+
+def test_far_fields_are_the_point_forms():
+    """One source cell: E_sol -> -V dB/dt x r/(4 pi r^3), H -> V J x r/(4 pi r^3)."""
+    v = np.array([0.3, -0.7, 0.5])
+    errs = []
+    for dist in (8, 16):
+        n = (dist + 1, 1, 1)
+        V = np.zeros((3, 1, 1, dist + 1))
+        V[:, 0, 0, 0] = v
+        S = E.self_S_window(n, CELL)
+        out = E.cross_S(V, S)[:, 0, 0, dist]   # at the cell dist away along x
+        r = np.array([dist * CELL[0], 0.0, 0.0])
+        ref = -_point_form(-v, r, np.prod(CELL))  # cross_S gives + V x S; E_sol takes the minus
+        errs.append(np.linalg.norm(out - ref) / np.linalg.norm(ref))
+    assert errs[0] < 1e-2 and errs[1] < errs[0] / 3, errs
+
+
+def test_solenoidal_field_curl_and_divergence_in_a_cube():
+    n = (14, 14, 14)
+    B = np.zeros((3, 14, 14, 14))
+    Bdot = np.array([2e9, -1e9, 3e9])
+    for c in range(3):
+        B[c] = Bdot[c]
+    Es = -E.cross_S(B, E.self_S_window(n, CELL))
+    d = CELL[0]
+    c = slice(5, 9)
+
+    def dd(F, ax):
+        return (np.roll(F, -1, axis=ax) - np.roll(F, 1, axis=ax)) / (2 * d)
+    curl = np.stack([dd(Es[2], 1) - dd(Es[1], 0), dd(Es[0], 0) - dd(Es[2], 2), dd(Es[1], 2) - dd(Es[0], 1)])
+    div = dd(Es[0], 2) + dd(Es[1], 1) + dd(Es[2], 0)
+    for a in range(3):
+        got = curl[a][c, c, c]
+        assert np.max(np.abs(got + (2.0 / 3.0) * Bdot[a])) < 2e-2 * np.max(np.abs(Bdot))
+    assert np.max(np.abs(div[c, c, c])) < 2e-2 * np.max(np.abs(Bdot)) * 1.0
+
+
+def test_neumann_solver_reproduces_a_manufactured_solution():
+    cell = (2e-9, 3e-9, 1.5e-9)
+    nx, ny, nz = 7, 6, 4
+    z, y, x = np.meshgrid(np.arange(nz) * cell[2], np.arange(ny) * cell[1], np.arange(nx) * cell[0], indexing="ij")
+    phi_star = x ** 2 - (cell[0] / cell[1]) ** 0 * y ** 2   # discrete Laplacian: 2 - 2 = 0
+    Es = np.zeros((3, nz, ny, nx))
+    # surface fluxes of phi*: forward differences on + faces, backward on - faces
+    for a, ax, coord in ((0, 2, x), (1, 1, y), (2, 0, z)):
+        d = cell[a]
+        f = lambda q: q ** 2 if a == 0 else (-(q ** 2) if a == 1 else 0.0 * q)
+        last = [slice(None)] * 3
+        first = [slice(None)] * 3
+        n_a = (nx, ny, nz)[a]
+        last[ax] = slice(n_a - 1, n_a)
+        first[ax] = slice(0, 1)
+        q_last, q_first = coord[tuple(last)], coord[tuple(first)]
+        Es[a][tuple(last)] = (f(q_last + d) - f(q_last)) / d
+        Es[a][tuple(first)] = (f(q_first) - f(q_first - d)) / d
+    phi = E.solve_phi((nx, ny, nz), cell, Es)
+    ref = phi_star - phi_star.mean()
+    assert np.max(np.abs(phi - ref)) <= 1e-9 * np.max(np.abs(ref))
+    # and the ghost gradient is the exact gradient of the quadratic at the cell centres
+    g = E.grad_with_ghosts(phi, Es, cell)
+    assert np.max(np.abs(g[0] - 2 * x)) <= 1e-9 * np.max(np.abs(2 * x))
+    assert np.max(np.abs(g[1] + 2 * y)) <= 1e-9 * np.max(np.abs(2 * y))
+
+
+def test_surface_source_is_compatible():
+    rng = np.random.default_rng(3)
+    n = (10, 9, 8)
+    B = rng.standard_normal((3, 8, 9, 10)) * 1e9
+    Es = -E.cross_S(B, E.self_S_window(n, CELL))
+    A, b = E.neumann_system(n, CELL, Es)
+    # before the mean is removed: the net outward flux of E_sol is small against its terms
+    raw = b + 0.0
+    nx, ny, nz = n
+    flux = 0.0
+    scale = 0.0
+    for a, ax in ((0, 2), (1, 1), (2, 0)):
+        area = np.prod(CELL) / CELL[a]
+        n_a = n[a]
+        last = [slice(None)] * 3
+        first = [slice(None)] * 3
+        last[ax] = slice(n_a - 1, n_a)
+        first[ax] = slice(0, 1)
+        flux += area * (Es[a][tuple(last)].sum() - Es[a][tuple(first)].sum())
+        scale += area * (np.abs(Es[a][tuple(last)]).sum() + np.abs(Es[a][tuple(first)]).sum())
+    assert abs(flux) < 5e-2 * scale
+    assert abs(raw.sum()) < 1e-12 * np.abs(raw).sum()  # the mean is removed
+
+
+def test_lenz_law_and_linearity():
+    n = (10, 10, 10)
+    B = np.zeros((3, 10, 10, 10))
+    B[2] = 1e9
+    S = E.self_S_window(n, CELL)
+    H = E.eddy_field(B, CELL, 1e6, S=S)
+    c = slice(4, 6)
+    assert np.all(H[2][c, c, c] < 0)
+    # (the central 2 x 2 x 2 cells sit half a cell off the centre: a small radial part)
+    assert np.max(np.abs(H[:2][:, c, c, c])) < 2e-2 * np.max(np.abs(H[2][c, c, c]))
+    H2 = E.eddy_field(-2.5 * B, CELL, 1e6, S=S)
+    assert np.max(np.abs(H2 + 2.5 * H)) <= 1e-9 * np.max(np.abs(H))
