@@ -42,7 +42,7 @@ typedef enum {
   MM_ENOMEM = -2,   /* device allocation failed */
   MM_ECUDA = -3,    /* CUDA runtime error (message in mm_last_error) */
   MM_ERANGE = -4,   /* displacement left the planned potential box */
-  MM_ETIMEOUT = -5, /* reserved */
+  MM_ETIMEOUT = -5, /* an iteration did not converge within its bound (mm_eddy_field) */
   MM_ESTATE = -6,   /* state buffer of the wrong size or version */
   MM_ENOTSUP = -7,  /* geometry or option the library does not support */
   MM_ETOOBIG = -8   /* larger than the fixed scratch of mm_spline_field_noalloc */
@@ -304,6 +304,31 @@ mm_status mm_compute_stray_field_fd4(mm_ctx* ctx, int src, float* H_dev);
  * energy.  Sources of more than 8 layers (z by FFT): MM_ENOTSUP.
  */
 mm_status mm_compute_stray_field_componentwise(mm_ctx* ctx, int src, float* H_dev);
+
+/*
+ * Eddy currents of conducting magnet `mag` (Sec. III.B, the method of Torres
+ * et al.), from the rate of change of the flux density in its cells,
+ * dBdt_dev (3 N floats, T/s, SoA like m; for B = mu0 (H_d + H_ext + M) the
+ * caller forms it, e.g. from dm/dt and the demag of dM/dt), and a uniform
+ * conductivity sigma (S/m):
+ *   1. E_sol(r_i) = -sum_j dB/dt(r_j) x S(r_i - r_j), S the cell-integrated
+ *      kernel of the scalar potential (Sec. III.A); the sign of the section's
+ *      first formula (Faraday's law), which its second form drops;
+ *   2. phi_E: Laplace's equation in the magnet with d phi_E / dn = E_sol . n
+ *      on its surface, cell-centred (flux (phi_nb - phi) / d between cells,
+ *      E_sol . n of the cell at surface faces, the source's mean removed),
+ *      solved by red-black successive over-relaxation in FP64 to a max-norm
+ *      residual of 1e-9 of the source (at most 40000 sweeps; MM_ETIMEOUT
+ *      otherwise), zero mean;
+ *   3. J = sigma (E_sol - grad phi_E), the gradient taking the boundary
+ *      condition's ghost values at surface faces;
+ *   4. H_eddy(r_i) = sum_j J(r_j) x S(r_i - r_j) (Biot-Savart), A/m.
+ * H_dev, J_dev: 3 N floats each (A/m, A/m^2), either may be NULL; sweeps_out:
+ * the SOR sweeps taken (may be NULL).  Device pointers, caller-owned.
+ * Synchronises.  MM_ENOTSUP under periodic boundaries.
+ */
+mm_status mm_eddy_field(mm_ctx* ctx, int mag, const float* dBdt_dev, double sigma, float* H_dev, float* J_dev,
+                        int* sweeps_out);
 
 /*
  * Divergence and curl diagnostics of a field (Sec. IV.A): for H_dev (3 N

@@ -172,6 +172,19 @@ class MovingMagnets:
         self._c(self.lib.mm_compute_stray_field_componentwise(self.ctx, src, _ptr(H)))
         return self._out(H)
 
+    def eddy_field(self, mag, dBdt, sigma):
+        """mm_eddy_field: (H_eddy (A/m), J (A/m^2), SOR sweeps) of magnet `mag`
+        for the flux-density rate dBdt ((3, nz, ny, nx) float32 CUDA, T/s) and
+        conductivity sigma (S/m)."""
+        _need_cuda_f32(dBdt, self.shapes[mag])
+        H = torch.empty(self.shapes[mag], dtype=torch.float32, device="cuda")
+        J = torch.empty(self.shapes[mag], dtype=torch.float32, device="cuda")
+        n = C.c_int()
+        self._in()
+        self._c(self.lib.mm_eddy_field(self.ctx, mag, _ptr(dBdt), float(sigma), _ptr(H), _ptr(J), C.byref(n)))
+        self._out(H, J)
+        return H, J, n.value
+
     def compute_demag(self, mag):
         H = torch.empty(self.shapes[mag], dtype=torch.float32, device="cuda")
         self._in()

@@ -132,6 +132,17 @@ struct Magnet {
   Dir cw;    // componentwise field variant: three coefficient boxes
   float2* cw_Y = nullptr;  // its y-forward spectra [3 nz][kxh][Qy]
   size_t cw_Y_bytes = 0;
+  // eddy currents: the potential path on the magnet's own cells, the
+  // rearranged input, E_sol, the Neumann source, phi_E, J, reduction scratch
+  Dir eddy;
+  float* ed_V = nullptr;
+  float* ed_E = nullptr;
+  double* ed_b = nullptr;
+  double* ed_phi = nullptr;
+  float* ed_J = nullptr;
+  double* ed_part = nullptr;
+  double* ed_stats = nullptr;  // max residual, max |b|, mean phi, mean b
+  size_t ed_bytes[7] = {};
 };
 
 struct TimedLaunch {
@@ -1484,6 +1495,9 @@ void mm_destroy(mm_ctx* ctx) {
     free_dir(M.aux);
     free_dir(M.cw);
     cudaFree(M.cw_Y);
+    free_dir(M.eddy);
+    cudaFree(M.ed_V); cudaFree(M.ed_E); cudaFree(M.ed_b); cudaFree(M.ed_phi); cudaFree(M.ed_J);
+    cudaFree(M.ed_part); cudaFree(M.ed_stats);
   }
   for (auto& kv : ctx->ffts) {
     cudaFree(kv.second.tw_f); cudaFree(kv.second.tw_d); cudaFree(kv.second.pos); cudaFree(kv.second.freq);
@@ -2032,6 +2046,95 @@ mm_status mm_compute_stray_field_componentwise(mm_ctx* ctx, int src, float* H_de
   const int nt[3] = {T.nx, T.ny, T.nz};
   CK(launch_field_values(D.C, bdim, nt, ctx->opt.margin, frac, H_dev, st));
   D.valid = false;
+  return MM_OK;
+}
+
+// sum_j V(r_j) x S(r_i - r_j) over the magnet's own cells, scaled by s, into
+// out (3 N): per component the potential path on the self box with the
+// rearranged input (the result of a pass is Ms S . V', hence s / Ms).
+static mm_status self_cross_S(mm_ctx* ctx, int g, const float* V, double s, float* out) {
+  Magnet& M = ctx->mag[g];
+  Dir& D = M.eddy;
+  const float* in[2] = {ctx->mag[0].m, ctx->mag[1].m};
+  in[g] = M.ed_V;
+  const int which[1] = {g};
+  const int what[1] = {2};
+  Dir* dirs[1] = {&D};
+  for (int comp = 0; comp < 3; ++comp) {
+    CK(launch_cross_input(V, M.N, comp, M.ed_V, ctx->st));
+    CKS(run_source_passes(ctx, in, which, 1, what, dirs));
+    CK(launch_scale_into(D.C, M.N, (float)(s / M.Ms), out + comp * M.N, ctx->st));
+  }
+  return MM_OK;
+}
+
+mm_status mm_eddy_field(mm_ctx* ctx, int mag, const float* dBdt_dev, double sigma, float* H_dev, float* J_dev,
+                        int* sweeps_out) {
+  if (!ctx || bad_mag(mag) || !dBdt_dev || !(sigma >= 0) || !std::isfinite(sigma))
+    return ctx ? fail(ctx, MM_EINVAL, "mm_eddy_field") : MM_EINVAL;
+  if (ctx->opt.periodic) return fail(ctx, MM_ENOTSUP, "mm_eddy_field: periodic boundaries");
+  CKS(prepare(ctx));
+  Magnet& M = ctx->mag[mag];
+  cudaStream_t st = ctx->st;
+  // the box of the potential path: output nodes are the magnet's own cells
+  Dir& D = M.eddy;
+  const int n[3] = {M.nx, M.ny, M.nz};
+  for (int a = 0; a < 3; ++a) {
+    D.U0[a] = 0;
+    D.box_lo[a] = -1 - ctx->opt.margin;
+    D.box_len[a] = n[a] + 3 + 2 * ctx->opt.margin;
+    D.start[a] = 1 + ctx->opt.margin;
+    D.r[a] = n[a];
+    D.guard[a] = 0;
+  }
+  D.full_box = false;
+  D.prefilter = 0;
+  if (!M.thick && (size_t)std::max(3 * M.nz, D.r[2]) * M.Qy * sizeof(float2) > 220 * 1024)
+    return fail(ctx, MM_ENOTSUP, "mm_eddy_field: magnet too tall for the fused y pass");
+  if (!M.zfft) CKS(build_T(ctx, mag, &D));
+  const size_t N = M.N;
+  const int nb = eddy_blocks(N);
+  if (M.thick) CKS(ensure_buf(ctx, &D.Z3C, &D.Z3C_bytes, sizeof(float2) * (size_t)D.r[2] * M.kxh * M.Qy));
+  CKS(ensure_buf(ctx, &D.YC, &D.YC_bytes, sizeof(float2) * (size_t)D.r[2] * M.kxh * D.r[1]));
+  CKS(ensure_buf(ctx, &D.C, &D.C_bytes, sizeof(float) * N));
+  CKS(ensure_buf(ctx, &M.ed_V, &M.ed_bytes[0], sizeof(float) * 3 * N));
+  CKS(ensure_buf(ctx, &M.ed_E, &M.ed_bytes[1], sizeof(float) * 3 * N));
+  CKS(ensure_buf(ctx, &M.ed_b, &M.ed_bytes[2], sizeof(double) * N));
+  CKS(ensure_buf(ctx, &M.ed_phi, &M.ed_bytes[3], sizeof(double) * N));
+  CKS(ensure_buf(ctx, &M.ed_J, &M.ed_bytes[4], sizeof(float) * 3 * N));
+  CKS(ensure_buf(ctx, &M.ed_part, &M.ed_bytes[5], sizeof(double) * 3 * (size_t)nb));
+  CKS(ensure_buf(ctx, &M.ed_stats, &M.ed_bytes[6], sizeof(double) * 4));
+  CKS(join_mech(ctx));
+  // 1. E_sol = -sum dB/dt x S
+  CKS(self_cross_S(ctx, mag, dBdt_dev, -1.0, M.ed_E));
+  // 2. phi_E: Neumann source (mean removed), red-black SOR to a residual of
+  //    kTol of the source, bounded sweeps; mean of phi removed in step 3
+  CK(launch_eddy_source(M.ed_E, M.nx, M.ny, M.nz, M.d, M.ed_b, M.ed_part, M.ed_stats + 3, st));
+  CK(cudaMemsetAsync(M.ed_phi, 0, sizeof(double) * N, st));
+  const int nmax = std::max(M.nx, std::max(M.ny, M.nz));
+  const double omega = 2.0 / (1.0 + sin(3.14159265358979323846 / std::max(nmax, 2)));
+  constexpr int kCheck = 25, kMaxSweeps = 40000;
+  constexpr double kTol = 1e-9;
+  int sweeps = 0;
+  double stats[3] = {0, 0, 0};
+  for (;;) {
+    CK(launch_sor_residual(M.ed_phi, M.ed_b, M.ed_stats + 3, M.nx, M.ny, M.nz, M.d, M.ed_part, M.ed_stats, st));
+    CK(cudaMemcpyAsync(stats, M.ed_stats, sizeof(stats), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (stats[0] <= kTol * stats[1] || stats[1] == 0.0) break;
+    if (sweeps >= kMaxSweeps) {
+      if (sweeps_out) *sweeps_out = sweeps;
+      return fail(ctx, MM_ETIMEOUT, "mm_eddy_field: the electric potential did not converge");
+    }
+    CK(launch_sor_sweeps(M.ed_phi, M.ed_b, M.ed_stats + 3, M.nx, M.ny, M.nz, M.d, omega, kCheck, st));
+    sweeps += kCheck;
+  }
+  if (sweeps_out) *sweeps_out = sweeps;
+  // 3. J = sigma (E_sol - grad phi_E)
+  float* J = J_dev ? J_dev : M.ed_J;
+  CK(launch_eddy_current(M.ed_phi, M.ed_stats, M.ed_E, M.nx, M.ny, M.nz, M.d, sigma, J, st));
+  // 4. H_eddy = sum J x S
+  if (H_dev) CKS(self_cross_S(ctx, mag, J, 1.0, H_dev));
   return MM_OK;
 }
 

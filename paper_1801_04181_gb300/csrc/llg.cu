@@ -58,11 +58,18 @@ __global__ void __launch_bounds__(256) k_stage(const Launch<StageJob> Lc, const 
       e1 += (coef) * (m[N + q] - m1);                                   \
       e2 += (coef) * (m[2 * N + q] - m2);                               \
     }
-    const bool wx = WRAP && J.wrap[0] && nx > 1, wy = WRAP && J.wrap[1] && ny > 1;
-    MM_NB(x > 0 || wx, x > 0 ? -1 : (ptrdiff_t)nx - 1, J.ex[0])
-    MM_NB(x < nx - 1 || wx, x < nx - 1 ? 1 : -((ptrdiff_t)nx - 1), J.ex[0])
-    MM_NB(y > 0 || wy, y > 0 ? -(ptrdiff_t)nx : (ptrdiff_t)nx * (ny - 1), J.ex[1])
-    MM_NB(y < ny - 1 || wy, y < ny - 1 ? (ptrdiff_t)nx : -(ptrdiff_t)nx * (ny - 1), J.ex[1])
+    if constexpr (WRAP) {
+      const bool wx = J.wrap[0] && nx > 1, wy = J.wrap[1] && ny > 1;
+      MM_NB(x > 0 || wx, x > 0 ? -1 : (ptrdiff_t)nx - 1, J.ex[0])
+      MM_NB(x < nx - 1 || wx, x < nx - 1 ? 1 : -((ptrdiff_t)nx - 1), J.ex[0])
+      MM_NB(y > 0 || wy, y > 0 ? -(ptrdiff_t)nx : (ptrdiff_t)nx * (ny - 1), J.ex[1])
+      MM_NB(y < ny - 1 || wy, y < ny - 1 ? (ptrdiff_t)nx : -(ptrdiff_t)nx * (ny - 1), J.ex[1])
+    } else {
+      MM_NB(x > 0, -1, J.ex[0])
+      MM_NB(x < nx - 1, 1, J.ex[0])
+      MM_NB(y > 0, -(ptrdiff_t)nx, J.ex[1])
+      MM_NB(y < ny - 1, (ptrdiff_t)nx, J.ex[1])
+    }
     MM_NB(z > 0, -(ptrdiff_t)nx * ny, J.ex[2])
     MM_NB(z < nz - 1, (ptrdiff_t)nx * ny, J.ex[2])
 #undef MM_NB

@@ -306,6 +306,19 @@ int power_blocks(size_t N);
 cudaError_t launch_mxh2(const float* m, const float* H, size_t N, double* partial, double* out, cudaStream_t st);
 // four-point difference gradient of the interpolant (variants.cu): V holds
 // (nx + 4)(ny + 4)(nz + 4) floats, H 3 nx ny nz; needs margin >= 2
+// eddy currents (eddy.cu)
+cudaError_t launch_cross_input(const float* V, size_t N, int comp, float* out, cudaStream_t st);
+cudaError_t launch_scale_into(const float* in, size_t N, float s, float* out, cudaStream_t st);
+int eddy_blocks(size_t N);
+cudaError_t launch_eddy_source(const float* E, int nx, int ny, int nz, const double d[3], double* b, double* part,
+                               double* bmean, cudaStream_t st);
+cudaError_t launch_sor_sweeps(double* phi, const double* b, const double* bmean, int nx, int ny, int nz,
+                              const double d[3], double omega, int sweeps, cudaStream_t st);
+cudaError_t launch_sor_residual(const double* phi, const double* b, const double* bmean, int nx, int ny, int nz,
+                                const double d[3], double* part, double* stats, cudaStream_t st);
+cudaError_t launch_eddy_current(const double* phi, const double* stats, const float* E, int nx, int ny, int nz,
+                                const double d[3], double sigma, float* J, cudaStream_t st);
+
 // componentwise field variant (variants.cu): H_a at every target centre from
 // the coefficients C [3][bdim z][bdim y][bdim x] of the three components on
 // the full box (taps of centre i start at node i + margin)
