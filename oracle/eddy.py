@@ -17,6 +17,9 @@ flux density in the magnet's cells,
          H_eddy(r_i) = sum_j J(r_j) x S(r_i - r_j)
      (Biot-Savart: (1/4 pi) integral of J x (r - r')/|r - r'|^3).
 
+EddyCoupledSystem / run_fixed_eddy put H_eddy into the effective field of
+the time step (the coupling, a reading stated there).
+
 Discretisation of step 2 (the paper's is not given; this reading is the
 plain cell-centred one): for every cell and axis a of spacing d_a, the face
 flux towards a neighbour is (phi_nb - phi)/d_a and, on a surface face,
@@ -31,6 +34,7 @@ from scipy.signal import fftconvolve
 from scipy.sparse import coo_matrix
 from scipy.sparse.linalg import cg
 
+from . import MU0
 from .kernels import S_kernel
 
 
@@ -143,3 +147,81 @@ def eddy_field(dBdt, cell, sigma, S=None, return_all=False):
     if return_all:
         return dict(H=H, Esol=Esol, phi=phi, Eirr=Eirr, J=J)
     return H
+
+
+class EddyCoupledSystem:
+    """dynamics.System with the eddy fields of conducting magnets in H_eff.
+
+    Reading of the coupling (the section gives the field computation, not
+    its place in the time step): explicit and lagged by one accepted step.
+    After step n the flux density of magnet g,
+        B_n = mu0 (H_demag + H_stray + H_ext + Ms y5),
+    is taken from the step's last field evaluation (the first-same-as-last
+    stage at the 5th-order solution y5), dB/dt = (B_n - B_{n-1}) / dt_n, and
+    H_eddy(dB/dt) of steps 1-4 is added to H_eff in every stage of step n + 1.
+    No eddy field before the first step, nor before a second B exists.
+    sigma: conductivity of each magnet (S/m, 0 = insulating)."""
+
+    def __init__(self, system, sigma):
+        self.sys = system
+        self.sigma = tuple(float(s) for s in sigma)
+        self.Heddy = [None, None]
+        self.B_prev = [None, None]
+        self.last_B = None
+        self.S = {}
+
+    def fields(self, m0, m1, x):
+        from .dynamics import anisotropy_field, exchange_field
+        from .interaction import stray_interaction
+        s = self.sys
+        u = s.displacement(x)
+        M0, M1 = s.mat[0]["Ms"] * m0, s.mat[1]["Ms"] * m1
+        on1 = stray_interaction(M0, M1, s.cell, s.offsets[0], s.offsets[1], u, True, kernel_cache=s.cache)
+        on0 = stray_interaction(M1, M0, s.cell, s.offsets[1], s.offsets[0], u, False, kernel_cache=s.cache)
+        H, B = [], []
+        for g, (m, stray) in enumerate(((m0, on0["H"]), (m1, on1["H"]))):
+            p = s.mat[g]
+            hd = s.demag(g, m) + stray + s.H_ext[:, None, None, None]
+            B.append(MU0 * (hd + p["Ms"] * m))
+            h = hd + exchange_field(m, p["Ms"], p["Aex"], s.cell)
+            h = h + anisotropy_field(m, p["Ms"], p["Ku"], p["ku_axis"])
+            if self.Heddy[g] is not None:
+                h = h + self.Heddy[g]
+            H.append(h)
+        self.last_B = B
+        return H, on1, on0
+
+    def rhs(self, t, y):
+        from .dynamics import llg_rhs
+        m0, m1, x, v = y
+        H, on1, _ = self.fields(m0, m1, x)
+        me = self.sys.mech
+        F = float(np.dot(on1["F"], self.sys.e))
+        acc = (me["k"] * (me["v_drive"] * t + me.get("x0_spring", 0.0) - x)
+               - me["gamma_v"] * me["mass"] * v + F) / me["mass"]
+        return [llg_rhs(m0, H[0], self.sys.mat[0]["alpha"]), llg_rhs(m1, H[1], self.sys.mat[1]["alpha"]), v, acc]
+
+    def accept(self, dt):
+        """After an accepted step (last evaluation at y5): update the eddy fields."""
+        for g in (0, 1):
+            B = self.last_B[g]
+            if self.sigma[g] > 0.0 and self.B_prev[g] is not None:
+                _, nz, ny, nx = B.shape
+                if g not in self.S:
+                    self.S[g] = self_S_window((nx, ny, nz), self.sys.cell)
+                self.Heddy[g] = eddy_field((B - self.B_prev[g]) / dt, self.sys.cell, self.sigma[g], S=self.S[g])
+            self.B_prev[g] = B
+
+
+def run_fixed_eddy(coupled, y0, dt, nsteps, t0=0.0):
+    """dynamics.run_fixed for an EddyCoupledSystem: fixed-dt Dormand-Prince
+    steps with first-same-as-last reuse, the eddy fields updated after each."""
+    from .dynamics import dp45_step, normalise
+    t, y, k1 = t0, list(y0), None
+    for _ in range(nsteps):
+        y5, _, k7 = dp45_step(coupled, t, y, dt, k1)
+        coupled.accept(dt)
+        y = [normalise(y5[0]), normalise(y5[1]), y5[2], y5[3]]
+        t += dt
+        k1 = k7
+    return t, y

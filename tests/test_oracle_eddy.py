@@ -129,3 +129,43 @@ def test_lenz_law_and_linearity():
     assert np.max(np.abs(H[:2][:, c, c, c])) < 2e-2 * np.max(np.abs(H[2][c, c, c]))
     H2 = E.eddy_field(-2.5 * B, CELL, 1e6, S=S)
     assert np.max(np.abs(H2 + 2.5 * H)) <= 1e-9 * np.max(np.abs(H))
+
+
+def test_coupled_system_without_conductivity_is_the_plain_system():
+    """sigma = 0: the eddy-coupled time step is the plain one (only the order
+    of the field sums differs)."""
+    import workloads
+    from oracle import dynamics as D
+    from tests.pair_setup import oracle_system
+
+    fp, m0, m1 = workloads.film_pair_stick_slip(n=(12, 8, 2), gap=3, seed=2)
+    fp.mech.x0_spring = 2e-9
+    y0 = [m0, m1, 0.0, 0.0]
+    t_a, ya = D.run_fixed(oracle_system(fp), y0, 5e-14, 3)
+    t_b, yb = E.run_fixed_eddy(E.EddyCoupledSystem(oracle_system(fp), (0.0, 0.0)), y0, 5e-14, 3)
+    assert t_a == t_b
+    for g in (0, 1):
+        assert np.max(np.abs(ya[g] - yb[g])) < 1e-12
+    assert abs(ya[2] - yb[2]) <= 1e-12 * abs(ya[2])
+
+
+def test_coupled_eddy_field_is_lagged_by_one_step():
+    """The first step runs without eddy field and only records B; after the
+    second, H_eddy is the eddy field of (B_2 - B_1)/dt, linear in sigma; an
+    insulating magnet gets none."""
+    import workloads
+    from tests.pair_setup import oracle_system
+
+    fp, m0, m1 = workloads.film_pair_stick_slip(n=(12, 8, 2), gap=3, seed=2)
+    y0 = [m0, m1, 0.0, 0.0]
+    one = E.EddyCoupledSystem(oracle_system(fp), (2e6, 0.0))
+    E.run_fixed_eddy(one, y0, 5e-14, 1)
+    assert one.Heddy[0] is None and one.B_prev[0] is not None
+    cs = E.EddyCoupledSystem(oracle_system(fp), (2e6, 0.0))
+    E.run_fixed_eddy(cs, y0, 5e-14, 2)
+    assert cs.Heddy[1] is None and cs.Heddy[0] is not None
+    ref = E.eddy_field((cs.B_prev[0] - one.B_prev[0]) / 5e-14, fp.cell, 2e6)
+    assert np.max(np.abs(cs.Heddy[0] - ref)) <= 1e-9 * np.max(np.abs(ref))
+    cs2 = E.EddyCoupledSystem(oracle_system(fp), (4e6, 0.0))
+    E.run_fixed_eddy(cs2, y0, 5e-14, 2)
+    assert np.max(np.abs(cs2.Heddy[0] - 2.0 * cs.Heddy[0])) <= 1e-9 * np.max(np.abs(cs.Heddy[0]))
