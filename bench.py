@@ -60,7 +60,8 @@ def parse():
     p.add_argument("--no-autotune", action="store_true",
                    help="batch256: keep the planner's model FFT plans instead of timing candidates per length")
     p.add_argument("--workload", default="stick_slip",
-                   choices=sorted(WORKLOADS) + ["plain64_sweep", "cubes64_gradients", "batch256", "divcurl_sweep"],
+                   choices=sorted(WORKLOADS) + ["plain64_sweep", "cubes64_gradients", "batch256", "divcurl_sweep",
+                                                "eddy_cube64"],
                    help="stick_slip (the headline workload), a thick-source workload, or the "
                         "plain 64x64x1 film pair swept over 16 sub-cell offsets (stray field only)")
     return p.parse_args()
@@ -702,6 +703,45 @@ def run_gradients(args):
     mm.close()
 
 
+def run_eddy(args):
+    """Eddy currents of a conducting 64^3 vortex cube (2 nm, Sec. III.B): one
+    step is mm_eddy_field -- E_sol and H_eddy by cross products with S
+    through the potential path, the electric potential by FP64 SOR to 1e-9 of
+    its source, the current.  Drive: dB/dt = mu0 Ms dm/dt of the cube's own
+    LLG motion at the seeded state (the rate of its demag field left out),
+    sigma = 1e6 S/m.  Metric: cells / time (host-timed, one synchronisation
+    per call, the SOR convergence checks included)."""
+    import torch
+    import workloads
+    from paper_1801_04181_gb300 import pair_context as gpu_pair
+
+    fp, m0, m1 = workloads.cube_pair((64, 64, 64), 3, args.seed)
+    mm = gpu_pair(fp, m0, m1, mech=False)
+    dm, _ = mm.compute_torque(0)
+    mu0 = 4e-7 * np.pi
+    dB = (mu0 * fp.mat_base.Ms * dm).contiguous()
+    sigma = 1e6
+    sweeps = 0
+    for _ in range(max(args.warmup, 3)):
+        _, _, sweeps = mm.eddy_field(0, dB, sigma)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        _, _, sweeps = mm.eddy_field(0, dB, sigma)
+    torch.cuda.synchronize()
+    s = time.perf_counter() - t0
+    N = int(np.prod(fp.n_base))
+    line = {"metric": "eddy-field cell-evaluations/s (64^3 conducting vortex cube)",
+            "value": N * args.steps / s, "unit": "cell-evaluations/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": 1e3 * s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (electric potential f64)", "data": "synthetic",
+            "config": {"workload": "vortex cube 64x64x64 (2 nm), dB/dt = mu0 Ms dm/dt, sigma = 1e6 S/m",
+                       "cells": N, "sor_sweeps": sweeps,
+                       "step": "mm_eddy_field: 6 potential-path passes, SOR, current; host-timed"}}
+    print(json.dumps(line))
+    mm.close()
+
+
 def batch_cost(fp):
     """Cost model for spreading pairs: grid area x (source layers + box layers)."""
     return fp.n_base[0] * fp.n_base[1] * (fp.n_base[2] + 4)
@@ -889,6 +929,8 @@ def main():
         run_batch(args)
     elif args.workload == "divcurl_sweep":
         run_divcurl(args)
+    elif args.workload == "eddy_cube64":
+        run_eddy(args)
     else:
         run_gpu(args)
 

@@ -331,6 +331,27 @@ mm_status mm_eddy_field(mm_ctx* ctx, int mag, const float* dBdt_dev, double sigm
                         int* sweeps_out);
 
 /*
+ * Conductivity sigma (S/m) of magnet `mag`; sigma > 0 couples its eddy field
+ * into the time step (Sec. III.B: the eddy field joins the effective field).
+ * Reading of the coupling (the paper gives the field computation, not its
+ * place in the step): explicit and lagged by one accepted step.  After each
+ * accepted step, B = mu0 (H_demag + H_stray + H_ext + Ms y5) of the step's
+ * last field evaluation (the first-same-as-last stage at the 5th-order
+ * solution y5); with the B of the previous step, dB/dt = (B - B_prev) / dt,
+ * and the eddy field of mm_eddy_field's steps 1-4 is added to H_eff in every
+ * stage of the next step.  Setting m, the displacement, the slider state, the
+ * external field, a material or the checkpoint state restarts the lag (no
+ * eddy field until two steps have passed).  sigma = 0 (default) turns it off.
+ * Each accepted step then runs the SOR of step 2 (synchronising).  Not under
+ * periodic boundaries (MM_ENOTSUP).
+ */
+mm_status mm_set_conductivity(mm_ctx* ctx, int mag, double sigma);
+
+/* The eddy field the next step's stages add for magnet `mag` (3 N floats,
+ * A/m, device pointer); zeros while there is none. */
+mm_status mm_get_eddy_field(mm_ctx* ctx, int mag, float* H_dev);
+
+/*
  * Divergence and curl diagnostics of a field (Sec. IV.A): for H_dev (3 N
  * floats, [3][nz][ny][nx], A/m, device) on cells dx x dy x dz,
  *   D = (1/N') sum |div H|,  C = (1/N') sum ||curl H||   (A/m^2)

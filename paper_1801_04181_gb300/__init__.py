@@ -185,6 +185,17 @@ class MovingMagnets:
         self._out(H, J)
         return H, J, n.value
 
+    def set_conductivity(self, mag, sigma):
+        """mm_set_conductivity: couple the eddy field of magnet `mag` (sigma S/m) into the step."""
+        self._c(self.lib.mm_set_conductivity(self.ctx, mag, float(sigma)))
+
+    def get_eddy_field(self, mag):
+        """mm_get_eddy_field: the eddy field the next step adds for magnet `mag`."""
+        H = torch.empty(self.shapes[mag], dtype=torch.float32, device="cuda")
+        self._in()
+        self._c(self.lib.mm_get_eddy_field(self.ctx, mag, _ptr(H)))
+        return self._out(H)
+
     def compute_demag(self, mag):
         H = torch.empty(self.shapes[mag], dtype=torch.float32, device="cuda")
         self._in()

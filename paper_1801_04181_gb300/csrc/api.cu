@@ -143,6 +143,14 @@ struct Magnet {
   double* ed_part = nullptr;
   double* ed_stats = nullptr;  // max residual, max |b|, mean phi, mean b
   size_t ed_bytes[7] = {};
+  // eddy currents coupled into the time step (a conducting magnet, sigma > 0):
+  // B of the last accepted step, its rate, the eddy field used by the stages
+  double sigma = 0;
+  float* Bprev = nullptr;
+  float* Bdot = nullptr;
+  float* Heddy = nullptr;
+  size_t eb_bytes[3] = {};
+  bool B_valid = false, Heddy_valid = false;
 };
 
 struct TimedLaunch {
@@ -214,8 +222,18 @@ struct mm_ctx {
   long long launches = 0;
 };
 
+// eddy-current field of one magnet (steps 1-4 of Sec. III.B), defined with mm_eddy_field
+static mm_status eddy_core(mm_ctx* ctx, int mag, const float* dBdt_dev, double sigma, float* H_dev, float* J_dev,
+                           int* sweeps_out);
+
 // ============================================================ helpers
 namespace {
+
+// A change made from outside the time step (m, displacement, slider, fields,
+// materials, state) breaks the eddy fields' lag: B starts afresh.
+void reset_eddy(mm_ctx* ctx) {
+  for (auto& M : ctx->mag) M.B_valid = M.Heddy_valid = false;
+}
 
 mm_status fail(mm_ctx* c, mm_status s, const std::string& msg) {
   if (c) c->err = msg;
@@ -1223,6 +1241,7 @@ StageJob stage_job(mm_ctx* ctx, int g, const float* ys, float* ys_next, int stag
   for (int i = 0; i < 7; ++i) J.k[i] = kptr[i];
   J.Hself = M.Hself;
   J.Hstray = M.Hstray;
+  J.Heddy = (M.sigma > 0.0 && M.Heddy_valid) ? M.Heddy : nullptr;
   J.Heff = Heff;
   J.nx = M.nx; J.ny = M.ny; J.nz = M.nz;
   J.wrap[0] = periodic_axis(ctx, 0) ? 1 : 0;
@@ -1367,6 +1386,23 @@ mm_status conclude_attempt(mm_ctx* ctx, double* dt_io, double err, bool* accepte
       Timer t(ctx, 6);
       CK(launch_normalise(L, ctx->st));
     }
+    // conducting magnets: B of this step's last evaluation (the stage-7 fields
+    // at the 5th-order solution ys[1]), its rate since the last step, and the
+    // eddy field the next step's stages add to H_eff (lagged by one step)
+    for (int g = 0; g < 2; ++g) {
+      Magnet& M = ctx->mag[g];
+      if (!(M.sigma > 0.0)) continue;
+      CKS(ensure_buf(ctx, &M.Bprev, &M.eb_bytes[0], sizeof(float) * 3 * M.N));
+      CKS(ensure_buf(ctx, &M.Bdot, &M.eb_bytes[1], sizeof(float) * 3 * M.N));
+      CKS(ensure_buf(ctx, &M.Heddy, &M.eb_bytes[2], sizeof(float) * 3 * M.N));
+      CK(launch_flux_rate(M.Hself, M.Hstray, M.ys[1], M.N, ctx->Hext, M.Ms, dt, M.B_valid ? 1 : 0, M.Bprev, M.Bdot,
+                          ctx->st));
+      if (M.B_valid) {
+        CKS(eddy_core(ctx, g, M.Bdot, M.sigma, M.Heddy, nullptr, nullptr));
+        M.Heddy_valid = true;
+      }
+      M.B_valid = true;
+    }
     for (int g = 0; g < 2; ++g) std::swap(ctx->mag[g].k[0], ctx->mag[g].k[6]);
     // the accepted slider state, beside the normalisation
     CKS(fork_mech(ctx, mech_params(ctx, 3, 7, dt, false, false)));
@@ -1498,6 +1534,7 @@ void mm_destroy(mm_ctx* ctx) {
     free_dir(M.eddy);
     cudaFree(M.ed_V); cudaFree(M.ed_E); cudaFree(M.ed_b); cudaFree(M.ed_phi); cudaFree(M.ed_J);
     cudaFree(M.ed_part); cudaFree(M.ed_stats);
+    cudaFree(M.Bprev); cudaFree(M.Bdot); cudaFree(M.Heddy);
   }
   for (auto& kv : ctx->ffts) {
     cudaFree(kv.second.tw_f); cudaFree(kv.second.tw_d); cudaFree(kv.second.pos); cudaFree(kv.second.freq);
@@ -1544,6 +1581,7 @@ mm_status mm_set_grid(mm_ctx* ctx, int mag, int nx, int ny, int nz, double dx, d
 
 mm_status mm_set_material(mm_ctx* ctx, int mag, double Ms, double Aex, double Ku, const double ku_axis[3],
                           double alpha) {
+  if (ctx) reset_eddy(ctx);
   if (!ctx) return MM_EINVAL;
   if (bad_mag(mag) || !(Ms > 0) || Aex < 0 || alpha < 0 || !ku_axis)
     return fail(ctx, MM_EINVAL, "mm_set_material: bad argument");
@@ -1561,6 +1599,7 @@ mm_status mm_set_material(mm_ctx* ctx, int mag, double Ms, double Aex, double Ku
 }
 
 mm_status mm_set_external_field(mm_ctx* ctx, const double H[3]) {
+  if (ctx) reset_eddy(ctx);
   if (!ctx || !H) return MM_EINVAL;
   for (int a = 0; a < 3; ++a) ctx->Hext[a] = H[a];
   ctx->k1_valid = false;
@@ -1582,6 +1621,7 @@ mm_status mm_set_mechanics(mm_ctx* ctx, double mass, double k_spring, double v_d
 }
 
 mm_status mm_set_magnetization(mm_ctx* ctx, int mag, const float* m_dev) {
+  if (ctx) reset_eddy(ctx);
   if (!ctx || bad_mag(mag) || !m_dev) return ctx ? fail(ctx, MM_EINVAL, "mm_set_magnetization") : MM_EINVAL;
   Magnet& M = ctx->mag[mag];
   if (!M.grid) return fail(ctx, MM_EINVAL, "mm_set_magnetization: grid not set");
@@ -1600,6 +1640,7 @@ mm_status mm_get_magnetization(mm_ctx* ctx, int mag, float* m_dev) {
 }
 
 mm_status mm_upload_magnetization(mm_ctx* ctx, int mag, const float* m_host) {
+  if (ctx) reset_eddy(ctx);
   if (!ctx || bad_mag(mag) || !m_host) return ctx ? fail(ctx, MM_EINVAL, "mm_upload_magnetization") : MM_EINVAL;
   Magnet& M = ctx->mag[mag];
   if (!M.grid) return fail(ctx, MM_EINVAL, "mm_upload_magnetization: grid not set");
@@ -1619,6 +1660,7 @@ mm_status mm_download_magnetization(mm_ctx* ctx, int mag, float* m_host) {
 }
 
 mm_status mm_set_displacement(mm_ctx* ctx, const double u_m[3]) {
+  if (ctx) reset_eddy(ctx);
   if (!ctx || !u_m) return MM_EINVAL;
   for (int a = 0; a < 3; ++a) {
     if (!isfinite(u_m[a])) return fail(ctx, MM_EINVAL, "mm_set_displacement: non-finite");
@@ -1631,6 +1673,7 @@ mm_status mm_set_displacement(mm_ctx* ctx, const double u_m[3]) {
 }
 
 mm_status mm_set_slider_state(mm_ctx* ctx, double x, double v, double t) {
+  if (ctx) reset_eddy(ctx);
   if (!ctx) return MM_EINVAL;
   ctx->host_mech.x = x; ctx->host_mech.v = v; ctx->host_mech.t = t;
   ctx->k1_valid = false;
@@ -2074,6 +2117,32 @@ mm_status mm_eddy_field(mm_ctx* ctx, int mag, const float* dBdt_dev, double sigm
     return ctx ? fail(ctx, MM_EINVAL, "mm_eddy_field") : MM_EINVAL;
   if (ctx->opt.periodic) return fail(ctx, MM_ENOTSUP, "mm_eddy_field: periodic boundaries");
   CKS(prepare(ctx));
+  return eddy_core(ctx, mag, dBdt_dev, sigma, H_dev, J_dev, sweeps_out);
+}
+
+mm_status mm_set_conductivity(mm_ctx* ctx, int mag, double sigma) {
+  if (!ctx || bad_mag(mag) || !(sigma >= 0) || !std::isfinite(sigma))
+    return ctx ? fail(ctx, MM_EINVAL, "mm_set_conductivity") : MM_EINVAL;
+  if (sigma > 0 && ctx->opt.periodic) return fail(ctx, MM_ENOTSUP, "mm_set_conductivity: periodic boundaries");
+  Magnet& M = ctx->mag[mag];
+  M.sigma = sigma;
+  M.B_valid = M.Heddy_valid = false;
+  return MM_OK;
+}
+
+mm_status mm_get_eddy_field(mm_ctx* ctx, int mag, float* H_dev) {
+  if (!ctx || bad_mag(mag) || !H_dev) return ctx ? fail(ctx, MM_EINVAL, "mm_get_eddy_field") : MM_EINVAL;
+  Magnet& M = ctx->mag[mag];
+  if (!M.grid) return fail(ctx, MM_EINVAL, "grid not set");
+  if (M.Heddy_valid) CK(cudaMemcpyAsync(H_dev, M.Heddy, sizeof(float) * 3 * M.N, cudaMemcpyDeviceToDevice, ctx->st));
+  else CK(cudaMemsetAsync(H_dev, 0, sizeof(float) * 3 * M.nx * M.ny * M.nz, ctx->st));
+  return MM_OK;
+}
+
+}  // extern "C"
+
+static mm_status eddy_core(mm_ctx* ctx, int mag, const float* dBdt_dev, double sigma, float* H_dev, float* J_dev,
+                           int* sweeps_out) {
   Magnet& M = ctx->mag[mag];
   cudaStream_t st = ctx->st;
   // the box of the potential path: output nodes are the magnet's own cells
@@ -2137,6 +2206,8 @@ mm_status mm_eddy_field(mm_ctx* ctx, int mag, const float* dBdt_dev, double sigm
   if (H_dev) CKS(self_cross_S(ctx, mag, J, 1.0, H_dev));
   return MM_OK;
 }
+
+extern "C" {
 
 mm_status mm_field_div_curl(mm_ctx* ctx, const float* H_dev, int nx, int ny, int nz, double dx, double dy,
                             double dz, double* D, double* C) {
@@ -2447,6 +2518,7 @@ mm_status mm_get_state(mm_ctx* ctx, void* buf, size_t* bytes) {
 }
 
 mm_status mm_set_state(mm_ctx* ctx, const void* buf, size_t bytes) {
+  if (ctx) reset_eddy(ctx);
   if (!ctx || !buf) return MM_EINVAL;
   if (bytes < sizeof(StateHeader)) return fail(ctx, MM_ESTATE, "mm_set_state: short buffer");
   StateHeader h;

@@ -213,7 +213,33 @@ __global__ void __launch_bounds__(256) k_eddy_current(const double* __restrict__
   J[2 * N + i] = (float)(sigma * (ez - (zp - zm) / (2.0 * dz)));
 }
 
+// Coupling into the time step: B = mu0 (H_demag + H_stray + H_ext + Ms y) of
+// the step's last evaluation; with a previous B, dB/dt = (B - B_prev) / dt;
+// then B_prev = B.
+__global__ void __launch_bounds__(256) k_flux_rate(const float* __restrict__ Hself, const float* __restrict__ Hstray,
+                                                   const float* __restrict__ y, size_t N, float hx, float hy, float hz,
+                                                   float Ms, float mu0, float inv_dt, int have_prev,
+                                                   float* __restrict__ Bprev, float* __restrict__ Bdot) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const float he[3] = {hx, hy, hz};
+  for (int c = 0; c < 3; ++c) {
+    const size_t k = c * N + i;
+    const float B = mu0 * (Hself[k] + Hstray[k] + he[c] + Ms * y[k]);
+    if (have_prev) Bdot[k] = (B - Bprev[k]) * inv_dt;
+    Bprev[k] = B;
+  }
+}
+
 static unsigned blocks(size_t N) { return (unsigned)((N + 255) / 256); }
+
+cudaError_t launch_flux_rate(const float* Hself, const float* Hstray, const float* y, size_t N, const double hext[3],
+                             double Ms, double dt, int have_prev, float* Bprev, float* Bdot, cudaStream_t st) {
+  k_flux_rate<<<blocks(N), 256, 0, st>>>(Hself, Hstray, y, N, (float)hext[0], (float)hext[1], (float)hext[2],
+                                         (float)Ms, (float)(4e-7 * 3.14159265358979323846), (float)(1.0 / dt),
+                                         have_prev, Bprev, Bdot);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_cross_input(const float* V, size_t N, int comp, float* out, cudaStream_t st) {
   k_cross_input<<<blocks(N), 256, 0, st>>>(V, N, comp, out);

@@ -3,7 +3,8 @@
 //
 // k_stage: one thread per cell.  Effective field = own demag + stray field of
 // the other magnet (both produced upstream) + 6-neighbour exchange (free
-// ends) + uniaxial anisotropy + uniform Zeeman; torque in Landau-Lifshitz
+// ends) + uniaxial anisotropy + uniform Zeeman (+ the eddy field of a
+// conducting magnet); torque in Landau-Lifshitz
 // form  dm/dt = -gamma0/(1+alpha^2) [m x H + alpha m x (m x H)];  then the
 // next stage input y + dt sum_j a_{i+1,j} k_j (or, at the last stage, the
 // max-norm of the embedded 5(4) error).
@@ -25,8 +26,10 @@ __device__ __forceinline__ float warp_max(float v) {
 
 // WRAP: some job has periodic x or y (exchange neighbours wrap around the
 // period); open boundaries run the instantiation without the wrap tests.
-template <bool WRAP>
-__global__ void __launch_bounds__(256) k_stage(const Launch<StageJob> Lc, const MechParams Perr, int* ticket) {
+// EDDY: some job is a conducting magnet carrying an eddy field; the plain
+// instantiation has no load of it (and no extra register pressure).
+template <bool WRAP, bool EDDY>
+__global__ void __launch_bounds__(256, 6) k_stage(const Launch<StageJob> Lc, const MechParams Perr, int* ticket) {
   __shared__ float red[8];
   const int j = find_job(Lc.tile_start, Lc.njobs, blockIdx.x);
   const StageJob& J = Lc.job[j];
@@ -48,6 +51,11 @@ __global__ void __launch_bounds__(256) k_stage(const Launch<StageJob> Lc, const 
     float h0 = J.Hself[idx] + J.Hstray[idx] + J.hext[0];
     float h1 = J.Hself[N + idx] + J.Hstray[N + idx] + J.hext[1];
     float h2 = J.Hself[2 * N + idx] + J.Hstray[2 * N + idx] + J.hext[2];
+    if (EDDY && J.Heddy) {  // conducting magnet: the eddy field of the last accepted step
+      h0 += J.Heddy[idx];
+      h1 += J.Heddy[N + idx];
+      h2 += J.Heddy[2 * N + idx];
+    }
     // exchange, free ends: only neighbours inside the magnet contribute;
     // periodic x / y: the neighbours wrap around the period
     float e0 = 0.f, e1 = 0.f, e2 = 0.f;
@@ -158,10 +166,15 @@ __global__ void __launch_bounds__(256) k_mech(const MechParams P) { mech_block(P
 cudaError_t launch_stage(const Launch<StageJob>& L, const MechParams& Perr, int* ticket, cudaStream_t st) {
   const int grid = L.tile_start[L.njobs];
   if (grid == 0) return cudaSuccess;
-  bool wrap = false;
-  for (int i = 0; i < L.njobs; ++i) wrap = wrap || L.job[i].wrap[0] || L.job[i].wrap[1];
-  if (wrap) k_stage<true><<<grid, 256, 0, st>>>(L, Perr, ticket);
-  else k_stage<false><<<grid, 256, 0, st>>>(L, Perr, ticket);
+  bool wrap = false, eddy = false;
+  for (int i = 0; i < L.njobs; ++i) {
+    wrap = wrap || L.job[i].wrap[0] || L.job[i].wrap[1];
+    eddy = eddy || L.job[i].Heddy != nullptr;
+  }
+  if (wrap && eddy) k_stage<true, true><<<grid, 256, 0, st>>>(L, Perr, ticket);
+  else if (wrap) k_stage<true, false><<<grid, 256, 0, st>>>(L, Perr, ticket);
+  else if (eddy) k_stage<false, true><<<grid, 256, 0, st>>>(L, Perr, ticket);
+  else k_stage<false, false><<<grid, 256, 0, st>>>(L, Perr, ticket);
   return cudaGetLastError();
 }
 cudaError_t launch_combine(const Launch<CombineJob>& L, cudaStream_t st) {

@@ -200,6 +200,7 @@ struct StageJob {
   float* k[7];            // stage derivatives
   const float* Hself;
   const float* Hstray;
+  const float* Heddy;     // eddy field of a conducting magnet (A/m), null if none
   float* Heff;            // optional effective field out
   int nx, ny, nz;
   float ex[3];            // 2 A / (mu0 Ms d_a^2)
@@ -318,6 +319,8 @@ cudaError_t launch_sor_residual(const double* phi, const double* b, const double
                                 const double d[3], double* part, double* stats, cudaStream_t st);
 cudaError_t launch_eddy_current(const double* phi, const double* stats, const float* E, int nx, int ny, int nz,
                                 const double d[3], double sigma, float* J, cudaStream_t st);
+cudaError_t launch_flux_rate(const float* Hself, const float* Hstray, const float* y, size_t N, const double hext[3],
+                             double Ms, double dt, int have_prev, float* Bprev, float* Bdot, cudaStream_t st);
 
 // componentwise field variant (variants.cu): H_a at every target centre from
 // the coefficients C [3][bdim z][bdim y][bdim x] of the three components on

@@ -17,6 +17,7 @@ from tests.pair_setup import gpu_pair, rel_l2
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-5
+EPS_B = 2e-7
 
 
 def _ctx(n, cell=(2e-9, 2e-9, 2e-9), gap=3, seed=0):
@@ -54,3 +55,54 @@ def test_eddy_field_of_no_change_is_zero():
     H, J, sweeps = mm.eddy_field(0, B, 1e6)
     assert sweeps == 0 and float(H.abs().max()) == 0.0 and float(J.abs().max()) == 0.0
     mm.close()
+
+
+def test_eddy_coupled_steps_match_oracle():
+    """Three fixed-dt Dormand-Prince steps of conducting films with the eddy
+    fields coupled in (lagged by one step) against the oracle's coupled run.
+    Random unit m (strong exchange, fast motion) and a conductivity far above
+    any metal's (1e11 S/m), so that the coupling moves the per-step change of
+    m by ~4e-3. Checked: m of both films within the field bar and their change
+    within 1e-3 (as for the other step tests), while the change without eddy
+    fields differs by more than twice that bar (the test is not vacuous); the
+    eddy field the next step would add within the bar widened by the
+    cancellation in B_n - B_{n-1}: each B carries the FP32 field path's error
+    (5e-8 of |B| measured on this pair; EPS_B = 2e-7 allows 4 times that), so
+    the difference is good to 2 EPS_B |B| / |B_n - B_{n-1}| (|B| is ~100
+    times the difference here)."""
+    from oracle import dynamics as D
+    from tests.pair_setup import oracle_system
+
+    fp, _, _ = workloads.film_pair_stick_slip(n=(16, 12, 2), gap=3, seed=5)
+    m0, m1 = workloads.random_unit(fp.n_base, 5), workloads.random_unit(fp.n_slider, 6)
+    fp.mech.x0_spring = 2e-9
+    sigma, dt, n = 1e11, 2e-14, 3
+    mm = gpu_pair(fp, m0, m1)
+    mm.set_conductivity(0, sigma)
+    mm.set_conductivity(1, sigma)
+    mm.step(n, dt)
+    got = [mm.get_magnetization(g).double().cpu().numpy() for g in (0, 1)]
+    He = [mm.get_eddy_field(g).double().cpu().numpy() for g in (0, 1)]
+    x, v, _ = mm.get_slider_state()
+    mm.close()
+
+    y0 = [m0, m1, 0.0, 0.0]
+    cs = OE.EddyCoupledSystem(oracle_system(fp), (sigma, sigma))
+    B_hist = []
+    t, y, k1 = 0.0, list(y0), None
+    for _ in range(n):
+        y5, _, k7 = D.dp45_step(cs, t, y, dt, k1)
+        B_hist.append([b.copy() for b in cs.last_B])
+        cs.accept(dt)
+        y = [D.normalise(y5[0]), D.normalise(y5[1]), y5[2], y5[3]]
+        t += dt
+        k1 = k7
+    _, yp = D.run_fixed(oracle_system(fp), y0, dt, n)
+    for g in (0, 1):
+        assert rel_l2(got[g], y[g]) < TOL
+        assert rel_l2(got[g] - y0[g], y[g] - y0[g]) < 1e-3
+        assert rel_l2(yp[g] - y0[g], y[g] - y0[g]) > 2e-3
+        dB = np.linalg.norm((B_hist[-1][g] - B_hist[-2][g]).ravel())
+        tol = max(TOL, 2 * EPS_B * np.linalg.norm(B_hist[-1][g].ravel()) / dB)
+        assert rel_l2(He[g], cs.Heddy[g]) < tol
+    assert abs(x - y[2]) <= 1e-5 * abs(y[2])
