@@ -42,18 +42,29 @@ typedef enum {
   MM_ENOMEM = -2,   /* device allocation failed */
   MM_ECUDA = -3,    /* CUDA runtime error (message in mm_last_error) */
   MM_ERANGE = -4,   /* displacement left the planned potential box */
-  MM_ETIMEOUT = -5, /* an iteration did not converge within its bound (mm_eddy_field) */
+  MM_ETIMEOUT = -5, /* an iteration did not converge, or a wait on the tensor core ran out, within its bound */
   MM_ESTATE = -6,   /* state buffer of the wrong size or version */
   MM_ENOTSUP = -7,  /* geometry or option the library does not support */
   MM_ETOOBIG = -8   /* larger than the fixed scratch of mm_spline_field_noalloc */
 } mm_status;
 
-enum { MM_FP32 = 0 };
+/*
+ * Precision of the field passes.  MM_FP32: every pass in FP32.  MM_MIXED: the
+ * reduced-precision form -- the y transforms of the convolutions (Sec. III.A)
+ * become complex DFT-matrix products on the tensor cores, with BF16 operands
+ * split into hi + lo parts (hi.hi + hi.lo + lo.hi, FP32 accumulation; about
+ * 2^-16 relative per dot product) and the y prefilter of the B-spline folded
+ * into the inverse DFT matrix; the x transforms, the z plane mixing, the
+ * gather and the LLG stage stay FP32.  Every source then takes the separate
+ * y-forward / plane-mixing / y-inverse passes; sources of more than 8 layers
+ * (z by FFT) return MM_ENOTSUP.  Fields agree with FP32 to ~1e-5 relative L2.
+ */
+enum { MM_FP32 = 0, MM_MIXED = 1 };
 
 enum { MM_PERIODIC_X = 1, MM_PERIODIC_Y = 2 };
 
 typedef struct {
-  int precision;     /* MM_FP32 */
+  int precision;     /* MM_FP32 or MM_MIXED */
   int margin;        /* potential box margin in cells beyond the spline support (Sec. III.A: 4) */
   int adaptive;      /* 1: Dormand-Prince 5(4) step-size control; 0: fixed dt */
   double rtol;       /* adaptive: accepted max-norm error of m per step */

@@ -18,6 +18,7 @@ fields       potential on a box, self-demag field, box convention (Sec. II.A, II
 spline       cubic B-spline prefilter (banded solve) and 64-term evaluation (Sec. III.A)
 interaction  stray field, Eq. (EQForce) force and interaction energy (Sec. III)
 dynamics     exchange/anisotropy/Zeeman, LLG (Sec. II eq. 1), DP45 + slider EOM (Sec. III, IV.B)
+mixed        split-bfloat16 arithmetic of the reduced-precision form and its error bound
 
 Parity status: every function is pinned by ``tests/test_oracle_*.py`` against
 closed forms, invariants or brute force; none is "parity unpinned".

@@ -14,6 +14,7 @@ MM_ETOOBIG = -8
 
 
 MM_PERIODIC_X, MM_PERIODIC_Y = 1, 2
+MM_FP32, MM_MIXED = 0, 1
 
 
 class mm_options(C.Structure):

@@ -11,7 +11,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "lib")
 LIB = os.path.join(OUT_DIR, "libmm.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["fft_passes.cu", "fft3d.cu", "gather.cu", "llg.cu", "kgen.cu", "api.cu", "noalloc.cu", "adjoint.cu", "power.cu", "variants.cu", "eddy.cu"]
+SOURCES = ["fft_passes.cu", "fft3d.cu", "gather.cu", "llg.cu", "kgen.cu", "api.cu", "noalloc.cu", "adjoint.cu", "power.cu", "variants.cu", "eddy.cu", "ydft.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(256) k_adj_scatter(const AdjScatterJob J) {
     int sh = J.guard[a] + ((int)fl - J.U0[a]);
     const int need = (a == 0 ? J.nx : a == 1 ? J.ny : J.nz) + 3;
     if (sh < 0 || sh + need > J.r[a]) {
-      atomicExch(J.err, 1);
+      atomicOr(J.err, 1);
       sh = 0x7fffffff;
     }
     sh_s[a] = sh;

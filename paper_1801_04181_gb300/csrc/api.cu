@@ -62,6 +62,16 @@ struct FftRes {
   int* freq = nullptr;
 };
 
+// a packed y-DFT matrix of the reduced-precision form and what it was built for
+struct DftMat {
+  uint16_t* hi = nullptr;
+  uint16_t* lo = nullptr;
+  size_t hi_bytes = 0, lo_bytes = 0;
+  bool valid = false;
+  DftSpec spec{};
+  DftShape shape{};
+};
+
 struct Dir {
   bool valid = false;
   bool full_box = false;   // potential query: whole box, optional prefilter
@@ -78,6 +88,7 @@ struct Dir {
   int ntiles = 0;
   float2* Z3C = nullptr;       // thick sources: z-pass coefficient planes [r_z][kxh][Qy]
   size_t Tq_bytes = 0, YC_bytes = 0, C_bytes = 0, partial_bytes = 0, Z3C_bytes = 0;
+  DftMat yiC;                  // reduced precision: inverse y DFT with the y prefilter
 };
 
 struct Magnet {
@@ -115,6 +126,9 @@ struct Magnet {
   float* S3 = nullptr;     // [3][kxh][kyq][kzq]
   float2* Y3 = nullptr;    // [kxh][Qy][3 nz]
   float2* Z3H = nullptr;   // [3 nz][kxh][Qy]
+  // reduced precision (every source through the split passes, z by the
+  // direct sum): forward and demag-row inverse y DFT matrices
+  DftMat yf, yiH;
   // energy gradients (mm_backward_energy) as a source: work arrays and the S
   // spectra per z offset of the box
   float* adj_box = nullptr;
@@ -768,8 +782,13 @@ mm_status ensure_plan(mm_ctx* ctx) {
     D.prefilter = 1;
     // separate y / z passes when the source is thick or the box around the
     // target is tall; z by FFT only for sources thicker than kMaxNzDirect
-    const bool thick = S.nz > kMaxNz || ctx->mag[1 - s].nz > kMaxNz;
+    // (the reduced-precision form takes every source through the separate
+    // passes: its y transforms are the tensor-core DFT products)
+    const bool mixed = ctx->opt.precision == MM_MIXED;
+    const bool thick = S.nz > kMaxNz || ctx->mag[1 - s].nz > kMaxNz || mixed;
     const bool zfft = thick && S.nz > kMaxNzDirect;
+    if (zfft && mixed)
+      return fail(ctx, MM_ENOTSUP, "reduced precision: sources of more than 8 layers (z by FFT)");
     if (zfft && ctx->opt.periodic)
       return fail(ctx, MM_ENOTSUP, "periodic boundaries: sources of more than 8 layers");
     const bool px = periodic_axis(ctx, 0), py = periodic_axis(ctx, 1);
@@ -912,6 +931,32 @@ Launch<XFwdJob> xfwd_launch(mm_ctx* ctx, const float* in[2], const int* which, i
   return L;
 }
 
+// The packed matrix of `spec` in *M, rebuilt (FP64 entries, on the stream)
+// when the geometry it was built for has changed.
+static mm_status ensure_dft(mm_ctx* ctx, DftMat* M, const DftSpec& spec) {
+  if (M->valid && memcmp(&M->spec, &spec, sizeof spec) == 0) return MM_OK;
+  const DftShape sh = dft_shape(spec.Nc, spec.Kc);
+  const size_t bytes = dft_matrix_elems(sh) * sizeof(uint16_t);
+  M->valid = false;
+  CKS(ensure_buf(ctx, &M->hi, &M->hi_bytes, bytes));
+  CKS(ensure_buf(ctx, &M->lo, &M->lo_bytes, bytes));
+  CK(launch_dft_pack(spec, sh, M->hi, M->lo, ctx->st));
+  M->spec = spec;
+  M->shape = sh;
+  M->valid = true;
+  return MM_OK;
+}
+
+static DftJob dft_job(mm_ctx* ctx, const DftMat& M, const float2* A, int lda, int rows, float2* D, int ldd) {
+  DftJob J{};
+  J.A = A; J.lda = lda; J.rows = rows; J.Kc = M.spec.Kc;
+  J.Bhi = M.hi; J.Blo = M.lo;
+  J.ntile = M.shape.ntile; J.ntiles = M.shape.ntiles; J.kchunks = M.shape.kchunks; J.Nc = M.spec.Nc;
+  J.D = D; J.ldd = ldd;
+  J.err = ctx->err_flag;
+  return J;
+}
+
 // what: bit 1 = own demag, bit 2 = coefficients of Dir (hot or aux)
 mm_status run_source_passes(mm_ctx* ctx, const float* in[2], const int* which, int n, const int* what,
                             Dir* const* dirs) {
@@ -971,7 +1016,11 @@ mm_status run_source_passes(mm_ctx* ctx, const float* in[2], const int* which, i
     Launch<ZJob> Lz{};
     Launch<ZMixJob> Lm{};
     Launch<YInvJob> Li{};
+    // reduced precision: the y transforms as tensor-core DFT products
+    Launch<DftJob> Ldf{}, Ldi{};
+    const bool mixed = ctx->opt.precision == MM_MIXED;
     int nf = 0, tf = 0, nzj = 0, tz = 0, nm = 0, tm = 0, ni = 0, ti = 0;
+    int ndf = 0, tdf = 0, ndi = 0, tdi = 0;
     for (int i = 0; i < n; ++i) {
       Magnet& S = ctx->mag[which[i]];
       if (!S.thick) continue;
@@ -983,12 +1032,22 @@ mm_status run_source_passes(mm_ctx* ctx, const float* in[2], const int* which, i
       const int group = std::max(1, std::min(16, (int)((48 * 1024) / ((S.Qy + 1) * sizeof(float2)))));
       const int P3 = 3 * S.nz;
       const int natural = S.zfft ? 0 : 1;
-      YFwdJob& F = Lf.job[nf];
-      F.in = S.X1; F.out = S.Y3; F.planes = P3; F.ny = S.ny; F.kxh = S.kxh; F.group = group; F.fy = fy;
-      F.natural = natural;
-      Lf.tile_start[nf] = tf;
-      tf += S.kxh * ((P3 + group - 1) / group);
-      ++nf;
+      if (mixed) {
+        DftSpec f{};
+        f.kind = kDftForward; f.Q = S.Qy; f.Nc = S.Qy; f.Kc = S.ny;
+        CKS(ensure_dft(ctx, &S.yf, f));
+        Ldf.job[ndf] = dft_job(ctx, S.yf, S.X1, S.ny, P3 * S.kxh, S.Y3, S.Qy);
+        Ldf.tile_start[ndf] = tdf;
+        tdf += dft_tiles(P3 * S.kxh, S.yf.shape);
+        ++ndf;
+      } else {
+        YFwdJob& F = Lf.job[nf];
+        F.in = S.X1; F.out = S.Y3; F.planes = P3; F.ny = S.ny; F.kxh = S.kxh; F.group = group; F.fy = fy;
+        F.natural = natural;
+        Lf.tile_start[nf] = tf;
+        tf += S.kxh * ((P3 + group - 1) / group);
+        ++nf;
+      }
       if (S.zfft) {
         FftTables fz;
         CKS(get_fft(ctx, S.Qz, &fz));
@@ -1019,6 +1078,30 @@ mm_status run_source_passes(mm_ctx* ctx, const float* in[2], const int* which, i
         tm += S.kxh * zmix_tiles(S.kyq, M.nH + M.n_out);
         ++nm;
       }
+      if (mixed) {
+        if (do_H) {
+          DftSpec h{};
+          h.kind = kDftInverse; h.Q = S.Qy; h.Nc = S.ny; h.Kc = S.Qy;
+          CKS(ensure_dft(ctx, &S.yiH, h));
+          Ldi.job[ndi] = dft_job(ctx, S.yiH, S.Z3H, S.Qy, P3 * S.kxh, S.YH, S.ny);
+          Ldi.tile_start[ndi] = tdi;
+          tdi += dft_tiles(P3 * S.kxh, S.yiH.shape);
+          ++ndi;
+        }
+        if (do_C) {
+          DftSpec c{};
+          c.kind = kDftInversePrefilter; c.Q = S.Qy; c.Nc = D->r[1]; c.Kc = S.Qy;
+          c.box_lo = D->box_lo[1]; c.box_len = D->box_len[1]; c.start = D->start[1];
+          c.periodic = periodic_axis(ctx, 1) ? 1 : 0;
+          c.fir = D->prefilter;
+          CKS(ensure_dft(ctx, &D->yiC, c));
+          Ldi.job[ndi] = dft_job(ctx, D->yiC, D->Z3C, S.Qy, D->r[2] * S.kxh, D->YC, D->r[1]);
+          Ldi.tile_start[ndi] = tdi;
+          tdi += dft_tiles(D->r[2] * S.kxh, D->yiC.shape);
+          ++ndi;
+        }
+        continue;
+      }
       if (do_H) {
         YInvJob& J = Li.job[ni];
         J = YInvJob{};
@@ -1041,14 +1124,17 @@ mm_status run_source_passes(mm_ctx* ctx, const float* in[2], const int* which, i
         ++ni;
       }
     }
-    if (nf) {
+    if (nf || ndf) {
       Lf.njobs = nf; Lf.tile_start[nf] = tf;
       Lz.njobs = nzj; Lz.tile_start[nzj] = tz;
       Lm.njobs = nm; Lm.tile_start[nm] = tm;
       Li.njobs = ni; Li.tile_start[ni] = ti;
+      Ldf.njobs = ndf; Ldf.tile_start[ndf] = tdf;
+      Ldi.njobs = ndi; Ldi.tile_start[ndi] = tdi;
       {
         Timer t(ctx, 7);
-        CK(launch_yfwd3(Lf, st));
+        if (ndf) CK(launch_ydft(Ldf, st));
+        if (nf) CK(launch_yfwd3(Lf, st));
       }
       if (nzj) {
         Timer t(ctx, 8);
@@ -1059,7 +1145,8 @@ mm_status run_source_passes(mm_ctx* ctx, const float* in[2], const int* which, i
         CK(launch_zmix3(Lm, st));
       }
       Timer t(ctx, 9);
-      CK(launch_yinv3(Li, st));
+      if (ndi) CK(launch_ydft(Ldi, st));
+      if (ni) CK(launch_yinv3(Li, st));
     }
   }
   {
@@ -1282,13 +1369,20 @@ mm_status run_stage(mm_ctx* ctx, const float* ys[2], float* ys_next[2], int stag
   return MM_OK;
 }
 
+// the device error flag: bit 1 from the gather (a target outside the box),
+// bit 2 from the tensor-core DFT (a bounded wait ran out)
+static mm_status device_error(mm_ctx* ctx, int e) {
+  if (e & 2) return fail(ctx, MM_ETIMEOUT, "tensor-core y DFT: a wait on the MMA completion ran out");
+  return fail(ctx, MM_ERANGE, "slider displacement left the planned potential box during a step");
+}
+
 mm_status check_device_error(mm_ctx* ctx) {
   int e = 0;
   CK(cudaMemcpyAsync(&e, ctx->err_flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
   if (e) {
     CK(cudaMemsetAsync(ctx->err_flag, 0, sizeof(int), ctx->st));
-    return fail(ctx, MM_ERANGE, "slider displacement left the planned potential box during a step");
+    return device_error(ctx, e);
   }
   return MM_OK;
 }
@@ -1350,9 +1444,10 @@ mm_status attempt_finish(mm_ctx* ctx, double* err) {
   CK(cudaEventSynchronize(ctx->ev_done));
   ctx->host_mech = ctx->rb->mech;
   if (ctx->rb->err) {
+    const int e = ctx->rb->err;
     ctx->rb->err = 0;
     CK(cudaMemsetAsync(ctx->err_flag, 0, sizeof(int), ctx->st));
-    return fail(ctx, MM_ERANGE, "slider displacement left the planned potential box during a step");
+    return device_error(ctx, e);
   }
   *err = ctx->host_mech.err;
   return MM_OK;
@@ -1474,7 +1569,7 @@ mm_status mm_create(mm_ctx** out, const mm_options* opt) {
   mm_ctx* ctx = new mm_ctx();
   if (opt) ctx->opt = *opt;
   else mm_default_options(&ctx->opt);
-  if (ctx->opt.precision != MM_FP32) {
+  if (ctx->opt.precision != MM_FP32 && ctx->opt.precision != MM_MIXED) {
     delete ctx;
     return MM_ENOTSUP;
   }
@@ -1507,8 +1602,14 @@ mm_status mm_create(mm_ctx** out, const mm_options* opt) {
   return MM_OK;
 }
 
+static void free_dft(DftMat& M) {
+  cudaFree(M.hi); cudaFree(M.lo);
+  M = DftMat();
+}
+
 static void free_dir(Dir& D) {
   cudaFree(D.Tq); cudaFree(D.YC); cudaFree(D.C); cudaFree(D.partial); cudaFree(D.Z3C);
+  free_dft(D.yiC);
   D = Dir();
 }
 
@@ -1525,6 +1626,7 @@ void mm_destroy(mm_ctx* ctx) {
     cudaFree(M.pow_H); cudaFree(M.pow_part);
     cudaFree(M.X1); cudaFree(M.YH); cudaFree(M.Nq);
     cudaFree(M.N3); cudaFree(M.S3); cudaFree(M.Y3); cudaFree(M.Z3H);
+    free_dft(M.yf); free_dft(M.yiH);
     cudaFree(M.adj_box); cudaFree(M.adj_grid); cudaFree(M.adj_X); cudaFree(M.adj_Y); cudaFree(M.adj_Z);
     cudaFree(M.adj_YH); cudaFree(M.adj_Sq);
     free_dir(M.dir);

@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(TX * TY, 4) k_gather(const Launch<GatherJob> L
       const int need = (a == 0 ? J.nx : a == 1 ? J.ny : J.nz) + 3;
       const int have = a == 0 ? J.rx : a == 1 ? J.ry : J.rz;
       if (sh < 0 || sh + need > have) {
-        atomicExch(J.err, 1);
+        atomicOr(J.err, 1);
         sh = 0x7fffffff;
       }
     }

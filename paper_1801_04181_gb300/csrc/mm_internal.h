@@ -144,6 +144,36 @@ struct ZMixJob {
 };
 constexpr int kMaxNzDirect = 8;
 
+// ---------------------------------------------------------------- reduced-precision y stage
+// y transforms as DFT-matrix products on the tensor cores (csrc/ydft.cu):
+// D[row][0:Nc] = sum_k A[row][k] F(k, .), complex rows of one (plane, kx)
+// line each; F in real form, split into BF16 hi + lo parts and packed in the
+// tensor core's no-swizzle K-major layout, [ntiles][kchunks][ntile x 64].
+enum DftKind { kDftForward = 0, kDftInverse = 1, kDftInversePrefilter = 2 };
+constexpr int kDftPrefTaps = 24;  // prefilter taps each side: |z1|^24 ~ 2e-14
+struct DftSpec {                  // what a packed matrix holds (compared bytewise)
+  int kind;
+  int Q;                          // y grid length
+  int Nc, Kc;                     // complex outputs / inputs per row
+  int box_lo, box_len, start;     // kDftInversePrefilter: the y box and the first row
+  int periodic, fir;              // wrapped box; prefilter on (else plain node values)
+};
+struct DftShape {
+  int ntile = 0;                  // real output columns per CTA (multiple of 32, <= 256)
+  int ntiles = 0;
+  int kchunks = 0;                // K chunks of 64 real values
+};
+struct DftJob {
+  const float2* A;                // [rows][lda], the first Kc of a row used
+  int lda, rows, Kc;
+  const uint16_t* Bhi;
+  const uint16_t* Blo;
+  int ntile, ntiles, kchunks, Nc;
+  float2* D;                      // [rows][ldd], the first Nc written
+  int ldd;
+  int* err;                       // bit 2 set when a wait on the tensor core ran out
+};
+
 // ---------------------------------------------------------------- adjoint (energy gradients)
 // transposed gradient evaluation: coefficient-region node n collects
 // escale * m_t,a(i) / d_a * (derivative weights of axis a) from the targets i
@@ -294,6 +324,11 @@ cudaError_t launch_yfwd3(const Launch<YFwdJob>& L, cudaStream_t st);
 cudaError_t launch_zpass3(const Launch<ZJob>& L, cudaStream_t st);
 cudaError_t launch_yinv3(const Launch<YInvJob>& L, cudaStream_t st);
 cudaError_t launch_zmix3(const Launch<ZMixJob>& L, cudaStream_t st);
+DftShape dft_shape(int Nc, int Kc);
+size_t dft_matrix_elems(const DftShape& s);
+int dft_tiles(int rows, const DftShape& s);
+cudaError_t launch_dft_pack(const DftSpec& P, const DftShape& s, uint16_t* hi, uint16_t* lo, cudaStream_t st);
+cudaError_t launch_ydft(const Launch<DftJob>& L, cudaStream_t st);
 cudaError_t launch_adj_scatter(const AdjScatterJob& J, cudaStream_t st);
 cudaError_t launch_pref_T(float* box, const int bdim[3], cudaStream_t st);
 cudaError_t launch_place(const float* box, const int bdim[3], const int box_lo[3], float* grid, int Qx, int Qy,

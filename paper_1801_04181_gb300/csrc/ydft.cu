@@ -1,0 +1,286 @@
+// Reduced-precision form of the y stage (Sec. III.A convolutions): the y
+// transforms as complex DFT-matrix products on the 5th-generation tensor
+// cores, BF16 operands split into hi + lo parts, FP32 accumulation in TMEM.
+//
+//   forward:  Y[row][ky] = sum_{y < ny} X[row][y] e^{-2 pi i ky y / Q}
+//   inverse:  H[row][y]  = sum_ky Z[row][ky] e^{+2 pi i ky y / Q},  y < ny
+//   inverse with the y prefilter folded in:
+//             C[row][k]  = sum_ky Z[row][ky] G[k][ky],
+//             G[k][ky]   = sum_d h(d) e^{+2 pi i ky g(k, d) / Q}
+//   where h(d) = -6 z1 z1^|d| / (1 - z1^2) is the impulse response of the
+//   cubic B-spline prefilter (z1 = sqrt(3) - 2) and g(k, d) the grid row of
+//   box node start + k + d with mirror ends (or wrapped around the period).
+//
+// A row is one (plane, kx) line; the rows of a launch are independent, so one
+// CTA takes 128 rows (the MMA's M) and one tile of at most 256 real output
+// columns (its N, FP32 accumulators in TMEM).  In real form a complex product
+// is [re im] . [[c, s], [-s, c]]; each complex matrix entry becomes four real
+// ones, so K = 2 Kc and N = 2 Nc.  The split product keeps three of the four
+// BF16 products, hi.hi + hi.lo + lo.hi (the dropped lo.lo is ~2^-18 of the
+// terms), which gives ~2^-16 relative per dot product.
+#include <cuda_bf16.h>
+
+#include "fft.cuh"
+#include "mm_internal.h"
+#include "umma.cuh"
+
+namespace mm {
+
+constexpr int kDftThreads = 256;
+constexpr int kDftRows = 128;     // MMA M: rows per CTA
+constexpr int kDftMaxN = 256;     // MMA N: real columns per CTA (TMEM columns)
+constexpr int kDftStages = 2;
+constexpr uint32_t kDftStageA = kDftRows * kKChunk * 2;  // one split of A, bytes
+constexpr uint32_t kDftStageB = kDftMaxN * kKChunk * 2;  // one split of B, bytes
+constexpr uint32_t kDftStageBytes = 2 * kDftStageA + 2 * kDftStageB;
+constexpr size_t kDftSmem = (size_t)kDftStages * kDftStageBytes + 64;
+// about one second at the SM clock: a wait on the tensor core never takes this
+// long unless something is wrong
+constexpr long long kDftSpinCycles = 2000000000LL;
+constexpr int kDftErrBit = 2;
+
+__device__ __forceinline__ uint32_t bf16x2_bits(float a, float b) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+__global__ void __launch_bounds__(kDftThreads, 1) k_ydft(const Launch<DftJob> Lc) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + kDftStages * kDftStageBytes);
+  uint32_t* slot = reinterpret_cast<uint32_t*>(bar + kDftStages);
+  __shared__ int ok;
+  const int j = find_job(Lc.tile_start, Lc.njobs, blockIdx.x);
+  const DftJob& J = Lc.job[j];
+  const int tile = blockIdx.x - Lc.tile_start[j];
+  const int mt = tile / J.ntiles, nt = tile - mt * J.ntiles;
+  const int row0 = mt * kDftRows;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (warp == 0) {
+    tmem_alloc(slot, kDftMaxN);
+    tmem_relinquish();
+  }
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kDftStages; ++s) mbar_init(&bar[s], 1);
+    ok = 1;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *slot;
+  const uint32_t idesc = idesc_bf16_f32(kDftRows, J.ntile);
+  const size_t bblock = (size_t)J.ntile * kKChunk;  // BF16 values of one (N tile, K chunk) block
+  const int nvec = J.ntile * kKChunk * 2 / 16;      // uint4 per block
+
+  for (int c = 0; c < J.kchunks; ++c) {
+    const int s = c % kDftStages;
+    uint8_t* st = sm + s * kDftStageBytes;
+    uint8_t* sAh = st;
+    uint8_t* sAl = st + kDftStageA;
+    uint8_t* sBh = st + 2 * kDftStageA;
+    uint8_t* sBl = sBh + kDftStageB;
+    if (c >= kDftStages) {
+      // the MMAs of chunk c - kDftStages read this stage's buffers
+      if (threadIdx.x == 0 &&
+          !mbar_wait(&bar[s], (uint32_t)((c - kDftStages) / kDftStages) & 1u, kDftSpinCycles))
+        ok = 0;
+      __syncthreads();
+      if (!ok) break;
+    }
+    // A: 128 rows x 32 complex of this chunk, split into BF16 hi + lo.  A
+    // warp covers 8 rows x 4 complex, so its 4-byte stores fill one 128-byte
+    // run of the core matrices (no bank conflicts) and its loads are 32-byte
+    // runs of 8 rows.
+    const int k0 = c * (int)(kKChunk / 2);
+    float2 v[kDftRows * 32 / kDftThreads];
+#pragma unroll
+    for (int it = 0; it < kDftRows * 32 / kDftThreads; ++it) {
+      const int w = (threadIdx.x >> 5) + it * (kDftThreads / 32);  // 0 .. 127
+      const int r = (w >> 3) * 8 + (lane & 7);
+      const int kc = (w & 7) * 4 + (lane >> 3);
+      const int row = row0 + r, k = k0 + kc;
+      v[it] = (row < J.rows && k < J.Kc) ? __ldg(J.A + (size_t)row * J.lda + k) : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int it = 0; it < kDftRows * 32 / kDftThreads; ++it) {
+      const int w = (threadIdx.x >> 5) + it * (kDftThreads / 32);
+      const int r = (w >> 3) * 8 + (lane & 7);
+      const int kc = (w & 7) * 4 + (lane >> 3);
+      const float hx = __bfloat162float(__float2bfloat16_rn(v[it].x));
+      const float hy = __bfloat162float(__float2bfloat16_rn(v[it].y));
+      const uint32_t off = tile_offset(r, 2 * kc);
+      *reinterpret_cast<uint32_t*>(sAh + off) = bf16x2_bits(hx, hy);
+      *reinterpret_cast<uint32_t*>(sAl + off) = bf16x2_bits(v[it].x - hx, v[it].y - hy);
+    }
+    // B: the packed (N tile, K chunk) block, hi and lo
+    const uint4* gh = reinterpret_cast<const uint4*>(J.Bhi + ((size_t)nt * J.kchunks + c) * bblock);
+    const uint4* gl = reinterpret_cast<const uint4*>(J.Blo + ((size_t)nt * J.kchunks + c) * bblock);
+    for (int i = threadIdx.x; i < nvec; i += kDftThreads) {
+      const uint4 a = __ldg(gh + i), b = __ldg(gl + i);
+      reinterpret_cast<uint4*>(sBh)[i] = a;
+      reinterpret_cast<uint4*>(sBl)[i] = b;
+    }
+    fence_async_smem();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      tc_fence_after();
+#pragma unroll
+      for (int q = 0; q < (int)kKChunk / 16; ++q) {
+        const uint32_t off = (uint32_t)q * 2u * kCoreBytes;  // 16 K values = two core matrices
+        const uint64_t ah = smem_desc(smem_u32(sAh) + off, kCoreBytes, kRowGroupBytes);
+        const uint64_t al = smem_desc(smem_u32(sAl) + off, kCoreBytes, kRowGroupBytes);
+        const uint64_t bh = smem_desc(smem_u32(sBh) + off, kCoreBytes, kRowGroupBytes);
+        const uint64_t bl = smem_desc(smem_u32(sBl) + off, kCoreBytes, kRowGroupBytes);
+        umma_bf16(tmem, ah, bh, idesc, (c > 0 || q > 0) ? 1u : 0u);
+        umma_bf16(tmem, ah, bl, idesc, 1u);
+        umma_bf16(tmem, al, bh, idesc, 1u);
+      }
+      umma_commit(&bar[s]);
+    }
+  }
+  // the last chunk's commit completes after every MMA issued before it
+  if (threadIdx.x == 0 && ok) {
+    const int c = J.kchunks - 1;
+    if (!mbar_wait(&bar[c % kDftStages], (uint32_t)(c / kDftStages) & 1u, kDftSpinCycles)) ok = 0;
+  }
+  __syncthreads();
+  tc_fence_after();
+  if (ok) {
+    // warps w and w + 4 share TMEM lanes 32 (w % 4) ..; each takes half the columns
+    const int q = warp & 3, half = warp >> 2;
+    const int row = row0 + 32 * q + lane;
+    const int cw = J.ntile / 2;
+    for (int c0 = half * cw; c0 < (half + 1) * cw; c0 += 16) {
+      float o[16];
+      tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, o);
+      if (row < J.rows) {
+        const int cc = (nt * J.ntile + c0) >> 1;  // complex column
+        float2* dst = J.D + (size_t)row * J.ldd + cc;
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+          if (cc + i < J.Nc) dst[i] = make_float2(o[2 * i], o[2 * i + 1]);
+      }
+    }
+  } else if (threadIdx.x == 0) {
+    atomicOr(J.err, kDftErrBit);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, kDftMaxN);
+}
+
+// ------------------------------------------------------------------ matrices
+// FP64 entries, rounded to BF16 hi and lo = BF16(v - hi).  One thread per
+// complex entry (n, k) writes its four real entries.
+__device__ __forceinline__ void dft_entry(const DftSpec& P, int n, int k, double* cr, double* ci) {
+  const long long Q = P.Q;
+  if (P.kind == kDftForward) {  // n = ky, k = y
+    double s, c;
+    sincospi(2.0 * (double)(((long long)n * k) % Q) / (double)Q, &s, &c);
+    *cr = c;
+    *ci = -s;  // e^{-i theta}
+    return;
+  }
+  if (P.kind == kDftInverse) {  // n = y, k = ky
+    double s, c;
+    sincospi(2.0 * (double)(((long long)n * k) % Q) / (double)Q, &s, &c);
+    *cr = c;
+    *ci = s;
+    return;
+  }
+  // inverse with the prefilter: n = box coefficient row, k = ky
+  const double z1 = -0.26794919243112270;  // sqrt(3) - 2
+  const double g0 = -6.0 * z1 / (1.0 - z1 * z1);
+  const int D = P.fir ? kDftPrefTaps : 0;
+  double sr = 0.0, si = 0.0, hd = g0;
+  for (int d = 0; d <= D; ++d) {
+    const double h = P.fir ? hd : 1.0;
+    for (int sgn = (d == 0 ? 1 : -1); sgn <= 1; sgn += 2) {
+      const int node = P.start + n + sgn * d;
+      int local;
+      if (P.periodic) {
+        local = node % P.box_len;
+        if (local < 0) local += P.box_len;
+      } else {
+        local = mirror_index(node, P.box_len);
+      }
+      const int g = wrap_once(P.box_lo + local, P.Q);
+      double s, c;
+      sincospi(2.0 * (double)(((long long)g * k) % Q) / (double)Q, &s, &c);
+      sr += h * c;
+      si += h * s;
+    }
+    hd *= z1;
+  }
+  *cr = sr;
+  *ci = si;
+}
+
+__device__ __forceinline__ void put_bf16(uint16_t* hi, uint16_t* lo, size_t at, double v) {
+  const __nv_bfloat16 h = __float2bfloat16_rn((float)v);
+  const __nv_bfloat16 l = __float2bfloat16_rn((float)(v - (double)__bfloat162float(h)));
+  hi[at] = *reinterpret_cast<const uint16_t*>(&h);
+  lo[at] = *reinterpret_cast<const uint16_t*>(&l);
+}
+
+__global__ void __launch_bounds__(256) k_dft_pack(const DftSpec P, int ntile, int ntiles, int kchunks, uint16_t* hi,
+                                                  uint16_t* lo) {
+  // one thread per complex (n, k) pair of the padded matrix
+  const int ncp = ntiles * ntile / 2, kcp = kchunks * (int)kKChunk / 2;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)ncp * kcp) return;
+  const int n = (int)(idx / kcp), k = (int)(idx - (long long)n * kcp);
+  double cr = 0.0, ci = 0.0;
+  if (n < P.Nc && k < P.Kc) dft_entry(P, n, k, &cr, &ci);
+  // D[.][2n + a] = sum_k A[.][2k + b] B[2n + a][2k + b]:
+  //   re out: (re in) cr - (im in) ci;  im out: (re in) ci + (im in) cr
+  const double e[2][2] = {{cr, -ci}, {ci, cr}};
+  for (int a = 0; a < 2; ++a) {
+    const int nr = 2 * n + a;
+    const int t = nr / ntile, nl = nr - t * ntile;
+    for (int b = 0; b < 2; ++b) {
+      const int kr = 2 * k + b;
+      const int c = kr / (int)kKChunk, kl = kr - c * (int)kKChunk;
+      const size_t blk = ((size_t)t * kchunks + c) * (size_t)ntile * kKChunk;
+      const size_t at = blk + (size_t)((nl >> 3) * (int)(kRowGroupBytes / 2) + (kl >> 3) * (int)(kCoreBytes / 2) +
+                                       (nl & 7) * 8 + (kl & 7));
+      put_bf16(hi, lo, at, e[a][b]);
+    }
+  }
+}
+
+DftShape dft_shape(int Nc, int Kc) {
+  DftShape s;
+  const int nreal = 2 * Nc;
+  s.ntiles = (nreal + kDftMaxN - 1) / kDftMaxN;
+  const int per = (nreal + s.ntiles - 1) / s.ntiles;
+  s.ntile = (per + 31) / 32 * 32;
+  s.kchunks = (2 * Kc + (int)kKChunk - 1) / (int)kKChunk;
+  return s;
+}
+
+size_t dft_matrix_elems(const DftShape& s) { return (size_t)s.ntiles * s.ntile * s.kchunks * kKChunk; }
+
+cudaError_t launch_dft_pack(const DftSpec& P, const DftShape& s, uint16_t* hi, uint16_t* lo, cudaStream_t st) {
+  const long long n = (long long)(s.ntiles * s.ntile / 2) * (s.kchunks * (int)kKChunk / 2);
+  if (n == 0) return cudaSuccess;
+  k_dft_pack<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P, s.ntile, s.ntiles, s.kchunks, hi, lo);
+  return cudaGetLastError();
+}
+
+// no CTAs for an empty product (the kernel needs at least one K chunk)
+int dft_tiles(int rows, const DftShape& s) {
+  if (rows <= 0 || s.kchunks <= 0 || s.ntiles <= 0) return 0;
+  return (rows + kDftRows - 1) / kDftRows * s.ntiles;
+}
+
+cudaError_t launch_ydft(const Launch<DftJob>& L, cudaStream_t st) {
+  const int grid = L.tile_start[L.njobs];
+  if (grid == 0) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(k_ydft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDftSmem);
+  if (e != cudaSuccess) return e;
+  k_ydft<<<grid, kDftThreads, kDftSmem, st>>>(L);
+  return cudaGetLastError();
+}
+
+}  // namespace mm
