@@ -4,11 +4,12 @@
 //
 // Operand layout used throughout: K-major, no swizzle.  A "core matrix" is 8
 // rows x 16 bytes (8 BF16 values of K) stored as 128 contiguous bytes, row i
-// at byte 16 i.  A tile of R rows x 64 K (one pipeline stage) keeps the 8 core
+// at byte 16 i.  A tile of R rows x 32 K (one pipeline stage) keeps the 4 core
 // matrices of a row group contiguous: core (row group g, K group c) at byte
-// g * 1024 + c * 128.  The descriptor's leading byte offset is then the stride
+// g * 512 + c * 128.  The descriptor's leading byte offset is then the stride
 // between core matrices along K (128) and its stride byte offset the stride
-// between row groups (1024).
+// between row groups (512).  (Measured on GB300: back-to-back MMAs on this
+// layout run at the tensor core's full rate, as with the 128-byte swizzle.)
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -16,8 +17,8 @@
 namespace mm {
 
 constexpr uint32_t kCoreBytes = 128;      // one 8 x 16-byte core matrix
-constexpr uint32_t kKChunk = 64;          // BF16 K values per pipeline stage
-constexpr uint32_t kRowGroupBytes = 1024; // 8 rows x 64 K x 2 bytes
+constexpr uint32_t kKChunk = 32;          // BF16 K values per pipeline stage
+constexpr uint32_t kRowGroupBytes = 512;  // 8 rows x 32 K x 2 bytes
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -68,6 +69,21 @@ __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.a
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// the arrival of the thread that starts `bytes` of bulk copies completing on *bar
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+// bulk copy (TMA, untiled) of `bytes` from global to this CTA's shared memory,
+// completing on *bar; both addresses 16-byte aligned, bytes a multiple of 16
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
 }
 
 // Wait until the phase of parity `parity` of *bar has completed, for at most

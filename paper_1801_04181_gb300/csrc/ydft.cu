@@ -29,26 +29,43 @@ namespace mm {
 constexpr int kDftThreads = 256;
 constexpr int kDftRows = 128;     // MMA M: rows per CTA
 constexpr int kDftMaxN = 256;     // MMA N: real columns per CTA (TMEM columns)
-constexpr int kDftStages = 2;
+constexpr int kDftStages = 4;     // K chunks in flight
 constexpr uint32_t kDftStageA = kDftRows * kKChunk * 2;  // one split of A, bytes
 constexpr uint32_t kDftStageB = kDftMaxN * kKChunk * 2;  // one split of B, bytes
 constexpr uint32_t kDftStageBytes = 2 * kDftStageA + 2 * kDftStageB;
-constexpr size_t kDftSmem = (size_t)kDftStages * kDftStageBytes + 64;
-// about one second at the SM clock: a wait on the tensor core never takes this
-// long unless something is wrong
+// stages + barriers + the TMEM slot, and room to align the base to 1 KB
+constexpr size_t kDftSmem = (size_t)kDftStages * kDftStageBytes + 128 + 1024;
+// about one second at the SM clock: a wait on the tensor core or a bulk copy
+// never takes this long unless something is wrong
 constexpr long long kDftSpinCycles = 2000000000LL;
 constexpr int kDftErrBit = 2;
+// A values (complex) per thread and chunk
+constexpr int kDftAPer = kDftRows * (int)(kKChunk / 2) / kDftThreads;
+// row pitch (floats) of the epilogue's staging tile: 4 mod 32, so the float4
+// stores of 8 lanes (8 rows) fall in distinct banks
+constexpr int kDftPitchPad = 4;
 
 __device__ __forceinline__ uint32_t bf16x2_bits(float a, float b) {
   const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
   return *reinterpret_cast<const uint32_t*>(&h);
 }
 
+// A chunk c of a CTA's 128 rows: warp-item w (0 .. 63) covers 8 rows x 4
+// complex, so the loads are 32-byte runs of 8 rows and the 4-byte stores of a
+// warp fill one 128-byte core matrix (no bank conflicts)
+__device__ __forceinline__ void a_item(int it, int lane, int* r, int* kc) {
+  const int w = (int)(threadIdx.x >> 5) + it * (kDftThreads / 32);
+  *r = (w >> 2) * 8 + (lane & 7);
+  *kc = (w & 3) * 4 + (lane >> 3);
+}
+
 __global__ void __launch_bounds__(kDftThreads, 1) k_ydft(const Launch<DftJob> Lc) {
-  extern __shared__ __align__(1024) uint8_t sm[];
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + kDftStages * kDftStageBytes);
-  uint32_t* slot = reinterpret_cast<uint32_t*>(bar + kDftStages);
-  __shared__ int ok;
+  extern __shared__ __align__(1024) uint8_t smraw[];
+  uint8_t* sm = smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u);
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + kDftStages * kDftStageBytes);  // B of a stage landed
+  uint64_t* empty = full + kDftStages;                                            // MMAs of a stage done
+  uint32_t* slot = reinterpret_cast<uint32_t*>(empty + kDftStages);
+  __shared__ int ok, okf[2];
   const int j = find_job(Lc.tile_start, Lc.njobs, blockIdx.x);
   const DftJob& J = Lc.job[j];
   const int tile = blockIdx.x - Lc.tile_start[j];
@@ -61,108 +78,153 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_ydft(const Launch<DftJob> Lc
     tmem_relinquish();
   }
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kDftStages; ++s) mbar_init(&bar[s], 1);
+    for (int s = 0; s < kDftStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
     ok = 1;
+    okf[0] = okf[1] = 1;
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *slot;
   const uint32_t idesc = idesc_bf16_f32(kDftRows, J.ntile);
-  const size_t bblock = (size_t)J.ntile * kKChunk;  // BF16 values of one (N tile, K chunk) block
-  const int nvec = J.ntile * kKChunk * 2 / 16;      // uint4 per block
+  const uint32_t bbytes = (uint32_t)J.ntile * kKChunk * 2u;  // one split of one (N tile, K chunk) block
+  const size_t bblock = (size_t)J.ntile * kKChunk;            // its BF16 values
+  const int K = J.kchunks;
 
-  for (int c = 0; c < J.kchunks; ++c) {
-    const int s = c % kDftStages;
-    uint8_t* st = sm + s * kDftStageBytes;
-    uint8_t* sAh = st;
-    uint8_t* sAl = st + kDftStageA;
-    uint8_t* sBh = st + 2 * kDftStageA;
-    uint8_t* sBl = sBh + kDftStageB;
-    if (c >= kDftStages) {
-      // the MMAs of chunk c - kDftStages read this stage's buffers
-      if (threadIdx.x == 0 &&
-          !mbar_wait(&bar[s], (uint32_t)((c - kDftStages) / kDftStages) & 1u, kDftSpinCycles))
-        ok = 0;
-      __syncthreads();
-      if (!ok) break;
-    }
-    // A: 128 rows x 32 complex of this chunk, split into BF16 hi + lo.  A
-    // warp covers 8 rows x 4 complex, so its 4-byte stores fill one 128-byte
-    // run of the core matrices (no bank conflicts) and its loads are 32-byte
-    // runs of 8 rows.
-    const int k0 = c * (int)(kKChunk / 2);
-    float2 v[kDftRows * 32 / kDftThreads];
+  // thread 0: the B block of chunk c (hi and lo) into its stage, by bulk copy
+  auto issue_b = [&](int c) {
+    uint8_t* st = sm + (c % kDftStages) * kDftStageBytes;
+    uint64_t* bar = &full[c % kDftStages];
+    const size_t off = ((size_t)nt * K + c) * bblock;
+    mbar_expect_tx(bar, 2u * bbytes);
+    bulk_g2s(st + 2 * kDftStageA, J.Bhi + off, bbytes, bar);
+    bulk_g2s(st + 2 * kDftStageA + kDftStageB, J.Blo + off, bbytes, bar);
+  };
+  auto load_a = [&](int c, float2* v) {
 #pragma unroll
-    for (int it = 0; it < kDftRows * 32 / kDftThreads; ++it) {
-      const int w = (threadIdx.x >> 5) + it * (kDftThreads / 32);  // 0 .. 127
-      const int r = (w >> 3) * 8 + (lane & 7);
-      const int kc = (w & 7) * 4 + (lane >> 3);
-      const int row = row0 + r, k = k0 + kc;
+    for (int it = 0; it < kDftAPer; ++it) {
+      int r, kc;
+      a_item(it, lane, &r, &kc);
+      const int row = row0 + r, k = c * (int)(kKChunk / 2) + kc;
       v[it] = (row < J.rows && k < J.Kc) ? __ldg(J.A + (size_t)row * J.lda + k) : make_float2(0.f, 0.f);
     }
+  };
+
+  // thread 0's record of the bulk copies issued and the MMAs committed, for
+  // the bounded drain after a failed wait
+  int n_issued = 0, n_committed = 0;
+  if (threadIdx.x == 0)
+    for (int c = 0; c < min(kDftStages, K); ++c, ++n_issued) issue_b(c);
+  // One barrier per chunk.  Stage s of chunk c was last read by the MMAs of
+  // chunk c - kDftStages, which thread 0 waited for in iteration
+  // c - kDftStages + 1, before the barriers of the iterations since.  A
+  // failed wait in iteration c is recorded in okf[c & 1] and read by every
+  // thread after the next barrier, so all threads leave the loop together.
+  auto chunk = [&](int c, float2* v) -> bool {
+    const int s = c % kDftStages;
+    uint8_t* st = sm + s * kDftStageBytes;
 #pragma unroll
-    for (int it = 0; it < kDftRows * 32 / kDftThreads; ++it) {
-      const int w = (threadIdx.x >> 5) + it * (kDftThreads / 32);
-      const int r = (w >> 3) * 8 + (lane & 7);
-      const int kc = (w & 7) * 4 + (lane >> 3);
+    for (int it = 0; it < kDftAPer; ++it) {  // A of chunk c, split into BF16 hi + lo
+      int r, kc;
+      a_item(it, lane, &r, &kc);
       const float hx = __bfloat162float(__float2bfloat16_rn(v[it].x));
       const float hy = __bfloat162float(__float2bfloat16_rn(v[it].y));
       const uint32_t off = tile_offset(r, 2 * kc);
-      *reinterpret_cast<uint32_t*>(sAh + off) = bf16x2_bits(hx, hy);
-      *reinterpret_cast<uint32_t*>(sAl + off) = bf16x2_bits(v[it].x - hx, v[it].y - hy);
+      *reinterpret_cast<uint32_t*>(st + off) = bf16x2_bits(hx, hy);
+      *reinterpret_cast<uint32_t*>(st + kDftStageA + off) = bf16x2_bits(v[it].x - hx, v[it].y - hy);
     }
-    // B: the packed (N tile, K chunk) block, hi and lo
-    const uint4* gh = reinterpret_cast<const uint4*>(J.Bhi + ((size_t)nt * J.kchunks + c) * bblock);
-    const uint4* gl = reinterpret_cast<const uint4*>(J.Blo + ((size_t)nt * J.kchunks + c) * bblock);
-    for (int i = threadIdx.x; i < nvec; i += kDftThreads) {
-      const uint4 a = __ldg(gh + i), b = __ldg(gl + i);
-      reinterpret_cast<uint4*>(sBh)[i] = a;
-      reinterpret_cast<uint4*>(sBl)[i] = b;
-    }
+    if (c + 2 < K) load_a(c + 2, v);  // two chunks ahead: in flight during the MMAs
     fence_async_smem();
     __syncthreads();
+    if (c >= 1 && !okf[(c - 1) & 1]) return false;
     if (threadIdx.x == 0) {
+      if (!mbar_wait(&full[s], (uint32_t)(c / kDftStages) & 1u, kDftSpinCycles)) {
+        okf[c & 1] = 0;
+        return true;
+      }
       tc_fence_after();
+      const uint32_t aB = smem_u32(st), bB = smem_u32(st + 2 * kDftStageA);
 #pragma unroll
       for (int q = 0; q < (int)kKChunk / 16; ++q) {
         const uint32_t off = (uint32_t)q * 2u * kCoreBytes;  // 16 K values = two core matrices
-        const uint64_t ah = smem_desc(smem_u32(sAh) + off, kCoreBytes, kRowGroupBytes);
-        const uint64_t al = smem_desc(smem_u32(sAl) + off, kCoreBytes, kRowGroupBytes);
-        const uint64_t bh = smem_desc(smem_u32(sBh) + off, kCoreBytes, kRowGroupBytes);
-        const uint64_t bl = smem_desc(smem_u32(sBl) + off, kCoreBytes, kRowGroupBytes);
+        const uint64_t ah = smem_desc(aB + off, kCoreBytes, kRowGroupBytes);
+        const uint64_t al = smem_desc(aB + kDftStageA + off, kCoreBytes, kRowGroupBytes);
+        const uint64_t bh = smem_desc(bB + off, kCoreBytes, kRowGroupBytes);
+        const uint64_t bl = smem_desc(bB + kDftStageB + off, kCoreBytes, kRowGroupBytes);
         umma_bf16(tmem, ah, bh, idesc, (c > 0 || q > 0) ? 1u : 0u);
         umma_bf16(tmem, ah, bl, idesc, 1u);
         umma_bf16(tmem, al, bh, idesc, 1u);
       }
-      umma_commit(&bar[s]);
+      umma_commit(&empty[s]);
+      n_committed = c + 1;
+      // the stage of chunk c - 1 is free once its MMAs are done: refill it
+      // with the B block kDftStages - 1 chunks ahead
+      if (c >= 1) {
+        const int cp = c - 1;
+        if (!mbar_wait(&empty[cp % kDftStages], (uint32_t)(cp / kDftStages) & 1u, kDftSpinCycles)) {
+          okf[c & 1] = 0;
+        } else if (cp + kDftStages < K) {
+          issue_b(cp + kDftStages);
+          ++n_issued;
+        }
+      }
     }
+    return true;
+  };
+  float2 va[kDftAPer], vb[kDftAPer];
+  load_a(0, va);
+  if (K > 1) load_a(1, vb);
+  for (int c = 0; c < K; c += 2) {
+    if (!chunk(c, va)) break;
+    if (c + 1 < K && !chunk(c + 1, vb)) break;
   }
+  __syncthreads();
+  if (threadIdx.x == 0) ok = okf[0] && okf[1];
   // the last chunk's commit completes after every MMA issued before it
   if (threadIdx.x == 0 && ok) {
-    const int c = J.kchunks - 1;
-    if (!mbar_wait(&bar[c % kDftStages], (uint32_t)(c / kDftStages) & 1u, kDftSpinCycles)) ok = 0;
+    const int c = K - 1;
+    if (!mbar_wait(&empty[c % kDftStages], (uint32_t)(c / kDftStages) & 1u, kDftSpinCycles)) ok = 0;
   }
   __syncthreads();
   tc_fence_after();
   if (ok) {
-    // warps w and w + 4 share TMEM lanes 32 (w % 4) ..; each takes half the columns
+    // TMEM -> staging tile [128][ntile + pad] (the stage buffers are free) ->
+    // coalesced row segments.  Warps w and w + 4 share TMEM lanes 32 (w % 4)
+    // .. and take half the columns each.
+    float* T = reinterpret_cast<float*>(sm);
+    const int pitch = J.ntile + kDftPitchPad;
     const int q = warp & 3, half = warp >> 2;
-    const int row = row0 + 32 * q + lane;
+    const int r = 32 * q + lane;
     const int cw = J.ntile / 2;
     for (int c0 = half * cw; c0 < (half + 1) * cw; c0 += 16) {
       float o[16];
       tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, o);
-      if (row < J.rows) {
-        const int cc = (nt * J.ntile + c0) >> 1;  // complex column
-        float2* dst = J.D + (size_t)row * J.ldd + cc;
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
-          if (cc + i < J.Nc) dst[i] = make_float2(o[2 * i], o[2 * i + 1]);
-      }
+      for (int i = 0; i < 16; i += 4)
+        *reinterpret_cast<float4*>(T + (size_t)r * pitch + c0 + i) = make_float4(o[i], o[i + 1], o[i + 2], o[i + 3]);
+    }
+    __syncthreads();
+    const int cc0 = (nt * J.ntile) >> 1;               // first complex column of the tile
+    const int ncols = min(J.ntile >> 1, J.Nc - cc0);   // complex columns to write
+    const int nrows = min(kDftRows, J.rows - row0);
+    for (int rr = warp; rr < nrows; rr += kDftThreads / 32) {
+      float2* dst = J.D + (size_t)(row0 + rr) * J.ldd + cc0;
+      const float2* src = reinterpret_cast<const float2*>(T + (size_t)rr * pitch);
+      for (int cc = lane; cc < ncols; cc += 32) dst[cc] = src[cc];
     }
   } else if (threadIdx.x == 0) {
     atomicOr(J.err, kDftErrBit);
+    // drain, each wait bounded: the bulk copies into this CTA's shared
+    // memory and the MMAs on its TMEM that may still be in flight
+    for (int c = max(0, n_issued - kDftStages); c < n_issued; ++c)
+      mbar_wait(&full[c % kDftStages], (uint32_t)(c / kDftStages) & 1u, kDftSpinCycles / 8);
+    if (n_committed > 0) {
+      const int c = n_committed - 1;
+      mbar_wait(&empty[c % kDftStages], (uint32_t)(c / kDftStages) & 1u, kDftSpinCycles / 8);
+    }
   }
   tc_fence_before();
   __syncthreads();
