@@ -43,6 +43,9 @@ WORKLOADS = {
 TIMING_CLASSES = ["fft_x_forward", "fft_y_pass_mix_prefilter", "fft_x_inverse_prefilter",
                   "spline_gather_force", "llg_stage", "slider_reduce", "combine_normalise",
                   "fft_y_forward_thick", "fft_z_pass_thick", "fft_y_inverse_thick"]
+# the same classes in the reduced-precision form (every source through the separate passes)
+MIXED_CLASSES = dict(enumerate(TIMING_CLASSES))
+MIXED_CLASSES.update({7: "ydft_forward_tensor", 8: "z_plane_mix", 9: "ydft_inverse_prefilter_tensor"})
 
 
 BATCH_LANES = 16
@@ -55,6 +58,9 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--precision", default="fp32", choices=["fp32", "mixed"],
+                   help="precision of the timed context; the fp32 line also reports the mixed form beside it")
+    p.add_argument("--no-mixed", action="store_true", help="fp32 line without the mixed-precision comparison")
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--lanes", type=int, default=BATCH_LANES, help="streams of the batch256 workload")
     p.add_argument("--no-autotune", action="store_true",
@@ -209,6 +215,101 @@ def profiled_traffic(cls):
     return int(t.group(1)), os.path.relpath(path, ROOT)
 
 
+def dft_flops(mm, fp):
+    """Flops of the tensor-core y DFT classes per launch (both magnets): three
+    BF16 products x 2 flops x rows x (2 Nc) x (2 Kc) of the real-form product,
+    unpadded.  Forward: rows (plane, kx) = 3 nz kxh, Kc = ny, Nc = Qy; inverse:
+    the demag rows (Kc = Qy, Nc = ny) and the coefficient rows (r_z kxh rows,
+    Nc = r_y)."""
+    fwd = inv = 0
+    for s, n in enumerate((fp.n_base, fp.n_slider)):
+        nz, ny = n[2], n[1]
+        info = mm.plan_info(s)
+        Qx, Qy = info["fft"]
+        kxh = Qx // 2 + 1
+        _, ry, rz = info["coef"]
+        fwd += 3 * 2 * (3 * nz * kxh) * (2 * Qy) * (2 * ny)
+        inv += 3 * 2 * (3 * nz * kxh) * (2 * ny) * (2 * Qy) + 3 * 2 * (rz * kxh) * (2 * ry) * (2 * Qy)
+    return {7: fwd, 9: inv}
+
+
+def measured_tensor_peak():
+    """Dense BF16 TFLOP/s of the GB300s: the sustained figure (a kernel
+    timed inside a long step), else the burst one, else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            P = json.load(f)
+        if "bf16_tflops_sustained" in P:
+            return float(P["bf16_tflops_sustained"]), "measured (sustained)"
+        return float(P["bf16_tflops"]), "measured (burst)"
+    except Exception:
+        return 1700.0, "fallback (sustained)"
+
+
+def field_set(mm):
+    """Stray fields both ways and both demag fields at the current state (host, FP64)."""
+    return [mm.compute_stray_field(0).double().cpu(), mm.compute_stray_field(1).double().cpu(),
+            mm.compute_demag(0).double().cpu(), mm.compute_demag(1).double().cpu()]
+
+
+def run_mixed_compare(fp, m0, m1, ref_fields, steps, warmup, fp32_value):
+    """The reduced-precision form on the same workload: throughput, its field
+    error against the FP32 path at the same initial state, and the tensor
+    roofline of its DFT kernel classes."""
+    import torch
+    from paper_1801_04181_gb300 import MMError
+    from paper_1801_04181_gb300 import pair_context as gpu_pair
+
+    if max(fp.n_base[2], fp.n_slider[2]) > 8:
+        return {"unavailable": "the reduced-precision form takes sources of at most 8 layers"}
+    try:
+        mm = gpu_pair(fp, m0, m1, adaptive=True, rtol=1e-5, precision="mixed")
+        got = field_set(mm)
+    except MMError as e:
+        return {"unavailable": str(e)}
+    names = ["H_stray_base_to_slider", "H_stray_slider_to_base", "H_demag_base", "H_demag_slider"]
+    err = {k: float((a - b).norm() / b.norm()) for k, a, b in zip(names, got, ref_fields)}
+    dt = 1e-13
+    for _ in range(max(warmup, 3)):
+        _, dt = mm.step(1, dt)
+    mm.set_timing(False)
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(steps):
+        _, dt = mm.step(1, dt)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    mm.reset_timing()
+    mm.set_timing(True)
+    for _ in range(max(1, min(steps, 20))):
+        _, dt = mm.step(1, dt)
+    torch.cuda.synchronize()
+    mm.set_timing(False)
+    kt = {c: mm.timing(c) for c in range(len(TIMING_CLASSES))}
+    flops = dft_flops(mm, fp)
+    peak, src = measured_tensor_peak()
+    tensor = {}
+    for c, f in flops.items():
+        tot, nl = kt[c]
+        if nl:
+            avg = tot / nl / 1e3
+            tensor[MIXED_CLASSES[c]] = {"achieved": round(f / avg / 1e12, 1), "peak": peak, "peak_source": src,
+                                         "unit": "TFLOP/s", "frac": round(f / avg / 1e12 / peak, 4),
+                                         "flops_per_launch": int(f), "avg_launch_ms": round(avg * 1e3, 5)}
+    value = fp.cells() * steps / (ms / 1e3)
+    mm.close()
+    return {"value": value, "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
+            "vs_fp32": round(value / fp32_value, 4),
+            "dtype": "split-bf16 (hi.hi + hi.lo + lo.hi) tensor-core y DFTs, f32 accumulation; rest f32",
+            "rel_l2_vs_fp32": err,
+            "roofline": {"bound": "tensor", "kernels": tensor},
+            "kernel_times": {MIXED_CLASSES[c]: {"ms": round(kt[c][0], 3), "launches": kt[c][1]}
+                             for c in kt if kt[c][1]}}
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -344,8 +445,11 @@ def run_gpu(args):
 
     wl_name, wl_make = WORKLOADS[args.workload]
     fp, m0, m1 = wl_make(args.seed + 101 * rank)
-    mm = gpu_pair(fp, m0, m1, adaptive=True, rtol=1e-5)
+    mm = gpu_pair(fp, m0, m1, adaptive=True, rtol=1e-5, precision=args.precision)
     cells = fp.cells()
+    # fields at the initial state, for the mixed form's error beside this line
+    want_mixed = args.precision == "fp32" and not args.no_mixed and rank == 0 and world == 1
+    ref_fields = field_set(mm) if want_mixed else None
     stream = torch.cuda.current_stream()
     dt = 1e-13
     for _ in range(max(args.warmup, 3)):
@@ -430,8 +534,23 @@ def run_gpu(args):
             "peak": peak, "peak_source": src, "unit": "GB/s", "frac": round(achieved / peak, 4),
             "algorithmic_bytes_per_launch": int(ab[dom]), "avg_launch_ms": round(avg_s * 1e3, 5),
             "traffic": traffic, "traffic_source": traffic_src}
-    ktab = {TIMING_CLASSES[c]: {"ms": round(kt[c][0], 3), "launches": kt[c][1]} for c in kt if kt[c][1]}
-    fft_cmp = cufft_compare(mm, fp, kt) if args.workload == "stick_slip" else None
+    if args.precision == "mixed":
+        # the dominant tensor-core DFT class against the BF16 tensor peak
+        fl = dft_flops(mm, fp)
+        dom = max(fl.keys(), key=lambda c: kt[c][0])
+        tot_ms, nl = kt[dom]
+        avg_s = tot_ms / max(nl, 1) / 1e3
+        tpk, tsrc = measured_tensor_peak()
+        roof = {"bound": "tensor", "kernel": MIXED_CLASSES[dom], "achieved": round(fl[dom] / avg_s / 1e12, 1),
+                "peak": tpk, "peak_source": tsrc, "unit": "TFLOP/s",
+                "frac": round(fl[dom] / avg_s / 1e12 / tpk, 4), "flops_per_launch": int(fl[dom]),
+                "avg_launch_ms": round(avg_s * 1e3, 5), "traffic": None}
+    names = MIXED_CLASSES if args.precision == "mixed" else dict(enumerate(TIMING_CLASSES))
+    ktab = {names[c]: {"ms": round(kt[c][0], 3), "launches": kt[c][1]} for c in kt if kt[c][1]}
+    fft_cmp = cufft_compare(mm, fp, kt) if args.workload == "stick_slip" and args.precision == "fp32" else None
+    mixed = None
+    if want_mixed:
+        mixed = run_mixed_compare(fp, m0, m1, ref_fields, max(1, min(args.steps, 50)), args.warmup, value)
     if pool is not None:
         try:
             cpu_base = cpu_oracle_sample(fp, m0, m1, pool, oracle_pool_size())
@@ -442,8 +561,10 @@ def run_gpu(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": wl_name, "cells": cells,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == "fp32" else "split-bf16 tensor-core y DFTs + f32",
+            "data": "synthetic",
+            "config": {"workload": wl_name, "cells": cells, "precision": args.precision,
                        "fft": [list(mm.plan_info(0)["fft"]) + [mm.plan_info(0)["Qz"]]],
                        "adaptive_rtol": 1e-5, "accepted": acc1 - acc0, "rejected": rej1 - rej0,
                        "dt_final_s": dt, "parallelism": "replicas" if world > 1 else "single",
@@ -455,6 +576,7 @@ def run_gpu(args):
             "roofline": roof,
             "kernel_times": ktab,
             "cufft_compare": fft_cmp,
+            "mixed": mixed,
             "power": power,
             "clocks": clk,
             "cpu_baseline": cpu_base,

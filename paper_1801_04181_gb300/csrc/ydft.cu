@@ -29,43 +29,78 @@ namespace mm {
 constexpr int kDftThreads = 256;
 constexpr int kDftRows = 128;     // MMA M: rows per CTA
 constexpr int kDftMaxN = 256;     // MMA N: real columns per CTA (TMEM columns)
-constexpr int kDftStages = 4;     // K chunks in flight
+constexpr int kDftStages = 2;     // K chunks in flight per CTA (two CTAs share an SM)
 constexpr uint32_t kDftStageA = kDftRows * kKChunk * 2;  // one split of A, bytes
 constexpr uint32_t kDftStageB = kDftMaxN * kKChunk * 2;  // one split of B, bytes
 constexpr uint32_t kDftStageBytes = 2 * kDftStageA + 2 * kDftStageB;
-// stages + barriers + the TMEM slot, and room to align the base to 1 KB
-constexpr size_t kDftSmem = (size_t)kDftStages * kDftStageBytes + 128 + 1024;
+constexpr size_t kDftSmem = (size_t)kDftStages * kDftStageBytes + 128;  // + barriers, TMEM slot
 // about one second at the SM clock: a wait on the tensor core or a bulk copy
 // never takes this long unless something is wrong
 constexpr long long kDftSpinCycles = 2000000000LL;
 constexpr int kDftErrBit = 2;
-// A values (complex) per thread and chunk
+// A values (complex) per thread and chunk in the split pass
 constexpr int kDftAPer = kDftRows * (int)(kKChunk / 2) / kDftThreads;
-// row pitch (floats) of the epilogue's staging tile: 4 mod 32, so the float4
-// stores of 8 lanes (8 rows) fall in distinct banks
-constexpr int kDftPitchPad = 4;
+// per-warp epilogue staging: 32 rows x 16 floats, row pitch 20 (the float4
+// stores of 8 lanes fall in distinct banks)
+constexpr int kDftEpiPitch = 20;
 
 __device__ __forceinline__ uint32_t bf16x2_bits(float a, float b) {
   const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
   return *reinterpret_cast<const uint32_t*>(&h);
 }
 
-// A chunk c of a CTA's 128 rows: warp-item w (0 .. 63) covers 8 rows x 4
+// A chunk of 128 rows x 16 complex: warp-item w (0 .. 63) covers 8 rows x 4
 // complex, so the loads are 32-byte runs of 8 rows and the 4-byte stores of a
-// warp fill one 128-byte core matrix (no bank conflicts)
+// warp fill one 128-byte core matrix
 __device__ __forceinline__ void a_item(int it, int lane, int* r, int* kc) {
   const int w = (int)(threadIdx.x >> 5) + it * (kDftThreads / 32);
   *r = (w >> 2) * 8 + (lane & 7);
   *kc = (w & 3) * 4 + (lane >> 3);
 }
 
-__global__ void __launch_bounds__(kDftThreads, 1) k_ydft(const Launch<DftJob> Lc) {
-  extern __shared__ __align__(1024) uint8_t smraw[];
-  uint8_t* sm = smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u);
-  uint64_t* full = reinterpret_cast<uint64_t*>(sm + kDftStages * kDftStageBytes);  // B of a stage landed
-  uint64_t* empty = full + kDftStages;                                            // MMAs of a stage done
+// Split pass: A (FP32 complex rows) -> BF16 hi | lo blocks in the tensor
+// core's layout, one 16 KB block per (128-row tile, K chunk), so the product
+// kernel moves them by bulk copy and every N tile reuses one split.  One CTA
+// per block.
+__global__ void __launch_bounds__(kDftThreads) k_dft_split(const Launch<DftJob> Lc) {
+  const int j = find_job(Lc.tile_start, Lc.njobs, blockIdx.x);
+  const DftJob& J = Lc.job[j];
+  const int b = blockIdx.x - Lc.tile_start[j];
+  const int mt = b / J.kchunks, c = b - mt * J.kchunks;
+  const int lane = threadIdx.x & 31;
+  uint8_t* dst = reinterpret_cast<uint8_t*>(J.Apk) + (size_t)b * 2 * kDftStageA;
+  float2 v[kDftAPer];
+#pragma unroll
+  for (int it = 0; it < kDftAPer; ++it) {
+    int r, kc;
+    a_item(it, lane, &r, &kc);
+    const int row = mt * kDftRows + r, k = c * (int)(kKChunk / 2) + kc;
+    v[it] = (row < J.rows && k < J.Kc) ? __ldg(J.A + (size_t)row * J.lda + k) : make_float2(0.f, 0.f);
+  }
+#pragma unroll
+  for (int it = 0; it < kDftAPer; ++it) {
+    int r, kc;
+    a_item(it, lane, &r, &kc);
+    const float hx = __bfloat162float(__float2bfloat16_rn(v[it].x));
+    const float hy = __bfloat162float(__float2bfloat16_rn(v[it].y));
+    const uint32_t off = tile_offset(r, 2 * kc);
+    *reinterpret_cast<uint32_t*>(dst + off) = bf16x2_bits(hx, hy);
+    *reinterpret_cast<uint32_t*>(dst + kDftStageA + off) = bf16x2_bits(v[it].x - hx, v[it].y - hy);
+  }
+}
+
+// Product pass.  Thread 0 alone runs the main loop: bulk copies of the A and
+// B blocks of each K chunk into a stage (completing on full[s]), the MMAs of
+// the chunk once they landed (their completion committed to empty[s]), and
+// the refill of a stage once its MMAs are done.  The other warps wait at the
+// barrier before the epilogue; two CTAs share an SM, so one's epilogue runs
+// beside the other's main loop.
+__global__ void __launch_bounds__(kDftThreads, 2) k_ydft(const Launch<DftJob> Lc) {
+  extern __shared__ __align__(128) uint8_t sm[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + kDftStages * kDftStageBytes);  // a stage's copies landed
+  uint64_t* empty = full + kDftStages;                                            // a stage's MMAs done
   uint32_t* slot = reinterpret_cast<uint32_t*>(empty + kDftStages);
-  __shared__ int ok, okf[2];
+  __shared__ int ok;
   const int j = find_job(Lc.tile_start, Lc.njobs, blockIdx.x);
   const DftJob& J = Lc.job[j];
   const int tile = blockIdx.x - Lc.tile_start[j];
@@ -83,70 +118,38 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_ydft(const Launch<DftJob> Lc
       mbar_init(&empty[s], 1);
     }
     ok = 1;
-    okf[0] = okf[1] = 1;
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *slot;
-  const uint32_t idesc = idesc_bf16_f32(kDftRows, J.ntile);
-  const uint32_t bbytes = (uint32_t)J.ntile * kKChunk * 2u;  // one split of one (N tile, K chunk) block
-  const size_t bblock = (size_t)J.ntile * kKChunk;            // its BF16 values
   const int K = J.kchunks;
 
-  // thread 0: the B block of chunk c (hi and lo) into its stage, by bulk copy
-  auto issue_b = [&](int c) {
-    uint8_t* st = sm + (c % kDftStages) * kDftStageBytes;
-    uint64_t* bar = &full[c % kDftStages];
-    const size_t off = ((size_t)nt * K + c) * bblock;
-    mbar_expect_tx(bar, 2u * bbytes);
-    bulk_g2s(st + 2 * kDftStageA, J.Bhi + off, bbytes, bar);
-    bulk_g2s(st + 2 * kDftStageA + kDftStageB, J.Blo + off, bbytes, bar);
-  };
-  auto load_a = [&](int c, float2* v) {
-#pragma unroll
-    for (int it = 0; it < kDftAPer; ++it) {
-      int r, kc;
-      a_item(it, lane, &r, &kc);
-      const int row = row0 + r, k = c * (int)(kKChunk / 2) + kc;
-      v[it] = (row < J.rows && k < J.Kc) ? __ldg(J.A + (size_t)row * J.lda + k) : make_float2(0.f, 0.f);
-    }
-  };
-
-  // thread 0's record of the bulk copies issued and the MMAs committed, for
-  // the bounded drain after a failed wait
-  int n_issued = 0, n_committed = 0;
-  if (threadIdx.x == 0)
-    for (int c = 0; c < min(kDftStages, K); ++c, ++n_issued) issue_b(c);
-  // One barrier per chunk.  Stage s of chunk c was last read by the MMAs of
-  // chunk c - kDftStages, which thread 0 waited for in iteration
-  // c - kDftStages + 1, before the barriers of the iterations since.  A
-  // failed wait in iteration c is recorded in okf[c & 1] and read by every
-  // thread after the next barrier, so all threads leave the loop together.
-  auto chunk = [&](int c, float2* v) -> bool {
-    const int s = c % kDftStages;
-    uint8_t* st = sm + s * kDftStageBytes;
-#pragma unroll
-    for (int it = 0; it < kDftAPer; ++it) {  // A of chunk c, split into BF16 hi + lo
-      int r, kc;
-      a_item(it, lane, &r, &kc);
-      const float hx = __bfloat162float(__float2bfloat16_rn(v[it].x));
-      const float hy = __bfloat162float(__float2bfloat16_rn(v[it].y));
-      const uint32_t off = tile_offset(r, 2 * kc);
-      *reinterpret_cast<uint32_t*>(st + off) = bf16x2_bits(hx, hy);
-      *reinterpret_cast<uint32_t*>(st + kDftStageA + off) = bf16x2_bits(v[it].x - hx, v[it].y - hy);
-    }
-    if (c + 2 < K) load_a(c + 2, v);  // two chunks ahead: in flight during the MMAs
-    fence_async_smem();
-    __syncthreads();
-    if (c >= 1 && !okf[(c - 1) & 1]) return false;
-    if (threadIdx.x == 0) {
+  if (threadIdx.x == 0) {
+    const uint32_t idesc = idesc_bf16_f32(kDftRows, J.ntile);
+    const uint32_t bbytes = (uint32_t)J.ntile * kKChunk * 2u;  // one split of one (N tile, K chunk) block
+    const size_t bblock = (size_t)J.ntile * kKChunk;            // its BF16 values
+    const uint8_t* Ablk = reinterpret_cast<const uint8_t*>(J.Apk) + (size_t)mt * K * 2 * kDftStageA;
+    auto issue = [&](int c) {
+      uint8_t* st = sm + (c % kDftStages) * kDftStageBytes;
+      uint64_t* bar = &full[c % kDftStages];
+      const size_t off = ((size_t)nt * K + c) * bblock;
+      mbar_expect_tx(bar, 2u * kDftStageA + 2u * bbytes);
+      bulk_g2s(st, Ablk + (size_t)c * 2 * kDftStageA, 2u * kDftStageA, bar);
+      bulk_g2s(st + 2 * kDftStageA, J.Bhi + off, bbytes, bar);
+      bulk_g2s(st + 2 * kDftStageA + kDftStageB, J.Blo + off, bbytes, bar);
+    };
+    int n_issued = 0, n_committed = 0;
+    bool good = true;
+    for (; n_issued < min(kDftStages, K); ++n_issued) issue(n_issued);
+    for (int c = 0; c < K && good; ++c) {
+      const int s = c % kDftStages;
       if (!mbar_wait(&full[s], (uint32_t)(c / kDftStages) & 1u, kDftSpinCycles)) {
-        okf[c & 1] = 0;
-        return true;
+        good = false;
+        break;
       }
       tc_fence_after();
-      const uint32_t aB = smem_u32(st), bB = smem_u32(st + 2 * kDftStageA);
+      const uint32_t aB = smem_u32(sm + s * kDftStageBytes), bB = aB + 2 * kDftStageA;
 #pragma unroll
       for (int q = 0; q < (int)kKChunk / 16; ++q) {
         const uint32_t off = (uint32_t)q * 2u * kCoreBytes;  // 16 K values = two core matrices
@@ -160,70 +163,60 @@ __global__ void __launch_bounds__(kDftThreads, 1) k_ydft(const Launch<DftJob> Lc
       }
       umma_commit(&empty[s]);
       n_committed = c + 1;
-      // the stage of chunk c - 1 is free once its MMAs are done: refill it
-      // with the B block kDftStages - 1 chunks ahead
-      if (c >= 1) {
+      // refill the stage of chunk c - 1 once its MMAs are done (the MMAs of
+      // chunk c keep the tensor core busy meanwhile)
+      if (c >= 1 && c - 1 + kDftStages < K) {
         const int cp = c - 1;
         if (!mbar_wait(&empty[cp % kDftStages], (uint32_t)(cp / kDftStages) & 1u, kDftSpinCycles)) {
-          okf[c & 1] = 0;
-        } else if (cp + kDftStages < K) {
-          issue_b(cp + kDftStages);
-          ++n_issued;
+          good = false;
+          break;
         }
+        issue(cp + kDftStages);
+        ++n_issued;
       }
     }
-    return true;
-  };
-  float2 va[kDftAPer], vb[kDftAPer];
-  load_a(0, va);
-  if (K > 1) load_a(1, vb);
-  for (int c = 0; c < K; c += 2) {
-    if (!chunk(c, va)) break;
-    if (c + 1 < K && !chunk(c + 1, vb)) break;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) ok = okf[0] && okf[1];
-  // the last chunk's commit completes after every MMA issued before it
-  if (threadIdx.x == 0 && ok) {
-    const int c = K - 1;
-    if (!mbar_wait(&empty[c % kDftStages], (uint32_t)(c / kDftStages) & 1u, kDftSpinCycles)) ok = 0;
+    if (good) {
+      const int c = K - 1;  // its commit completes after every MMA issued before it
+      good = mbar_wait(&empty[c % kDftStages], (uint32_t)(c / kDftStages) & 1u, kDftSpinCycles);
+    }
+    if (!good) {
+      atomicOr(J.err, kDftErrBit);
+      // drain, each wait bounded: copies into this CTA's shared memory and
+      // MMAs on its TMEM that may still be in flight
+      for (int c = max(0, n_issued - kDftStages); c < n_issued; ++c)
+        mbar_wait(&full[c % kDftStages], (uint32_t)(c / kDftStages) & 1u, kDftSpinCycles / 8);
+      if (n_committed > 0) {
+        const int c = n_committed - 1;
+        mbar_wait(&empty[c % kDftStages], (uint32_t)(c / kDftStages) & 1u, kDftSpinCycles / 8);
+      }
+      ok = 0;
+    }
   }
   __syncthreads();
   tc_fence_after();
   if (ok) {
-    // TMEM -> staging tile [128][ntile + pad] (the stage buffers are free) ->
-    // coalesced row segments.  Warps w and w + 4 share TMEM lanes 32 (w % 4)
-    // .. and take half the columns each.
-    float* T = reinterpret_cast<float*>(sm);
-    const int pitch = J.ntile + kDftPitchPad;
+    // TMEM -> per-warp staging (the stage buffers are free now) -> row
+    // segments of 8 complex (64 bytes).  Warps w and w + 4 share TMEM lanes
+    // 32 (w % 4) .. and take alternate 16-column blocks.
+    float* W = reinterpret_cast<float*>(sm) + warp * 32 * kDftEpiPitch;
     const int q = warp & 3, half = warp >> 2;
-    const int r = 32 * q + lane;
-    const int cw = J.ntile / 2;
-    for (int c0 = half * cw; c0 < (half + 1) * cw; c0 += 16) {
+    const int cc0 = (nt * J.ntile) >> 1;  // first complex column of the tile
+    for (int c0 = 16 * half; c0 < J.ntile; c0 += 32) {
       float o[16];
       tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, o);
 #pragma unroll
       for (int i = 0; i < 16; i += 4)
-        *reinterpret_cast<float4*>(T + (size_t)r * pitch + c0 + i) = make_float4(o[i], o[i + 1], o[i + 2], o[i + 3]);
-    }
-    __syncthreads();
-    const int cc0 = (nt * J.ntile) >> 1;               // first complex column of the tile
-    const int ncols = min(J.ntile >> 1, J.Nc - cc0);   // complex columns to write
-    const int nrows = min(kDftRows, J.rows - row0);
-    for (int rr = warp; rr < nrows; rr += kDftThreads / 32) {
-      float2* dst = J.D + (size_t)(row0 + rr) * J.ldd + cc0;
-      const float2* src = reinterpret_cast<const float2*>(T + (size_t)rr * pitch);
-      for (int cc = lane; cc < ncols; cc += 32) dst[cc] = src[cc];
-    }
-  } else if (threadIdx.x == 0) {
-    atomicOr(J.err, kDftErrBit);
-    // drain, each wait bounded: the bulk copies into this CTA's shared
-    // memory and the MMAs on its TMEM that may still be in flight
-    for (int c = max(0, n_issued - kDftStages); c < n_issued; ++c)
-      mbar_wait(&full[c % kDftStages], (uint32_t)(c / kDftStages) & 1u, kDftSpinCycles / 8);
-    if (n_committed > 0) {
-      const int c = n_committed - 1;
-      mbar_wait(&empty[c % kDftStages], (uint32_t)(c / kDftStages) & 1u, kDftSpinCycles / 8);
+        *reinterpret_cast<float4*>(W + lane * kDftEpiPitch + i) = make_float4(o[i], o[i + 1], o[i + 2], o[i + 3]);
+      __syncwarp();
+      const int cc = cc0 + (c0 >> 1) + (lane & 7);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int rr = 4 * i + (lane >> 3);
+        const int row = row0 + 32 * q + rr;
+        if (row < J.rows && cc < J.Nc)
+          J.D[(size_t)row * J.ldd + cc] = *reinterpret_cast<const float2*>(W + rr * kDftEpiPitch + 2 * (lane & 7));
+      }
+      __syncwarp();
     }
   }
   tc_fence_before();
@@ -336,10 +329,27 @@ int dft_tiles(int rows, const DftShape& s) {
   return (rows + kDftRows - 1) / kDftRows * s.ntiles;
 }
 
+size_t dft_a_bytes(int rows, const DftShape& s) {
+  if (rows <= 0 || s.kchunks <= 0) return 0;
+  return (size_t)((rows + kDftRows - 1) / kDftRows) * s.kchunks * 2 * kDftStageA;
+}
+
 cudaError_t launch_ydft(const Launch<DftJob>& L, cudaStream_t st) {
   const int grid = L.tile_start[L.njobs];
   if (grid == 0) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(k_ydft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDftSmem);
+  // the split pass: one CTA per (128-row tile, K chunk) of every job
+  Launch<DftJob> Ls = L;
+  int blocks = 0;
+  for (int i = 0; i < L.njobs; ++i) {
+    Ls.tile_start[i] = blocks;
+    const int rows = L.job[i].rows;
+    blocks += rows > 0 ? (rows + kDftRows - 1) / kDftRows * L.job[i].kchunks : 0;
+  }
+  Ls.tile_start[L.njobs] = blocks;
+  if (blocks) k_dft_split<<<blocks, kDftThreads, 0, st>>>(Ls);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_ydft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDftSmem);
   if (e != cudaSuccess) return e;
   k_ydft<<<grid, kDftThreads, kDftSmem, st>>>(L);
   return cudaGetLastError();
