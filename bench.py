@@ -908,7 +908,8 @@ def run_batch(args):
     batch = []
     for i, l in zip(mine, lanes):
         m0, m1 = workloads.batch_patterns(specs[i])
-        batch.append(gpu_pair(specs[i], m0, m1, adaptive=True, rtol=1e-5, stream=streams[l]))
+        batch.append(gpu_pair(specs[i], m0, m1, adaptive=True, rtol=1e-5, stream=streams[l],
+                              precision=args.precision))
     cells = sum(specs[i].cells() for i in mine)
     # the project's autotuner: candidate radix orders per transform length,
     # timed on the pairs themselves (a length is timed once, then shared)
@@ -965,10 +966,14 @@ def run_batch(args):
         _, dts = step_batch(batch, 1, dts)
     torch.cuda.synchronize()
     bytes_step = 0.0
+    flops_step = 0.0  # reduced precision: split-product flops of the tensor-core DFTs
     for i, mm in zip(mine, batch):
         ab = algorithmic_bytes(mm, specs[i])
         for c, b in ab.items():
             bytes_step += b * mm.timing(c)[1] / k_t
+        if args.precision == "mixed":
+            for c, f in dft_flops(mm, specs[i]).items():
+                flops_step += f * mm.timing(c)[1] / k_t
         mm.set_timing(False)
     ms = max_over_ranks(ms, world, "cuda")
     total_cells = sum(fp.cells() for fp in specs)  # every rank's pairs together
@@ -1002,6 +1007,13 @@ def run_batch(args):
             "frac": round(achieved / peak, 4), "algorithmic_bytes_per_step": int(bytes_step),
             "traffic": None,
             "traffic_source": "not captured: a batched step is thousands of concurrent launches"}
+    if args.precision == "mixed":
+        tpk, tsrc = measured_tensor_peak()
+        rate = flops_step / (ms / args.steps / 1e3) / 1e12
+        roof["tensor"] = {"what": "split-product flops of the tensor-core y DFTs of all pairs per batched step "
+                                  "/ step time", "achieved": round(rate, 1), "peak": tpk, "peak_source": tsrc,
+                          "unit": "TFLOP/s", "frac": round(rate / tpk, 4), "flops_per_step": int(flops_step)}
+        roof["algorithmic_bytes_note"] = "FP32 classes only (the tensor-core DFT and split passes not counted)"
     cpu_base = None
     if pool is not None:
         try:
@@ -1016,8 +1028,11 @@ def run_batch(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "batch of 256 PMA film pairs, sizes U{64..512}xU{64..256}xU{1..4} "
+            "scaling": "strong", "vs_baseline": None,
+            "dtype": "f32" if args.precision == "fp32" else "split-bf16 tensor-core y DFTs + f32",
+            "data": "synthetic",
+            "config": {"precision": args.precision,
+                       "workload": "batch of 256 PMA film pairs, sizes U{64..512}xU{64..256}xU{1..4} "
                                    "(4 nm), slider at U[0, 50) cells, pulled at U[0.1, 10] m/s, "
                                    "adaptive DP45 per pair",
                        "pairs": len(batch), "cells": cells, "lanes": args.lanes,

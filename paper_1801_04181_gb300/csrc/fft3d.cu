@@ -253,11 +253,68 @@ static cudaError_t prep(const void* f, size_t smem) {
 // output plane.  (Staging inputs and looping over all outputs inside one
 // thread measured 1.3-2.7x slower than streaming; this layout keeps a warp
 // per output plane.)
-constexpr int kZMixThreads = 256;
+constexpr int kZMixThreads = 128;
 constexpr int kZMixChunk = 32;  // frequency pairs per CTA, one per lane
 
-__device__ __forceinline__ float2 zm_kmul(float v, bool imag, float2 m) {
-  return imag ? make_float2(-v * m.y, v * m.x) : make_float2(v * m.x, v * m.y);
+// Sums of one output plane at frequency k (acc0) and Qy - k (acc1).  Terms
+// whose kernel spectrum is real and those whose spectrum is imaginary are
+// summed apart (r*, i*) and the factor i is applied once at the end, so a
+// term is one load of the spectrum, two shared-memory loads and four FMAs;
+// every parity below is a compile-time constant of the output component A.
+struct ZAcc {
+  float2 r0, r1, i0, i1;
+  __device__ ZAcc() : r0(make_float2(0.f, 0.f)), r1(r0), i0(r0), i1(r0) {}
+  __device__ __forceinline__ void add(bool imag, float v0, float v1, float2 m0, float2 m1) {
+    float2& a0 = imag ? i0 : r0;
+    float2& a1 = imag ? i1 : r1;
+    a0.x = fmaf(v0, m0.x, a0.x); a0.y = fmaf(v0, m0.y, a0.y);
+    a1.x = fmaf(v1, m1.x, a1.x); a1.y = fmaf(v1, m1.y, a1.y);
+  }
+  __device__ __forceinline__ float2 out0() const { return make_float2(r0.x - i0.y, r0.y + i0.x); }
+  __device__ __forceinline__ float2 out1() const { return make_float2(r1.x - i1.y, r1.y + i1.x); }
+};
+
+// H_A(iz) = sum_jz sum_b Ns_Ab(iz - jz) m_b(jz): xz, yz odd in dz and
+// imaginary, xy and yz odd in y (Nq holds dz >= 0)
+template <int A>
+__device__ __forceinline__ ZAcc zmix_demag(const ZMixJob& J, int iz, const float* __restrict__ nq,
+                                           const float2* s0, const float2* s1, size_t kstride) {
+  ZAcc acc;
+  const int nz = J.nz;
+  for (int jz = 0; jz < nz; ++jz) {
+    const int adz = iz >= jz ? iz - jz : jz - iz;
+    const float sz = iz >= jz ? 1.f : -1.f;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const int comp = A == b ? A : (A + b == 1 ? 3 : (A + b == 2 ? 4 : 5));
+      const bool imag = comp >= 4;               // xz, yz
+      const bool odd_y = comp == 3 || comp == 5; // xy, yz
+      const float v = (imag ? sz : 1.f) * __ldg(nq + (size_t)(comp * nz + adz) * kstride);
+      acc.add(imag, v, odd_y ? -v : v, s0[(b * nz + jz) * kZMixChunk], s1[(b * nz + jz) * kZMixChunk]);
+    }
+  }
+  return acc;
+}
+
+// c(o) = sum_jz sum_c T_c(o, jz) m_c(jz), T_x, T_y imaginary, T_y odd in y
+// (A = 2: rows with the parities of S); field variant: H_A(o) with the rows
+// of -N, imaginary when odd in x (xz, zx) or y (yz, zy), odd in y for xy,
+// yx, yz, zy
+template <int A>
+__device__ __forceinline__ ZAcc zmix_coef(const ZMixJob& J, int oc, const float* __restrict__ tq,
+                                          const float2* s0, const float2* s1, size_t kstride) {
+  ZAcc acc;
+  const int nz = J.nz;
+  for (int jz = 0; jz < nz; ++jz) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const bool imag = (A == 2) != (c == 2);
+      const bool odd_y = (A == 1) != (c == 1);
+      const float v = __ldg(tq + (size_t)((oc * nz + jz) * 3 + c) * kstride);
+      acc.add(imag, v, odd_y ? -v : v, s0[(c * nz + jz) * kZMixChunk], s1[(c * nz + jz) * kZMixChunk]);
+    }
+  }
+  return acc;
 }
 
 __global__ void __launch_bounds__(kZMixThreads) k_zmix3(const Launch<ZMixJob> Lc) {
@@ -292,58 +349,28 @@ __global__ void __launch_bounds__(kZMixThreads) k_zmix3(const Launch<ZMixJob> Lc
   const float2* s0 = zs + l;
   const float2* s1 = zs + P3 * kZMixChunk + l;
   const int planes = J.nH + J.n_out;
+  // one output plane per warp at a time (warp-uniform branches below)
   for (int o = threadIdx.x / kZMixChunk; o < planes; o += kZMixThreads / kZMixChunk) {
-    float2 acc0 = make_float2(0.f, 0.f), acc1 = acc0;
+    ZAcc acc;
+    float2* dst;
     if (o < J.nH) {
-      // H_a(iz) = sum_jz sum_b Ns_ab(iz - jz) m_b(jz): xz, yz odd in dz and
-      // imaginary, xy and yz odd in y
       const int a = o / nz, iz = o - a * nz;
-      for (int jz = 0; jz < nz; ++jz) {
-        const int adz = iz >= jz ? iz - jz : jz - iz;
-        const float sz = iz >= jz ? 1.f : -1.f;
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-          int comp;
-          bool imag = false;
-          float sgn = 1.f, sy = 1.f;
-          if (a == b) comp = a;
-          else if (a + b == 1) { comp = 3; sy = -1.f; }
-          else if (a + b == 2) { comp = 4; sgn = sz; imag = true; }
-          else { comp = 5; sgn = sz; sy = -1.f; imag = true; }
-          const float v = sgn * __ldg(J.Nq + (size_t)(comp * nz + adz) * kstride + koff);
-          const float2 m0 = s0[(b * nz + jz) * kZMixChunk];
-          const float2 m1 = s1[(b * nz + jz) * kZMixChunk];
-          const float2 p0 = zm_kmul(v, imag, m0), p1 = zm_kmul(sy * v, imag, m1);
-          acc0.x += p0.x; acc0.y += p0.y;
-          acc1.x += p1.x; acc1.y += p1.y;
-        }
-      }
-      float2* dst = J.outH + (size_t)o * pstride + (size_t)kx * Qy;
-      dst[k] = acc0;
-      if (two) dst[Qy - k] = acc1;
+      const float* nq = J.Nq + koff;
+      if (a == 0) acc = zmix_demag<0>(J, iz, nq, s0, s1, kstride);
+      else if (a == 1) acc = zmix_demag<1>(J, iz, nq, s0, s1, kstride);
+      else acc = zmix_demag<2>(J, iz, nq, s0, s1, kstride);
+      dst = J.outH + (size_t)o * pstride + (size_t)kx * Qy;
     } else {
-      // c(o) = sum_jz sum_c T_c(o, jz) m_c(jz); T_x, T_y imaginary, T_y odd in y.
-      // Field variant: H_a(o) = sum_jz sum_c TN_ac(o, jz) m_c(jz), TN_ac from
-      // N_ac, imaginary when odd in x (xz, zx) or y (yz, zy), odd in y for xy, yx, yz, zy.
       const int oc = o - J.nH;
       const int a = J.field_nbox > 0 ? oc / J.field_nbox : 2;  // row z of N has the parities of S
-      for (int jz = 0; jz < nz; ++jz) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const float v = __ldg(J.Tq + (size_t)((oc * nz + jz) * 3 + c) * kstride + koff);
-          const float2 m0 = s0[(c * nz + jz) * kZMixChunk];
-          const float2 m1 = s1[(c * nz + jz) * kZMixChunk];
-          const bool imag = (a == 2) != (c == 2);
-          const bool odd_y = (a == 1) != (c == 1);
-          const float2 p0 = zm_kmul(v, imag, m0), p1 = zm_kmul(odd_y ? -v : v, imag, m1);
-          acc0.x += p0.x; acc0.y += p0.y;
-          acc1.x += p1.x; acc1.y += p1.y;
-        }
-      }
-      float2* dst = J.outC + (size_t)oc * pstride + (size_t)kx * Qy;
-      dst[k] = acc0;
-      if (two) dst[Qy - k] = acc1;
+      const float* tq = J.Tq + koff;
+      if (a == 0) acc = zmix_coef<0>(J, oc, tq, s0, s1, kstride);
+      else if (a == 1) acc = zmix_coef<1>(J, oc, tq, s0, s1, kstride);
+      else acc = zmix_coef<2>(J, oc, tq, s0, s1, kstride);
+      dst = J.outC + (size_t)oc * pstride + (size_t)kx * Qy;
     }
+    dst[k] = acc.out0();
+    if (two) dst[Qy - k] = acc.out1();
   }
 }
 
