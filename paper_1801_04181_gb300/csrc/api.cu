@@ -89,6 +89,9 @@ struct Dir {
   float2* Z3C = nullptr;       // thick sources: z-pass coefficient planes [r_z][kxh][Qy]
   size_t Tq_bytes = 0, YC_bytes = 0, C_bytes = 0, partial_bytes = 0, Z3C_bytes = 0;
   DftMat yiC;                  // reduced precision: inverse y DFT with the y prefilter
+  uint16_t* pkC = nullptr;     // reduced precision: z-mixed coefficient planes, split and packed
+  size_t pkC_bytes = 0;
+  long long pkC_key = -1;
 };
 
 struct Magnet {
@@ -129,6 +132,9 @@ struct Magnet {
   // reduced precision (every source through the split passes, z by the
   // direct sum): forward and demag-row inverse y DFT matrices
   DftMat yf, yiH;
+  uint16_t* pkH = nullptr;  // z-mixed demag planes, split and packed for the inverse DFT
+  size_t pkH_bytes = 0;
+  long long pkH_key = -1;
   // energy gradients (mm_backward_energy) as a source: work arrays and the S
   // spectra per z offset of the box
   float* adj_box = nullptr;
@@ -959,11 +965,27 @@ static DftJob dft_job(mm_ctx* ctx, const DftMat& M, const float2* A, int lda, in
   return J;
 }
 
+// A packed split operand of `rows` rows and Kc complex columns: allocated,
+// and zeroed whenever its layout changes (the K padding of the last chunk is
+// never written and must read as zero: the matrix is zero there, and a stale
+// NaN would not cancel)
+static mm_status ensure_packed(mm_ctx* ctx, uint16_t** p, size_t* have, long long* key, int rows, int Kc) {
+  DftShape sh = dft_shape(1, Kc);
+  const size_t bytes = dft_a_bytes(rows, sh);
+  const long long k = (long long)rows * 1000003LL + Kc;
+  if (*p && *have >= bytes && *key == k) return MM_OK;
+  CKS(ensure_buf(ctx, p, have, bytes));
+  CK(cudaMemsetAsync(*p, 0, bytes, ctx->st));
+  *key = k;
+  return MM_OK;
+}
+
 // the packed-A scratch of a launch of DFT jobs: one buffer, 16 KB-aligned per job
 static mm_status assign_dft_scratch(mm_ctx* ctx, Launch<DftJob>* L) {
   size_t total = 0;
   for (int i = 0; i < L->njobs; ++i) {
     const DftJob& J = L->job[i];
+    if (J.prepacked) continue;
     DftShape sh;
     sh.ntile = J.ntile; sh.ntiles = J.ntiles; sh.kchunks = J.kchunks;
     total += dft_a_bytes(J.rows, sh);
@@ -972,6 +994,7 @@ static mm_status assign_dft_scratch(mm_ctx* ctx, Launch<DftJob>* L) {
   size_t off = 0;
   for (int i = 0; i < L->njobs; ++i) {
     DftJob& J = L->job[i];
+    if (J.prepacked) continue;
     DftShape sh;
     sh.ntile = J.ntile; sh.ntiles = J.ntiles; sh.kchunks = J.kchunks;
     J.Apk = ctx->dft_a + off / sizeof(uint16_t);
@@ -1106,7 +1129,12 @@ mm_status run_source_passes(mm_ctx* ctx, const float* in[2], const int* which, i
           DftSpec h{};
           h.kind = kDftInverse; h.Q = S.Qy; h.Nc = S.ny; h.Kc = S.Qy;
           CKS(ensure_dft(ctx, &S.yiH, h));
+          // the mixing pass writes the split operand itself
+          CKS(ensure_packed(ctx, &S.pkH, &S.pkH_bytes, &S.pkH_key, P3 * S.kxh, S.Qy));
+          Lm.job[nm - 1].pkH = S.pkH;
           Ldi.job[ndi] = dft_job(ctx, S.yiH, S.Z3H, S.Qy, P3 * S.kxh, S.YH, S.ny);
+          Ldi.job[ndi].Apk = S.pkH;
+          Ldi.job[ndi].prepacked = 1;
           Ldi.tile_start[ndi] = tdi;
           tdi += dft_tiles(P3 * S.kxh, S.yiH.shape);
           ++ndi;
@@ -1118,7 +1146,11 @@ mm_status run_source_passes(mm_ctx* ctx, const float* in[2], const int* which, i
           c.periodic = periodic_axis(ctx, 1) ? 1 : 0;
           c.fir = D->prefilter;
           CKS(ensure_dft(ctx, &D->yiC, c));
+          CKS(ensure_packed(ctx, &D->pkC, &D->pkC_bytes, &D->pkC_key, D->r[2] * S.kxh, S.Qy));
+          Lm.job[nm - 1].pkC = D->pkC;
           Ldi.job[ndi] = dft_job(ctx, D->yiC, D->Z3C, S.Qy, D->r[2] * S.kxh, D->YC, D->r[1]);
+          Ldi.job[ndi].Apk = D->pkC;
+          Ldi.job[ndi].prepacked = 1;
           Ldi.tile_start[ndi] = tdi;
           tdi += dft_tiles(D->r[2] * S.kxh, D->yiC.shape);
           ++ndi;
@@ -1637,7 +1669,7 @@ static void free_dft(DftMat& M) {
 }
 
 static void free_dir(Dir& D) {
-  cudaFree(D.Tq); cudaFree(D.YC); cudaFree(D.C); cudaFree(D.partial); cudaFree(D.Z3C);
+  cudaFree(D.Tq); cudaFree(D.YC); cudaFree(D.C); cudaFree(D.partial); cudaFree(D.Z3C); cudaFree(D.pkC);
   free_dft(D.yiC);
   D = Dir();
 }
@@ -1655,7 +1687,7 @@ void mm_destroy(mm_ctx* ctx) {
     cudaFree(M.pow_H); cudaFree(M.pow_part);
     cudaFree(M.X1); cudaFree(M.YH); cudaFree(M.Nq);
     cudaFree(M.N3); cudaFree(M.S3); cudaFree(M.Y3); cudaFree(M.Z3H);
-    free_dft(M.yf); free_dft(M.yiH);
+    free_dft(M.yf); free_dft(M.yiH); cudaFree(M.pkH);
     cudaFree(M.adj_box); cudaFree(M.adj_grid); cudaFree(M.adj_X); cudaFree(M.adj_Y); cudaFree(M.adj_Z);
     cudaFree(M.adj_YH); cudaFree(M.adj_Sq);
     free_dir(M.dir);

@@ -27,6 +27,7 @@
 #include "fft.cuh"
 #include "mm_internal.h"
 #include "prefilter.cuh"
+#include "umma.cuh"
 
 namespace mm {
 
@@ -353,6 +354,8 @@ __global__ void __launch_bounds__(kZMixThreads) k_zmix3(const Launch<ZMixJob> Lc
   for (int o = threadIdx.x / kZMixChunk; o < planes; o += kZMixThreads / kZMixChunk) {
     ZAcc acc;
     float2* dst;
+    uint16_t* pk;
+    int prow;  // row (plane, kx) of the packed output
     if (o < J.nH) {
       const int a = o / nz, iz = o - a * nz;
       const float* nq = J.Nq + koff;
@@ -360,6 +363,8 @@ __global__ void __launch_bounds__(kZMixThreads) k_zmix3(const Launch<ZMixJob> Lc
       else if (a == 1) acc = zmix_demag<1>(J, iz, nq, s0, s1, kstride);
       else acc = zmix_demag<2>(J, iz, nq, s0, s1, kstride);
       dst = J.outH + (size_t)o * pstride + (size_t)kx * Qy;
+      pk = J.pkH;
+      prow = o * J.kxh + kx;
     } else {
       const int oc = o - J.nH;
       const int a = J.field_nbox > 0 ? oc / J.field_nbox : 2;  // row z of N has the parities of S
@@ -368,9 +373,17 @@ __global__ void __launch_bounds__(kZMixThreads) k_zmix3(const Launch<ZMixJob> Lc
       else if (a == 1) acc = zmix_coef<1>(J, oc, tq, s0, s1, kstride);
       else acc = zmix_coef<2>(J, oc, tq, s0, s1, kstride);
       dst = J.outC + (size_t)oc * pstride + (size_t)kx * Qy;
+      pk = J.pkC;
+      prow = oc * J.kxh + kx;
     }
-    dst[k] = acc.out0();
-    if (two) dst[Qy - k] = acc.out1();
+    if (pk) {  // reduced precision: straight into the inverse DFT's split operand
+      const int kch = (Qy + (int)(kKChunk / 2) - 1) / (int)(kKChunk / 2);
+      store_split(pk, kch, prow, k, acc.out0());
+      if (two) store_split(pk, kch, prow, Qy - k, acc.out1());
+    } else {
+      dst[k] = acc.out0();
+      if (two) dst[Qy - k] = acc.out1();
+    }
   }
 }
 

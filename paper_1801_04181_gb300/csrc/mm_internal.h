@@ -141,6 +141,10 @@ struct ZMixJob {
   // n_out = 3 field_nbox planes are H_a of box plane o at a field_nbox + o,
   // with Tq the W-folded rows of -N (build_TN_spectra)
   int field_nbox;
+  // reduced precision: outputs written split into BF16 hi | lo blocks for the
+  // inverse DFT (rows (plane, kx), ceil(Qy / 16) K chunks) instead of outH / outC
+  uint16_t* pkH;
+  uint16_t* pkC;
 };
 constexpr int kMaxNzDirect = 8;
 
@@ -167,6 +171,7 @@ struct DftJob {
   const float2* A;                // [rows][lda], the first Kc of a row used
   int lda, rows, Kc;
   uint16_t* Apk;                  // A split into BF16 hi | lo, packed per (128-row tile, K chunk)
+  int prepacked;                  // Apk written by the producing pass (no split pass)
   const uint16_t* Bhi;
   const uint16_t* Blo;
   int ntile, ntiles, kchunks, Nc;

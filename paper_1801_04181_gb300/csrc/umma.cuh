@@ -11,6 +11,7 @@
 // between row groups (512).  (Measured on GB300: back-to-back MMAs on this
 // layout run at the tensor core's full rate, as with the 128-byte swizzle.)
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -28,6 +29,26 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
 __device__ __forceinline__ uint32_t tile_offset(int row, int k) {
   return (uint32_t)(row >> 3) * kRowGroupBytes + (uint32_t)(k >> 3) * kCoreBytes + (uint32_t)(row & 7) * 16u +
          (uint32_t)(k & 7) * 2u;
+}
+
+// Packed split operand: rows of complex values stored as BF16 hi | lo blocks,
+// one block per (128-row tile, K chunk of 16 complex): the hi tile (8 KB, the
+// layout above) followed by the lo tile, so a stage loads it by one bulk copy.
+constexpr int kTileRows = 128;
+constexpr uint32_t kTileSplitBytes = kTileRows * kKChunk * 2;  // one split of one block
+
+// v = (re, im) of row `row`, complex column `kc`, into the packed operand
+// with `kchunks` K chunks per 128-row tile: hi = BF16(v), lo = BF16(v - hi)
+__device__ __forceinline__ void store_split(void* packed, int kchunks, int row, int kc, float2 v) {
+  const int cpx = (int)(kKChunk / 2);
+  uint8_t* blk = reinterpret_cast<uint8_t*>(packed) +
+                 ((size_t)(row / kTileRows) * kchunks + kc / cpx) * 2 * kTileSplitBytes;
+  const uint32_t off = tile_offset(row % kTileRows, 2 * (kc % cpx));
+  const __nv_bfloat162 h = __floats2bfloat162_rn(v.x, v.y);
+  const float2 hf = __bfloat1622float2(h);
+  const __nv_bfloat162 l = __floats2bfloat162_rn(v.x - hf.x, v.y - hf.y);
+  *reinterpret_cast<__nv_bfloat162*>(blk + off) = h;
+  *reinterpret_cast<__nv_bfloat162*>(blk + kTileSplitBytes + off) = l;
 }
 
 // shared-memory matrix descriptor: start address, leading / stride byte

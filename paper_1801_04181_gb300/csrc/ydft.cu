@@ -343,7 +343,7 @@ cudaError_t launch_ydft(const Launch<DftJob>& L, cudaStream_t st) {
   for (int i = 0; i < L.njobs; ++i) {
     Ls.tile_start[i] = blocks;
     const int rows = L.job[i].rows;
-    blocks += rows > 0 ? (rows + kDftRows - 1) / kDftRows * L.job[i].kchunks : 0;
+    if (!L.job[i].prepacked) blocks += rows > 0 ? (rows + kDftRows - 1) / kDftRows * L.job[i].kchunks : 0;
   }
   Ls.tile_start[L.njobs] = blocks;
   if (blocks) k_dft_split<<<blocks, kDftThreads, 0, st>>>(Ls);
