@@ -132,6 +132,9 @@ struct Magnet {
   // reduced precision (every source through the split passes, z by the
   // direct sum): forward and demag-row inverse y DFT matrices
   DftMat yf, yiH;
+  uint16_t* pkX = nullptr;  // x-transformed rows, split and packed for the forward DFT
+  size_t pkX_bytes = 0;
+  long long pkX_key = -1;
   uint16_t* pkH = nullptr;  // z-mixed demag planes, split and packed for the inverse DFT
   size_t pkH_bytes = 0;
   long long pkH_key = -1;
@@ -1010,6 +1013,12 @@ mm_status run_source_passes(mm_ctx* ctx, const float* in[2], const int* which, i
   int Qmax = 0;
   {
     Launch<XFwdJob> L = xfwd_launch(ctx, in, which, n, &Qmax);
+    if (ctx->opt.precision == MM_MIXED)  // the forward y DFT's split operand, written by this pass
+      for (int i = 0; i < n; ++i) {
+        Magnet& S = ctx->mag[which[i]];
+        CKS(ensure_packed(ctx, &S.pkX, &S.pkX_bytes, &S.pkX_key, 3 * S.nz * S.kxh, S.ny));
+        L.job[i].pk = S.pkX;
+      }
     Timer t(ctx, 0);
     CK(launch_xfwd(L, Qmax, st));
   }
@@ -1083,6 +1092,8 @@ mm_status run_source_passes(mm_ctx* ctx, const float* in[2], const int* which, i
         f.kind = kDftForward; f.Q = S.Qy; f.Nc = S.Qy; f.Kc = S.ny;
         CKS(ensure_dft(ctx, &S.yf, f));
         Ldf.job[ndf] = dft_job(ctx, S.yf, S.X1, S.ny, P3 * S.kxh, S.Y3, S.Qy);
+        Ldf.job[ndf].Apk = S.pkX;  // written by the x-forward pass
+        Ldf.job[ndf].prepacked = 1;
         Ldf.tile_start[ndf] = tdf;
         tdf += dft_tiles(P3 * S.kxh, S.yf.shape);
         ++ndf;
@@ -1687,7 +1698,7 @@ void mm_destroy(mm_ctx* ctx) {
     cudaFree(M.pow_H); cudaFree(M.pow_part);
     cudaFree(M.X1); cudaFree(M.YH); cudaFree(M.Nq);
     cudaFree(M.N3); cudaFree(M.S3); cudaFree(M.Y3); cudaFree(M.Z3H);
-    free_dft(M.yf); free_dft(M.yiH); cudaFree(M.pkH);
+    free_dft(M.yf); free_dft(M.yiH); cudaFree(M.pkH); cudaFree(M.pkX);
     cudaFree(M.adj_box); cudaFree(M.adj_grid); cudaFree(M.adj_X); cudaFree(M.adj_Y); cudaFree(M.adj_Z);
     cudaFree(M.adj_YH); cudaFree(M.adj_Sq);
     free_dir(M.dir);

@@ -18,6 +18,7 @@
 #include "fft.cuh"
 #include "mm_internal.h"
 #include "prefilter.cuh"
+#include "umma.cuh"
 
 namespace mm {
 
@@ -95,12 +96,18 @@ __global__ void __launch_bounds__(256, 3) k_xfwd(const Launch<XFwdJob> Lc) {
     while (ya >= ny) { ++pa; ya -= ny; }
     float2* dst0 = J.out + (size_t)pa * J.kxh * ny + ya;
     const float2* line = sm + l * ldl;
+    const int kch = (ny + (int)(kKChunk / 2) - 1) / (int)(kKChunk / 2);
     for (int kx = threadIdx.x / kLines; kx < J.kxh; kx += blockDim.x / kLines) {
       const ushort2 pp = ptab[kx];
       const float2 Zk = line[pp.x];
       const float2 Zm = line[pp.y];
-      *reinterpret_cast<float4*>(dst0 + (size_t)kx * ny) =
-          make_float4(0.5f * (Zk.x + Zm.x), 0.5f * (Zk.y - Zm.y), 0.5f * (Zk.y + Zm.y), -0.5f * (Zk.x - Zm.x));
+      if (J.pk) {  // reduced precision: straight into the forward DFT's split operand
+        store_split(J.pk, kch, pa * J.kxh + kx, ya, make_float2(0.5f * (Zk.x + Zm.x), 0.5f * (Zk.y - Zm.y)));
+        store_split(J.pk, kch, pa * J.kxh + kx, ya + 1, make_float2(0.5f * (Zk.y + Zm.y), -0.5f * (Zk.x - Zm.x)));
+      } else {
+        *reinterpret_cast<float4*>(dst0 + (size_t)kx * ny) =
+            make_float4(0.5f * (Zk.x + Zm.x), 0.5f * (Zk.y - Zm.y), 0.5f * (Zk.y + Zm.y), -0.5f * (Zk.x - Zm.x));
+      }
     }
     return;
   }
@@ -115,6 +122,16 @@ __global__ void __launch_bounds__(256, 3) k_xfwd(const Launch<XFwdJob> Lc) {
     const float2 B = make_float2(0.5f * (Zk.y + Zm.y), -0.5f * (Zk.x - Zm.x));
     int pa = pa0, ya = r0 + 2 * l - pa0 * ny;
     while (ya >= ny) { ++pa; ya -= ny; }
+    if (J.pk) {
+      const int kch = (ny + (int)(kKChunk / 2) - 1) / (int)(kKChunk / 2);
+      store_split(J.pk, kch, pa * J.kxh + kx, ya, A);
+      if (2 * l + 1 < nrows) {
+        int pb = pa, yb = ya + 1;
+        if (yb >= ny) { ++pb; yb -= ny; }
+        store_split(J.pk, kch, pb * J.kxh + kx, yb, B);
+      }
+      continue;
+    }
     float2* dst = J.out + ((size_t)pa * J.kxh + kx) * ny + ya;
     if (pairs) {
       *reinterpret_cast<float4*>(dst) = make_float4(A.x, A.y, B.x, B.y);

@@ -53,6 +53,9 @@ struct XFwdJob {
   int nx, ny, nz;
   int kxh;
   FftTables fx;
+  // reduced precision: the rows (plane, kx) written split into BF16 hi | lo
+  // blocks for the forward y DFT (ceil(ny / 16) K chunks) instead of `out`
+  uint16_t* pk;
 };
 
 // ---------------------------------------------------------------- y pass
