@@ -211,8 +211,6 @@ struct mm_ctx {
   Readback* rb = nullptr;
   cudaEvent_t ev_done = nullptr;
   int* err_flag = nullptr;            // device
-  uint16_t* dft_a = nullptr;          // reduced precision: A of the y DFTs split into BF16 hi | lo
-  size_t dft_a_bytes = 0;
   int* tickets = nullptr;             // device: last-block counters of the gather and stage launches
   bool k1_valid = false;
   long long accepted = 0, rejected = 0;
@@ -983,29 +981,6 @@ static mm_status ensure_packed(mm_ctx* ctx, uint16_t** p, size_t* have, long lon
   return MM_OK;
 }
 
-// the packed-A scratch of a launch of DFT jobs: one buffer, 16 KB-aligned per job
-static mm_status assign_dft_scratch(mm_ctx* ctx, Launch<DftJob>* L) {
-  size_t total = 0;
-  for (int i = 0; i < L->njobs; ++i) {
-    const DftJob& J = L->job[i];
-    if (J.prepacked) continue;
-    DftShape sh;
-    sh.ntile = J.ntile; sh.ntiles = J.ntiles; sh.kchunks = J.kchunks;
-    total += dft_a_bytes(J.rows, sh);
-  }
-  CKS(ensure_buf(ctx, &ctx->dft_a, &ctx->dft_a_bytes, total));
-  size_t off = 0;
-  for (int i = 0; i < L->njobs; ++i) {
-    DftJob& J = L->job[i];
-    if (J.prepacked) continue;
-    DftShape sh;
-    sh.ntile = J.ntile; sh.ntiles = J.ntiles; sh.kchunks = J.kchunks;
-    J.Apk = ctx->dft_a + off / sizeof(uint16_t);
-    off += dft_a_bytes(J.rows, sh);
-  }
-  return MM_OK;
-}
-
 // what: bit 1 = own demag, bit 2 = coefficients of Dir (hot or aux)
 mm_status run_source_passes(mm_ctx* ctx, const float* in[2], const int* which, int n, const int* what,
                             Dir* const* dirs) {
@@ -1093,7 +1068,6 @@ mm_status run_source_passes(mm_ctx* ctx, const float* in[2], const int* which, i
         CKS(ensure_dft(ctx, &S.yf, f));
         Ldf.job[ndf] = dft_job(ctx, S.yf, S.X1, S.ny, P3 * S.kxh, S.Y3, S.Qy);
         Ldf.job[ndf].Apk = S.pkX;  // written by the x-forward pass
-        Ldf.job[ndf].prepacked = 1;
         Ldf.tile_start[ndf] = tdf;
         tdf += dft_tiles(P3 * S.kxh, S.yf.shape);
         ++ndf;
@@ -1145,7 +1119,6 @@ mm_status run_source_passes(mm_ctx* ctx, const float* in[2], const int* which, i
           Lm.job[nm - 1].pkH = S.pkH;
           Ldi.job[ndi] = dft_job(ctx, S.yiH, S.Z3H, S.Qy, P3 * S.kxh, S.YH, S.ny);
           Ldi.job[ndi].Apk = S.pkH;
-          Ldi.job[ndi].prepacked = 1;
           Ldi.tile_start[ndi] = tdi;
           tdi += dft_tiles(P3 * S.kxh, S.yiH.shape);
           ++ndi;
@@ -1161,7 +1134,6 @@ mm_status run_source_passes(mm_ctx* ctx, const float* in[2], const int* which, i
           Lm.job[nm - 1].pkC = D->pkC;
           Ldi.job[ndi] = dft_job(ctx, D->yiC, D->Z3C, S.Qy, D->r[2] * S.kxh, D->YC, D->r[1]);
           Ldi.job[ndi].Apk = D->pkC;
-          Ldi.job[ndi].prepacked = 1;
           Ldi.tile_start[ndi] = tdi;
           tdi += dft_tiles(D->r[2] * S.kxh, D->yiC.shape);
           ++ndi;
@@ -1199,10 +1171,7 @@ mm_status run_source_passes(mm_ctx* ctx, const float* in[2], const int* which, i
       Ldi.njobs = ndi; Ldi.tile_start[ndi] = tdi;
       {
         Timer t(ctx, 7);
-        if (ndf) {
-          CKS(assign_dft_scratch(ctx, &Ldf));
-          CK(launch_ydft(Ldf, st));
-        }
+        if (ndf) CK(launch_ydft(Ldf, st));
         if (nf) CK(launch_yfwd3(Lf, st));
       }
       if (nzj) {
@@ -1214,10 +1183,7 @@ mm_status run_source_passes(mm_ctx* ctx, const float* in[2], const int* which, i
         CK(launch_zmix3(Lm, st));
       }
       Timer t(ctx, 9);
-      if (ndi) {
-        CKS(assign_dft_scratch(ctx, &Ldi));
-        CK(launch_ydft(Ldi, st));
-      }
+      if (ndi) CK(launch_ydft(Ldi, st));
       if (ni) CK(launch_yinv3(Li, st));
     }
   }
@@ -1715,7 +1681,7 @@ void mm_destroy(mm_ctx* ctx) {
   }
   cudaFree(ctx->gen_work); cudaFree(ctx->gen_q); cudaFree(ctx->W_dev); cudaFree(ctx->dc_buf);
   cudaFree(ctx->fd4_C); cudaFree(ctx->fd4_V);
-  cudaFree(ctx->mech); cudaFree(ctx->err_flag); cudaFree(ctx->tickets); cudaFree(ctx->dft_a);
+  cudaFree(ctx->mech); cudaFree(ctx->err_flag); cudaFree(ctx->tickets);
   for (auto& p : ctx->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);

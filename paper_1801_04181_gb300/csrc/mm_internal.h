@@ -173,8 +173,8 @@ struct DftShape {
 struct DftJob {
   const float2* A;                // [rows][lda], the first Kc of a row used
   int lda, rows, Kc;
-  uint16_t* Apk;                  // A split into BF16 hi | lo, packed per (128-row tile, K chunk)
-  int prepacked;                  // Apk written by the producing pass (no split pass)
+  uint16_t* Apk;                  // A split into BF16 hi | lo, packed per (128-row tile, K chunk),
+                                  // written by the pass that produces A (store_split)
   const uint16_t* Bhi;
   const uint16_t* Blo;
   int ntile, ntiles, kchunks, Nc;
@@ -336,7 +336,7 @@ cudaError_t launch_zmix3(const Launch<ZMixJob>& L, cudaStream_t st);
 DftShape dft_shape(int Nc, int Kc);
 size_t dft_matrix_elems(const DftShape& s);
 int dft_tiles(int rows, const DftShape& s);
-size_t dft_a_bytes(int rows, const DftShape& s);  // packed A of a job
+size_t dft_a_bytes(int rows, const DftShape& s);  // a packed split operand
 cudaError_t launch_dft_pack(const DftSpec& P, const DftShape& s, uint16_t* hi, uint16_t* lo, cudaStream_t st);
 cudaError_t launch_ydft(const Launch<DftJob>& L, cudaStream_t st);
 cudaError_t launch_adj_scatter(const AdjScatterJob& J, cudaStream_t st);

@@ -30,7 +30,7 @@ constexpr int kDftThreads = 256;
 constexpr int kDftRows = 128;     // MMA M: rows per CTA
 constexpr int kDftMaxN = 256;     // MMA N: real columns per CTA (TMEM columns)
 constexpr int kDftStages = 2;     // K chunks in flight per CTA (two CTAs share an SM)
-constexpr uint32_t kDftStageA = kDftRows * kKChunk * 2;  // one split of A, bytes
+constexpr uint32_t kDftStageA = kTileSplitBytes;          // one split of A, bytes
 constexpr uint32_t kDftStageB = kDftMaxN * kKChunk * 2;  // one split of B, bytes
 constexpr uint32_t kDftStageBytes = 2 * kDftStageA + 2 * kDftStageB;
 constexpr size_t kDftSmem = (size_t)kDftStages * kDftStageBytes + 128;  // + barriers, TMEM slot
@@ -38,56 +38,9 @@ constexpr size_t kDftSmem = (size_t)kDftStages * kDftStageBytes + 128;  // + bar
 // never takes this long unless something is wrong
 constexpr long long kDftSpinCycles = 2000000000LL;
 constexpr int kDftErrBit = 2;
-// A values (complex) per thread and chunk in the split pass
-constexpr int kDftAPer = kDftRows * (int)(kKChunk / 2) / kDftThreads;
 // per-warp epilogue staging: 32 rows x 16 floats, row pitch 20 (the float4
 // stores of 8 lanes fall in distinct banks)
 constexpr int kDftEpiPitch = 20;
-
-__device__ __forceinline__ uint32_t bf16x2_bits(float a, float b) {
-  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-  return *reinterpret_cast<const uint32_t*>(&h);
-}
-
-// A chunk of 128 rows x 16 complex: warp-item w (0 .. 63) covers 8 rows x 4
-// complex, so the loads are 32-byte runs of 8 rows and the 4-byte stores of a
-// warp fill one 128-byte core matrix
-__device__ __forceinline__ void a_item(int it, int lane, int* r, int* kc) {
-  const int w = (int)(threadIdx.x >> 5) + it * (kDftThreads / 32);
-  *r = (w >> 2) * 8 + (lane & 7);
-  *kc = (w & 3) * 4 + (lane >> 3);
-}
-
-// Split pass: A (FP32 complex rows) -> BF16 hi | lo blocks in the tensor
-// core's layout, one 16 KB block per (128-row tile, K chunk), so the product
-// kernel moves them by bulk copy and every N tile reuses one split.  One CTA
-// per block.
-__global__ void __launch_bounds__(kDftThreads) k_dft_split(const Launch<DftJob> Lc) {
-  const int j = find_job(Lc.tile_start, Lc.njobs, blockIdx.x);
-  const DftJob& J = Lc.job[j];
-  const int b = blockIdx.x - Lc.tile_start[j];
-  const int mt = b / J.kchunks, c = b - mt * J.kchunks;
-  const int lane = threadIdx.x & 31;
-  uint8_t* dst = reinterpret_cast<uint8_t*>(J.Apk) + (size_t)b * 2 * kDftStageA;
-  float2 v[kDftAPer];
-#pragma unroll
-  for (int it = 0; it < kDftAPer; ++it) {
-    int r, kc;
-    a_item(it, lane, &r, &kc);
-    const int row = mt * kDftRows + r, k = c * (int)(kKChunk / 2) + kc;
-    v[it] = (row < J.rows && k < J.Kc) ? __ldg(J.A + (size_t)row * J.lda + k) : make_float2(0.f, 0.f);
-  }
-#pragma unroll
-  for (int it = 0; it < kDftAPer; ++it) {
-    int r, kc;
-    a_item(it, lane, &r, &kc);
-    const float hx = __bfloat162float(__float2bfloat16_rn(v[it].x));
-    const float hy = __bfloat162float(__float2bfloat16_rn(v[it].y));
-    const uint32_t off = tile_offset(r, 2 * kc);
-    *reinterpret_cast<uint32_t*>(dst + off) = bf16x2_bits(hx, hy);
-    *reinterpret_cast<uint32_t*>(dst + kDftStageA + off) = bf16x2_bits(v[it].x - hx, v[it].y - hy);
-  }
-}
 
 // Product pass.  Thread 0 alone runs the main loop: bulk copies of the A and
 // B blocks of each K chunk into a stage (completing on full[s]), the MMAs of
@@ -337,19 +290,7 @@ size_t dft_a_bytes(int rows, const DftShape& s) {
 cudaError_t launch_ydft(const Launch<DftJob>& L, cudaStream_t st) {
   const int grid = L.tile_start[L.njobs];
   if (grid == 0) return cudaSuccess;
-  // the split pass: one CTA per (128-row tile, K chunk) of every job
-  Launch<DftJob> Ls = L;
-  int blocks = 0;
-  for (int i = 0; i < L.njobs; ++i) {
-    Ls.tile_start[i] = blocks;
-    const int rows = L.job[i].rows;
-    if (!L.job[i].prepacked) blocks += rows > 0 ? (rows + kDftRows - 1) / kDftRows * L.job[i].kchunks : 0;
-  }
-  Ls.tile_start[L.njobs] = blocks;
-  if (blocks) k_dft_split<<<blocks, kDftThreads, 0, st>>>(Ls);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_ydft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDftSmem);
+  cudaError_t e = cudaFuncSetAttribute(k_ydft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDftSmem);
   if (e != cudaSuccess) return e;
   k_ydft<<<grid, kDftThreads, kDftSmem, st>>>(L);
   return cudaGetLastError();
