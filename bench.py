@@ -183,9 +183,9 @@ def algorithmic_bytes(mm, fp):
     return {0: xf, 1: yp, 2: xi, 3: ga, 4: st}
 
 
-KERNEL_OF_CLASS = {0: ("k_xfwd", ["fft_passes.cu", "fft.cuh", "prefilter.cuh", "mm_internal.h"]),
-                   1: ("k_ypass", ["fft_passes.cu", "fft.cuh", "prefilter.cuh", "mm_internal.h"]),
-                   2: ("k_xinv", ["fft_passes.cu", "fft.cuh", "prefilter.cuh", "mm_internal.h"]),
+KERNEL_OF_CLASS = {0: ("k_xfwd", ["fft_passes.cu", "fft.cuh", "prefilter.cuh", "umma.cuh", "mm_internal.h"]),
+                   1: ("k_ypass", ["fft_passes.cu", "fft.cuh", "prefilter.cuh", "umma.cuh", "mm_internal.h"]),
+                   2: ("k_xinv", ["fft_passes.cu", "fft.cuh", "prefilter.cuh", "umma.cuh", "mm_internal.h"]),
                    3: ("k_gather", ["gather.cu", "dfloat.cuh", "spline_w.cuh", "mm_internal.h"]),
                    4: ("k_stage", ["llg.cu", "mm_internal.h"])}
 
@@ -546,7 +546,16 @@ def run_gpu(args):
                 "frac": round(fl[dom] / avg_s / 1e12 / tpk, 4), "flops_per_launch": int(fl[dom]),
                 "avg_launch_ms": round(avg_s * 1e3, 5), "traffic": None}
     names = MIXED_CLASSES if args.precision == "mixed" else dict(enumerate(TIMING_CLASSES))
-    ktab = {names[c]: {"ms": round(kt[c][0], 3), "launches": kt[c][1]} for c in kt if kt[c][1]}
+    ktab = {}
+    for c in kt:
+        if not kt[c][1]:
+            continue
+        e = {"ms": round(kt[c][0], 3), "launches": kt[c][1]}
+        if c in ab:  # the FP32 classes with a byte model: per-launch HBM roofline
+            avg = kt[c][0] / kt[c][1] / 1e3
+            e.update({"algorithmic_bytes_per_launch": int(ab[c]), "achieved_GBs": round(ab[c] / avg / 1e9, 1),
+                      "frac": round(ab[c] / avg / 1e9 / peak, 4)})
+        ktab[names[c]] = e
     fft_cmp = cufft_compare(mm, fp, kt) if args.workload == "stick_slip" and args.precision == "fp32" else None
     mixed = None
     if want_mixed:
