@@ -227,3 +227,128 @@ def test_mixed_full_size_films_512x512x8(pool):
     fp, m0, m1 = workloads.film_pair_plain((512, 512, 8), 1, 3)
     fp.u0 = (0.3, 0.2, 0.0)
     _full_check(fp, m0, m1, pool)
+
+
+@pytest.mark.parametrize("n0,n1,gap,u,lateral", [
+    ((21, 13, 1), (19, 17, 3), 2, (0.45, 0.3, 0.0), (1, -1)),   # odd extents: unpaired x-forward rows
+    ((16, 1, 1), (16, 1, 1), 1, (0.7, 0.0, 0.0), (0, 0)),       # one y row: one K chunk, mostly padding
+    ((20, 14, 8), (18, 12, 2), 2, (0.35, 0.2, 0.0), (0, 0)),    # 8 layers: the thickest source offered
+])
+def test_mixed_ragged_geometries_match_oracle(n0, n1, gap, u, lateral):
+    fp, m0, m1 = _pair(n0, n1, gap, 23, u, lateral=lateral)
+    mm = _mixed(fp, m0, m1)
+    offs = fp.offsets
+    for src in (0, 1):
+        t = 1 - src
+        Hg = mm.compute_stray_field(src).double().cpu().numpy()
+        F, _ = mm.get_force(t)
+        Ms = fp.mat_base.Ms if src == 0 else fp.mat_slider.Ms
+        M_s = Ms * (m0 if src == 0 else m1)
+        M_t = (fp.mat_slider.Ms if t == 1 else fp.mat_base.Ms) * (m1 if t == 1 else m0)
+        ref = stray_interaction(M_s, M_t, fp.cell, offs[src], offs[t], u, t == 1, return_box=True)
+        assert rel_l2(Hg, ref["H"]) < TOL
+        scale = force_scale(ref["hess_n"], M_t, fp.cell)
+        assert np.max(np.abs(np.array(F) - ref["F"])) < TOL * scale
+        Hd = mm.compute_demag(src).double().cpu().numpy()
+        assert rel_l2(Hd, OF.demag_conv(M_s, fp.cell)) < TOL
+    mm.close()
+
+
+def test_mixed_batch_equals_pairs_stepped_alone():
+    """Pairs of uneven sizes stepped together in reduced precision on two lane
+    streams take, bit for bit, the steps they take alone."""
+    import torch
+
+    from paper_1801_04181_gb300 import assign_lanes, step_batch
+
+    pairs = []
+    for n, u, v, seed in [((40, 24, 1), (0.25, 0.0, 0.0), 3.0, 11), ((33, 20, 2), (7.6, 0.0, 0.0), 0.4, 12),
+                          ((48, 16, 3), (1.9, 0.0, 0.0), 9.0, 13)]:
+        fp, m0, m1 = workloads.film_pair_stick_slip(n=n, gap=5, seed=seed)
+        fp.u0, fp.mech.v_drive, fp.mech.x0_spring = u, v, 1e-9
+        pairs.append((fp, m0, m1))
+    lanes = assign_lanes([fp.cells() for fp, _, _ in pairs], 2)
+    streams = [torch.cuda.Stream() for _ in range(max(lanes) + 1)]
+    batch = [gpu_pair(fp, m0, m1, adaptive=True, rtol=1e-5, stream=streams[l], precision="mixed")
+             for (fp, m0, m1), l in zip(pairs, lanes)]
+    step_batch(batch, 3, [1e-14] * len(batch))
+    torch.cuda.synchronize()
+    got = [([mm.get_magnetization(g).cpu().numpy() for g in (0, 1)], mm.get_slider_state()) for mm in batch]
+    for mm in batch:
+        mm.close()
+    for (fp, m0, m1), (m_b, s_b) in zip(pairs, got):
+        mm = _mixed(fp, m0, m1, adaptive=True, mech=True)
+        mm.step(3, 1e-14)
+        for g in (0, 1):
+            assert np.array_equal(mm.get_magnetization(g).cpu().numpy(), m_b[g])
+        assert mm.get_slider_state() == s_b
+        mm.close()
+
+
+def test_mixed_adaptive_steps_accept_and_stay_normalised():
+    fp, m0, m1 = workloads.film_pair_stick_slip(n=(48, 24, 2), gap=5, seed=9)
+    mm = _mixed(fp, m0, m1, adaptive=True, mech=True)
+    t, dt = mm.step(10, 1e-14)
+    acc, _ = mm.step_stats()
+    assert acc == 10 and t > 0 and dt > 0
+    for g in (0, 1):
+        m = mm.get_magnetization(g).double().cpu().numpy()
+        assert np.max(np.abs(np.sqrt((m ** 2).sum(axis=0)) - 1)) < 1e-6
+    mm.close()
+
+
+def test_mixed_componentwise_variant_stays_fp32():
+    """The comparison variant runs its own FP32 passes in a reduced-precision
+    context: it meets the FP32 bar (1e-5) against the oracle."""
+    from oracle.variants import stray_field_componentwise
+
+    fp, m0, m1 = _pair((20, 17, 2), (18, 15, 2), 2, 17, (0.3, 0.45, 0.0), lateral=(1, -2))
+    mm = _mixed(fp, m0, m1)
+    offs = fp.offsets
+    for src in (0, 1):
+        t = 1 - src
+        H = mm.compute_stray_field_componentwise(src).double().cpu().numpy()
+        Ms = fp.mat_base.Ms if src == 0 else fp.mat_slider.Ms
+        n_t = fp.n_slider if t == 1 else fp.n_base
+        ref = stray_field_componentwise(Ms * (m0 if src == 0 else m1), fp.cell, offs[src], offs[t], n_t,
+                                        (0.3, 0.45, 0.0), t == 1)
+        assert rel_l2(H, ref) < 1e-5
+    mm.close()
+
+
+def test_mixed_eddy_coupled_steps_match_oracle():
+    """Three coupled steps of conducting films (as the FP32 test in
+    test_gpu_eddy.py) in reduced precision: m within the 1e-4 bar while the
+    coupling moves the per-step change by ~4e-3; the next eddy field within
+    2 EPS_B |B| / |B_n - B_{n-1}| with EPS_B = 2e-5 (the reduced-precision
+    field error, ~1e-5 measured, times 2)."""
+    from oracle import dynamics as D
+    from oracle import eddy as OE
+
+    fp, _, _ = workloads.film_pair_stick_slip(n=(16, 12, 2), gap=3, seed=5)
+    m0, m1 = workloads.random_unit(fp.n_base, 5), workloads.random_unit(fp.n_slider, 6)
+    fp.mech.x0_spring = 2e-9
+    sigma, dt, n = 1e11, 2e-14, 3
+    mm = _mixed(fp, m0, m1, mech=True)
+    mm.set_conductivity(0, sigma)
+    mm.set_conductivity(1, sigma)
+    mm.step(n, dt)
+    got = [mm.get_magnetization(g).double().cpu().numpy() for g in (0, 1)]
+    He = [mm.get_eddy_field(g).double().cpu().numpy() for g in (0, 1)]
+    mm.close()
+    y0 = [m0, m1, 0.0, 0.0]
+    cs = OE.EddyCoupledSystem(oracle_system(fp), (sigma, sigma))
+    B_hist, t, y, k1 = [], 0.0, list(y0), None
+    for _ in range(n):
+        y5, _, k7 = D.dp45_step(cs, t, y, dt, k1)
+        B_hist.append([b.copy() for b in cs.last_B])
+        cs.accept(dt)
+        y = [D.normalise(y5[0]), D.normalise(y5[1]), y5[2], y5[3]]
+        t += dt
+        k1 = k7
+    for g in (0, 1):
+        assert rel_l2(got[g], y[g]) < TOL
+        assert rel_l2(got[g] - y0[g], y[g] - y0[g]) < 1e-2
+        dB = np.linalg.norm((B_hist[-1][g] - B_hist[-2][g]).ravel())
+        tol = max(TOL, 2 * 2e-5 * np.linalg.norm(B_hist[-1][g].ravel()) / dB)
+        assert rel_l2(He[g], cs.Heddy[g]) < tol
