@@ -166,7 +166,7 @@ struct DftSpec {                  // what a packed matrix holds (compared bytewi
   int periodic, fir;              // wrapped box; prefilter on (else plain node values)
 };
 struct DftShape {
-  int ntile = 0;                  // real output columns per CTA (multiple of 32, <= 256)
+  int ntile = 0;                  // real output columns per CTA (a multiple of 16, <= 160)
   int ntiles = 0;
   int kchunks = 0;                // K chunks of 64 real values
 };

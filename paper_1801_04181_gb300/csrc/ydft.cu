@@ -12,7 +12,7 @@
 //   box node start + k + d with mirror ends (or wrapped around the period).
 //
 // A row is one (plane, kx) line; the rows of a launch are independent, so one
-// CTA takes 128 rows (the MMA's M) and one tile of at most 256 real output
+// CTA takes 128 rows (the MMA's M) and one tile of at most 160 real output
 // columns (its N, FP32 accumulators in TMEM).  In real form a complex product
 // is [re im] . [[c, s], [-s, c]]; each complex matrix entry becomes four real
 // ones, so K = 2 Kc and N = 2 Nc.  The split product keeps three of the four
@@ -28,8 +28,9 @@ namespace mm {
 
 constexpr int kDftThreads = 256;
 constexpr int kDftRows = 128;     // MMA M: rows per CTA
-constexpr int kDftMaxN = 256;     // MMA N: real columns per CTA (TMEM columns)
-constexpr int kDftStages = 2;     // K chunks in flight per CTA (two CTAs share an SM)
+constexpr int kDftMaxN = 160;     // MMA N: real columns per CTA (a multiple of 16)
+constexpr uint32_t kDftTmemCols = 256;  // TMEM allocation: the power of two >= kDftMaxN
+constexpr int kDftStages = 3;     // K chunks in flight per CTA (two CTAs share an SM)
 constexpr uint32_t kDftStageA = kTileSplitBytes;          // one split of A, bytes
 constexpr uint32_t kDftStageB = kDftMaxN * kKChunk * 2;  // one split of B, bytes
 constexpr uint32_t kDftStageBytes = 2 * kDftStageA + 2 * kDftStageB;
@@ -62,7 +63,7 @@ __global__ void __launch_bounds__(kDftThreads, 2) k_ydft(const Launch<DftJob> Lc
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (warp == 0) {
-    tmem_alloc(slot, kDftMaxN);
+    tmem_alloc(slot, kDftTmemCols);
     tmem_relinquish();
   }
   if (threadIdx.x == 0) {
@@ -174,7 +175,7 @@ __global__ void __launch_bounds__(kDftThreads, 2) k_ydft(const Launch<DftJob> Lc
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, kDftMaxN);
+  if (warp == 0) tmem_dealloc(tmem, kDftTmemCols);
 }
 
 // ------------------------------------------------------------------ matrices
@@ -262,7 +263,7 @@ DftShape dft_shape(int Nc, int Kc) {
   const int nreal = 2 * Nc;
   s.ntiles = (nreal + kDftMaxN - 1) / kDftMaxN;
   const int per = (nreal + s.ntiles - 1) / s.ntiles;
-  s.ntile = (per + 31) / 32 * 32;
+  s.ntile = (per + 15) / 16 * 16;
   s.kchunks = (2 * Kc + (int)kKChunk - 1) / (int)kKChunk;
   return s;
 }
