@@ -17,6 +17,14 @@ flux density in the magnet's cells,
          H_eddy(r_i) = sum_j J(r_j) x S(r_i - r_j)
      (Biot-Savart: (1/4 pi) integral of J x (r - r')/|r - r'|^3).
 
+current_field_on_other evaluates the field of one magnet's currents inside
+the other magnet.  Sec. II says the eddy field, not being the gradient of a
+potential, is interpolated as field vectors inside the moving magnet (as a
+non-uniform external field is); the reading: step 4's sum at the nodes of
+the potential box around the other magnet (Sec. III.A's box), each component
+prefiltered and evaluated by the cubic B-spline at the displaced cell
+centres, as the stray field's potential is.
+
 EddyCoupledSystem / run_fixed_eddy put H_eddy into the effective field of
 the time step (the coupling, a reading stated there).
 
@@ -149,6 +157,29 @@ def eddy_field(dBdt, cell, sigma, S=None, return_all=False):
     return H
 
 
+def current_field_on_other(J, cell, o_s, o_t, n_t, u, target_is_slider, kernel=None):
+    """The field (A/m) of currents J (A/m^2, (3, nz, ny, nx)) of one magnet
+    inside the other, at its displaced cell centres (3, nz_t, ny_t, nx_t).
+
+    On the nodes n of the box around the target, (J x S)_a(n) = sum_j
+    S(n - r_j) . R_a J(r_j) with R_x J = (0, -J_z, J_y), R_y J = (J_z, 0,
+    -J_x), R_z J = (-J_y, J_x, 0), i.e. the potential sum of Sec. III.A with
+    the rearranged vector as the source; each component is then interpolated
+    by the cubic B-spline (mirror ends) at the displaced centres.  `kernel`:
+    the S window of the box (fields.potential_kernel_window), else computed."""
+    from .fields import box_for_target, potential_conv, target_positions
+    from .spline import evaluate, prefilter_3d
+    z = np.zeros_like(J[0])
+    R = (np.stack([z, -J[2], J[1]]), np.stack([J[2], z, -J[0]]), np.stack([-J[1], J[0], z]))
+    box_lo, box_dims = box_for_target(n_t, o_t, o_s, u, target_is_slider)
+    pos = target_positions(n_t, o_t, o_s, u, target_is_slider) - np.asarray(box_lo, float)
+    out = []
+    for a in range(3):
+        node = potential_conv(R[a], cell, box_lo, box_dims, kernel=kernel)
+        out.append(evaluate(prefilter_3d(node), pos)[0])
+    return np.stack(out)
+
+
 class EddyCoupledSystem:
     """dynamics.System with the eddy fields of conducting magnets in H_eff.
 
@@ -159,6 +190,10 @@ class EddyCoupledSystem:
     is taken from the step's last field evaluation (the first-same-as-last
     stage at the 5th-order solution y5), dB/dt = (B_n - B_{n-1}) / dt_n, and
     H_eddy(dB/dt) of steps 1-4 is added to H_eff in every stage of step n + 1.
+    The currents of a conducting magnet also act on the other magnet: their
+    field there (current_field_on_other, at the displacement of the same
+    last evaluation) is added to the other magnet's H_eff in the same way,
+    whether or not that magnet conducts.
     No eddy field before the first step, nor before a second B exists.
     sigma: conductivity of each magnet (S/m, 0 = insulating)."""
 
@@ -168,6 +203,7 @@ class EddyCoupledSystem:
         self.Heddy = [None, None]
         self.B_prev = [None, None]
         self.last_B = None
+        self.last_u = None
         self.S = {}
 
     def fields(self, m0, m1, x):
@@ -175,6 +211,7 @@ class EddyCoupledSystem:
         from .interaction import stray_interaction
         s = self.sys
         u = s.displacement(x)
+        self.last_u = u
         M0, M1 = s.mat[0]["Ms"] * m0, s.mat[1]["Ms"] * m1
         on1 = stray_interaction(M0, M1, s.cell, s.offsets[0], s.offsets[1], u, True, kernel_cache=s.cache)
         on0 = stray_interaction(M1, M0, s.cell, s.offsets[1], s.offsets[0], u, False, kernel_cache=s.cache)
@@ -202,15 +239,35 @@ class EddyCoupledSystem:
         return [llg_rhs(m0, H[0], self.sys.mat[0]["alpha"]), llg_rhs(m1, H[1], self.sys.mat[1]["alpha"]), v, acc]
 
     def accept(self, dt):
-        """After an accepted step (last evaluation at y5): update the eddy fields."""
+        """After an accepted step (last evaluation at y5): update the eddy fields,
+        each magnet's own and those of the other magnet's currents."""
+        s = self.sys
+        own, J = [None, None], [None, None]
         for g in (0, 1):
             B = self.last_B[g]
             if self.sigma[g] > 0.0 and self.B_prev[g] is not None:
                 _, nz, ny, nx = B.shape
                 if g not in self.S:
-                    self.S[g] = self_S_window((nx, ny, nz), self.sys.cell)
-                self.Heddy[g] = eddy_field((B - self.B_prev[g]) / dt, self.sys.cell, self.sigma[g], S=self.S[g])
+                    self.S[g] = self_S_window((nx, ny, nz), s.cell)
+                r = eddy_field((B - self.B_prev[g]) / dt, s.cell, self.sigma[g], S=self.S[g], return_all=True)
+                own[g], J[g] = r["H"], r["J"]
             self.B_prev[g] = B
+        if J[0] is None and J[1] is None:
+            return
+        for t in (0, 1):
+            H = own[t]
+            g = 1 - t
+            if J[g] is not None:
+                from .fields import box_for_target, potential_kernel_window
+                n_t = tuple(s.shapes[t])
+                lo, dims = box_for_target(n_t, s.offsets[t], s.offsets[g], self.last_u, t == 1)
+                key = ("X", g, tuple(lo), tuple(dims))
+                if key not in self.S:
+                    self.S[key] = potential_kernel_window(tuple(s.shapes[g]), s.cell, lo, dims)
+                cross = current_field_on_other(J[g], s.cell, s.offsets[g], s.offsets[t], n_t, self.last_u, t == 1,
+                                               kernel=self.S[key])
+                H = cross if H is None else H + cross
+            self.Heddy[t] = H
 
 
 def run_fixed_eddy(coupled, y0, dt, nsteps, t0=0.0):
