@@ -352,15 +352,34 @@ mm_status mm_eddy_field(mm_ctx* ctx, int mag, const float* dBdt_dev, double sigm
  * and the eddy field of mm_eddy_field's steps 1-4 is added to H_eff in every
  * stage of the next step.  Setting m, the displacement, the slider state, the
  * external field, a material or the checkpoint state restarts the lag (no
- * eddy field until two steps have passed).  sigma = 0 (default) turns it off.
- * Each accepted step then runs the SOR of step 2 (synchronising).  Not under
- * periodic boundaries (MM_ENOTSUP).
+ * eddy field until two steps have passed).  The currents of a conducting
+ * magnet also act on the other magnet: their field there
+ * (mm_eddy_field_on_other, at the accepted displacement) is added to that
+ * magnet's H_eff in the same way, whether or not it conducts.  sigma = 0
+ * (default) turns it off.  Each accepted step then runs the SOR of step 2
+ * (synchronising).  Not under periodic boundaries (MM_ENOTSUP).
  */
 mm_status mm_set_conductivity(mm_ctx* ctx, int mag, double sigma);
 
 /* The eddy field the next step's stages add for magnet `mag` (3 N floats,
- * A/m, device pointer); zeros while there is none. */
+ * A/m, device pointer): its own and that of the other magnet's currents;
+ * zeros while there is none. */
 mm_status mm_get_eddy_field(mm_ctx* ctx, int mag, float* H_dev);
+
+/*
+ * The field of currents J of magnet `mag` inside the other magnet, at its
+ * displaced cell centres (Sec. III.B's H_eddy = sum_j J(r_j) x S(r - r_j);
+ * Sec. II: not being the gradient of a potential, the eddy field is
+ * interpolated inside the moving magnet as field vectors).  On the nodes of
+ * the potential box around the other magnet (Sec. III.A's box, margin from
+ * mm_options) each component is a potential sum with the rearranged input
+ * (0, -J_z, J_y), (J_z, 0, -J_x), (-J_y, J_x, 0), then prefiltered and
+ * evaluated by the cubic B-spline at the displaced centres.  J_dev: 3 N
+ * floats of magnet `mag` (A/m^2, [3][nz][ny][nx]); H_dev: 3 N_t floats of
+ * the other magnet (A/m).  Device pointers, caller-owned; runs on the
+ * context's stream.  MM_ENOTSUP under periodic boundaries.
+ */
+mm_status mm_eddy_field_on_other(mm_ctx* ctx, int mag, const float* J_dev, float* H_dev);
 
 /*
  * Divergence and curl diagnostics of a field (Sec. IV.A): for H_dev (3 N

@@ -193,6 +193,15 @@ class MovingMagnets:
         """mm_set_conductivity: couple the eddy field of magnet `mag` (sigma S/m) into the step."""
         self._c(self.lib.mm_set_conductivity(self.ctx, mag, float(sigma)))
 
+    def eddy_field_on_other(self, mag, J):
+        """mm_eddy_field_on_other: the field (A/m) of currents J ((3, nz, ny, nx)
+        float32 CUDA, A/m^2) of magnet `mag` inside the other magnet."""
+        _need_cuda_f32(J, self.shapes[mag])
+        H = torch.empty(self.shapes[1 - mag], dtype=torch.float32, device="cuda")
+        self._in()
+        self._c(self.lib.mm_eddy_field_on_other(self.ctx, mag, _ptr(J), _ptr(H)))
+        return self._out(H)
+
     def get_eddy_field(self, mag):
         """mm_get_eddy_field: the eddy field the next step adds for magnet `mag`."""
         H = torch.empty(self.shapes[mag], dtype=torch.float32, device="cuda")

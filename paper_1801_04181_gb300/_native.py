@@ -71,6 +71,7 @@ SIGNATURES = [
                                 C.POINTER(C.c_int)]),
     ("mm_set_conductivity", C.c_int, [C.c_void_p, C.c_int, C.c_double]),
     ("mm_get_eddy_field", C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    ("mm_eddy_field_on_other", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     ("mm_field_div_curl", C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
                                     C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     ("mm_get_step_stats", C.c_int, [C.c_void_p, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),

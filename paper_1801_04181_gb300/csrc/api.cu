@@ -171,9 +171,16 @@ struct Magnet {
   double sigma = 0;
   float* Bprev = nullptr;
   float* Bdot = nullptr;
-  float* Heddy = nullptr;
+  float* Heddy = nullptr;      // own eddy field plus the field of the other magnet's currents
   size_t eb_bytes[3] = {};
   bool B_valid = false, Heddy_valid = false;
+  // as the source of the field of its currents inside the other magnet: the
+  // potential path over the box around the other magnet, the three
+  // rearranged-input coefficient boxes, and a scratch for the field
+  Dir eddyx;
+  float* ex_C3 = nullptr;
+  float* ex_H = nullptr;
+  size_t ex_bytes[2] = {};
 };
 
 struct TimedLaunch {
@@ -248,6 +255,7 @@ struct mm_ctx {
 // eddy-current field of one magnet (steps 1-4 of Sec. III.B), defined with mm_eddy_field
 static mm_status eddy_core(mm_ctx* ctx, int mag, const float* dBdt_dev, double sigma, float* H_dev, float* J_dev,
                            int* sweeps_out);
+static mm_status cross_eddy_field(mm_ctx* ctx, int g, const float* J, float* H);
 
 // ============================================================ helpers
 namespace {
@@ -1366,7 +1374,7 @@ StageJob stage_job(mm_ctx* ctx, int g, const float* ys, float* ys_next, int stag
   for (int i = 0; i < 7; ++i) J.k[i] = kptr[i];
   J.Hself = M.Hself;
   J.Hstray = M.Hstray;
-  J.Heddy = (M.sigma > 0.0 && M.Heddy_valid) ? M.Heddy : nullptr;
+  J.Heddy = M.Heddy_valid ? M.Heddy : nullptr;
   J.Heff = Heff;
   J.nx = M.nx; J.ny = M.ny; J.nz = M.nz;
   J.wrap[0] = periodic_axis(ctx, 0) ? 1 : 0;
@@ -1522,6 +1530,10 @@ mm_status conclude_attempt(mm_ctx* ctx, double* dt_io, double err, bool* accepte
     // conducting magnets: B of this step's last evaluation (the stage-7 fields
     // at the 5th-order solution ys[1]), its rate since the last step, and the
     // eddy field the next step's stages add to H_eff (lagged by one step)
+    // (the currents of a conducting magnet also act on the other magnet: their
+    // field there is added to that magnet's eddy field below, whether or not
+    // it conducts)
+    bool own[2] = {false, false};
     for (int g = 0; g < 2; ++g) {
       Magnet& M = ctx->mag[g];
       if (!(M.sigma > 0.0)) continue;
@@ -1531,7 +1543,8 @@ mm_status conclude_attempt(mm_ctx* ctx, double* dt_io, double err, bool* accepte
       CK(launch_flux_rate(M.Hself, M.Hstray, M.ys[1], M.N, ctx->Hext, M.Ms, dt, M.B_valid ? 1 : 0, M.Bprev, M.Bdot,
                           ctx->st));
       if (M.B_valid) {
-        CKS(eddy_core(ctx, g, M.Bdot, M.sigma, M.Heddy, nullptr, nullptr));
+        CKS(eddy_core(ctx, g, M.Bdot, M.sigma, M.Heddy, nullptr, nullptr));  // J in M.ed_J
+        own[g] = true;
         M.Heddy_valid = true;
       }
       M.B_valid = true;
@@ -1546,6 +1559,22 @@ mm_status conclude_attempt(mm_ctx* ctx, double* dt_io, double err, bool* accepte
     ctx->host_mech.kv[0] = ctx->host_mech.kv[6];
     ctx->k1_valid = true;
     ctx->accepted++;
+    // the field of each conducting magnet's currents inside the other, at the
+    // accepted displacement (that of the step's last evaluation)
+    for (int t = 0; t < 2; ++t) {
+      const int g = 1 - t;
+      if (!own[g]) continue;
+      Magnet& T = ctx->mag[t];
+      CKS(ensure_buf(ctx, &T.Heddy, &T.eb_bytes[2], sizeof(float) * 3 * T.N));
+      if (own[t]) {
+        CKS(ensure_buf(ctx, &T.ex_H, &T.ex_bytes[1], sizeof(float) * 3 * T.N));
+        CKS(cross_eddy_field(ctx, g, ctx->mag[g].ed_J, T.ex_H));
+        CK(launch_accumulate(T.ex_H, 3 * T.N, T.Heddy, ctx->st));
+      } else {
+        CKS(cross_eddy_field(ctx, g, ctx->mag[g].ed_J, T.Heddy));
+      }
+      T.Heddy_valid = true;
+    }
     // a whole-cell move beyond the guard needs new boxes (and a fresh k1)
     bool moved = false;
     for (int s = 0; s < 2 && !moved; ++s)
@@ -1672,6 +1701,8 @@ void mm_destroy(mm_ctx* ctx) {
     free_dir(M.cw);
     cudaFree(M.cw_Y);
     free_dir(M.eddy);
+    free_dir(M.eddyx);
+    cudaFree(M.ex_C3); cudaFree(M.ex_H);
     cudaFree(M.ed_V); cudaFree(M.ed_E); cudaFree(M.ed_b); cudaFree(M.ed_phi); cudaFree(M.ed_J);
     cudaFree(M.ed_part); cudaFree(M.ed_stats);
     cudaFree(M.Bprev); cudaFree(M.Bdot); cudaFree(M.Heddy);
@@ -2270,6 +2301,14 @@ mm_status mm_set_conductivity(mm_ctx* ctx, int mag, double sigma) {
   return MM_OK;
 }
 
+mm_status mm_eddy_field_on_other(mm_ctx* ctx, int mag, const float* J_dev, float* H_dev) {
+  if (!ctx || bad_mag(mag) || !J_dev || !H_dev)
+    return ctx ? fail(ctx, MM_EINVAL, "mm_eddy_field_on_other") : MM_EINVAL;
+  if (ctx->opt.periodic) return fail(ctx, MM_ENOTSUP, "mm_eddy_field_on_other: periodic boundaries");
+  CKS(prepare(ctx));
+  return cross_eddy_field(ctx, mag, J_dev, H_dev);
+}
+
 mm_status mm_get_eddy_field(mm_ctx* ctx, int mag, float* H_dev) {
   if (!ctx || bad_mag(mag) || !H_dev) return ctx ? fail(ctx, MM_EINVAL, "mm_get_eddy_field") : MM_EINVAL;
   Magnet& M = ctx->mag[mag];
@@ -2280,6 +2319,49 @@ mm_status mm_get_eddy_field(mm_ctx* ctx, int mag, float* H_dev) {
 }
 
 }  // extern "C"
+
+// The field of the currents J (A/m^2, [3][N] of magnet g) inside the other
+// magnet, at its displaced cell centres, into H ([3][N_t]).  The eddy field
+// is not the gradient of a potential, so it is interpolated inside the
+// moving magnet as field vectors (Sec. II): on the nodes of the potential box
+// around the other magnet, (J x S)_a = the potential sum with the rearranged
+// input (as self_cross_S), each component prefiltered and evaluated by the
+// tricubic spline at the displaced centres (as the componentwise variant).
+static mm_status cross_eddy_field(mm_ctx* ctx, int g, const float* J, float* H) {
+  Magnet& S = ctx->mag[g];
+  const Magnet& T = ctx->mag[1 - g];
+  cudaStream_t st = ctx->st;
+  Dir& D = S.eddyx;
+  dir_geometry(ctx, g, true, &D);
+  D.prefilter = 1;
+  if (!S.zfft) CKS(build_T(ctx, g, &D));
+  CKS(alloc_dir_outputs(ctx, g, &D));
+  const size_t box = (size_t)D.r[0] * D.r[1] * D.r[2];
+  CKS(ensure_buf(ctx, &S.ex_C3, &S.ex_bytes[0], sizeof(float) * 3 * box));
+  CKS(ensure_buf(ctx, &S.ed_V, &S.ed_bytes[0], sizeof(float) * 3 * S.N));
+  CKS(join_mech(ctx));
+  const float* in[2] = {ctx->mag[0].m, ctx->mag[1].m};
+  in[g] = S.ed_V;
+  const int which[1] = {g};
+  const int what[1] = {2};
+  Dir* dirs[1] = {&D};
+  for (int comp = 0; comp < 3; ++comp) {
+    CK(launch_cross_input(J, S.N, comp, S.ed_V, st));
+    CKS(run_source_passes(ctx, in, which, 1, what, dirs));
+    // the path's spectra carry Ms of the source: divide it out
+    CK(launch_scale_into(D.C, box, (float)(1.0 / S.Ms), S.ex_C3 + comp * box, st));
+  }
+  const double sigma = g == 0 ? 1.0 : -1.0;  // +1: the target is the slider
+  double frac[3];
+  for (int a = 0; a < 3; ++a) {
+    const double su = sigma * u_cells(ctx, a, ctx->host_mech.x);
+    frac[a] = su - floor(su);
+  }
+  const int bdim[3] = {D.r[0], D.r[1], D.r[2]};
+  const int nt[3] = {T.nx, T.ny, T.nz};
+  CK(launch_field_values(S.ex_C3, bdim, nt, ctx->opt.margin, frac, H, st));
+  return MM_OK;
+}
 
 static mm_status eddy_core(mm_ctx* ctx, int mag, const float* dBdt_dev, double sigma, float* H_dev, float* J_dev,
                            int* sweeps_out) {

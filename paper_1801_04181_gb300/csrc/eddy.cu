@@ -54,6 +54,12 @@ __global__ void __launch_bounds__(256) k_scale_into(const float* __restrict__ in
   if (i < N) out[i] = s * in[i];
 }
 
+__global__ void __launch_bounds__(256) k_accumulate(const float* __restrict__ in, size_t N,
+                                                    float* __restrict__ out) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) out[i] += in[i];
+}
+
 // b of every cell and per-block sums of b (for its mean)
 __global__ void __launch_bounds__(256) k_eddy_source(const float* __restrict__ E, int nx, int ny, int nz,
                                                      double idx_, double idy, double idz, double* __restrict__ b,
@@ -248,6 +254,12 @@ cudaError_t launch_cross_input(const float* V, size_t N, int comp, float* out, c
 
 cudaError_t launch_scale_into(const float* in, size_t N, float s, float* out, cudaStream_t st) {
   k_scale_into<<<blocks(N), 256, 0, st>>>(in, N, s, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_accumulate(const float* in, size_t N, float* out, cudaStream_t st) {
+  if (N == 0) return cudaSuccess;
+  k_accumulate<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(in, N, out);
   return cudaGetLastError();
 }
 

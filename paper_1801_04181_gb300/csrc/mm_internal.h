@@ -355,6 +355,7 @@ cudaError_t launch_mxh2(const float* m, const float* H, size_t N, double* partia
 // eddy currents (eddy.cu)
 cudaError_t launch_cross_input(const float* V, size_t N, int comp, float* out, cudaStream_t st);
 cudaError_t launch_scale_into(const float* in, size_t N, float s, float* out, cudaStream_t st);
+cudaError_t launch_accumulate(const float* in, size_t N, float* out, cudaStream_t st);  // out += in
 int eddy_blocks(size_t N);
 cudaError_t launch_eddy_source(const float* E, int nx, int ny, int nz, const double d[3], double* b, double* part,
                                double* bmean, cudaStream_t st);

@@ -106,3 +106,65 @@ def test_eddy_coupled_steps_match_oracle():
         tol = max(TOL, 2 * EPS_B * np.linalg.norm(B_hist[-1][g].ravel()) / dB)
         assert rel_l2(He[g], cs.Heddy[g]) < tol
     assert abs(x - y[2]) <= 1e-5 * abs(y[2])
+
+
+@pytest.mark.parametrize("n0,n1,gap,u,lateral", [
+    ((12, 10, 2), (12, 10, 2), 2, (0.37, 0.0, 0.0), (0, 0)),
+    ((14, 9, 3), (10, 11, 2), 3, (1.6, -0.45, 0.0), (2, -1)),
+])
+def test_eddy_field_on_other_matches_oracle(n0, n1, gap, u, lateral):
+    """The field of one magnet's currents inside the other (interpolated on the
+    potential box), both directions, against the oracle."""
+    fp, _, _ = workloads.film_pair_plain(n=n0, gap=gap, seed=4)
+    fp.n_slider = n1
+    fp.u0 = u
+    fp.lateral = lateral
+    fp.cell = (2e-9, 2e-9, 2e-9)
+    m0, m1 = workloads.random_unit(n0, 1), workloads.random_unit(n1, 2)
+    mm = gpu_pair(fp, m0, m1, mech=False)
+    rng = np.random.default_rng(9)
+    for src in (0, 1):
+        t = 1 - src
+        n_s = n0 if src == 0 else n1
+        J = rng.standard_normal((3, n_s[2], n_s[1], n_s[0])) * 1e10
+        H = mm.eddy_field_on_other(src, torch.as_tensor(J, dtype=torch.float32, device="cuda"))
+        n_t = n1 if t == 1 else n0
+        ref = OE.current_field_on_other(J.astype(np.float32).astype(np.float64), fp.cell, fp.offsets[src],
+                                        fp.offsets[t], n_t, u, t == 1)
+        assert rel_l2(H.double().cpu().numpy(), ref) < TOL
+    mm.close()
+
+
+def test_eddy_of_a_conducting_base_reaches_an_insulating_slider():
+    """Only the base conducts: after three coupled steps the slider's eddy
+    field is the field of the base's currents, against the oracle's coupled
+    run (bar widened by the flux-difference cancellation as above)."""
+    from oracle import dynamics as D
+    from tests.pair_setup import oracle_system
+
+    fp, _, _ = workloads.film_pair_stick_slip(n=(16, 12, 2), gap=3, seed=5)
+    m0, m1 = workloads.random_unit(fp.n_base, 5), workloads.random_unit(fp.n_slider, 6)
+    fp.mech.x0_spring = 2e-9
+    sigma, dt, n = 1e11, 2e-14, 3
+    mm = gpu_pair(fp, m0, m1)
+    mm.set_conductivity(0, sigma)
+    mm.step(n, dt)
+    got = [mm.get_magnetization(g).double().cpu().numpy() for g in (0, 1)]
+    He = [mm.get_eddy_field(g).double().cpu().numpy() for g in (0, 1)]
+    mm.close()
+    y0 = [m0, m1, 0.0, 0.0]
+    cs = OE.EddyCoupledSystem(oracle_system(fp), (sigma, 0.0))
+    B_hist, t, y, k1 = [], 0.0, list(y0), None
+    for _ in range(n):
+        y5, _, k7 = D.dp45_step(cs, t, y, dt, k1)
+        B_hist.append([b.copy() for b in cs.last_B])
+        cs.accept(dt)
+        y = [D.normalise(y5[0]), D.normalise(y5[1]), y5[2], y5[3]]
+        t += dt
+        k1 = k7
+    assert np.linalg.norm(He[1]) > 0.0
+    dB = np.linalg.norm((B_hist[-1][0] - B_hist[-2][0]).ravel())
+    tol = max(TOL, 2 * EPS_B * np.linalg.norm(B_hist[-1][0].ravel()) / dB)
+    for g in (0, 1):
+        assert rel_l2(got[g], y[g]) < TOL
+        assert rel_l2(He[g], cs.Heddy[g]) < tol
