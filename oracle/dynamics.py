@@ -188,6 +188,23 @@ def run_fixed(system, y0, dt, nsteps, t0=0.0):
     return t, y
 
 
+def euler_step(system, t, y, dt):
+    """One explicit Euler step of the LLG equation and the slider's Newton
+    equation together (Sec. III: the equations of motion are solved in the
+    Euler solver as in the RK45 one): y + dt f(t, y), then m renormalised."""
+    y1 = _axpy_state(y, [system.rhs(t, y)], [1.0], dt)
+    return [normalise(y1[0]), normalise(y1[1]), y1[2], y1[3]]
+
+
+def run_euler(system, y0, dt, nsteps, t0=0.0):
+    """nsteps explicit Euler steps of size dt."""
+    t, y = t0, list(y0)
+    for _ in range(nsteps):
+        y = euler_step(system, t, y, dt)
+        t += dt
+    return t, y
+
+
 def run_adaptive(system, y0, dt, nsteps, rtol, t0=0.0, dt_min=0.0, dt_max=np.inf, trace=None):
     """nsteps accepted adaptive DP45 steps; controller dt *= clamp(0.9 (rtol/err)^(1/5), 0.2, 5).
 

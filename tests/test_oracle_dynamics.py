@@ -13,7 +13,10 @@
   dt_max when nothing moves, tolerance proportionality of the global error;
 * exchange field of a spin wave: eigenvalue (2A/mu0 Ms)(2 cos(k d) - 2)/d^2;
 * anisotropy field along the axis, 2 Ku/(mu0 Ms) (m.k);
-* slider without magnetic force: critically damped spring, closed form.
+* slider without magnetic force: critically damped spring, closed form;
+* the explicit Euler integrator: first order on the single spin (the error
+  against the closed form halves with dt), and on the slider alone, a linear
+  ODE, it is the explicit recurrence x += dt v, v += dt a(t, x, v) exactly.
 """
 
 import numpy as np
@@ -347,3 +350,40 @@ def test_run_adaptive_tolerance_proportionality():
         th_ref = 2 * np.arctan(np.tan(0.4) * np.exp(-alpha * gamma0 * H0 * t / (1 + alpha ** 2)))
         errs.append(abs(np.arccos(y[0][2, 0, 0, 0]) - th_ref))
     assert errs[1] < 1e-2 * errs[0], errs
+
+
+def test_euler_is_first_order_on_the_single_spin():
+    H0, alpha = 1e5, 0.1
+    th0 = 0.8
+    m0 = np.array([np.sin(th0), 0.0, np.cos(th0)])
+    sys = SingleSpin((0, 0, H0), alpha)
+    gamma0 = MU0 * GAMMA_LL
+    T = 2e-11
+    errs = []
+    for n in (200, 400, 800):
+        y = [m0[:, None, None, None].copy(), m0[:, None, None, None].copy(), 0.0, 0.0]
+        t, y = D.run_euler(sys, y, T / n, n)
+        th = np.arccos(y[0][2, 0, 0, 0])
+        th_ref = 2 * np.arctan(np.tan(th0 / 2) * np.exp(-alpha * gamma0 * H0 * t / (1 + alpha ** 2)))
+        errs.append(abs(th - th_ref))
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 1.8 < r1 < 2.2 and 1.8 < r2 < 2.2
+
+
+def test_euler_steps_the_slider_explicitly():
+    from oracle.dynamics import System
+    cell = (4e-9, 4e-9, 4e-9)
+    mat = dict(Ms=1.0, Aex=0.0, Ku=0.0, ku_axis=(0, 0, 1), alpha=0.5)
+    k, mass, v_d = 1e-3, 2.5e-18, 1.0
+    w = np.sqrt(k / mass)
+    mech = dict(mass=mass, k=k, v_drive=v_d, gamma_v=2 * w, dir=(1, 0, 0), x0_spring=3e-10)
+    sys = System([(2, 2, 1), (2, 2, 1)], cell, [(0, 0, 0), (0, 0, 40)], [mat, mat], mech)
+    m = np.zeros((3, 1, 2, 2))
+    m[2] = 1.0
+    dt, n = 1e-10, 60
+    _, y = D.run_euler(sys, [m.copy(), m.copy(), 0.0, 0.0], dt, n)
+    x = v = t = 0.0
+    for _ in range(n):
+        a = k / mass * (v_d * t + 3e-10 - x) - 2 * w * v  # the magnets' force is ~1e-19 of this
+        x, v, t = x + dt * v, v + dt * a, t + dt
+    assert abs(y[2] - x) <= 1e-9 * abs(x) and abs(y[3] - v) <= 1e-9 * abs(v)
