@@ -63,6 +63,8 @@ enum { MM_FP32 = 0, MM_MIXED = 1 };
 
 enum { MM_PERIODIC_X = 1, MM_PERIODIC_Y = 2 };
 
+enum { MM_RK45 = 0, MM_EULER = 1 };
+
 typedef struct {
   int precision;     /* MM_FP32 or MM_MIXED */
   int margin;        /* potential box margin in cells beyond the spline support (Sec. III.A: 4) */
@@ -86,6 +88,16 @@ typedef struct {
    */
   int periodic;
   int pbc_images;    /* images on each side of the period, 0 .. 64 */
+  /*
+   * Time integrator of the LLG and the slider's Newton equation (Sec. III:
+   * the equations of motion are solved in the Euler solver and in the
+   * adaptive Dormand-Prince RK45 solver).  MM_RK45 (default): Dormand-Prince
+   * 5(4) with first-same-as-last reuse, adaptive or fixed dt.  MM_EULER:
+   * explicit Euler, y + dt f(t, y) with one field evaluation per step and m
+   * renormalised, fixed dt only (adaptive = 1 gives MM_EINVAL); no eddy
+   * coupling (mm_set_conductivity with sigma > 0 gives MM_ENOTSUP).
+   */
+  int integrator;
 } mm_options;
 
 /* Defaults: FP32, margin 4, adaptive, rtol 1e-5, dt in [1e-16, 1e-11] s, default stream,

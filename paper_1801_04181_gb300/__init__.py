@@ -41,16 +41,21 @@ class MovingMagnets:
     """Two magnets (0 base, 1 slider) and the slider's motion; one libmm context."""
 
     def __init__(self, margin=4, adaptive=True, rtol=1e-5, dt_min=1e-16, dt_max=1e-11, stream=None,
-                 periodic=0, pbc_images=2, precision="fp32"):
+                 periodic=0, pbc_images=2, precision="fp32", integrator="rk45"):
         """periodic: 0 (open), or MM_PERIODIC_X | MM_PERIODIC_Y (1, 2, 3) with
         pbc_images periodic images on each side.  precision: "fp32", or
-        "mixed" for the y transforms as split-BF16 tensor-core DFT products."""
+        "mixed" for the y transforms as split-BF16 tensor-core DFT products.
+        integrator: "rk45" (Dormand-Prince 5(4)) or "euler" (explicit, fixed dt:
+        needs adaptive=False)."""
         if precision not in ("fp32", "mixed"):
             raise ValueError("precision must be 'fp32' or 'mixed'")
+        if integrator not in ("rk45", "euler"):
+            raise ValueError("integrator must be 'rk45' or 'euler'")
         self.lib = _native.load()
         opt = mm_options()
         self.lib.mm_default_options(C.byref(opt))
         opt.precision = _native.MM_MIXED if precision == "mixed" else _native.MM_FP32
+        opt.integrator = _native.MM_EULER if integrator == "euler" else _native.MM_RK45
         opt.periodic = int(periodic)
         opt.pbc_images = int(pbc_images)
         opt.margin = margin

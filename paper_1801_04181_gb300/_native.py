@@ -15,12 +15,14 @@ MM_ETOOBIG = -8
 
 MM_PERIODIC_X, MM_PERIODIC_Y = 1, 2
 MM_FP32, MM_MIXED = 0, 1
+MM_RK45, MM_EULER = 0, 1
 
 
 class mm_options(C.Structure):
     _fields_ = [("precision", C.c_int), ("margin", C.c_int), ("adaptive", C.c_int),
                 ("rtol", C.c_double), ("dt_min", C.c_double), ("dt_max", C.c_double),
-                ("stream", C.c_void_p), ("periodic", C.c_int), ("pbc_images", C.c_int)]
+                ("stream", C.c_void_p), ("periodic", C.c_int), ("pbc_images", C.c_int),
+                ("integrator", C.c_int)]
 
 
 _d3 = C.c_double * 3

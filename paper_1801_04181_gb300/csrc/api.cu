@@ -1312,6 +1312,10 @@ MechParams mech_params(mm_ctx* ctx, int mode, int stage, double dt, bool dir0, b
   if (mode == 2)
     for (int j = 0; j < 7; ++j) P.a[j] = DP_A[1][j];
   P.c_next = (mode == 2) ? DP_C[1] : (stage >= 1 && stage < 7 ? DP_C[stage] : 0.0);
+  if (ctx->opt.integrator == MM_EULER && mode == 0 && stage == 1) {  // x + dt v, v + dt a at t + dt
+    for (int j = 0; j < 7; ++j) P.a[j] = j == 0 ? 1.0 : 0.0;
+    P.c_next = 1.0;
+  }
   P.move = ctx->move ? 1 : 0;
   P.mass = ctx->mass;
   P.inv_mass = ctx->mass > 0 ? 1.0 / ctx->mass : 0.0;
@@ -1392,6 +1396,7 @@ StageJob stage_job(mm_ctx* ctx, int g, const float* ys, float* ys_next, int stag
   J.mode = mode;
   if (mode == 0 && stage < 7)
     for (int j = 0; j < stage; ++j) J.comb[j] = (float)(dt * DP_A[stage][j]);
+  if (mode == 0 && stage == 1 && ctx->opt.integrator == MM_EULER) J.comb[0] = (float)dt;  // y + dt k1
   if (mode == 0 && stage == 7)
     for (int j = 0; j < 7; ++j) J.ecoef[j] = (float)(dt * (DP_B5[j] - DP_B4[j]));
   J.err_partial = M.err_partial;
@@ -1437,6 +1442,20 @@ mm_status check_device_error(mm_ctx* ctx) {
 // and range flag; attempt_finish waits for them.
 mm_status attempt_enqueue(mm_ctx* ctx, double dt) {
   Magnet* M = ctx->mag;
+  if (ctx->opt.integrator == MM_EULER) {
+    // one field evaluation at the accepted state, y + dt f(t, y) into ys[1]
+    // (the accept renormalises it into m); the slider by the same stage
+    CKS(run_mech(ctx, mech_params(ctx, 4, 0, dt, false, false)));
+    const float* in[2] = {M[0].m, M[1].m};
+    CKS(evaluate_fields(ctx, in, mech_params(ctx, 0, 1, dt, true, true)));
+    float* nxt[2] = {M[0].ys[1], M[1].ys[1]};
+    CKS(run_stage(ctx, in, nxt, 1, dt));
+    CKS(join_mech(ctx));
+    CK(cudaMemcpyAsync(&ctx->rb->mech, ctx->mech, sizeof(MechState), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaMemcpyAsync(&ctx->rb->err, ctx->err_flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaEventRecord(ctx->ev_done, ctx->st));
+    return MM_OK;
+  }
   if (!ctx->k1_valid) {
     CKS(run_mech(ctx, mech_params(ctx, 4, 0, dt, false, false)));
     const float* in[2] = {M[0].m, M[1].m};
@@ -1549,7 +1568,9 @@ mm_status conclude_attempt(mm_ctx* ctx, double* dt_io, double err, bool* accepte
       }
       M.B_valid = true;
     }
-    for (int g = 0; g < 2; ++g) std::swap(ctx->mag[g].k[0], ctx->mag[g].k[6]);
+    const bool fsal = ctx->opt.integrator == MM_RK45;  // Euler evaluates afresh every step
+    if (fsal)
+      for (int g = 0; g < 2; ++g) std::swap(ctx->mag[g].k[0], ctx->mag[g].k[6]);
     // the accepted slider state, beside the normalisation
     CKS(fork_mech(ctx, mech_params(ctx, 3, 7, dt, false, false)));
     ctx->host_mech.x = ctx->host_mech.xs;
@@ -1557,7 +1578,7 @@ mm_status conclude_attempt(mm_ctx* ctx, double* dt_io, double err, bool* accepte
     ctx->host_mech.t = ctx->host_mech.t + dt;
     ctx->host_mech.kx[0] = ctx->host_mech.kx[6];
     ctx->host_mech.kv[0] = ctx->host_mech.kv[6];
-    ctx->k1_valid = true;
+    ctx->k1_valid = fsal;
     ctx->accepted++;
     // the field of each conducting magnet's currents inside the other, at the
     // accepted displacement (that of the step's last evaluation)
@@ -1613,6 +1634,7 @@ void mm_default_options(mm_options* o) {
   o->stream = nullptr;
   o->periodic = 0;
   o->pbc_images = 2;
+  o->integrator = MM_RK45;
 }
 
 const char* mm_status_string(mm_status s) {
@@ -1641,7 +1663,9 @@ mm_status mm_create(mm_ctx** out, const mm_options* opt) {
     return MM_ENOTSUP;
   }
   if (ctx->opt.margin < 0 || ctx->opt.margin > 64 || ctx->opt.periodic < 0 || ctx->opt.periodic > 3 ||
-      ctx->opt.pbc_images < 0 || ctx->opt.pbc_images > 64) {
+      ctx->opt.pbc_images < 0 || ctx->opt.pbc_images > 64 ||
+      (ctx->opt.integrator != MM_RK45 && ctx->opt.integrator != MM_EULER) ||
+      (ctx->opt.integrator == MM_EULER && ctx->opt.adaptive)) {
     delete ctx;
     return MM_EINVAL;
   }
@@ -2295,6 +2319,8 @@ mm_status mm_set_conductivity(mm_ctx* ctx, int mag, double sigma) {
   if (!ctx || bad_mag(mag) || !(sigma >= 0) || !std::isfinite(sigma))
     return ctx ? fail(ctx, MM_EINVAL, "mm_set_conductivity") : MM_EINVAL;
   if (sigma > 0 && ctx->opt.periodic) return fail(ctx, MM_ENOTSUP, "mm_set_conductivity: periodic boundaries");
+  if (sigma > 0 && ctx->opt.integrator == MM_EULER)
+    return fail(ctx, MM_ENOTSUP, "mm_set_conductivity: the Euler integrator (the coupling's lag is defined for RK45)");
   Magnet& M = ctx->mag[mag];
   M.sigma = sigma;
   M.B_valid = M.Heddy_valid = false;

@@ -13,16 +13,18 @@ import torch
 from . import MovingMagnets
 
 
-def pair_context(desc, m0, m1, margin=4, adaptive=False, rtol=1e-5, mech=True, stream=None, precision="fp32"):
+def pair_context(desc, m0, m1, margin=4, adaptive=False, rtol=1e-5, mech=True, stream=None, precision="fp32",
+                 integrator="rk45"):
     """A MovingMagnets context for `desc` with unit magnetisations m0, m1
     ((3, nz, ny, nx) arrays or tensors), on `stream` (a torch.cuda.Stream;
     default: the current stream).  mech=False leaves the slider fixed.  A
     description with `periodic` (and `pbc_images`) set gets periodic in-plane
-    boundaries.  precision: "fp32" or "mixed" (tensor-core y transforms)."""
+    boundaries.  precision: "fp32" or "mixed" (tensor-core y transforms);
+    integrator: "rk45" or "euler" (fixed dt)."""
     st = stream if stream is not None else torch.cuda.current_stream()
     mm = MovingMagnets(margin=margin, adaptive=adaptive, rtol=rtol, stream=st,
                        periodic=getattr(desc, "periodic", 0), pbc_images=getattr(desc, "pbc_images", 2),
-                       precision=precision)
+                       precision=precision, integrator=integrator)
     for g, (n, mat, m) in enumerate(((desc.n_base, desc.mat_base, m0), (desc.n_slider, desc.mat_slider, m1))):
         mm.set_grid(g, n, desc.cell, desc.offsets[g])
         mm.set_material(g, mat.Ms, mat.Aex, mat.Ku, mat.ku_axis, mat.alpha)

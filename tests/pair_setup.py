@@ -11,13 +11,14 @@ def rel_l2(a, b):
     return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
 
 
-def gpu_pair(fp, m0, m1, margin=4, adaptive=False, rtol=1e-5, mech=True, stream=None, precision="fp32"):
+def gpu_pair(fp, m0, m1, margin=4, adaptive=False, rtol=1e-5, mech=True, stream=None, precision="fp32",
+             integrator="rk45"):
     """MovingMagnets context for a workloads.FilmPair with the given unit m arrays,
     on `stream` (a torch.cuda.Stream; default: the current stream)."""
     from paper_1801_04181_gb300 import pair_context
 
     return pair_context(fp, m0, m1, margin=margin, adaptive=adaptive, rtol=rtol, mech=mech, stream=stream,
-                        precision=precision)
+                        precision=precision, integrator=integrator)
 
 
 def oracle_system(fp):

@@ -199,6 +199,52 @@ def test_fixed_dt_steps_match_oracle():
     mm.close()
 
 
+def test_euler_steps_match_oracle():
+    """Five fixed-dt explicit Euler steps of the same spring-pulled films: one
+    field evaluation per step, the slider advanced by the same step (Sec. III)."""
+    fp, m0, m1 = workloads.film_pair_stick_slip(n=(40, 24, 2), gap=5, seed=4)
+    fp.u0 = (0.25, 0.0, 0.0)
+    fp.mech.x0_spring = 2e-9
+    fp.mech.v_drive = 50.0
+    mm = gpu_pair(fp, m0, m1, integrator="euler")
+    from tests.pair_setup import oracle_system
+    from oracle import dynamics as D
+
+    dt = 5e-14
+    t_ref, y = D.run_euler(oracle_system(fp), [m0, m1, 0.0, 0.0], dt, 5)
+    t, _ = mm.step(5, dt)
+    x, v, tt = mm.get_slider_state()
+    for g in (0, 1):
+        got = mm.get_magnetization(g).double().cpu().numpy()
+        init = m0 if g == 0 else m1
+        assert rel_l2(got, y[g]) < TOL
+        assert rel_l2(got - init, y[g] - init) < 1e-3
+    assert abs(tt - t_ref) < 1e-20
+    assert abs(x - y[2]) <= 1e-5 * abs(y[2])
+    assert abs(v - y[3]) <= 1e-5 * abs(y[3])
+    # the Euler and RK45 results differ by the Euler step's O(dt^2) error:
+    # the test would not tell them apart if the two paths were the same
+    _, y45 = D.run_fixed(oracle_system(fp), [m0, m1, 0.0, 0.0], dt, 5)
+    assert rel_l2(y[0] - m0, y45[0] - m0) > 1e-2
+    mm.close()
+
+
+def test_euler_rejects_adaptive_and_conduction():
+    """The Euler integrator steps with a fixed dt (no error estimate), and the
+    eddy coupling is defined on the RK45 step: both requests are refused."""
+    from paper_1801_04181_gb300 import MMError, MovingMagnets
+
+    with pytest.raises(MMError):
+        MovingMagnets(adaptive=True, integrator="euler")
+    with pytest.raises(ValueError):
+        MovingMagnets(integrator="midpoint")
+    fp, m0, m1 = workloads.film_pair_stick_slip(n=(16, 8, 1), gap=5, seed=4)
+    mm = gpu_pair(fp, m0, m1, integrator="euler")
+    with pytest.raises(MMError):
+        mm.set_conductivity(0, 1e6)
+    mm.close()
+
+
 def test_checkpoint_resume_is_bitwise():
     fp, m0, m1 = workloads.film_pair_stick_slip(n=(32, 16, 2), gap=5, seed=8)
     fp.mech.x0_spring = 1e-9
