@@ -923,6 +923,7 @@ mm_status upload_mech(mm_ctx* ctx) {
   MechState& H = ctx->host_mech;
   H.xs = H.x; H.vs = H.v; H.ts = H.t;
   for (int a = 0; a < 3; ++a) H.u[a] = u_cells(ctx, a, H.x);
+  split_displacement(H.u, H.ucell, H.ufrac);
   CK(cudaMemcpyAsync(ctx->mech, &H, sizeof(MechState), cudaMemcpyHostToDevice, ctx->st));
   return MM_OK;
 }
@@ -1245,8 +1246,8 @@ GatherJob gather_job(mm_ctx* ctx, int s, const float* m_t, float* H) {
   J.C = D.C;
   J.rx = D.r[0]; J.ry = D.r[1]; J.rz = D.r[2];
   J.nx = T.nx; J.ny = T.ny; J.nz = T.nz;
-  J.u = ctx->mech->u;
-  J.sigma = s == 0 ? 1.0 : -1.0;
+  J.ucell = ctx->mech->ucell[s];
+  J.ufrac = ctx->mech->ufrac[s];
   for (int a = 0; a < 3; ++a) {
     J.U0[a] = D.U0[a];
     J.guard[a] = D.guard[a];

@@ -381,8 +381,9 @@ __global__ void __launch_bounds__(256, 3) k_xinv(const Launch<XInvJob> Lc) {
   const int n = J.kxh * nlines;
   if (paired && nlines == kLines) {
     // full tile: blockDim is a multiple of kLines, so every thread keeps one
-    // line (its input row pair) for all its kx; kBatchX reads in flight
-    constexpr int kBatchX = 4;
+    // line (its input row pair) for all its kx; kBatchX reads in flight (three
+    // rounds of loads for a 2160-point line)
+    constexpr int kBatchX = 6;
     const int l = threadIdx.x % kLines;
     const float2* src = rowptr(2 * l);
     const int step = blockDim.x / kLines;

@@ -105,7 +105,6 @@ template <bool WRAP>
 __global__ void __launch_bounds__(TX * TY, 4) k_gather(const Launch<GatherJob> Lc) {
   extern __shared__ float gsm[];
   __shared__ float w_s[3][12];
-  __shared__ int shift_s[3];
   __shared__ float red_s[TX * TY / 32][4];
 
   const int j = find_job(Lc.tile_start, Lc.njobs, blockIdx.x);
@@ -121,58 +120,56 @@ __global__ void __launch_bounds__(TX * TY, 4) k_gather(const Launch<GatherJob> L
   const int nz = min(kMaxNz, J.nz - z0);
   const int cz = nz + 3;
 
-  if (threadIdx.x < 3) {
-    const int a = threadIdx.x;
-    // sigma * u in source lattice cells; floor -> integer shift, rest -> weights
-    const double su = J.sigma * J.u[a];
-    const double fl = floor(su);
-    const int U = (int)fl;
-    bspline_w((float)(su - fl), w_s[a]);
-    int sh;
+  // Every thread finds the integer tap shifts itself, so the coefficient
+  // loads below are in flight before the barrier that publishes the weights.
+  // sigma u in source lattice cells arrives split: floor(sigma u) -> integer
+  // shift, the rest -> weights.
+  int sh[3];
+  bool bad = false;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int U = J.ucell[a];
+    if (threadIdx.x == a) bspline_w(J.ufrac[a], w_s[a]);
     if (WRAP && a < 2 && J.wrapP[a] > 0) {
       // periodic axis: the coefficients span the period, the taps wrap
       const int P = J.wrapP[a];
-      sh = (J.tap0[a] + (U % P + P) % P) % P;
+      sh[a] = (J.tap0[a] + (U % P + P) % P) % P;
     } else {
-      sh = J.guard[a] + (U - J.U0[a]);
+      sh[a] = J.guard[a] + (U - J.U0[a]);
       const int need = (a == 0 ? J.nx : a == 1 ? J.ny : J.nz) + 3;
       const int have = a == 0 ? J.rx : a == 1 ? J.ry : J.rz;
-      if (sh < 0 || sh + need > have) {
-        atomicOr(J.err, 1);
-        sh = 0x7fffffff;
-      }
+      bad = bad || sh[a] < 0 || sh[a] + need > have;
     }
-    shift_s[a] = sh;
   }
-  __syncthreads();
-  const bool bad = shift_s[0] == 0x7fffffff || shift_s[1] == 0x7fffffff || shift_s[2] == 0x7fffffff;
+  if (bad && threadIdx.x == 0) atomicOr(J.err, 1);
 
   // x-filtered coefficient rows A[d][zz][yy][x] (d: w, w', w''), one warp per
   // (zz, yy) row, filtered straight from global memory: a warp's four tap
   // loads are four coalesced 128-byte reads of one coefficient row (L1 hits
   // after the first).  Lanes past the target's edge read clamped, in-box
-  // positions and their results are never used.
+  // positions and their results are never used.  kRowBatch rows per warp
+  // are loaded at once (all of them for open targets of up to two layers).
   float* A = gsm;
   const int a_n = cz * (TY + 3) * TX;
-  if (!bad) {
-    const int sx = shift_s[0], sy = shift_s[1], sz = shift_s[2];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // column of each of the four x taps (wrapped around a periodic x)
-    const int P0 = WRAP ? J.wrapP[0] : 0, P1 = WRAP ? J.wrapP[1] : 0;
-    const int xb = min(x0 + lane, J.nx - 1) + sx;
-    int xt[4];
+  const int sx = sh[0], sy = sh[1], sz = sh[2];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // column of each of the four x taps (wrapped around a periodic x)
+  const int P0 = WRAP ? J.wrapP[0] : 0, P1 = WRAP ? J.wrapP[1] : 0;
+  const int xb = min(x0 + lane, J.nx - 1) + sx;
+  int xt[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) xt[k] = P0 > 0 ? (xb + k) % P0 : xb + k;
-    const float w0 = w_s[0][0], w1 = w_s[0][1], w2 = w_s[0][2], w3 = w_s[0][3];
-    const float d0 = w_s[0][4], d1 = w_s[0][5], d2 = w_s[0][6], d3 = w_s[0][7];
-    const float e0 = w_s[0][8], e1 = w_s[0][9], e2 = w_s[0][10], e3 = w_s[0][11];
-    const int nrow = cz * (TY + 3);
-    constexpr int kRowBatch = 2;
-    for (int r0 = warp; r0 < nrow; r0 += kRowBatch * (TX * TY / 32)) {
-      float c[kRowBatch][4];
+  for (int k = 0; k < 4; ++k) xt[k] = P0 > 0 ? (xb + k) % P0 : xb + k;
+  const int nrow = cz * (TY + 3);
+  constexpr int kWarps = TX * TY / 32;
+  constexpr int kRowBatch = WRAP ? 2 : 7;  // the wrapped taps take registers of their own
+  // every warp has rows in the first batch (nrow >= 44 > kWarps), so the
+  // barrier that publishes the weights sits in that batch, after its loads
+  for (int r0 = warp; r0 < nrow; r0 += kRowBatch * kWarps) {
+    float c[kRowBatch][4];
+    if (!bad) {
 #pragma unroll
       for (int b = 0; b < kRowBatch; ++b) {
-        const int r = min(r0 + b * (TX * TY / 32), nrow - 1);
+        const int r = min(r0 + b * kWarps, nrow - 1);
         const int zz = r / (TY + 3), yy = r - zz * (TY + 3);
         // rows past the target's last support row are clamped in the box
         // (a periodic y wraps them around the period instead)
@@ -181,9 +178,15 @@ __global__ void __launch_bounds__(TX * TY, 4) k_gather(const Launch<GatherJob> L
 #pragma unroll
         for (int k = 0; k < 4; ++k) c[b][k] = __ldg(src + xt[k]);
       }
+    }
+    if (r0 == warp) __syncthreads();  // the weights
+    if (!bad) {
+      const float w0 = w_s[0][0], w1 = w_s[0][1], w2 = w_s[0][2], w3 = w_s[0][3];
+      const float d0 = w_s[0][4], d1 = w_s[0][5], d2 = w_s[0][6], d3 = w_s[0][7];
+      const float e0 = w_s[0][8], e1 = w_s[0][9], e2 = w_s[0][10], e3 = w_s[0][11];
 #pragma unroll
       for (int b = 0; b < kRowBatch; ++b) {
-        const int r = r0 + b * (TX * TY / 32);
+        const int r = r0 + b * kWarps;
         if (r >= nrow) break;
         const int o = r * TX + lane;
         A[o] = w0 * c[b][0] + w1 * c[b][1] + w2 * c[b][2] + w3 * c[b][3];
@@ -209,12 +212,11 @@ __global__ void __launch_bounds__(TX * TY, 4) k_gather(const Launch<GatherJob> L
   // FP32 within a warp (at most 32 x nz cells), FP64 from there on: the FP64
   // pipe of this GPU is narrow, and a warp's partial sum keeps ~1e-6 of the
   // magnitude of its terms, well inside the force tolerance
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    float s = acc[c];
+  for (int q = 0; q < 4; ++q) {
+    float s = acc[q];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (lane == 0) red_s[warp][c] = s;
+    if (lane == 0) red_s[warp][q] = s;
   }
   __syncthreads();
   if (warp != 0) return;

@@ -23,6 +23,8 @@ __device__ __forceinline__ void store_state(MechState* d, const MechState& s) {
   d->xs = s.xs; d->vs = s.vs; d->ts = s.ts;
   for (int i = 0; i < 7; ++i) { d->kx[i] = s.kx[i]; d->kv[i] = s.kv[i]; }
   for (int c = 0; c < 3; ++c) { d->u[c] = s.u[c]; d->F_slider[c] = s.F_slider[c]; d->F_base[c] = s.F_base[c]; }
+  for (int r = 0; r < 2; ++r)
+    for (int c = 0; c < 3; ++c) { d->ucell[r][c] = s.ucell[r][c]; d->ufrac[r][c] = s.ufrac[r][c]; }
   d->E_slider = s.E_slider;
   d->E_base = s.E_base;
 }
@@ -128,8 +130,10 @@ __device__ __forceinline__ void mech_block(const MechParams& P) {
   } else if (P.mode == 4) {  // restart an attempt from the accepted state
     S->xs = S->x; S->vs = S->v; S->ts = S->t;
   }
-  if (P.mode == 0 || P.mode == 2 || P.mode == 3 || P.mode == 4)
+  if (P.mode == 0 || P.mode == 2 || P.mode == 3 || P.mode == 4) {
     for (int c = 0; c < 3; ++c) S->u[c] = P.u_base[c] + S->xs * P.e[c] * P.inv_d[c];
+    split_displacement(S->u, S->ucell, S->ufrac);
+  }
   store_state(P.state, Sc);
 }
 

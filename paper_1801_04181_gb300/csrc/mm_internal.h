@@ -216,8 +216,8 @@ struct GatherJob {
   const float* C;         // coefficients [rz][ry][rx]
   int rx, ry, rz;
   int nx, ny, nz;         // target grid
-  const double* u;        // slider displacement, lattice cells (device)
-  double sigma;           // +1 target is the slider, -1 source is the slider
+  const int* ucell;       // floor(sigma u) per axis (device), u the slider displacement in lattice cells
+  const float* ufrac;     // sigma u - floor(sigma u) per axis (device)
   int U0[3];              // floor(sigma u) when the box was planned
   int guard[3];           // extra coefficient nodes kept on each side
   float inv_d[3];         // 1 / cell size (1/m)
@@ -272,7 +272,24 @@ struct MechState {
   double u[3];            // displacement (lattice cells) seen by the gathers
   double F_slider[3], E_slider, F_base[3], E_base;
   double err;
+  // u split for the gathers, row 0 for sigma = +1 (target is the slider) and
+  // row 1 for sigma = -1: floor(sigma u) and sigma u - floor(sigma u)
+  int ucell[2][3];
+  float ufrac[2][3];
 };
+
+// The integer and fractional lattice offsets of both directions (FP64 floor,
+// the fraction exact in FP64 and then rounded to float), on the host or in the
+// one thread that writes u.
+__host__ __device__ inline void split_displacement(const double* u, int (*ucell)[3], float (*ufrac)[3]) {
+  for (int r = 0; r < 2; ++r)
+    for (int a = 0; a < 3; ++a) {
+      const double su = r == 0 ? u[a] : -u[a];
+      const double fl = floor(su);
+      ucell[r][a] = (int)fl;
+      ufrac[r][a] = (float)(su - fl);
+    }
+}
 
 struct MechParams {
   MechState* state;

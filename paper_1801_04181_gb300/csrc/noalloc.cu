@@ -27,7 +27,8 @@
 namespace mm {
 
 constexpr int kNoAllocMaxTiles = 65536;  // 32 x 8 target columns per tile -> 16.7M columns
-constexpr int kNoAllocHeader = 32;       // [0] error flag, [1..3] displacement, rest spare
+constexpr int kNoAllocHeader = 32;       // [0] error flag, [1..3] displacement, [4..6] its cell,
+                                         // [7..9] its fraction, rest spare
 constexpr int kNoAllocMaxDevices = 64;
 
 // 2 MiB: header + 4 doubles per gather tile
@@ -40,6 +41,13 @@ __global__ void k_noalloc_begin(double p0, double p1, double p2) {
     g_noalloc_scratch[1] = p0;
     g_noalloc_scratch[2] = p1;
     g_noalloc_scratch[3] = p2;
+    int ucell[2][3];
+    float ufrac[2][3];
+    split_displacement(g_noalloc_scratch + 1, ucell, ufrac);
+    for (int a = 0; a < 3; ++a) {
+      reinterpret_cast<int*>(g_noalloc_scratch + 4)[a] = ucell[0][a];
+      reinterpret_cast<float*>(g_noalloc_scratch + 7)[a] = ufrac[0][a];
+    }
   }
 }
 
@@ -136,8 +144,8 @@ extern "C" mm_status mm_spline_field_noalloc(const float* coef_dev, const int co
   J.C = coef_dev;
   J.rx = coef_dims[0]; J.ry = coef_dims[1]; J.rz = coef_dims[2];
   J.nx = nx; J.ny = ny; J.nz = nz;
-  J.u = scratch + 1;
-  J.sigma = 1.0;
+  J.ucell = reinterpret_cast<const int*>(scratch + 4);
+  J.ufrac = reinterpret_cast<const float*>(scratch + 7);
   J.inv_d[0] = (float)(1.0 / dx);
   J.inv_d[1] = (float)(1.0 / dy);
   J.inv_d[2] = (float)(1.0 / dz);

@@ -85,6 +85,32 @@ def test_fixed_dt_batch_matches_oracle():
         mm.close()
 
 
+def test_mixed_integrator_batch_matches_oracle():
+    """A batch whose pairs step with different solvers (explicit Euler and
+    DP45, Sec. III), each matching its own oracle integrator."""
+    from oracle import dynamics as D
+
+    pairs = _small_batch()[:3]
+    integ = ["euler", "rk45", "euler"]
+    streams = [torch.cuda.Stream() for _ in range(2)]
+    batch = [gpu_pair(fp, m0, m1, adaptive=False, stream=streams[i % 2], integrator=it)
+             for i, ((fp, m0, m1), it) in enumerate(zip(pairs, integ))]
+    dt = 5e-14
+    t_b, _ = step_batch(batch, 3, [dt] * len(batch))
+    for (fp, m0, m1), mm, t, it in zip(pairs, batch, t_b, integ):
+        run = D.run_euler if it == "euler" else D.run_fixed
+        t_ref, y = run(oracle_system(fp), [m0, m1, 0.0, 0.0], dt, 3)
+        assert abs(t - t_ref) < 1e-20
+        x, v, _ = mm.get_slider_state()
+        for g, init in ((0, m0), (1, m1)):
+            got = mm.get_magnetization(g).double().cpu().numpy()
+            assert rel_l2(got, y[g]) < TOL
+            assert rel_l2(got - init, y[g] - init) < 1e-3
+        assert abs(x - y[2]) <= 1e-5 * abs(y[2])
+        assert abs(v - y[3]) <= 1e-5 * abs(y[3])
+        mm.close()
+
+
 def test_batch_rejects_repeated_context_and_bad_dt():
     pairs = _small_batch()[:2]
     batch = _make(pairs, [0, 0], adaptive=True)
