@@ -23,13 +23,16 @@
 namespace mm {
 
 constexpr int kLines = kRowsPerCta / 2;  // complex lines per CTA in the x passes
+// threads per CTA of the x passes (multiples of kLines)
+constexpr int kXFwdThreads = 256;
+constexpr int kXInvThreads = 256;
 constexpr int kLinePad = 4;              // float2 between lines of an x-pass CTA
 
 cudaError_t init_fft_constants_passes() { return upload_roots(); }
 
 // ------------------------------------------------------------------ x forward
 template <unsigned RSET>
-__global__ void __launch_bounds__(256, 3) k_xfwd(const Launch<XFwdJob> Lc) {
+__global__ void __launch_bounds__(kXFwdThreads, 3) k_xfwd(const Launch<XFwdJob> Lc) {
   extern __shared__ float2 sm[];
   const int j = find_job(Lc.tile_start, Lc.njobs, blockIdx.x);
   const XFwdJob& J = Lc.job[j];
@@ -356,7 +359,7 @@ __device__ __forceinline__ void xinv_put(float2* sm, int off, int Q, int kx, flo
 }
 
 template <unsigned RSET>
-__global__ void __launch_bounds__(256, 3) k_xinv(const Launch<XInvJob> Lc) {
+__global__ void __launch_bounds__(kXInvThreads, 3) k_xinv(const Launch<XInvJob> Lc) {
   extern __shared__ float2 sm[];
   const int j = find_job(Lc.tile_start, Lc.njobs, blockIdx.x);
   const XInvJob& J = Lc.job[j];
@@ -484,7 +487,7 @@ cudaError_t launch_xfwd(const Launch<XFwdJob>& L, int Qmax, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   const int grid = L.tile_start[L.njobs];
   if (grid == 0) return cudaSuccess;
-  k<<<grid, 256, smem, st>>>(L);
+  k<<<grid, kXFwdThreads, smem, st>>>(L);
   return cudaGetLastError();
 }
 
@@ -537,7 +540,7 @@ cudaError_t launch_xinv(const Launch<XInvJob>& L, int Qmax, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   const int grid = L.tile_start[L.njobs];
   if (grid == 0) return cudaSuccess;
-  k<<<grid, 256, smem, st>>>(L);
+  k<<<grid, kXInvThreads, smem, st>>>(L);
   return cudaGetLastError();
 }
 
