@@ -329,6 +329,52 @@ __device__ __forceinline__ void fft_smem(C* buf, int ldl, int nlines, const FftP
   }
 }
 
+// The quotient multiplier of the plan's per-stage divisors: n / d =
+// __umulhi(n, fft_magic(d)) for n d < 2^32, 0 for d = 1 (no division); the
+// same formula as the host planner's.
+__host__ __device__ constexpr unsigned fft_magic(int d) {
+  return d == 1 ? 0u : (unsigned)(0xFFFFFFFFull / (unsigned)d) + 1u;
+}
+
+// fft_smem for one plan known at compile time: three stages of radices R0, R1,
+// R2 (first to last DIF stage, L = R0 R1 R2) on lines of stride L.  The same
+// stage code with every length a constant, so the butterflies' shared-memory
+// and twiddle offsets fold into the instructions (the results are those of
+// fft_smem with the same plan, bit for bit).  The caller checks that P is
+// this plan.
+template <int MODE, typename C, int R0, int R1, int R2>
+__device__ __forceinline__ void fft_smem_fixed(C* buf, int nlines, const FftPlanDev& P,
+                                               const C* __restrict__ stw, int tid0, int nthr) {
+  static_assert(MODE == kFwdDif || MODE == kInvDit, "fixed plans: forward DIF and inverse DIT");
+  constexpr int L = R0 * R1 * R2;
+  const int tid = (int)threadIdx.x - tid0;
+  const bool mine = tid >= 0 && tid < nthr;
+  // stage s: block length Lb, M = Lb / R butterfly stride, L / R butterflies
+  // per line; the quotient multipliers are the planner's (fft_magic)
+  constexpr int Lb0 = L, Lb1 = R1 * R2, Lb2 = R2;
+  constexpr unsigned mpl0 = fft_magic(L / R0), mM0 = fft_magic(Lb0 / R0);
+  constexpr unsigned mpl1 = fft_magic(L / R1), mM1 = fft_magic(Lb1 / R1);
+  constexpr unsigned mpl2 = fft_magic(L / R2), mM2 = fft_magic(Lb2 / R2);
+  const C* tw0 = stw + P.stw_off[0];
+  const C* tw1 = stw + P.stw_off[1];
+  const C* tw2 = stw + P.stw_off[2];
+  if (MODE == kFwdDif) {
+    if (mine) fft_stage<R0, false, C>(buf, L, nlines, L, Lb0, mpl0, mM0, tw0, tid, nthr);
+    __syncthreads();
+    if (mine) fft_stage<R1, false, C>(buf, L, nlines, L, Lb1, mpl1, mM1, tw1, tid, nthr);
+    __syncthreads();
+    if (mine) fft_stage<R2, false, C>(buf, L, nlines, L, Lb2, mpl2, mM2, tw2, tid, nthr);
+    __syncthreads();
+  } else {
+    if (mine) fft_stage<R2, true, C>(buf, L, nlines, L, Lb2, mpl2, mM2, tw2, tid, nthr);
+    __syncthreads();
+    if (mine) fft_stage<R1, true, C>(buf, L, nlines, L, Lb1, mpl1, mM1, tw1, tid, nthr);
+    __syncthreads();
+    if (mine) fft_stage<R0, true, C>(buf, L, nlines, L, Lb0, mpl0, mM0, tw0, tid, nthr);
+    __syncthreads();
+  }
+}
+
 // Position of frequency k in the DIF output: sum_s M_s digit_s(k).
 __device__ __forceinline__ int fft_pos(int k, const FftPlanDev& P) {
   int p = 0;

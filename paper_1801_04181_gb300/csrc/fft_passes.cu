@@ -258,7 +258,8 @@ __device__ __forceinline__ void ypass_mix(const YJob& J, float2* sm, int kx, int
 // warps) covers the 271 frequency pairs of a 540-point line in one round of
 // the spectral products.
 constexpr int kYThreads = 288;
-template <int NZ, unsigned RSET>
+// FIX540: every job's y plan is 540 = 4 9 15, run with its lengths as constants.
+template <int NZ, unsigned RSET, bool FIX540>
 __global__ void __launch_bounds__(kYThreads, NZ <= 2 ? 3 : 2) k_ypass(const Launch<YJob> Lc) {
   constexpr int Pin = 3 * NZ;
   extern __shared__ float2 sm[];
@@ -316,10 +317,12 @@ __global__ void __launch_bounds__(kYThreads, NZ <= 2 ? 3 : 2) k_ypass(const Laun
   if (J.do_C)
     build_pref_table(tab, J.r + 2 * kPrefWarm + kYChunk, J.box_lo, J.box_len, J.start, Q, nullptr, J.periodic != 0);
   __syncthreads();
-  fft_smem<kFwdDif, float2, RSET>(sm, Q, Pin, J.fy.plan, J.fy.tw_f, 0, blockDim.x);
+  if constexpr (FIX540) fft_smem_fixed<kFwdDif, float2, 4, 9, 15>(sm, Pin, J.fy.plan, J.fy.tw_f, 0, blockDim.x);
+  else fft_smem<kFwdDif, float2, RSET>(sm, Q, Pin, J.fy.plan, J.fy.tw_f, 0, blockDim.x);
   ypass_mix<NZ>(J, sm, kx, Q, nH);
   __syncthreads();
-  fft_smem<kInvDit, float2, RSET>(sm, Q, Pout, J.fy.plan, J.fy.tw_f, 0, blockDim.x);
+  if constexpr (FIX540) fft_smem_fixed<kInvDit, float2, 4, 9, 15>(sm, Pout, J.fy.plan, J.fy.tw_f, 0, blockDim.x);
+  else fft_smem<kInvDit, float2, RSET>(sm, Q, Pout, J.fy.plan, J.fy.tw_f, 0, blockDim.x);
 
   if (J.do_H) {
     float2* out0 = J.outH + (size_t)kx * ny;
@@ -494,8 +497,14 @@ cudaError_t launch_xfwd(const Launch<XFwdJob>& L, int Qmax, cudaStream_t st) {
 template <int NZ>
 static cudaError_t launch_ypass_nz(const Launch<YJob>& L, size_t smem, cudaStream_t st) {
   unsigned rs = 0;
-  for (int i = 0; i < L.njobs; ++i) rs |= plan_radix_set(L.job[i].fy.plan);
-  auto k = (rs & ~kRadixSetA) == 0u ? k_ypass<NZ, kRadixSetA> : k_ypass<NZ, kAllRadices>;
+  bool fix540 = true;
+  for (int i = 0; i < L.njobs; ++i) {
+    const FftPlanDev& P = L.job[i].fy.plan;
+    rs |= plan_radix_set(P);
+    fix540 = fix540 && P.L == 540 && P.nstages == 3 && P.radix[0] == 4 && P.radix[1] == 9 && P.radix[2] == 15;
+  }
+  auto k = fix540 ? k_ypass<NZ, kRadixSetA, true>
+                  : (rs & ~kRadixSetA) == 0u ? k_ypass<NZ, kRadixSetA, false> : k_ypass<NZ, kAllRadices, false>;
   max_carveout((const void*)k);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

@@ -106,6 +106,39 @@ def test_stray_field_force_energy_match_oracle(n0, n1, gap, u, lateral):
     mm.close()
 
 
+def test_y_transform_of_540_points_matches_oracle():
+    """Films 256 cells wide in y take the 540-point y transform of the stick-slip
+    pair (plan 4 x 9 x 15, run with its lengths as compile-time constants): the
+    stray field, force and energy both ways and the demag field against the
+    oracle on a short strip of that width."""
+    from paper_1801_04181_gb300 import fft_plan, tuned_plan
+
+    fp, m0, m1, offs = _pair((12, 256, 2), (12, 256, 2), 5, 9, (0.43, 0.0, 0.0))
+    mm = _gpu(fp, m0, m1, offs)
+    for src in (0, 1):
+        Qy = mm.plan_info(src)["fft"][1]
+        assert Qy == 540 and (tuned_plan(540) or fft_plan(540)) == [4, 9, 15]
+    for src in (0, 1):
+        t = 1 - src
+        Hg = mm.compute_stray_field(src).double().cpu().numpy()
+        F, E = mm.get_force(t)
+        Ms_s = fp.mat_base.Ms if src == 0 else fp.mat_slider.Ms
+        Ms_t = fp.mat_slider.Ms if t == 1 else fp.mat_base.Ms
+        M_s = Ms_s * (m0 if src == 0 else m1)
+        M_t = Ms_t * (m1 if t == 1 else m0)
+        ref = stray_interaction(M_s, M_t, fp.cell, offs[src], offs[t], (0.43, 0.0, 0.0), t == 1, return_box=True)
+        assert rel_l2(Hg, ref["H"]) < TOL
+        scale = force_scale(ref["hess_n"], M_t, fp.cell)
+        assert np.max(np.abs(np.array(F) - ref["F"])) < TOL * scale
+        assert abs(E - ref["E"]) < TOL * abs(ref["E"]) + 1e-6 * scale * fp.cell[0]
+    for g in (0, 1):
+        Hd = mm.compute_demag(g).double().cpu().numpy()
+        Ms = fp.mat_base.Ms if g == 0 else fp.mat_slider.Ms
+        ref = OF.demag_conv(Ms * (m0 if g == 0 else m1), fp.cell)
+        assert rel_l2(Hd, ref) < TOL
+    mm.close()
+
+
 @pytest.mark.parametrize("n", [(40, 24, 1), (37, 21, 2), (33, 17, 3), (19, 31, 4)])
 def test_demag_matches_oracle(n):
     fp, m0, m1, offs = _pair(n, n, 2, 21, (0.0, 0.0, 0.0))
