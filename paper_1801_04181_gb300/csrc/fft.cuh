@@ -337,15 +337,14 @@ __host__ __device__ constexpr unsigned fft_magic(int d) {
 }
 
 // fft_smem for one plan known at compile time: three stages of radices R0, R1,
-// R2 (first to last DIF stage, L = R0 R1 R2) on lines of stride L.  The same
-// stage code with every length a constant, so the butterflies' shared-memory
-// and twiddle offsets fold into the instructions (the results are those of
-// fft_smem with the same plan, bit for bit).  The caller checks that P is
-// this plan.
-template <int MODE, typename C, int R0, int R1, int R2>
+// R2 (first to last DIF stage, L = R0 R1 R2) on lines of stride LDL.  The
+// same stage code with every length a constant, so the butterflies'
+// shared-memory and twiddle offsets fold into the instructions (the results
+// are those of fft_smem with the same plan, bit for bit).  The caller checks
+// that P is this plan.  nvalid as for fft_smem (kFwdDif only).
+template <int MODE, typename C, int R0, int R1, int R2, int LDL = R0 * R1 * R2>
 __device__ __forceinline__ void fft_smem_fixed(C* buf, int nlines, const FftPlanDev& P,
-                                               const C* __restrict__ stw, int tid0, int nthr) {
-  static_assert(MODE == kFwdDif || MODE == kInvDit, "fixed plans: forward DIF and inverse DIT");
+                                               const C* __restrict__ stw, int tid0, int nthr, int nvalid = 0) {
   constexpr int L = R0 * R1 * R2;
   const int tid = (int)threadIdx.x - tid0;
   const bool mine = tid >= 0 && tid < nthr;
@@ -359,18 +358,30 @@ __device__ __forceinline__ void fft_smem_fixed(C* buf, int nlines, const FftPlan
   const C* tw1 = stw + P.stw_off[1];
   const C* tw2 = stw + P.stw_off[2];
   if (MODE == kFwdDif) {
-    if (mine) fft_stage<R0, false, C>(buf, L, nlines, L, Lb0, mpl0, mM0, tw0, tid, nthr);
+    if (mine) {
+      if (nvalid > 0 && nvalid < L)
+        fft_stage<R0, false, C, true>(buf, LDL, nlines, L, Lb0, mpl0, mM0, tw0, tid, nthr, nvalid);
+      else
+        fft_stage<R0, false, C>(buf, LDL, nlines, L, Lb0, mpl0, mM0, tw0, tid, nthr);
+    }
     __syncthreads();
-    if (mine) fft_stage<R1, false, C>(buf, L, nlines, L, Lb1, mpl1, mM1, tw1, tid, nthr);
+    if (mine) fft_stage<R1, false, C>(buf, LDL, nlines, L, Lb1, mpl1, mM1, tw1, tid, nthr);
     __syncthreads();
-    if (mine) fft_stage<R2, false, C>(buf, L, nlines, L, Lb2, mpl2, mM2, tw2, tid, nthr);
+    if (mine) fft_stage<R2, false, C>(buf, LDL, nlines, L, Lb2, mpl2, mM2, tw2, tid, nthr);
+    __syncthreads();
+  } else if (MODE == kInvDit) {
+    if (mine) fft_stage<R2, true, C>(buf, LDL, nlines, L, Lb2, mpl2, mM2, tw2, tid, nthr);
+    __syncthreads();
+    if (mine) fft_stage<R1, true, C>(buf, LDL, nlines, L, Lb1, mpl1, mM1, tw1, tid, nthr);
+    __syncthreads();
+    if (mine) fft_stage<R0, true, C>(buf, LDL, nlines, L, Lb0, mpl0, mM0, tw0, tid, nthr);
     __syncthreads();
   } else {
-    if (mine) fft_stage<R2, true, C>(buf, L, nlines, L, Lb2, mpl2, mM2, tw2, tid, nthr);
+    if (mine) fft_stage_dif_inv<R0, C>(buf, LDL, nlines, L, Lb0, mpl0, mM0, tw0, tid, nthr);
     __syncthreads();
-    if (mine) fft_stage<R1, true, C>(buf, L, nlines, L, Lb1, mpl1, mM1, tw1, tid, nthr);
+    if (mine) fft_stage_dif_inv<R1, C>(buf, LDL, nlines, L, Lb1, mpl1, mM1, tw1, tid, nthr);
     __syncthreads();
-    if (mine) fft_stage<R0, true, C>(buf, L, nlines, L, Lb0, mpl0, mM0, tw0, tid, nthr);
+    if (mine) fft_stage_dif_inv<R2, C>(buf, LDL, nlines, L, Lb2, mpl2, mM2, tw2, tid, nthr);
     __syncthreads();
   }
 }

@@ -106,18 +106,20 @@ def test_stray_field_force_energy_match_oracle(n0, n1, gap, u, lateral):
     mm.close()
 
 
-def test_y_transform_of_540_points_matches_oracle():
-    """Films 256 cells wide in y take the 540-point y transform of the stick-slip
-    pair (plan 4 x 9 x 15, run with its lengths as compile-time constants): the
-    stray field, force and energy both ways and the demag field against the
-    oracle on a short strip of that width."""
+@pytest.mark.parametrize("n,axis,Q,plan", [((12, 256, 2), 1, 540, [4, 9, 15]),
+                                           ((1024, 12, 2), 0, 2160, [16, 9, 15])])
+def test_stick_slip_transform_lengths_match_oracle(n, axis, Q, plan):
+    """Films 256 cells wide in y (1024 long in x) take the 540-point y (2160-point
+    x) transform of the stick-slip pair, whose plans run with their lengths as
+    compile-time constants: the stray field, force and energy both ways and the
+    demag field against the oracle on a strip of that width (length)."""
     from paper_1801_04181_gb300 import fft_plan, tuned_plan
 
-    fp, m0, m1, offs = _pair((12, 256, 2), (12, 256, 2), 5, 9, (0.43, 0.0, 0.0))
+    fp, m0, m1, offs = _pair(n, n, 5, 9, (0.43, 0.0, 0.0))
     mm = _gpu(fp, m0, m1, offs)
     for src in (0, 1):
-        Qy = mm.plan_info(src)["fft"][1]
-        assert Qy == 540 and (tuned_plan(540) or fft_plan(540)) == [4, 9, 15]
+        assert mm.plan_info(src)["fft"][axis] == Q
+        assert (tuned_plan(Q) or fft_plan(Q)) == plan
     for src in (0, 1):
         t = 1 - src
         Hg = mm.compute_stray_field(src).double().cpu().numpy()
