@@ -152,12 +152,18 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ algorithmic bytes
-def algorithmic_bytes(mm, fp):
-    """Bytes each kernel class must move per launch (both magnets), FP32 path."""
+def algorithmic_bytes(mm, fp, mixed=False):
+    """Bytes each kernel class must move per launch (both magnets): the FP32
+    classes, and with mixed=True those of the reduced-precision form that are
+    not tensor-core products (whose measure is flops, dft_flops)."""
     n = [fp.n_base, fp.n_slider]
     N = [int(np.prod(x)) for x in n]
     info = [mm.plan_info(0), mm.plan_info(1)]
-    xf = yp = xi = ga = 0
+    # thick route (either magnet above 4 layers, and every source of the
+    # reduced-precision form): y forward, z pass (direct sum up to 8 source
+    # layers, else z FFT), y inverse as passes of their own
+    thick = mixed or max(n[0][2], n[1][2]) > 4
+    xf = yp = xi = ga = yf3 = z3 = yi3 = 0
     for s in (0, 1):
         nx, ny, nz = n[s]
         Qx, Qy = info[s]["fft"]
@@ -171,6 +177,13 @@ def algorithmic_bytes(mm, fp):
         yp += x1 + 6 * nz * kxh * kyq * 4 + rz * nz * 3 * kxh * kyq * 4 + x1 + yc
         xi += x1 + yc + 3 * N[s] * 4 + coef
         ga += coef + 3 * N[t] * 4 + 3 * N[t] * 4
+        yf3 += 24 * nz * kxh * (ny + Qy)
+        Qz = info[s]["Qz"]
+        if Qz == 0:  # direct z sum: Y in, N and per-box-plane S spectra, H and C spectra out
+            z3 += 8 * 3 * nz * kxh * Qy + 4 * (6 * nz + 3 * nz * rz) * kxh * kyq + 8 * (3 * nz + rz) * kxh * Qy
+        else:        # z FFT: Y in, H spectra out, C spectra out, N and S quarter spectra
+            z3 += 2 * 24 * nz * kxh * Qy + 8 * rz * kxh * Qy + 36 * kxh * kyq * (Qz // 2 + 1)
+        yi3 += 24 * nz * kxh * (Qy + ny) + 8 * rz * kxh * (Qy + ry)
     # LLG stage i reads ys, y, Hself, Hstray and k_1..k_{i-1}, writes k_i and
     # (i < 7) the next stage input; stage 7 reads k_1..k_6 for the error norm
     per_stage = []
@@ -180,6 +193,10 @@ def algorithmic_bytes(mm, fp):
             arrays = 3 + 6 + 1
         per_stage.append(arrays)
     st = sum(3 * x * 4 for x in N) * float(np.mean(per_stage[1:]))
+    if mixed:
+        return {0: xf, 2: xi, 3: ga, 4: st, 8: z3}
+    if thick:
+        return {0: xf, 2: xi, 3: ga, 4: st, 7: yf3, 8: z3, 9: yi3}
     return {0: xf, 1: yp, 2: xi, 3: ga, 4: st}
 
 
@@ -523,7 +540,7 @@ def run_gpu(args):
                      "viscous drive loss"}
 
     # roofline of the dominant kernel class
-    ab = algorithmic_bytes(mm, fp)
+    ab = algorithmic_bytes(mm, fp, mixed=args.precision == "mixed")
     dom = max(ab.keys(), key=lambda c: kt[c][0])
     tot_ms, nl = kt[dom]
     avg_s = tot_ms / max(nl, 1) / 1e3
@@ -977,7 +994,7 @@ def run_batch(args):
     bytes_step = 0.0
     flops_step = 0.0  # reduced precision: split-product flops of the tensor-core DFTs
     for i, mm in zip(mine, batch):
-        ab = algorithmic_bytes(mm, specs[i])
+        ab = algorithmic_bytes(mm, specs[i], mixed=args.precision == "mixed")
         for c, b in ab.items():
             bytes_step += b * mm.timing(c)[1] / k_t
         if args.precision == "mixed":

@@ -386,6 +386,31 @@ __device__ __forceinline__ void fft_smem_fixed(C* buf, int nlines, const FftPlan
   }
 }
 
+// The plans with compile-time builds: 1 = 2160 = 16 9 15 and 3 = 540 = 4 9 15
+// (the stick-slip grid's x and y), 2 = 1080 = 12 6 15 (the 512 x 512 films').
+template <int ID> struct FixedPlan;
+template <> struct FixedPlan<1> { static constexpr int R0 = 16, R1 = 9, R2 = 15, L = 2160; };
+template <> struct FixedPlan<2> { static constexpr int R0 = 12, R1 = 6, R2 = 15, L = 1080; };
+template <> struct FixedPlan<3> { static constexpr int R0 = 4, R1 = 9, R2 = 15, L = 540; };
+
+// the id of P among the fixed plans, 0 if none
+inline int fixed_plan_id(const FftPlanDev& P) {
+  if (P.nstages != 3) return 0;
+  const int r0 = P.radix[0], r1 = P.radix[1], r2 = P.radix[2];
+  if (P.L == 2160 && r0 == 16 && r1 == 9 && r2 == 15) return 1;
+  if (P.L == 1080 && r0 == 12 && r1 == 6 && r2 == 15) return 2;
+  if (P.L == 540 && r0 == 4 && r1 == 9 && r2 == 15) return 3;
+  return 0;
+}
+
+// fft_smem_fixed for fixed plan ID on lines of stride LDL
+template <int MODE, int ID, int LDL, typename C>
+__device__ __forceinline__ void fft_smem_plan(C* buf, int nlines, const FftPlanDev& P, const C* __restrict__ stw,
+                                              int tid0, int nthr, int nvalid = 0) {
+  typedef FixedPlan<ID> F;
+  fft_smem_fixed<MODE, C, F::R0, F::R1, F::R2, LDL>(buf, nlines, P, stw, tid0, nthr, nvalid);
+}
+
 // Position of frequency k in the DIF output: sum_s M_s digit_s(k).
 __device__ __forceinline__ int fft_pos(int k, const FftPlanDev& P) {
   int p = 0;

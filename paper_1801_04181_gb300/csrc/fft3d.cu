@@ -35,7 +35,8 @@ namespace mm {
 cudaError_t init_fft_constants_3d() { return upload_roots(); }
 
 // ------------------------------------------------------------------ y forward
-template <unsigned RSET>
+// FIXP > 0: every job's y plan is fixed plan FIXP, run with its lengths as constants.
+template <unsigned RSET, int FIXP>
 __global__ void __launch_bounds__(256, 3) k_yfwd3(const Launch<YFwdJob> Lc) {
   extern __shared__ float2 sm[];
   const int j = find_job(Lc.tile_start, Lc.njobs, blockIdx.x);
@@ -45,7 +46,7 @@ __global__ void __launch_bounds__(256, 3) k_yfwd3(const Launch<YFwdJob> Lc) {
   const int kx = tile / ng;
   const int p0 = (tile - kx * ng) * J.group;
   const int np = min(J.group, J.planes - p0);
-  const int Q = J.fy.plan.L;
+  const int Q = FIXP ? FixedPlan<FIXP ? FIXP : 1>::L : J.fy.plan.L;
   const int ldl = Q + 1;  // odd stride: the plane-fastest reads below spread over the banks
   for (int l = 0; l < np; ++l) {
     const float2* col = J.in + ((size_t)(p0 + l) * J.kxh + kx) * J.ny;
@@ -53,7 +54,10 @@ __global__ void __launch_bounds__(256, 3) k_yfwd3(const Launch<YFwdJob> Lc) {
       sm[l * ldl + y] = y < J.ny ? col[y] : make_float2(0.f, 0.f);
   }
   __syncthreads();
-  fft_smem<kFwdDif, float2, RSET>(sm, ldl, np, J.fy.plan, J.fy.tw_f, 0, blockDim.x);
+  if constexpr (FIXP > 0)
+    fft_smem_plan<kFwdDif, FIXP, FixedPlan<FIXP>::L + 1>(sm, np, J.fy.plan, J.fy.tw_f, 0, blockDim.x);
+  else
+    fft_smem<kFwdDif, float2, RSET>(sm, ldl, np, J.fy.plan, J.fy.tw_f, 0, blockDim.x);
   if (J.natural) {
     // frequency ky read from its DIF position: whole contiguous output rows
     for (int l = 0; l < np; ++l) {
@@ -184,7 +188,7 @@ __global__ void __launch_bounds__(256, 2) k_zpass3(const Launch<ZJob> Lc) {
 }
 
 // ------------------------------------------------------------------ y inverse
-template <unsigned RSET>
+template <unsigned RSET, int FIXP>
 __global__ void __launch_bounds__(256, 3) k_yinv3(const Launch<YInvJob> Lc) {
   extern __shared__ float2 sm[];
   const int j = find_job(Lc.tile_start, Lc.njobs, blockIdx.x);
@@ -194,7 +198,7 @@ __global__ void __launch_bounds__(256, 3) k_yinv3(const Launch<YInvJob> Lc) {
   const int kx = tile / ng;
   const int p0 = (tile - kx * ng) * J.group;
   const int np = min(J.group, J.planes - p0);
-  const int Q = J.fy.plan.L;
+  const int Q = FIXP ? FixedPlan<FIXP ? FIXP : 1>::L : J.fy.plan.L;
   const int ldl = Q + 1;
   int* tab = reinterpret_cast<int*>(sm + J.group * ldl);
   for (int l = 0; l < np; ++l) {
@@ -208,8 +212,13 @@ __global__ void __launch_bounds__(256, 3) k_yinv3(const Launch<YInvJob> Lc) {
     build_pref_table(tab, J.r + 2 * kPrefWarm + kYChunk, J.box_lo, J.box_len, J.start, Q,
                      J.natural ? J.fy.pos : nullptr, J.periodic != 0);
   __syncthreads();
-  if (J.natural) fft_smem<kInvDif, float2, RSET>(sm, ldl, np, J.fy.plan, J.fy.tw_f, 0, blockDim.x);
-  else fft_smem<kInvDit, float2, RSET>(sm, ldl, np, J.fy.plan, J.fy.tw_f, 0, blockDim.x);
+  if constexpr (FIXP > 0) {
+    if (J.natural) fft_smem_plan<kInvDif, FIXP, FixedPlan<FIXP>::L + 1>(sm, np, J.fy.plan, J.fy.tw_f, 0, blockDim.x);
+    else fft_smem_plan<kInvDit, FIXP, FixedPlan<FIXP>::L + 1>(sm, np, J.fy.plan, J.fy.tw_f, 0, blockDim.x);
+  } else {
+    if (J.natural) fft_smem<kInvDif, float2, RSET>(sm, ldl, np, J.fy.plan, J.fy.tw_f, 0, blockDim.x);
+    else fft_smem<kInvDit, float2, RSET>(sm, ldl, np, J.fy.plan, J.fy.tw_f, 0, blockDim.x);
+  }
   if (!J.is_C) {
     for (int l = 0; l < np; ++l) {
       float2* dst = J.outH + ((size_t)(p0 + l) * J.kxh + kx) * J.ny;
@@ -409,13 +418,21 @@ cudaError_t launch_zmix3(const Launch<ZMixJob>& L, cudaStream_t st) {
 int zpass_tile(int Qz) { return std::max(8, (80 * 1024) / (4 * (Qz + 1) * (int)sizeof(float2))); }
 int zpass_tiles(int Qy, int ztile) { return (Qy + ztile - 1) / ztile; }
 
+// every job's y plan is 1080 = 12 6 15 (fixed plan 2: the 512 x 512 films)
+template <typename JobT> static bool y_fixed_1080(const Launch<JobT>& L) {
+  for (int i = 0; i < L.njobs; ++i)
+    if (fixed_plan_id(L.job[i].fy.plan) != 2) return false;
+  return L.njobs > 0;
+}
+
 cudaError_t launch_yfwd3(const Launch<YFwdJob>& L, cudaStream_t st) {
   size_t smem = 0;
   for (int i = 0; i < L.njobs; ++i)
     smem = std::max(smem, sizeof(float2) * (size_t)L.job[i].group * (L.job[i].fy.plan.L + 1));
   unsigned rs = 0;
   for (int i = 0; i < L.njobs; ++i) rs |= plan_radix_set(L.job[i].fy.plan);
-  auto k = (rs & ~kRadixSetA) == 0u ? k_yfwd3<kRadixSetA> : k_yfwd3<kAllRadices>;
+  auto k = y_fixed_1080(L) ? k_yfwd3<kAllRadices, 2>
+           : (rs & ~kRadixSetA) == 0u ? k_yfwd3<kRadixSetA, 0> : k_yfwd3<kAllRadices, 0>;
   cudaError_t e = prep((const void*)k, smem);
   if (e != cudaSuccess) return e;
   const int grid = L.tile_start[L.njobs];
@@ -453,7 +470,8 @@ cudaError_t launch_yinv3(const Launch<YInvJob>& L, cudaStream_t st) {
   }
   unsigned rs = 0;
   for (int i = 0; i < L.njobs; ++i) rs |= plan_radix_set(L.job[i].fy.plan);
-  auto k = (rs & ~kRadixSetA) == 0u ? k_yinv3<kRadixSetA> : k_yinv3<kAllRadices>;
+  auto k = y_fixed_1080(L) ? k_yinv3<kAllRadices, 2>
+           : (rs & ~kRadixSetA) == 0u ? k_yinv3<kRadixSetA, 0> : k_yinv3<kAllRadices, 0>;
   cudaError_t e = prep((const void*)k, smem);
   if (e != cudaSuccess) return e;
   const int grid = L.tile_start[L.njobs];

@@ -31,14 +31,14 @@ constexpr int kLinePad = 4;              // float2 between lines of an x-pass CT
 cudaError_t init_fft_constants_passes() { return upload_roots(); }
 
 // ------------------------------------------------------------------ x forward
-// FIX2160: every job's x plan is 2160 = 16 9 15, run with its lengths as constants.
-template <unsigned RSET, bool FIX2160>
+// FIXP > 0: every job's x plan is fixed plan FIXP, run with its lengths as constants.
+template <unsigned RSET, int FIXP>
 __global__ void __launch_bounds__(kXFwdThreads, 3) k_xfwd(const Launch<XFwdJob> Lc) {
   extern __shared__ float2 sm[];
   const int j = find_job(Lc.tile_start, Lc.njobs, blockIdx.x);
   const XFwdJob& J = Lc.job[j];
   const int tile = blockIdx.x - Lc.tile_start[j];
-  const int Q = FIX2160 ? 2160 : J.fx.plan.L;
+  const int Q = FIXP ? FixedPlan<FIXP ? FIXP : 1>::L : J.fx.plan.L;
   const int ldl = Q + kLinePad;  // padded line stride: the lines start in different banks
   const int rows = 3 * J.nz * J.ny;
   const int r0 = tile * kRowsPerCta;
@@ -85,8 +85,8 @@ __global__ void __launch_bounds__(kXFwdThreads, 3) k_xfwd(const Launch<XFwdJob> 
     ptab[kx] = make_ushort2((unsigned short)__ldg(J.fx.pos + kx),
                             (unsigned short)__ldg(J.fx.pos + (kx == 0 ? 0 : Q - kx)));
   __syncthreads();
-  if constexpr (FIX2160)
-    fft_smem_fixed<kFwdDif, float2, 16, 9, 15, 2160 + kLinePad>(sm, nlines, J.fx.plan, J.fx.tw_f, 0, blockDim.x, nx);
+  if constexpr (FIXP > 0)
+    fft_smem_plan<kFwdDif, FIXP, FixedPlan<FIXP>::L + kLinePad>(sm, nlines, J.fx.plan, J.fx.tw_f, 0, blockDim.x, nx);
   else
     fft_smem<kFwdDif, float2, RSET>(sm, ldl, nlines, J.fx.plan, J.fx.tw_f, 0, blockDim.x, nx);
 
@@ -365,13 +365,13 @@ __device__ __forceinline__ void xinv_put(float2* sm, int off, int Q, int kx, flo
   if (kx > 0 && 2 * kx != Q) sm[off + Q - kx] = make_float2(A.x + B.y, B.x - A.y);
 }
 
-template <unsigned RSET, bool FIX2160>
+template <unsigned RSET, int FIXP>
 __global__ void __launch_bounds__(kXInvThreads, 3) k_xinv(const Launch<XInvJob> Lc) {
   extern __shared__ float2 sm[];
   const int j = find_job(Lc.tile_start, Lc.njobs, blockIdx.x);
   const XInvJob& J = Lc.job[j];
   const int tile = blockIdx.x - Lc.tile_start[j];
-  const int Q = FIX2160 ? 2160 : J.fx.plan.L;
+  const int Q = FIXP ? FixedPlan<FIXP ? FIXP : 1>::L : J.fx.plan.L;
   const int ldl = Q + kLinePad;  // padded line stride: the lines start in different banks
   const int rpp = J.rows_per_plane;
   const int rows = J.planes * rpp;
@@ -446,8 +446,8 @@ __global__ void __launch_bounds__(kXInvThreads, 3) k_xinv(const Launch<XInvJob> 
                    J.periodic != 0);
   __syncthreads();
   // natural-order input, digit-reversed output: the table above maps through it
-  if constexpr (FIX2160)
-    fft_smem_fixed<kInvDif, float2, 16, 9, 15, 2160 + kLinePad>(sm, nlines, J.fx.plan, J.fx.tw_f, 0, blockDim.x);
+  if constexpr (FIXP > 0)
+    fft_smem_plan<kInvDif, FIXP, FixedPlan<FIXP>::L + kLinePad>(sm, nlines, J.fx.plan, J.fx.tw_f, 0, blockDim.x);
   else
     fft_smem<kInvDif, float2, RSET>(sm, ldl, nlines, J.fx.plan, J.fx.tw_f, 0, blockDim.x);
 
@@ -482,13 +482,12 @@ static size_t xinv_smem(int Qmax, int out_max) {
          sizeof(int) * (size_t)(out_max + 2 * kPrefWarm + kXChunk);
 }
 
-// every job's x plan is 2160 = 16 9 15 (the x kernels' compile-time form)
-template <typename JobT> static bool x_fixed_2160(const Launch<JobT>& L) {
-  for (int i = 0; i < L.njobs; ++i) {
-    const FftPlanDev& P = L.job[i].fx.plan;
-    if (!(P.L == 2160 && P.nstages == 3 && P.radix[0] == 16 && P.radix[1] == 9 && P.radix[2] == 15)) return false;
-  }
-  return L.njobs > 0;
+// the fixed plan every job's x plan is (fixed_plan_id), 0 if they differ or none is
+template <typename JobT> static int x_fixed_plan(const Launch<JobT>& L) {
+  int id = L.njobs > 0 ? fixed_plan_id(L.job[0].fx.plan) : 0;
+  for (int i = 1; i < L.njobs; ++i)
+    if (fixed_plan_id(L.job[i].fx.plan) != id) id = 0;
+  return id;
 }
 
 static void max_carveout(const void* f) {
@@ -500,8 +499,10 @@ cudaError_t launch_xfwd(const Launch<XFwdJob>& L, int Qmax, cudaStream_t st) {
       (size_t)kLines * (Qmax + kLinePad) * sizeof(float2) + sizeof(ushort2) * (size_t)(Qmax / 2 + 1);
   unsigned rs = 0;
   for (int i = 0; i < L.njobs; ++i) rs |= plan_radix_set(L.job[i].fx.plan);
-  auto k = x_fixed_2160(L) ? k_xfwd<kRadixSetA, true>
-                           : (rs & ~kRadixSetA) == 0u ? k_xfwd<kRadixSetA, false> : k_xfwd<kAllRadices, false>;
+  const int fx = x_fixed_plan(L);
+  auto k = fx == 1 ? k_xfwd<kRadixSetA, 1>
+           : fx == 2 ? k_xfwd<kAllRadices, 2>
+           : (rs & ~kRadixSetA) == 0u ? k_xfwd<kRadixSetA, 0> : k_xfwd<kAllRadices, 0>;
   max_carveout((const void*)k);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -516,9 +517,8 @@ static cudaError_t launch_ypass_nz(const Launch<YJob>& L, size_t smem, cudaStrea
   unsigned rs = 0;
   bool fix540 = true;
   for (int i = 0; i < L.njobs; ++i) {
-    const FftPlanDev& P = L.job[i].fy.plan;
-    rs |= plan_radix_set(P);
-    fix540 = fix540 && P.L == 540 && P.nstages == 3 && P.radix[0] == 4 && P.radix[1] == 9 && P.radix[2] == 15;
+    rs |= plan_radix_set(L.job[i].fy.plan);
+    fix540 = fix540 && fixed_plan_id(L.job[i].fy.plan) == 3;
   }
   auto k = fix540 ? k_ypass<NZ, kRadixSetA, true>
                   : (rs & ~kRadixSetA) == 0u ? k_ypass<NZ, kRadixSetA, false> : k_ypass<NZ, kAllRadices, false>;
@@ -560,8 +560,10 @@ cudaError_t launch_xinv(const Launch<XInvJob>& L, int Qmax, cudaStream_t st) {
   const size_t smem = xinv_smem(Qmax, out_max);
   unsigned rs = 0;
   for (int i = 0; i < L.njobs; ++i) rs |= plan_radix_set(L.job[i].fx.plan);
-  auto k = x_fixed_2160(L) ? k_xinv<kRadixSetA, true>
-                           : (rs & ~kRadixSetA) == 0u ? k_xinv<kRadixSetA, false> : k_xinv<kAllRadices, false>;
+  const int fx = x_fixed_plan(L);
+  auto k = fx == 1 ? k_xinv<kRadixSetA, 1>
+           : fx == 2 ? k_xinv<kAllRadices, 2>
+           : (rs & ~kRadixSetA) == 0u ? k_xinv<kRadixSetA, 0> : k_xinv<kAllRadices, 0>;
   max_carveout((const void*)k);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
