@@ -28,7 +28,9 @@ __device__ __forceinline__ float warp_max(float v) {
 // period); open boundaries run the instantiation without the wrap tests.
 // EDDY: some job is a conducting magnet carrying an eddy field; the plain
 // instantiation has no load of it (and no extra register pressure).
-template <bool WRAP, bool EDDY>
+// SG > 0: every job is RK stage SG of mode 0 (the combination unrolls, its k
+// loads can overlap); SG = 0: stage and mode of the job, at run time.
+template <bool WRAP, bool EDDY, int SG>
 __global__ void __launch_bounds__(256, 6) k_stage(const Launch<StageJob> Lc, const MechParams Perr, int* ticket) {
   __shared__ float red[8];
   const int j = find_job(Lc.tile_start, Lc.njobs, blockIdx.x);
@@ -97,34 +99,57 @@ __global__ void __launch_bounds__(256, 6) k_stage(const Launch<StageJob> Lc, con
     const float k0 = J.pref * (c0 + J.alpha * d0);
     const float k1 = J.pref * (c1 + J.alpha * d1);
     const float k2 = J.pref * (c2 + J.alpha * d2);
-    float* ko = J.k[J.stage - 1];
+    const int stage = SG > 0 ? SG : J.stage;
+    const int mode = SG > 0 ? 0 : J.mode;
+    float* ko = J.k[stage - 1];
     ko[idx] = k0; ko[N + idx] = k1; ko[2 * N + idx] = k2;
-    if (J.mode == 0 && J.stage < 7) {
+    if (mode == 0 && stage < 7) {
       float s0 = J.y[idx], s1 = J.y[N + idx], s2 = J.y[2 * N + idx];
-      for (int jj = 0; jj < J.stage - 1; ++jj) {
-        const float a = J.comb[jj];
-        if (a != 0.f) {
+      if constexpr (SG > 0) {
+        // every a_ij below the diagonal enters (a zero one adds an exact zero)
+#pragma unroll
+        for (int jj = 0; jj < SG - 1; ++jj) {
+          const float a = J.comb[jj];
           const float* kj = J.k[jj];
           s0 += a * kj[idx]; s1 += a * kj[N + idx]; s2 += a * kj[2 * N + idx];
         }
+      } else {
+        for (int jj = 0; jj < stage - 1; ++jj) {
+          const float a = J.comb[jj];
+          if (a != 0.f) {
+            const float* kj = J.k[jj];
+            s0 += a * kj[idx]; s1 += a * kj[N + idx]; s2 += a * kj[2 * N + idx];
+          }
+        }
       }
-      const float a = J.comb[J.stage - 1];
+      const float a = J.comb[stage - 1];
       s0 += a * k0; s1 += a * k1; s2 += a * k2;
       J.ys_next[idx] = s0; J.ys_next[N + idx] = s1; J.ys_next[2 * N + idx] = s2;
-    } else if (J.mode == 0 && J.stage == 7) {
+    } else if (mode == 0 && stage == 7) {
       float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-      for (int jj = 0; jj < 6; ++jj) {
-        const float a = J.ecoef[jj];
-        if (a != 0.f) {
-          const float* kj = J.k[jj];
-          s0 += a * kj[idx]; s1 += a * kj[N + idx]; s2 += a * kj[2 * N + idx];
+      if constexpr (SG > 0) {
+#pragma unroll
+        for (int jj = 0; jj < 6; ++jj) {
+          const float a = J.ecoef[jj];
+          if (a != 0.f) {
+            const float* kj = J.k[jj];
+            s0 += a * kj[idx]; s1 += a * kj[N + idx]; s2 += a * kj[2 * N + idx];
+          }
+        }
+      } else {
+        for (int jj = 0; jj < 6; ++jj) {
+          const float a = J.ecoef[jj];
+          if (a != 0.f) {
+            const float* kj = J.k[jj];
+            s0 += a * kj[idx]; s1 += a * kj[N + idx]; s2 += a * kj[2 * N + idx];
+          }
         }
       }
       s0 += J.ecoef[6] * k0; s1 += J.ecoef[6] * k1; s2 += J.ecoef[6] * k2;
       emax = fmaxf(fabsf(s0), fmaxf(fabsf(s1), fabsf(s2)));
     }
   }
-  if (J.mode == 0 && J.stage == 7) {
+  if ((SG > 0 ? SG == 7 : J.mode == 0 && J.stage == 7)) {
     emax = warp_max(emax);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = emax;
     __syncthreads();
@@ -171,10 +196,26 @@ cudaError_t launch_stage(const Launch<StageJob>& L, const MechParams& Perr, int*
     wrap = wrap || L.job[i].wrap[0] || L.job[i].wrap[1];
     eddy = eddy || L.job[i].Heddy != nullptr;
   }
-  if (wrap && eddy) k_stage<true, true><<<grid, 256, 0, st>>>(L, Perr, ticket);
-  else if (wrap) k_stage<true, false><<<grid, 256, 0, st>>>(L, Perr, ticket);
-  else if (eddy) k_stage<false, true><<<grid, 256, 0, st>>>(L, Perr, ticket);
-  else k_stage<false, false><<<grid, 256, 0, st>>>(L, Perr, ticket);
+  // one RK stage of mode 0 for every job: the build for that stage (open
+  // boundaries, no eddy field), else the run-time one
+  int sg = L.job[0].mode == 0 ? L.job[0].stage : 0;
+  for (int i = 1; i < L.njobs; ++i)
+    if (L.job[i].mode != 0 || L.job[i].stage != sg) sg = 0;
+  if (wrap || eddy) sg = 0;
+  switch (sg) {
+    case 1: k_stage<false, false, 1><<<grid, 256, 0, st>>>(L, Perr, ticket); break;
+    case 2: k_stage<false, false, 2><<<grid, 256, 0, st>>>(L, Perr, ticket); break;
+    case 3: k_stage<false, false, 3><<<grid, 256, 0, st>>>(L, Perr, ticket); break;
+    case 4: k_stage<false, false, 4><<<grid, 256, 0, st>>>(L, Perr, ticket); break;
+    case 5: k_stage<false, false, 5><<<grid, 256, 0, st>>>(L, Perr, ticket); break;
+    case 6: k_stage<false, false, 6><<<grid, 256, 0, st>>>(L, Perr, ticket); break;
+    case 7: k_stage<false, false, 7><<<grid, 256, 0, st>>>(L, Perr, ticket); break;
+    default:
+      if (wrap && eddy) k_stage<true, true, 0><<<grid, 256, 0, st>>>(L, Perr, ticket);
+      else if (wrap) k_stage<true, false, 0><<<grid, 256, 0, st>>>(L, Perr, ticket);
+      else if (eddy) k_stage<false, true, 0><<<grid, 256, 0, st>>>(L, Perr, ticket);
+      else k_stage<false, false, 0><<<grid, 256, 0, st>>>(L, Perr, ticket);
+  }
   return cudaGetLastError();
 }
 cudaError_t launch_combine(const Launch<CombineJob>& L, cudaStream_t st) {
